@@ -1,0 +1,173 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module is shared by the CUDA path's tests/benchmark and by the CPU oracle's
+tests.  It draws random parameters and observation layouts only; it contains
+none of the method's arithmetic (no velocity, no particle step, no estimator).
+
+Every draw uses numpy's PCG64 generator with a fixed seed, so a workload is a
+pure function of its name.  Shapes follow Section 4 of the paper: about 100
+observations (Example 1), a Fourier stream function over a square lattice of
+wave numbers (Eq. v_expand) with a |k|^-4 prior on each real coefficient,
+Dirichlet data on a disk.  The concrete recipe of each workload is listed in
+DESIGN.md under "Input recipe".
+
+Layout conventions (the library's input format, shared by both sides):
+  * ``u``: float64 array of length 2H, pairs (a_h, b_h) over the half-plane
+    lattice {m > 0, |n| <= K} U {m = 0, 0 < n <= K}, ordered by m then n;
+  * ``x``: float64 [n_obs, 2]; ``t``: float64 [n_obs];
+  * theta0: integer wave vectors [nq, 2] with cosine/sine amplitudes.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import Optional
+
+import numpy as np
+
+
+def half_mode_list(K: int) -> np.ndarray:
+    """Wave vectors of the coefficient layout, [H, 2] int32, in storage order."""
+    out = [(0, n) for n in range(1, K + 1)]
+    out += [(m, n) for m in range(1, K + 1) for n in range(-K, K + 1)]
+    return np.asarray(out, dtype=np.int32).reshape(-1, 2)
+
+
+def prior_field(K: int, seed: int, scale: float = 1.0, counter: int = 0) -> np.ndarray:
+    """Coefficients u with each real a_h, b_h ~ N(0, |k_h|_2^-4), times ``scale``.
+
+    ``counter`` selects an independent draw for the same seed (instance b of a
+    batch)."""
+    k = half_mode_list(K).astype(np.float64)
+    knorm2 = (k ** 2).sum(axis=1)
+    rng = np.random.Generator(np.random.PCG64([seed, counter]))
+    z = rng.standard_normal((k.shape[0], 2))
+    std = knorm2 ** -1.0  # |k|^-2 standard deviation
+    return (scale * z * std[:, None]).reshape(-1).astype(np.float64)
+
+
+def grid_points(n: int) -> np.ndarray:
+    """Cell-centred n x n grid on the unit square, row-major, [n*n, 2]."""
+    c = (np.arange(n) + 0.5) / n
+    xx, yy = np.meshgrid(c, c, indexing="ij")
+    return np.stack([xx.reshape(-1), yy.reshape(-1)], axis=1).astype(np.float64)
+
+
+def disk_points(n: int, rmax: float, seed: int) -> np.ndarray:
+    """n points uniform in area on the disk r <= rmax."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    u1 = rng.random(n)
+    u2 = rng.random(n)
+    r = rmax * np.sqrt(u1)
+    phi = 2.0 * np.pi * u2
+    return np.stack([r * np.cos(phi), r * np.sin(phi)], axis=1)
+
+
+def random_theta0(nq: int, kmax: int, seed: int):
+    """nq distinct half-plane wave vectors with |k|_inf <= kmax, amplitudes
+    N(0, 1/nq) each (so that theta0 has unit variance)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    cand = half_mode_list(kmax)
+    idx = rng.choice(cand.shape[0], size=nq, replace=False)
+    k = cand[np.sort(idx)].astype(np.int32)
+    a = rng.standard_normal(nq) / np.sqrt(nq)
+    b = rng.standard_normal(nq) / np.sqrt(nq)
+    return k, a.astype(np.float64), b.astype(np.float64)
+
+
+@dataclass
+class Fourier:
+    """theta0(x) = sum_q a_q cos(2 pi k_q.x) + b_q sin(2 pi k_q.x)."""
+    k: np.ndarray  # [nq, 2] int32
+    a: np.ndarray  # [nq]
+    b: np.ndarray  # [nq]
+
+
+@dataclass
+class DirichletData:
+    """Disk of radius R; g = quad (y1^2 - y2^2) + sum_m a_m cos(m phi) + b_m sin(m phi); f = f_const."""
+    R: float = 1.0
+    quad: float = 0.0
+    f_const: float = 0.0
+    a: np.ndarray = field(default_factory=lambda: np.zeros(0))
+    b: np.ndarray = field(default_factory=lambda: np.zeros(0))
+
+
+@dataclass
+class TimedepWorkload:
+    name: str
+    K: int
+    u: np.ndarray
+    kappa: float
+    theta0: Fourier
+    x: np.ndarray
+    t: np.ndarray
+    M: int
+    dt: float
+    seed: int
+
+
+@dataclass
+class DirichletWorkload:
+    name: str
+    K: int
+    u: np.ndarray
+    drift_scale: float
+    kappa: float
+    g: DirichletData
+    x: np.ndarray
+    M: int
+    dt: float
+    max_steps: int
+    seed: int
+
+
+def plain_fp64_k2() -> TimedepWorkload:
+    """K=2 (24 reals), kappa=0.05, theta0 = sin 2pi x1 sin 2pi x2, 3x3 grid, t=1, M=1000, dt=0.01."""
+    th = Fourier(k=np.array([[1, -1], [1, 1]], dtype=np.int32),
+                 a=np.array([0.5, -0.5]), b=np.zeros(2))
+    x = grid_points(3)
+    return TimedepWorkload("timedep_k2_3x3_t1_M1000_fp64", 2, prior_field(2, 1000), 0.05, th,
+                           x, np.ones(len(x)), 1000, 0.01, 4000)
+
+
+def timedep_k10(M: int = 10_000) -> TimedepWorkload:
+    """K=10 (440 reals), kappa=0.01, 16-mode theta0, 10x10 grid x t in {0.25, 0.5, 1},
+    M=1e4, dt=1e-3.  Observation index = t_index * 100 + grid index."""
+    k, a, b = random_theta0(16, 4, 2001)
+    g = grid_points(10)
+    times = [0.25, 0.5, 1.0]
+    x = np.concatenate([g for _ in times], axis=0)
+    t = np.concatenate([np.full(len(g), tt) for tt in times])
+    return TimedepWorkload("timedep_k10_300obs_M1e4_dt1e-3", 10, prior_field(10, 1001), 0.01,
+                           Fourier(k, a, b), x, t, M, 1e-3, 4001)
+
+
+def dirichlet_disk_k10(M: int = 100_000) -> DirichletWorkload:
+    """Unit disk, K=10 field x 0.5, kappa=0.05, g = y1^2 - y2^2 + 0.1 sin 3phi,
+    50 uniform-area points r <= 0.9, M=1e5, dt=1e-4."""
+    g = DirichletData(R=1.0, quad=1.0, f_const=0.0, a=np.zeros(3), b=np.array([0.0, 0.0, 0.1]))
+    return DirichletWorkload("dirichlet_disk_k10_50obs_M1e5_dt1e-4", 10, prior_field(10, 1002), 0.5,
+                             0.05, g, disk_points(50, 0.9, 3002), M, 1e-4, 10_000_000, 4002)
+
+
+def batched_instances(B: int = 256, M: int = 4096, seed: int = 1003):
+    """Instance b: even b time-dependent (K=10 field, kappa=0.01, dt=1e-3, 10x10 grid,
+    t_j in {0.25, 0.5, 0.75, 1.0} by (i+j) mod 4); odd b Dirichlet (unit disk,
+    field x 0.5, kappa=0.05, dt=1e-3, 100 uniform-area points r <= 0.9).
+    Each instance draws its own u from the prior (counter b)."""
+    k, a, bq = random_theta0(16, 4, 2003)
+    theta0 = Fourier(k, a, bq)
+    g = DirichletData(R=1.0, quad=1.0, f_const=0.0, a=np.zeros(3), b=np.array([0.0, 0.0, 0.1]))
+    grid = grid_points(10)
+    tvals = np.array([0.25, 0.5, 0.75, 1.0])
+    ij = np.array([(i + j) % 4 for i in range(10) for j in range(10)])
+    out = []
+    for b in range(B):
+        u = prior_field(10, seed, counter=b)
+        if b % 2 == 0:
+            out.append(TimedepWorkload(f"batched_td_{b}", 10, u, 0.01, theta0, grid.copy(),
+                                       tvals[ij].copy(), M, 1e-3, 4003))
+        else:
+            out.append(DirichletWorkload(f"batched_dir_{b}", 10, u, 0.5, 0.05, g,
+                                         disk_points(100, 0.9, 3003 + b), M, 1e-3, 1_000_000, 4003))
+    return out
