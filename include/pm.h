@@ -1,0 +1,212 @@
+/*
+ * pm.h -- C ABI of the GB300 particle forward-map library (libpm_gb300.so).
+ *
+ * The library evaluates the parameter-to-observation map G(u) of
+ * Borggaard, Glatt-Holtz & Krometis (arXiv:1808.10580) directly with backward
+ * stochastic particles instead of solving the PDE on a grid:
+ *   - Problem 1 / Algorithm 1 (time-dependent advection-diffusion, Eq.
+ *     pde_diffusion): G_j(u) = theta(t_j, x_j) = E theta0(X_{t_j}) with
+ *     dX = -v_u(X) ds + sqrt(2 kappa) dW, X_0 = x_j (Theorem 3.1, Eq. adr);
+ *   - Problem 2 / Algorithm 2 (Dirichlet problem, Eq. bvp): G_j(u) =
+ *     E[g(X_tau)] - E int_0^tau f(X_s) ds, tau the first exit time from the
+ *     domain (Theorem 3.2, Eq. bvp_solution);
+ * both with Euler-Maruyama steps (Eq. euler) and Monte Carlo averages over M
+ * particles per observation.  v_u is the divergence-free velocity of a
+ * Fourier stream function (Eq. v_expand).
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ * Field.  psi(x) = sum_h a_h cos(2 pi k_h.x) + b_h sin(2 pi k_h.x) over the
+ *   half-plane lattice H_K = {(m,n): m > 0, |n| <= K} U {(0,n): 0 < n <= K},
+ *   ordered by m, then n ascending; u = (a_0, b_0, a_1, b_1, ...) has 2|H_K| =
+ *   (2K+1)^2 - 1 doubles.  v = (-d psi/dx2, d psi/dx1), i.e. the paper's
+ *   k_perp = (-k_y, k_x) direction.  Supported K: 0..6, 8, 10, 12, 16.
+ * Random numbers.  Step n of path i of observation j in instance b draws
+ *   Philox4x32-10 (Salmon et al., SC'11) on counter {n/2, i, j, b} under key
+ *   {seed & 0xffffffff, seed >> 32}; words (r0, r1) feed even n and (r2, r3)
+ *   odd n; u = (2 (r >> 9) + 1) / 2^24; Box-Muller gives xi = sqrt(-2 ln u_a)
+ *   (cos 2 pi u_b, sin 2 pi u_b).  Results therefore depend only on the inputs
+ *   and the seed, never on launch shapes or the GPU count.
+ * Steps.  Time-dependent: N_j = ceil(t_j/dt - 1e-9) steps, all of length dt
+ *   except the last, t_j - (N_j - 1) dt; positions wrap into [0,1)^2 after each
+ *   step.  Dirichlet: domain |x| < R; a path exits at the first step n with
+ *   |X_n|^2 >= R^2; g is evaluated at R X_n/|X_n|; int f = f_const n dt; a path
+ *   that has not exited after max_steps contributes 0 and is counted as
+ *   unexited.
+ * Estimator.  mean_j = (1/M) sum_i g_i, var_j = unbiased sample variance
+ *   (n - 1); both are accumulated in double precision in a fixed order, so
+ *   repeated calls return identical bits.
+ * Precision.  Default (PM_FP32): particle arithmetic in float, positions kept
+ *   as compensated float pairs; reductions in double.  PM_FP64: particle
+ *   arithmetic in double (the plain FP64 path).
+ * Memory.  Pointers are host pointers unless PM_DEVICE_PTRS is set, in which
+ *   case the per-observation arrays (x, t, mean, var, and the optional
+ *   per-path outputs) are device pointers on the context's device.  The field
+ *   coefficients u of pm_forward_timedep / pm_forward_dirichlet and the small
+ *   description tables (theta0, boundary data) are always host pointers; they
+ *   are packed into the kernel's launch parameters.  The caller owns all
+ *   arrays; the library owns its context, its device workspace and its pinned
+ *   staging buffers.
+ * Synchronisation.  Calls return after their outputs are written unless
+ *   PM_ASYNC is set together with PM_DEVICE_PTRS; then the work is queued on
+ *   the context's stream and the outputs are valid once that stream has been
+ *   synchronised.  (With host pointers the call always synchronises.)
+ * Errors.  0 = success; negative = error (nothing useful written; message from
+ *   pm_last_error()); positive = warning (outputs written).  No call aborts
+ *   the process.  A context is used by one host thread at a time.
+ */
+#ifndef PM_H
+#define PM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PM_OK 0
+#define PM_EINVAL (-1)      /* bad argument: sizes, dt <= 0, unsupported K, NaN */
+#define PM_ENOMEM (-2)      /* device or pinned host allocation failed */
+#define PM_ECUDA (-3)       /* CUDA runtime error; message holds its string */
+#define PM_ETIMEOUT (-4)    /* a bounded wait expired */
+#define PM_WARN_UNEXITED 1  /* Dirichlet: some paths hit max_steps */
+
+#define PM_FP32 0u
+#define PM_FP64 1u
+#define PM_DEVICE_PTRS 2u
+#define PM_ASYNC 4u
+
+#define PM_MAX_THETA0_MODES 64
+#define PM_MAX_BOUNDARY_MODES 32
+
+typedef struct pm_ctx pm_ctx;
+
+/* Library version, 10000*major + 100*minor + patch. */
+int pm_version(void);
+
+/* Creates a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * to queue all work on (NULL: the context creates and owns a stream; pass
+ * cudaStreamLegacy to use the legacy default stream).
+ * Returns PM_OK and stores the context in *out, or an error. */
+int pm_create(pm_ctx** out, int device, void* cuda_stream);
+
+/* Synchronises the context's stream and frees everything the context owns.
+ * NULL is ignored. */
+void pm_destroy(pm_ctx* ctx);
+
+/* Message of the last failing call made by this host thread ("" if none). */
+const char* pm_last_error(void);
+
+/* The context's stream (a cudaStream_t). */
+void* pm_stream(const pm_ctx* ctx);
+
+/* Stream-function coefficients.  u: host pointer, 2|H_K| doubles. */
+typedef struct pm_field {
+    int32_t K;
+    int32_t reserved;
+    const double* u;
+} pm_field;
+
+/* theta0(x) = sum_q a_q cos(2 pi k_q.x) + b_q sin(2 pi k_q.x); k: [n][2] int32.
+ * n <= PM_MAX_THETA0_MODES.  Host pointers. */
+typedef struct pm_fourier {
+    int32_t n;
+    int32_t reserved;
+    const int32_t* k;
+    const double* a;
+    const double* b;
+} pm_fourier;
+
+/* Disk of radius R centred at 0.  Boundary data at y = R (cos phi, sin phi):
+ * g(y) = quad (y1^2 - y2^2) + sum_{m=1..n_ang} a[m-1] cos(m phi) + b[m-1] sin(m phi).
+ * Forcing f = f_const.  n_ang <= PM_MAX_BOUNDARY_MODES.  Host pointers. */
+typedef struct pm_dirichlet_data {
+    double R;
+    double quad;
+    double f_const;
+    int32_t n_ang;
+    int32_t reserved;
+    const double* a;
+    const double* b;
+} pm_dirichlet_data;
+
+/* Optional per-call settings (NULL = all defaults). */
+typedef struct pm_path_opts {
+    int64_t path_offset; /* index i of the first path (shards of one estimate); default 0 */
+    uint32_t instance;   /* b of the RNG counter; default 0 */
+    int32_t reserved;
+    double* g_out;       /* [n_obs][M] per-path values g_i, or NULL */
+    double* x_out;       /* [n_obs][M][2] end (or exit) positions, or NULL */
+} pm_path_opts;
+
+/* Algorithm 1 (Section 3.1): time-dependent map G_j(u) = theta(t_j, x_j).
+ *   field   stream-function coefficients (host)
+ *   kappa   diffusion coefficient, >= 0 (sigma = sqrt(2 kappa) I, Eq. adr)
+ *   theta0  initial condition (host)
+ *   x       [n_obs][2] observation points; t [n_obs] observation times >= 0
+ *   M       particles per observation, 1 <= M, path_offset + M <= 2^32
+ *   dt      Euler-Maruyama step > 0
+ *   seed    64-bit Philox key
+ *   flags   PM_FP32 | PM_FP64, PM_DEVICE_PTRS, PM_ASYNC
+ *   mean    [n_obs] output; var [n_obs] output or NULL
+ * n_obs == 0 is a no-op.  Returns PM_OK or an error. */
+int pm_forward_timedep(pm_ctx* ctx, const pm_field* field, double kappa, const pm_fourier* theta0,
+                       const double* x, const double* t, int64_t n_obs, int64_t M, double dt,
+                       uint64_t seed, uint32_t flags, double* mean, double* var,
+                       const pm_path_opts* opts);
+
+/* Algorithm 2 (Section 3.2): Dirichlet map G_j(u) = theta(x_j) in the disk.
+ *   drift_scale  multiplies v_u (the drift is -drift_scale v_u)
+ *   g            domain, boundary data and forcing (host)
+ *   max_steps    cap on the steps of one path (>= 1)
+ *   exit_step    [n_obs][M] steps taken to exit (-1 = capped), or NULL
+ *   n_unexited   total capped paths, or NULL (host or device per flags)
+ * Paths of uneven length are load-balanced by a persistent kernel in which
+ * every lane takes a new path as soon as its current one exits.
+ * Returns PM_OK, PM_WARN_UNEXITED (outputs written), or an error. */
+int pm_forward_dirichlet(pm_ctx* ctx, const pm_field* field, double drift_scale, double kappa,
+                         const pm_dirichlet_data* g, const double* x, int64_t n_obs, int64_t M,
+                         double dt, int64_t max_steps, uint64_t seed, uint32_t flags,
+                         double* mean, double* var, int32_t* exit_step, int64_t* n_unexited,
+                         const pm_path_opts* opts);
+
+/* ---------------------------------------------------------------------------
+ * Diagnostics: the building blocks of the particle step, exposed so that each
+ * can be checked on its own against an independent implementation.
+ * ------------------------------------------------------------------------- */
+
+/* Philox4x32-10 of n counters ctr[n][4] under key {key0, key1} -> out[n][4].
+ * Pointers follow PM_DEVICE_PTRS. */
+int pm_philox(pm_ctx* ctx, const uint32_t* ctr, uint32_t key0, uint32_t key1, int64_t n,
+              uint32_t* out, uint32_t flags);
+
+/* The normals (xi1, xi2) of steps n0 .. n0+count-1 of path (b, j, i) as the
+ * kernels draw them, in the precision the flags select -> out[count][2]
+ * (double).  Pointers follow PM_DEVICE_PTRS. */
+int pm_normals(pm_ctx* ctx, uint64_t seed, uint32_t b, uint32_t j, uint32_t i, int64_t n0,
+               int64_t count, double* out, uint32_t flags);
+
+/* Velocity v_u at npts points x[npts][2] -> v[npts][2], evaluated by the same
+ * device code as the particle step (product basis, trigonometric
+ * recurrences) in the precision the flags select. */
+int pm_velocity(pm_ctx* ctx, const pm_field* field, const double* x, int64_t npts, double* v,
+                uint32_t flags);
+
+/* ---------------------------------------------------------------------------
+ * Measurement support.
+ * ------------------------------------------------------------------------- */
+
+/* When on, the context brackets the main particle kernel of each forward call
+ * with CUDA events on its stream; pm_last_kernel_ms() then returns that
+ * kernel's duration (synchronising on the end event). */
+int pm_set_kernel_timing(pm_ctx* ctx, int on);
+float pm_last_kernel_ms(pm_ctx* ctx);
+
+/* Number of kernels the context has launched since it was created. */
+int64_t pm_launch_count(const pm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PM_H */

@@ -1,0 +1,234 @@
+"""ctypes binding of the C ABI in include/pm.h (argument marshalling only).
+
+Every function here has the name of its C entry point and forwards its
+arguments unchanged; all arithmetic runs in the CUDA library
+``_build/libpm_gb300.so``.  Arrays may be numpy arrays (host pointers) or
+CUDA torch tensors (device pointers, which set PM_DEVICE_PTRS).  If the
+library is missing this module raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+PM_OK = 0
+PM_EINVAL = -1
+PM_ENOMEM = -2
+PM_ECUDA = -3
+PM_ETIMEOUT = -4
+PM_WARN_UNEXITED = 1
+
+PM_FP32 = 0
+PM_FP64 = 1
+PM_DEVICE_PTRS = 2
+PM_ASYNC = 4
+
+
+class PMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"pm error {code}: {msg}")
+        self.code = code
+
+
+class pm_field(C.Structure):
+    _fields_ = [("K", C.c_int32), ("reserved", C.c_int32), ("u", C.POINTER(C.c_double))]
+
+
+class pm_fourier(C.Structure):
+    _fields_ = [("n", C.c_int32), ("reserved", C.c_int32), ("k", C.POINTER(C.c_int32)),
+                ("a", C.POINTER(C.c_double)), ("b", C.POINTER(C.c_double))]
+
+
+class pm_dirichlet_data(C.Structure):
+    _fields_ = [("R", C.c_double), ("quad", C.c_double), ("f_const", C.c_double), ("n_ang", C.c_int32),
+                ("reserved", C.c_int32), ("a", C.POINTER(C.c_double)), ("b", C.POINTER(C.c_double))]
+
+
+class pm_path_opts(C.Structure):
+    _fields_ = [("path_offset", C.c_int64), ("instance", C.c_uint32), ("reserved", C.c_int32),
+                ("g_out", C.c_void_p), ("x_out", C.c_void_p)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads the CUDA library (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and (not os.path.exists(path) or _build.stale()):
+        _build.build()
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library {path} is missing; run paper_1808_10580_gb300/build.py")
+    L = C.CDLL(path)
+    vp = C.c_void_p
+    i64, u32, i32, dbl = C.c_int64, C.c_uint32, C.c_int32, C.c_double
+    L.pm_version.restype = C.c_int
+    L.pm_create.argtypes = [C.POINTER(vp), C.c_int, vp]
+    L.pm_destroy.argtypes = [vp]
+    L.pm_destroy.restype = None
+    L.pm_last_error.restype = C.c_char_p
+    L.pm_stream.argtypes = [vp]
+    L.pm_stream.restype = vp
+    L.pm_forward_timedep.argtypes = [vp, C.POINTER(pm_field), dbl, C.POINTER(pm_fourier), vp, vp, i64, i64, dbl,
+                                     C.c_uint64, u32, vp, vp, C.POINTER(pm_path_opts)]
+    L.pm_forward_dirichlet.argtypes = [vp, C.POINTER(pm_field), dbl, dbl, C.POINTER(pm_dirichlet_data), vp, i64,
+                                       i64, dbl, i64, C.c_uint64, u32, vp, vp, vp, vp, C.POINTER(pm_path_opts)]
+    L.pm_philox.argtypes = [vp, vp, u32, u32, i64, vp, u32]
+    L.pm_normals.argtypes = [vp, C.c_uint64, u32, u32, u32, i64, i64, vp, u32]
+    L.pm_velocity.argtypes = [vp, C.POINTER(pm_field), vp, i64, vp, u32]
+    L.pm_set_kernel_timing.argtypes = [vp, C.c_int]
+    L.pm_last_kernel_ms.argtypes = [vp]
+    L.pm_last_kernel_ms.restype = C.c_float
+    L.pm_launch_count.argtypes = [vp]
+    L.pm_launch_count.restype = i64
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc < 0:
+        raise PMError(rc, load().pm_last_error().decode())
+    return rc
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a):
+    """Address of an array: numpy (host) or torch tensor (device or host)."""
+    if a is None:
+        return None
+    if _is_torch(a):
+        assert a.is_contiguous()
+        return a.data_ptr()
+    assert isinstance(a, np.ndarray) and a.flags["C_CONTIGUOUS"], "arrays must be C-contiguous"
+    return a.ctypes.data
+
+
+def _device(*arrays):
+    dev = [a is not None and _is_torch(a) and a.is_cuda for a in arrays]
+    present = [a is not None for a in arrays]
+    if any(dev) and not all(d for d, p in zip(dev, present) if p):
+        raise ValueError("mix of device and host arrays")
+    return any(dev)
+
+
+class Field:
+    """Keeps the host arrays of a pm_field alive."""
+
+    def __init__(self, K, u):
+        self.u = np.ascontiguousarray(u, dtype=np.float64)
+        self.s = pm_field(int(K), 0, self.u.ctypes.data_as(C.POINTER(C.c_double)))
+
+
+class Fourier:
+    def __init__(self, k, a, b):
+        self.k = np.ascontiguousarray(np.asarray(k, dtype=np.int32).reshape(-1, 2))
+        self.a = np.ascontiguousarray(a, dtype=np.float64)
+        self.b = np.ascontiguousarray(b, dtype=np.float64)
+        self.s = pm_fourier(len(self.a), 0, self.k.ctypes.data_as(C.POINTER(C.c_int32)),
+                            self.a.ctypes.data_as(C.POINTER(C.c_double)), self.b.ctypes.data_as(C.POINTER(C.c_double)))
+
+
+class DirichletData:
+    def __init__(self, R, quad, f_const, a, b):
+        self.a = np.ascontiguousarray(a, dtype=np.float64)
+        self.b = np.ascontiguousarray(b, dtype=np.float64)
+        self.s = pm_dirichlet_data(float(R), float(quad), float(f_const), len(self.a), 0,
+                                   self.a.ctypes.data_as(C.POINTER(C.c_double)),
+                                   self.b.ctypes.data_as(C.POINTER(C.c_double)))
+
+
+def pm_version():
+    return load().pm_version()
+
+
+CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy
+
+
+def pm_create(device=0, stream=None):
+    """stream: a cudaStream_t value (e.g. torch.cuda.Stream().cuda_stream); 0
+    (torch's default stream) maps to cudaStreamLegacy; None lets the library
+    create its own stream."""
+    h = C.c_void_p()
+    if stream == 0:
+        stream = CUDA_STREAM_LEGACY
+    _check(load().pm_create(C.byref(h), int(device), stream))
+    return h
+
+
+def pm_destroy(ctx):
+    load().pm_destroy(ctx)
+
+
+def pm_stream(ctx):
+    return load().pm_stream(ctx)
+
+
+def pm_set_kernel_timing(ctx, on):
+    return _check(load().pm_set_kernel_timing(ctx, int(bool(on))))
+
+
+def pm_last_kernel_ms(ctx):
+    return float(load().pm_last_kernel_ms(ctx))
+
+
+def pm_launch_count(ctx):
+    return int(load().pm_launch_count(ctx))
+
+
+def _opts(path_offset=0, instance=0, g_out=None, x_out=None):
+    return pm_path_opts(int(path_offset), int(instance), 0, _ptr(g_out), _ptr(x_out))
+
+
+def pm_forward_timedep(ctx, field: Field, kappa, theta0: Fourier, x, t, n_obs, M, dt, seed, flags, mean, var=None,
+                       path_offset=0, instance=0, g_out=None, x_out=None):
+    if _device(x, t, mean, var, g_out, x_out):
+        flags |= PM_DEVICE_PTRS
+    o = _opts(path_offset, instance, g_out, x_out)
+    return _check(load().pm_forward_timedep(ctx, C.byref(field.s), float(kappa), C.byref(theta0.s), _ptr(x), _ptr(t),
+                                            int(n_obs), int(M), float(dt), int(seed), int(flags), _ptr(mean),
+                                            _ptr(var), C.byref(o)))
+
+
+def pm_forward_dirichlet(ctx, field: Field, drift_scale, kappa, g: DirichletData, x, n_obs, M, dt, max_steps, seed,
+                         flags, mean, var=None, exit_step=None, n_unexited=None, path_offset=0, instance=0,
+                         g_out=None, x_out=None):
+    if _device(x, mean, var, exit_step, n_unexited, g_out, x_out):
+        flags |= PM_DEVICE_PTRS
+    o = _opts(path_offset, instance, g_out, x_out)
+    return _check(load().pm_forward_dirichlet(ctx, C.byref(field.s), float(drift_scale), float(kappa), C.byref(g.s),
+                                              _ptr(x), int(n_obs), int(M), float(dt), int(max_steps), int(seed),
+                                              int(flags), _ptr(mean), _ptr(var), _ptr(exit_step), _ptr(n_unexited),
+                                              C.byref(o)))
+
+
+def pm_philox(ctx, ctr, key0, key1, n, out, flags=0):
+    if _device(ctr, out):
+        flags |= PM_DEVICE_PTRS
+    return _check(load().pm_philox(ctx, _ptr(ctr), int(key0), int(key1), int(n), _ptr(out), int(flags)))
+
+
+def pm_normals(ctx, seed, b, j, i, n0, count, out, flags=0):
+    if _device(out):
+        flags |= PM_DEVICE_PTRS
+    return _check(load().pm_normals(ctx, int(seed), int(b), int(j), int(i), int(n0), int(count), _ptr(out),
+                                    int(flags)))
+
+
+def pm_velocity(ctx, field: Field, x, npts, v, flags=0):
+    if _device(x, v):
+        flags |= PM_DEVICE_PTRS
+    return _check(load().pm_velocity(ctx, C.byref(field.s), _ptr(x), int(npts), _ptr(v), int(flags)))

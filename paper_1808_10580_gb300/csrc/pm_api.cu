@@ -1,0 +1,706 @@
+// pm_api.cu -- the C ABI of include/pm.h: argument checking, coefficient
+// staging, workspace management and kernel sequencing.  Every arithmetic step
+// of the forward maps runs in the CUDA kernels (pm_kernels.cuh,
+// pm_support.cu); the host only validates, stages and copies.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/pm.h"
+#include "pm_launch.h"
+
+using namespace pm;
+
+// ---------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------
+namespace {
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(PM_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    }
+    return fail(PM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define PM_CUDA(call, what)                              \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+bool supported_K(int K)
+{
+    switch (K) {
+    case 0: case 1: case 2: case 3: case 4: case 5: case 6: case 8: case 10: case 12: case 16: return true;
+    default: return false;
+    }
+}
+
+#define PM_K_LIST(X) X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(8) X(10) X(12) X(16)
+
+template <typename Real>
+cudaError_t dispatch_timedep(int K, const TimedepLaunch& L, cudaStream_t s)
+{
+    switch (K) {
+#define PM_CASE(k) case k: return launch_timedep<Real, k>(L, s);
+        PM_K_LIST(PM_CASE)
+#undef PM_CASE
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename Real>
+cudaError_t dispatch_dirichlet(int K, const DirichletLaunch& L, cudaStream_t s)
+{
+    switch (K) {
+#define PM_CASE(k) case k: return launch_dirichlet<Real, k>(L, s);
+        PM_K_LIST(PM_CASE)
+#undef PM_CASE
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename Real>
+int dispatch_dirichlet_occupancy(int K)
+{
+    switch (K) {
+#define PM_CASE(k) case k: return dirichlet_blocks_per_sm<Real, k>();
+        PM_K_LIST(PM_CASE)
+#undef PM_CASE
+    }
+    return 1;
+}
+
+template <typename Real>
+cudaError_t dispatch_velocity(int K, const double* coef, const double* x, int64_t n, double* v, cudaStream_t s)
+{
+    switch (K) {
+#define PM_CASE(k) case k: return launch_velocity<Real, k>(coef, x, n, v, s);
+        PM_K_LIST(PM_CASE)
+#undef PM_CASE
+    }
+    return cudaErrorInvalidValue;
+}
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+// Half-mode index of (m, n) in the coefficient layout of pm_field.
+inline int64_t half_index(int K, int m, int n) { return m == 0 ? (n - 1) : K + (int64_t)(m - 1) * (2 * K + 1) + (n + K); }
+
+// Section 4.1, Eq. v_expand: stream-function coefficients (a_h, b_h) of the
+// half-plane modes -> the product-basis velocity table the kernels read.
+// For m, n >= 1 the pair (m, n), (m, -n) folds into
+//   A = a(m,n) + a(m,-n), B = b(m,n) - b(m,-n), G = b(m,n) + b(m,-n), D = a(m,-n) - a(m,n)
+// (psi = A C1 C2 + B C1 S2 + G S1 C2 + D S1 S2); then e = 2 pi n (A, -B, G, -D)
+// feed v1 = -d2 psi and f = 2 pi m (G, D, -A, -B) feed v2 = d1 psi.
+std::vector<double> stage_coefficients(int K, const double* u)
+{
+    std::vector<double> tab((size_t)table_size(K), 0.0);
+    auto a = [&](int m, int n) { return u[2 * half_index(K, m, n)]; };
+    auto b = [&](int m, int n) { return u[2 * half_index(K, m, n) + 1]; };
+    for (int m = 0; m <= K; ++m) {
+        for (int n = 0; n <= K; ++n) {
+            double A = 0, B = 0, G = 0, D = 0;
+            if (m == 0 && n == 0) continue;
+            if (m == 0) { A = a(0, n); B = b(0, n); }
+            else if (n == 0) { A = a(m, 0); G = b(m, 0); }
+            else {
+                A = a(m, n) + a(m, -n);
+                B = b(m, n) - b(m, -n);
+                G = b(m, n) + b(m, -n);
+                D = a(m, -n) - a(m, n);
+            }
+            double* e = &tab[(size_t)(m * (K + 1) + n) * 8];
+            const double sn = kTwoPi * n, sm = kTwoPi * m;
+            e[0] = sn * A; e[1] = -sn * B; e[2] = sn * G; e[3] = -sn * D;
+            e[4] = sm * G; e[5] = sm * D; e[6] = -sm * A; e[7] = -sm * B;
+        }
+    }
+    return tab;
+}
+
+bool finite_array(const double* p, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+bool is_device_pointer(const void* p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+struct pm_ctx {
+    int device = 0;
+    int sm_count = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void* ws = nullptr;      // device workspace
+    size_t ws_size = 0;
+    void* host = nullptr;    // pinned staging
+    size_t host_size = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool timing = false;
+    bool timed = false;
+    int64_t launches = 0;
+};
+
+namespace {
+
+struct Bump {
+    char* base;
+    size_t off = 0;
+    explicit Bump(void* b) : base((char*)b) {}
+    template <typename T> T* take(size_t count)
+    {
+        off = (off + 255) & ~(size_t)255;
+        T* p = (T*)(base ? base + off : nullptr);
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+int ensure_workspace(pm_ctx* c, size_t bytes)
+{
+    if (bytes <= c->ws_size) return PM_OK;
+    if (c->ws) {
+        PM_CUDA(cudaStreamSynchronize(c->stream), "workspace resize");
+        cudaFree(c->ws);
+        c->ws = nullptr;
+        c->ws_size = 0;
+    }
+    size_t want = bytes + bytes / 4 + 4096;
+    PM_CUDA(cudaMalloc(&c->ws, want), "device workspace");
+    c->ws_size = want;
+    return PM_OK;
+}
+
+int ensure_host(pm_ctx* c, size_t bytes)
+{
+    if (bytes <= c->host_size) return PM_OK;
+    if (c->host) {
+        PM_CUDA(cudaStreamSynchronize(c->stream), "staging resize");
+        cudaFreeHost(c->host);
+        c->host = nullptr;
+        c->host_size = 0;
+    }
+    size_t want = bytes + bytes / 4 + 4096;
+    PM_CUDA(cudaHostAlloc(&c->host, want, cudaHostAllocDefault), "pinned staging");
+    c->host_size = want;
+    return PM_OK;
+}
+
+int set_device(pm_ctx* c)
+{
+    PM_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
+    return PM_OK;
+}
+
+// Common checks of a field description.
+int check_field(const pm_field* f)
+{
+    if (!f) return fail(PM_EINVAL, "field is NULL");
+    if (!supported_K(f->K)) return fail(PM_EINVAL, "K=%d is not one of the compiled bounds 0..6, 8, 10, 12, 16", f->K);
+    const int64_t nu = (int64_t)(2 * f->K + 1) * (2 * f->K + 1) - 1;
+    if (nu > 0 && !f->u) return fail(PM_EINVAL, "field coefficients are NULL");
+    if (nu > 0 && !finite_array(f->u, nu)) return fail(PM_EINVAL, "field coefficients contain NaN or Inf");
+    return PM_OK;
+}
+
+int check_ptrs(uint32_t flags, std::initializer_list<const void*> ptrs)
+{
+    if (!(flags & PM_DEVICE_PTRS)) return PM_OK;
+    for (const void* p : ptrs)
+        if (p && !is_device_pointer(p))
+            return fail(PM_EINVAL, "PM_DEVICE_PTRS is set but a pointer is not device memory");
+    return PM_OK;
+}
+
+void count_launch(pm_ctx* c, int n = 1) { c->launches += n; }
+
+}  // namespace
+
+extern "C" {
+
+int pm_version(void) { return 10000; }
+
+const char* pm_last_error(void) { return g_err; }
+
+int pm_create(pm_ctx** out, int device, void* cuda_stream)
+{
+    if (!out) return fail(PM_EINVAL, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev) return fail(PM_EINVAL, "device %d out of range (%d devices)", device, ndev);
+    pm_ctx* c = new (std::nothrow) pm_ctx;
+    if (!c) return fail(PM_ENOMEM, "context allocation");
+    c->device = device;
+    e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) {
+        if (cuda_stream) c->stream = (cudaStream_t)cuda_stream;
+        else {
+            e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+            c->own_stream = true;
+        }
+    }
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+    if (e != cudaSuccess) {
+        pm_destroy(c);
+        return cuda_fail(e, "pm_create");
+    }
+    *out = c;
+    return PM_OK;
+}
+
+void pm_destroy(pm_ctx* c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->ws) cudaFree(c->ws);
+    if (c->host) cudaFreeHost(c->host);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+void* pm_stream(const pm_ctx* c) { return c ? (void*)c->stream : nullptr; }
+
+int pm_set_kernel_timing(pm_ctx* c, int on)
+{
+    if (!c) return fail(PM_EINVAL, "ctx is NULL");
+    c->timing = on != 0;
+    c->timed = false;
+    return PM_OK;
+}
+
+float pm_last_kernel_ms(pm_ctx* c)
+{
+    if (!c || !c->timed) return -1.0f;
+    if (cudaEventSynchronize(c->ev1) != cudaSuccess) return -1.0f;
+    float ms = -1.0f;
+    if (cudaEventElapsedTime(&ms, c->ev0, c->ev1) != cudaSuccess) return -1.0f;
+    return ms;
+}
+
+int64_t pm_launch_count(const pm_ctx* c) { return c ? c->launches : 0; }
+
+// ---------------------------------------------------------------------------
+// Algorithm 1
+// ---------------------------------------------------------------------------
+int pm_forward_timedep(pm_ctx* c, const pm_field* field, double kappa, const pm_fourier* th, const double* x,
+                       const double* t, int64_t n_obs, int64_t M, double dt, uint64_t seed, uint32_t flags,
+                       double* mean, double* var, const pm_path_opts* opts)
+{
+    if (!c) return fail(PM_EINVAL, "ctx is NULL");
+    int rc = check_field(field);
+    if (rc) return rc;
+    if (!th) return fail(PM_EINVAL, "theta0 is NULL");
+    if (th->n < 0 || th->n > PM_MAX_THETA0_MODES) return fail(PM_EINVAL, "theta0 has %d modes (max %d)", th->n, PM_MAX_THETA0_MODES);
+    if (th->n > 0 && (!th->k || !th->a || !th->b)) return fail(PM_EINVAL, "theta0 arrays are NULL");
+    if (th->n > 0 && (!finite_array(th->a, th->n) || !finite_array(th->b, th->n)))
+        return fail(PM_EINVAL, "theta0 amplitudes contain NaN or Inf");
+    for (int q = 0; q < th->n; ++q)
+        if (std::abs(th->k[2 * q]) > 4096 || std::abs(th->k[2 * q + 1]) > 4096)
+            return fail(PM_EINVAL, "theta0 wave number out of range");
+    if (!(std::isfinite(kappa) && kappa >= 0)) return fail(PM_EINVAL, "kappa must be finite and >= 0");
+    if (!(std::isfinite(dt) && dt > 0)) return fail(PM_EINVAL, "dt must be finite and > 0");
+    if (n_obs < 0) return fail(PM_EINVAL, "n_obs < 0");
+    if (n_obs == 0) return PM_OK;
+    if (n_obs > (int64_t)1 << 30) return fail(PM_EINVAL, "n_obs too large");
+    if (M < 1) return fail(PM_EINVAL, "M must be >= 1");
+    const int64_t off = opts ? opts->path_offset : 0;
+    if (off < 0 || off + M > ((int64_t)1 << 32)) return fail(PM_EINVAL, "path_offset + M exceeds 2^32");
+    if (!x || !t || !mean) return fail(PM_EINVAL, "x, t and mean must not be NULL");
+    double* g_out = opts ? opts->g_out : nullptr;
+    double* x_out = opts ? opts->x_out : nullptr;
+    if ((rc = check_ptrs(flags, {x, t, mean, var, g_out, x_out}))) return rc;
+    const bool dev = flags & PM_DEVICE_PTRS;
+    const bool fp64 = flags & PM_FP64;
+    const int64_t chunks64 = (M + kTimedepBlock - 1) / kTimedepBlock;
+    if (n_obs * chunks64 > 0x7fffffffLL) return fail(PM_EINVAL, "n_obs * ceil(M/%d) exceeds the grid limit", kTimedepBlock);
+    const int32_t chunks = (int32_t)chunks64;
+    if ((rc = set_device(c))) return rc;
+
+    // Workspace layout.
+    const bool sort = n_obs <= 8192;
+    auto layout = [&](Bump& b) {
+        struct P { unsigned* err; ObsRec* rec; int32_t* order; double2* part; double *x, *t, *mean, *var, *g, *xo; } p{};
+        p.err = b.take<unsigned>(4);
+        p.rec = b.take<ObsRec>((size_t)n_obs);
+        p.order = sort ? b.take<int32_t>((size_t)n_obs) : nullptr;
+        p.part = b.take<double2>((size_t)(n_obs * chunks));
+        if (!dev) {
+            p.x = b.take<double>((size_t)(3 * n_obs));  // x then t, one copy
+            p.t = p.x + 2 * n_obs;
+            p.mean = b.take<double>((size_t)n_obs);
+            p.var = var ? b.take<double>((size_t)n_obs) : nullptr;
+            p.g = g_out ? b.take<double>((size_t)(n_obs * M)) : nullptr;
+            p.xo = x_out ? b.take<double>((size_t)(2 * n_obs * M)) : nullptr;
+        }
+        return p;
+    };
+    Bump probe(nullptr);
+    layout(probe);
+    if ((rc = ensure_workspace(c, probe.off))) return rc;
+    Bump bump(c->ws);
+    auto W = layout(bump);
+
+    const double *dx = x, *dtm = t;
+    double *dmean = mean, *dvar = var, *dg = g_out, *dxo = x_out;
+    size_t hbytes = 0;
+    if (!dev) {
+        hbytes = (size_t)n_obs * 8 * 3 + 64;
+        const size_t outb = (size_t)n_obs * 8 * 2 + (g_out ? (size_t)(n_obs * M) * 8 : 0) +
+                            (x_out ? (size_t)(2 * n_obs * M) * 8 : 0) + 64;
+        if ((rc = ensure_host(c, hbytes > outb ? hbytes : outb))) return rc;
+        double* h = (double*)c->host;
+        memcpy(h, x, (size_t)n_obs * 16);
+        memcpy(h + 2 * n_obs, t, (size_t)n_obs * 8);
+        PM_CUDA(cudaMemcpyAsync(W.x, h, (size_t)n_obs * 24, cudaMemcpyHostToDevice, c->stream), "copy x, t");
+        dx = W.x;
+        dtm = W.t;
+        dmean = W.mean;
+        dvar = W.var;
+        dg = W.g;
+        dxo = W.xo;
+    }
+
+    const std::vector<double> tab = stage_coefficients(field->K, field->u);
+    PM_CUDA(cudaMemsetAsync(W.err, 0, 16, c->stream), "clear flags");
+    PM_CUDA(launch_prep_timedep(dx, dtm, n_obs, dt, kappa, W.rec, W.order, W.err, c->stream), "prep kernel");
+    count_launch(c, sort ? 2 : 1);
+
+    TimedepLaunch L{};
+    L.coef = tab.data();
+    L.nq = th->n;
+    L.qk = th->k;
+    L.qa = th->a;
+    L.qb = th->b;
+    L.obs = W.rec;
+    L.order = W.order;
+    L.part = W.part;
+    L.g_out = dg;
+    L.x_out = dxo;
+    L.dt = dt;
+    L.s_dt = std::sqrt(2.0 * kappa * dt);
+    L.M = M;
+    L.path_offset = off;
+    L.n_obs = (int32_t)n_obs;
+    L.chunks = chunks;
+    L.inst = opts ? opts->instance : 0u;
+    L.key0 = (uint32_t)(seed & 0xffffffffu);
+    L.key1 = (uint32_t)(seed >> 32);
+    if (c->timing) PM_CUDA(cudaEventRecord(c->ev0, c->stream), "event");
+    cudaError_t e = fp64 ? dispatch_timedep<double>(field->K, L, c->stream) : dispatch_timedep<float>(field->K, L, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "timedep kernel launch");
+    if (c->timing) {
+        PM_CUDA(cudaEventRecord(c->ev1, c->stream), "event");
+        c->timed = true;
+    }
+    count_launch(c);
+    PM_CUDA(launch_reduce(W.part, n_obs, chunks, M, dmean, dvar, c->stream), "reduce kernel");
+    count_launch(c);
+
+    if (dev && (flags & PM_ASYNC)) return PM_OK;
+    unsigned err_flag = 0;
+    if (!dev) {
+        double* h = (double*)c->host;
+        size_t o = 0;
+        PM_CUDA(cudaMemcpyAsync(h + o, dmean, (size_t)n_obs * 8, cudaMemcpyDeviceToHost, c->stream), "copy mean");
+        o += (size_t)n_obs;
+        if (var) { PM_CUDA(cudaMemcpyAsync(h + o, dvar, (size_t)n_obs * 8, cudaMemcpyDeviceToHost, c->stream), "copy var"); o += (size_t)n_obs; }
+        if (g_out) { PM_CUDA(cudaMemcpyAsync(h + o, dg, (size_t)(n_obs * M) * 8, cudaMemcpyDeviceToHost, c->stream), "copy g"); o += (size_t)(n_obs * M); }
+        if (x_out) { PM_CUDA(cudaMemcpyAsync(h + o, dxo, (size_t)(2 * n_obs * M) * 8, cudaMemcpyDeviceToHost, c->stream), "copy x_out"); }
+    }
+    PM_CUDA(cudaMemcpyAsync(&err_flag, W.err, 4, cudaMemcpyDeviceToHost, c->stream), "copy flags");
+    PM_CUDA(cudaStreamSynchronize(c->stream), "timedep");
+    if (!dev) {
+        const double* h = (const double*)c->host;
+        size_t o = 0;
+        memcpy(mean, h + o, (size_t)n_obs * 8);
+        o += (size_t)n_obs;
+        if (var) { memcpy(var, h + o, (size_t)n_obs * 8); o += (size_t)n_obs; }
+        if (g_out) { memcpy(g_out, h + o, (size_t)(n_obs * M) * 8); o += (size_t)(n_obs * M); }
+        if (x_out) memcpy(x_out, h + o, (size_t)(2 * n_obs * M) * 8);
+    }
+    if (err_flag) return fail(PM_EINVAL, "observation points or times are not finite, a time is negative, or a step count exceeds 2^31");
+    return PM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 2
+// ---------------------------------------------------------------------------
+int pm_forward_dirichlet(pm_ctx* c, const pm_field* field, double drift_scale, double kappa,
+                         const pm_dirichlet_data* gd, const double* x, int64_t n_obs, int64_t M, double dt,
+                         int64_t max_steps, uint64_t seed, uint32_t flags, double* mean, double* var,
+                         int32_t* exit_step, int64_t* n_unexited, const pm_path_opts* opts)
+{
+    if (!c) return fail(PM_EINVAL, "ctx is NULL");
+    int rc = check_field(field);
+    if (rc) return rc;
+    if (!gd) return fail(PM_EINVAL, "boundary data is NULL");
+    if (!(std::isfinite(gd->R) && gd->R > 0)) return fail(PM_EINVAL, "R must be finite and > 0");
+    if (!std::isfinite(gd->quad) || !std::isfinite(gd->f_const)) return fail(PM_EINVAL, "quad and f_const must be finite");
+    if (gd->n_ang < 0 || gd->n_ang > PM_MAX_BOUNDARY_MODES) return fail(PM_EINVAL, "n_ang out of range (max %d)", PM_MAX_BOUNDARY_MODES);
+    if (gd->n_ang > 0 && (!gd->a || !gd->b)) return fail(PM_EINVAL, "boundary arrays are NULL");
+    if (gd->n_ang > 0 && (!finite_array(gd->a, gd->n_ang) || !finite_array(gd->b, gd->n_ang)))
+        return fail(PM_EINVAL, "boundary amplitudes contain NaN or Inf");
+    if (!std::isfinite(drift_scale)) return fail(PM_EINVAL, "drift_scale must be finite");
+    if (!(std::isfinite(kappa) && kappa >= 0)) return fail(PM_EINVAL, "kappa must be finite and >= 0");
+    if (!(std::isfinite(dt) && dt > 0)) return fail(PM_EINVAL, "dt must be finite and > 0");
+    if (max_steps < 1 || max_steps > 0x7fffffffLL) return fail(PM_EINVAL, "max_steps must be in [1, 2^31)");
+    if (n_obs < 0) return fail(PM_EINVAL, "n_obs < 0");
+    if (n_obs == 0) {
+        if (n_unexited && !(flags & PM_DEVICE_PTRS)) *n_unexited = 0;
+        return PM_OK;
+    }
+    if (M < 1) return fail(PM_EINVAL, "M must be >= 1");
+    if (n_obs > 0xffffffffLL) return fail(PM_EINVAL, "n_obs too large");
+    const int64_t off = opts ? opts->path_offset : 0;
+    if (off < 0 || off + M > ((int64_t)1 << 32)) return fail(PM_EINVAL, "path_offset + M exceeds 2^32");
+    if (n_obs > (((int64_t)1 << 62) / M)) return fail(PM_EINVAL, "n_obs * M too large");
+    if (!x || !mean) return fail(PM_EINVAL, "x and mean must not be NULL");
+    double* g_out = opts ? opts->g_out : nullptr;
+    double* x_out = opts ? opts->x_out : nullptr;
+    if ((rc = check_ptrs(flags, {x, mean, var, exit_step, n_unexited, g_out, x_out}))) return rc;
+    const bool dev = flags & PM_DEVICE_PTRS;
+    const bool fp64 = flags & PM_FP64;
+    if (!dev && !finite_array(x, 2 * n_obs)) return fail(PM_EINVAL, "observation points contain NaN or Inf");
+    if ((rc = set_device(c))) return rc;
+    const int64_t total = n_obs * M;
+
+    auto layout = [&](Bump& b) {
+        struct P { unsigned long long* ctr; double *g, *x, *mean, *var, *xo; int32_t* es; } p{};
+        p.ctr = b.take<unsigned long long>(2);
+        p.g = (dev && g_out) ? nullptr : b.take<double>((size_t)total);
+        if (!dev) {
+            p.x = b.take<double>((size_t)(2 * n_obs));
+            p.mean = b.take<double>((size_t)n_obs);
+            p.var = var ? b.take<double>((size_t)n_obs) : nullptr;
+            p.es = exit_step ? b.take<int32_t>((size_t)total) : nullptr;
+            p.xo = x_out ? b.take<double>((size_t)(2 * total)) : nullptr;
+        }
+        return p;
+    };
+    Bump probe(nullptr);
+    layout(probe);
+    if ((rc = ensure_workspace(c, probe.off))) return rc;
+    Bump bump(c->ws);
+    auto W = layout(bump);
+
+    const double* dx = x;
+    double *dmean = mean, *dvar = var, *dg = (dev && g_out) ? g_out : W.g, *dxo = x_out;
+    int32_t* des = exit_step;
+    if (!dev) {
+        const size_t outb = (size_t)n_obs * 16 + (g_out ? (size_t)total * 8 : 0) + (exit_step ? (size_t)total * 4 : 0) +
+                            (x_out ? (size_t)total * 16 : 0) + 256;
+        const size_t inb = (size_t)n_obs * 16 + 64;
+        if ((rc = ensure_host(c, inb > outb ? inb : outb))) return rc;
+        memcpy(c->host, x, (size_t)n_obs * 16);
+        PM_CUDA(cudaMemcpyAsync(W.x, c->host, (size_t)n_obs * 16, cudaMemcpyHostToDevice, c->stream), "copy x");
+        dx = W.x;
+        dmean = W.mean;
+        dvar = W.var;
+        des = W.es;
+        dxo = W.xo;
+    }
+    const std::vector<double> tab = stage_coefficients(field->K, field->u);
+    PM_CUDA(cudaMemsetAsync(W.ctr, 0, 16, c->stream), "clear counters");
+
+    DirichletLaunch L{};
+    L.coef = tab.data();
+    L.drift_scale = drift_scale;
+    L.R = gd->R;
+    L.quad = gd->quad;
+    L.f_const = gd->f_const;
+    L.n_ang = gd->n_ang;
+    L.ga = gd->a;
+    L.gb = gd->b;
+    L.x = dx;
+    L.n_obs = n_obs;
+    L.M = M;
+    L.dt = dt;
+    L.s_dt = std::sqrt(2.0 * kappa * dt);
+    L.max_steps = max_steps;
+    L.counter = W.ctr;
+    L.n_unexited = W.ctr + 1;
+    L.g = dg;
+    L.exit_step = des;
+    L.x_out = dxo;
+    L.path_offset = off;
+    L.inst = opts ? opts->instance : 0u;
+    L.key0 = (uint32_t)(seed & 0xffffffffu);
+    L.key1 = (uint32_t)(seed >> 32);
+    const int per_sm = fp64 ? dispatch_dirichlet_occupancy<double>(field->K) : dispatch_dirichlet_occupancy<float>(field->K);
+    int64_t grid = (int64_t)per_sm * c->sm_count;
+    const int64_t need = (total + kDirichletBlock - 1) / kDirichletBlock;
+    if (grid > need) grid = need;
+    L.grid = (int)(grid > 0 ? grid : 1);
+    if (c->timing) PM_CUDA(cudaEventRecord(c->ev0, c->stream), "event");
+    cudaError_t e = fp64 ? dispatch_dirichlet<double>(field->K, L, c->stream) : dispatch_dirichlet<float>(field->K, L, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "dirichlet kernel launch");
+    if (c->timing) {
+        PM_CUDA(cudaEventRecord(c->ev1, c->stream), "event");
+        c->timed = true;
+    }
+    count_launch(c);
+    PM_CUDA(launch_reduce_paths(dg, n_obs, M, dmean, dvar, c->stream), "reduce kernel");
+    count_launch(c);
+    if (dev && n_unexited)
+        PM_CUDA(cudaMemcpyAsync(n_unexited, W.ctr + 1, 8, cudaMemcpyDeviceToDevice, c->stream), "copy n_unexited");
+    if (dev && (flags & PM_ASYNC)) return PM_OK;
+
+    unsigned long long unexited = 0;
+    if (!dev) {
+        char* h = (char*)c->host;
+        size_t o = 0;
+        PM_CUDA(cudaMemcpyAsync(h + o, dmean, (size_t)n_obs * 8, cudaMemcpyDeviceToHost, c->stream), "copy mean");
+        o += (size_t)n_obs * 8;
+        if (var) { PM_CUDA(cudaMemcpyAsync(h + o, dvar, (size_t)n_obs * 8, cudaMemcpyDeviceToHost, c->stream), "copy var"); o += (size_t)n_obs * 8; }
+        if (g_out) { PM_CUDA(cudaMemcpyAsync(h + o, dg, (size_t)total * 8, cudaMemcpyDeviceToHost, c->stream), "copy g"); o += (size_t)total * 8; }
+        if (x_out) { PM_CUDA(cudaMemcpyAsync(h + o, dxo, (size_t)total * 16, cudaMemcpyDeviceToHost, c->stream), "copy x_out"); o += (size_t)total * 16; }
+        if (exit_step) { PM_CUDA(cudaMemcpyAsync(h + o, des, (size_t)total * 4, cudaMemcpyDeviceToHost, c->stream), "copy exit steps"); }
+    }
+    PM_CUDA(cudaMemcpyAsync(&unexited, W.ctr + 1, 8, cudaMemcpyDeviceToHost, c->stream), "copy n_unexited");
+    PM_CUDA(cudaStreamSynchronize(c->stream), "dirichlet");
+    if (!dev) {
+        const char* h = (const char*)c->host;
+        size_t o = 0;
+        memcpy(mean, h + o, (size_t)n_obs * 8);
+        o += (size_t)n_obs * 8;
+        if (var) { memcpy(var, h + o, (size_t)n_obs * 8); o += (size_t)n_obs * 8; }
+        if (g_out) { memcpy(g_out, h + o, (size_t)total * 8); o += (size_t)total * 8; }
+        if (x_out) { memcpy(x_out, h + o, (size_t)total * 16); o += (size_t)total * 16; }
+        if (exit_step) memcpy(exit_step, h + o, (size_t)total * 4);
+        if (n_unexited) *n_unexited = (int64_t)unexited;
+    }
+    return unexited ? PM_WARN_UNEXITED : PM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostics
+// ---------------------------------------------------------------------------
+int pm_philox(pm_ctx* c, const uint32_t* ctr, uint32_t key0, uint32_t key1, int64_t n, uint32_t* out, uint32_t flags)
+{
+    if (!c) return fail(PM_EINVAL, "ctx is NULL");
+    if (n < 0) return fail(PM_EINVAL, "n < 0");
+    if (n == 0) return PM_OK;
+    if (!ctr || !out) return fail(PM_EINVAL, "NULL array");
+    int rc = check_ptrs(flags, {ctr, out});
+    if (rc) return rc;
+    if ((rc = set_device(c))) return rc;
+    const bool dev = flags & PM_DEVICE_PTRS;
+    const uint32_t* dctr = ctr;
+    uint32_t* dout = out;
+    if (!dev) {
+        Bump probe(nullptr);
+        probe.take<uint32_t>((size_t)(4 * n));
+        probe.take<uint32_t>((size_t)(4 * n));
+        if ((rc = ensure_workspace(c, probe.off))) return rc;
+        Bump b(c->ws);
+        uint32_t* a = b.take<uint32_t>((size_t)(4 * n));
+        dout = b.take<uint32_t>((size_t)(4 * n));
+        PM_CUDA(cudaMemcpyAsync(a, ctr, (size_t)n * 16, cudaMemcpyHostToDevice, c->stream), "copy counters");
+        dctr = a;
+    }
+    PM_CUDA(launch_philox(dctr, key0, key1, n, dout, c->stream), "philox kernel");
+    count_launch(c);
+    if (!dev) PM_CUDA(cudaMemcpyAsync(out, dout, (size_t)n * 16, cudaMemcpyDeviceToHost, c->stream), "copy out");
+    if (dev && (flags & PM_ASYNC)) return PM_OK;
+    PM_CUDA(cudaStreamSynchronize(c->stream), "philox");
+    return PM_OK;
+}
+
+int pm_normals(pm_ctx* c, uint64_t seed, uint32_t b, uint32_t j, uint32_t i, int64_t n0, int64_t count, double* out,
+               uint32_t flags)
+{
+    if (!c) return fail(PM_EINVAL, "ctx is NULL");
+    if (count < 0 || n0 < 0) return fail(PM_EINVAL, "negative step range");
+    if (count == 0) return PM_OK;
+    if (!out) return fail(PM_EINVAL, "out is NULL");
+    int rc = check_ptrs(flags, {out});
+    if (rc) return rc;
+    if ((rc = set_device(c))) return rc;
+    const bool dev = flags & PM_DEVICE_PTRS;
+    double* dout = out;
+    if (!dev) {
+        if ((rc = ensure_workspace(c, (size_t)count * 16 + 256))) return rc;
+        dout = (double*)c->ws;
+    }
+    PM_CUDA(launch_normals(seed, b, j, i, n0, count, dout, flags & PM_FP64, c->stream), "normals kernel");
+    count_launch(c);
+    if (!dev) PM_CUDA(cudaMemcpyAsync(out, dout, (size_t)count * 16, cudaMemcpyDeviceToHost, c->stream), "copy out");
+    if (dev && (flags & PM_ASYNC)) return PM_OK;
+    PM_CUDA(cudaStreamSynchronize(c->stream), "normals");
+    return PM_OK;
+}
+
+int pm_velocity(pm_ctx* c, const pm_field* field, const double* x, int64_t npts, double* v, uint32_t flags)
+{
+    if (!c) return fail(PM_EINVAL, "ctx is NULL");
+    int rc = check_field(field);
+    if (rc) return rc;
+    if (npts < 0) return fail(PM_EINVAL, "npts < 0");
+    if (npts == 0) return PM_OK;
+    if (!x || !v) return fail(PM_EINVAL, "NULL array");
+    if ((rc = check_ptrs(flags, {x, v}))) return rc;
+    if ((rc = set_device(c))) return rc;
+    const bool dev = flags & PM_DEVICE_PTRS;
+    const double* dx = x;
+    double* dv = v;
+    if (!dev) {
+        Bump probe(nullptr);
+        probe.take<double>((size_t)(2 * npts));
+        probe.take<double>((size_t)(2 * npts));
+        if ((rc = ensure_workspace(c, probe.off))) return rc;
+        Bump b(c->ws);
+        double* a = b.take<double>((size_t)(2 * npts));
+        dv = b.take<double>((size_t)(2 * npts));
+        PM_CUDA(cudaMemcpyAsync(a, x, (size_t)npts * 16, cudaMemcpyHostToDevice, c->stream), "copy x");
+        dx = a;
+    }
+    const std::vector<double> tab = stage_coefficients(field->K, field->u);
+    cudaError_t e = (flags & PM_FP64) ? dispatch_velocity<double>(field->K, tab.data(), dx, npts, dv, c->stream)
+                                      : dispatch_velocity<float>(field->K, tab.data(), dx, npts, dv, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "velocity kernel");
+    count_launch(c);
+    if (!dev) PM_CUDA(cudaMemcpyAsync(v, dv, (size_t)npts * 16, cudaMemcpyDeviceToHost, c->stream), "copy v");
+    if (dev && (flags & PM_ASYNC)) return PM_OK;
+    PM_CUDA(cudaStreamSynchronize(c->stream), "velocity");
+    return PM_OK;
+}
+
+}  // extern "C"

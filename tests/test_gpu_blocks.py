@@ -1,0 +1,53 @@
+"""GPU parity of the building blocks of the particle step against the oracle:
+Philox words (bit-exact), Box-Muller normals, and the velocity field."""
+import numpy as np
+import pytest
+
+from paper_1808_10580_gb300 import inputs
+from tests import _gpu
+
+pytestmark = pytest.mark.gpu
+pm = _gpu.pm
+
+
+@pytest.fixture(scope="module")
+def c():
+    h = _gpu.ctx()
+    yield h
+    pm.pm_destroy(h)
+
+
+def test_philox_bit_exact_on_a_million_counters(c, orc):
+    rng = np.random.default_rng(11)
+    ctr = rng.integers(0, 2 ** 32, size=(1_000_000, 4), dtype=np.uint64).astype(np.uint32)
+    key = (0xDEADBEEF, 0x01234567)
+    out = np.empty_like(ctr)
+    pm.pm_philox(c, ctr, key[0], key[1], len(ctr), out)
+    ref = orc.philox(ctr, key)
+    assert np.array_equal(out, ref)
+
+
+@pytest.mark.parametrize("fp64", [False, True])
+def test_normals_match_oracle(c, orc, fp64):
+    seed = (12345 << 32) | 678
+    out = np.empty((4096, 2))
+    pm.pm_normals(c, seed, 3, 7, 11, 5, 4096, out, pm.PM_FP64 if fp64 else pm.PM_FP32)
+    ref = orc.normals(seed, 3, 7, 11, 5, 4096)
+    tol = 1e-13 if fp64 else 4e-6  # float: log, sqrt and sincospi each within a few ulp
+    assert np.abs(out - ref).max() < tol
+
+
+@pytest.mark.parametrize("K", [0, 1, 2, 3, 4, 5, 6, 8, 10, 12, 16])
+@pytest.mark.parametrize("fp64", [False, True])
+def test_velocity_matches_direct_sum(c, orc, K, fp64):
+    u = inputs.prior_field(K, 100 + K)
+    rng = np.random.default_rng(K)
+    x = np.concatenate([rng.random((4000, 2)), rng.random((1000, 2)) * 2 - 0.5])  # also outside [0,1)^2
+    v = np.empty_like(x)
+    pm.pm_velocity(c, pm.Field(K, u), x, len(x), v, pm.PM_FP64 if fp64 else pm.PM_FP32)
+    ref = orc.velocity(K, u, x)
+    modes = orc.half_modes(K).astype(float)
+    # bound on the size of the terms of the sum: sum_h 2 pi |k_h| (|a_h| + |b_h|)
+    scale = float((2 * np.pi * np.sqrt((modes ** 2).sum(1)) * np.abs(u.reshape(-1, 2)).sum(1)).sum()) if K else 1.0
+    tol = (1e-13 if fp64 else 2e-6 * max(K, 1)) * scale
+    assert np.abs(v - ref).max() <= tol, (np.abs(v - ref).max(), tol)
