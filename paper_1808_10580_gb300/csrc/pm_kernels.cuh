@@ -116,13 +116,14 @@ __global__ void __launch_bounds__(BLOCK) timedep_kernel(const __grid_constant__ 
         auto tab = [&](int t) { return p.field.c[t]; };
         for (int n = 0; n < N; n += 2) {
             const u32x4 r = philox4x32_10(u32x4{(uint32_t)(n >> 1), pid, (uint32_t)j, p.inst}, p.key0, p.key1);
-#pragma unroll
+            // One copy of the step body (kept rolled): the unrolled velocity sum is
+            // ~1000 instructions, and two copies overflow the instruction cache.
+#pragma unroll 1
             for (int half = 0; half < 2; ++half) {
                 const int nn = n + half;
-                if (half == 1 && nn >= N) break;
+                if (nn >= N) break;
                 Real xi1, xi2;
-                if (half == 0) box_muller<Real>(r.x, r.y, xi1, xi2);
-                else box_muller<Real>(r.z, r.w, xi1, xi2);
+                box_muller<Real>(half ? r.z : r.x, half ? r.w : r.y, xi1, xi2);
                 const bool last = (nn == N - 1);
                 const Real h = last ? h_last : p.dt;
                 const Real s = last ? s_last : p.s_dt;
@@ -273,11 +274,10 @@ __global__ void __launch_bounds__(kDirichletBlock) dirichlet_kernel(const __grid
         if (__all_sync(full, done)) break;
         if (pid < 0) continue;
         const u32x4 r = philox4x32_10(u32x4{(uint32_t)(n >> 1), i, j, p.inst}, p.key0, p.key1);
-#pragma unroll
+#pragma unroll 1
         for (int half = 0; half < 2; ++half) {
             Real xi1, xi2;
-            if (half == 0) box_muller<Real>(r.x, r.y, xi1, xi2);
-            else box_muller<Real>(r.z, r.w, xi1, xi2);
+            box_muller<Real>(half ? r.z : r.x, half ? r.w : r.y, xi1, xi2);
             Real x1[1] = {X1.val()}, x2[1] = {X2.val()}, v1[1], v2[1];
             velocity<Real, K, 1>(tab, x1, x2, v1, v2);
             em_update<Real>(X1, v1[0], p.drift_dt, p.s_dt, xi1);
