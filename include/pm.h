@@ -171,6 +171,39 @@ int pm_forward_dirichlet(pm_ctx* ctx, const pm_field* field, double drift_scale,
                          const pm_path_opts* opts);
 
 /* ---------------------------------------------------------------------------
+ * Allocation-free variant (the paper has no counterpart; this is a library
+ * convenience).
+ *
+ * For callers that cannot allocate device memory -- code that runs while
+ * another allocator owns the device's memory, latency-critical loops where
+ * cudaMalloc's implicit synchronisation is not acceptable, hosts that forbid
+ * allocation after start-up.  Same arguments, kernels and results as
+ * pm_forward_timedep with device pointers (x, t, mean, var on the current
+ * device), but no context: work is queued on `cuda_stream` (NULL = legacy
+ * default stream) on the current device, and the scratch comes from one
+ * fixed device array of PM_NOALLOC_SCRATCH_BYTES that the library declares
+ * and that every GPU which loads the library holds until the process exits.
+ * The call allocates nothing: no cudaMalloc, cudaFree or allocating library
+ * routine.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Problems whose scratch (about n_obs * (48 + 16 * ceil(M/128)) bytes)
+ *     exceeds PM_NOALLOC_SCRATCH_BYTES are rejected with PM_EINVAL.
+ *   - All calls share the one array: calls whose work overlaps on the GPU
+ *     (other streams, other host threads) race and give wrong results;
+ *     serialise them.
+ *   - flags: PM_FP32 or PM_FP64, plus PM_ASYNC to return without waiting
+ *     (then invalid x/t values are not reported).
+ * ------------------------------------------------------------------------- */
+#define PM_NOALLOC_SCRATCH_BYTES (4u << 20)
+
+int pm_forward_timedep_noalloc(const pm_field* field, double kappa, const pm_fourier* theta0,
+                               const double* x, const double* t, int64_t n_obs, int64_t M, double dt,
+                               uint64_t seed, uint32_t flags, double* mean, double* var,
+                               void* cuda_stream);
+
+/* ---------------------------------------------------------------------------
  * Diagnostics: the building blocks of the particle step, exposed so that each
  * can be checked on its own against an independent implementation.
  * ------------------------------------------------------------------------- */

@@ -87,6 +87,8 @@ def load(build_if_missing: bool = True):
     L.pm_philox.argtypes = [vp, vp, u32, u32, i64, vp, u32]
     L.pm_normals.argtypes = [vp, C.c_uint64, u32, u32, u32, i64, i64, vp, u32]
     L.pm_velocity.argtypes = [vp, C.POINTER(pm_field), vp, i64, vp, u32]
+    L.pm_forward_timedep_noalloc.argtypes = [C.POINTER(pm_field), dbl, C.POINTER(pm_fourier), vp, vp, i64, i64,
+                                             dbl, C.c_uint64, u32, vp, vp, vp]
     L.pm_set_kernel_timing.argtypes = [vp, C.c_int]
     L.pm_last_kernel_ms.argtypes = [vp]
     L.pm_last_kernel_ms.restype = C.c_float
@@ -232,3 +234,12 @@ def pm_velocity(ctx, field: Field, x, npts, v, flags=0):
     if _device(x, v):
         flags |= PM_DEVICE_PTRS
     return _check(load().pm_velocity(ctx, C.byref(field.s), _ptr(x), int(npts), _ptr(v), int(flags)))
+
+
+def pm_forward_timedep_noalloc(field: Field, kappa, theta0: Fourier, x, t, n_obs, M, dt, seed, flags, mean, var=None,
+                               stream=None):
+    """Allocation-free time-dependent map: device tensors only, scratch from the
+    library's fixed device array (see include/pm.h)."""
+    return _check(load().pm_forward_timedep_noalloc(C.byref(field.s), float(kappa), C.byref(theta0.s), _ptr(x),
+                                                    _ptr(t), int(n_obs), int(M), float(dt), int(seed), int(flags),
+                                                    _ptr(mean), _ptr(var), stream))

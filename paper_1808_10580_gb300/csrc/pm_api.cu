@@ -154,6 +154,9 @@ bool is_device_pointer(const void* p)
 
 }  // namespace
 
+// Records a message for pm_last_error() from other translation units.
+int pm::set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
 // ---------------------------------------------------------------------------
 // Context
 // ---------------------------------------------------------------------------

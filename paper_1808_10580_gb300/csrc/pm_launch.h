@@ -71,6 +71,9 @@ template <typename Real, int K> cudaError_t launch_velocity(const double* coef, 
                                                             double* v, cudaStream_t s);
 template <typename Real, int K> int dirichlet_blocks_per_sm();
 
+// Stores `msg` as the calling thread's pm_last_error() text; returns `code`.
+int set_error(int code, const char* msg);
+
 // Support kernels (pm_support.cu).
 cudaError_t launch_prep_timedep(const double* x, const double* t, int64_t n_obs, double dt, double kappa,
                                 ObsRec* rec, int32_t* order, unsigned int* err, cudaStream_t s);
