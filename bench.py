@@ -317,6 +317,81 @@ def run_gpu(args):
     return 0
 
 
+def run_aux(args):
+    """Auxiliary measurements (not the headline line): the Dirichlet disk workload
+    (50 obs x M = 1e5, dt = 1e-4) or the 256-instance batched workload (mixed
+    time-dependent / Dirichlet, 100 obs x M = 4096 each).  Throughput counts the
+    Euler steps the paths actually took (pm_last_step_count)."""
+    import torch
+
+    import paper_1808_10580_gb300 as pm
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    ctx = pm.pm_create(0, stream.cuda_stream)
+    pm.pm_set_kernel_timing(ctx, 1)
+    if args.workload == "dirichlet":
+        w = inputs.dirichlet_disk_k10(M=args.M or 100_000)
+        fld = pm.Field(w.K, w.u)
+        gd = pm.DirichletData(w.g.R, w.g.quad, w.g.f_const, w.g.a, w.g.b)
+        x = torch.from_numpy(w.x).to(dev)
+        mean = torch.empty(len(w.x), dtype=torch.float64, device=dev)
+        var = torch.empty_like(mean)
+
+        def step():
+            pm.pm_forward_dirichlet(ctx, fld, w.drift_scale, w.kappa, gd, x, len(w.x), w.M, w.dt, w.max_steps,
+                                    w.seed, pm.PM_FP32, mean, var)
+        name, cfg = w.name, {"n_obs": len(w.x), "M": w.M, "dt": w.dt, "kappa": w.kappa, "drift_scale": w.drift_scale}
+    else:
+        ws = inputs.batched_instances(B=args.B, M=args.M or 4096)
+        xs, ts, inst = [], [], []
+        row = 0
+        for w in ws:
+            n = len(w.x)
+            xs.append(w.x)
+            ts.append(w.t if isinstance(w, inputs.TimedepWorkload) else np.zeros(n))
+            d = dict(kind=pm.PM_KIND_TIMEDEP if isinstance(w, inputs.TimedepWorkload) else pm.PM_KIND_DIRICHLET,
+                     u=torch.from_numpy(w.u).to(dev), kappa=w.kappa, dt=w.dt, row0=row, n_obs=n, M=w.M, seed=w.seed)
+            if d["kind"] == pm.PM_KIND_DIRICHLET:
+                d.update(drift_scale=w.drift_scale, max_steps=w.max_steps)
+            inst.append(d)
+            row += n
+        th = next(w.theta0 for w in ws if isinstance(w, inputs.TimedepWorkload))
+        g = next(w.g for w in ws if isinstance(w, inputs.DirichletWorkload))
+        xt = torch.from_numpy(np.ascontiguousarray(np.concatenate(xs))).to(dev)
+        tt = torch.from_numpy(np.ascontiguousarray(np.concatenate(ts))).to(dev)
+        batch = pm.Batch(10, inst, xt, tt, pm.Fourier(th.k, th.a, th.b), pm.DirichletData(g.R, g.quad, g.f_const, g.a, g.b))
+        mean = torch.empty(row, dtype=torch.float64, device=dev)
+        var = torch.empty_like(mean)
+
+        def step():
+            pm.pm_forward_batched(ctx, batch, pm.PM_FP32, mean, var)
+        name, cfg = f"batched_{args.B}x100obs_M{args.M or 4096}", {"B": args.B, "rows": row}
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    times, steps = [], []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        times.append(e0.elapsed_time(e1) / 1e3)
+        steps.append(pm.pm_last_step_count(ctx))
+    total = sum(times)
+    line = {"metric": METRIC, "value": sum(steps) / total, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic", "auxiliary": True,
+            "config": dict(workload=name, particle_steps_per_call=steps[-1], **cfg)}
+    if args.workload == "dirichlet":
+        line["kernel_ms"] = pm.pm_last_kernel_ms(ctx)
+    print(json.dumps(line), flush=True)
+    pm.pm_destroy(ctx)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -324,13 +399,18 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--M", type=int, default=0, help="particles per observation (default: the workload's 1e4; "
+    ap.add_argument("--M", type=int, default=0, help="particles per observation (default: the workload's own; "
                     "smaller values are for profiling captures only)")
+    ap.add_argument("--workload", default="timedep", choices=["timedep", "dirichlet", "batched"],
+                    help="timedep: the headline line; dirichlet / batched: auxiliary measurements")
+    ap.add_argument("--B", type=int, default=256, help="instances of the batched workload")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "timedep":
+        return run_aux(args)
     return run_gpu(args)
 
 

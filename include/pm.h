@@ -171,6 +171,67 @@ int pm_forward_dirichlet(pm_ctx* ctx, const pm_field* field, double drift_scale,
                          const pm_path_opts* opts);
 
 /* ---------------------------------------------------------------------------
+ * Batched map: many parameter samples in one persistent launch.
+ *
+ * B instances, each a time-dependent (Algorithm 1) or a Dirichlet
+ * (Algorithm 2) problem with its own coefficients u_b, observation rows,
+ * particle count, step and seed; all share the wave-number bound K, theta0
+ * (time-dependent instances) and the disk data (Dirichlet instances).  The
+ * observations of instance b are rows [row0, row0 + n_obs) of the batch's x
+ * (and t); the rows of all instances must tile [0, n_rows) without overlap.
+ * The RNG counter of instance b uses b as its instance word and the row's
+ * offset j within the instance, so an instance gives the same estimate as
+ * pm_forward_timedep / pm_forward_dirichlet with opts->instance = b and the
+ * same seed (up to the float rounding of the coefficient table).
+ * Section 3.3 makes every path independent: one persistent kernel runs all
+ * paths of all instances; each lane takes a new path of its warp's instance
+ * as soon as its path ends, and warps move between instances as these run
+ * out of paths, so uneven path lengths stay load-balanced.
+ * The call sequence (coefficient staging, row preparation, persistent kernel,
+ * reduction, copies) is captured once into a CUDA graph per call shape and
+ * replayed on later calls with the same shape; a context created on the
+ * legacy default stream launches directly instead (that stream cannot be
+ * captured).  Float paths, double reductions; PM_FP64 is not supported here.
+ * ------------------------------------------------------------------------- */
+#define PM_KIND_TIMEDEP 0
+#define PM_KIND_DIRICHLET 1
+
+typedef struct pm_instance {
+    int32_t kind;          /* PM_KIND_TIMEDEP or PM_KIND_DIRICHLET */
+    int32_t reserved;
+    const double* u;       /* 2|H_K| coefficients; host, or device with PM_DEVICE_PTRS */
+    double kappa;          /* >= 0 */
+    double dt;             /* > 0 */
+    double drift_scale;    /* Dirichlet: drift is -drift_scale v_u (time-dependent: ignored, 1) */
+    int64_t max_steps;     /* Dirichlet: cap on the steps of a path, >= 1 */
+    int64_t row0;          /* first observation row */
+    int64_t n_obs;         /* >= 1 rows */
+    int64_t M;             /* >= 1 particles per observation */
+    uint64_t seed;
+} pm_instance;
+
+typedef struct pm_batch {
+    int32_t K;
+    int32_t B;                       /* >= 1 instances */
+    const pm_instance* inst;         /* host array [B] */
+    const pm_fourier* theta0;        /* host; required if any instance is time-dependent */
+    const pm_dirichlet_data* disk;   /* host; required if any instance is Dirichlet */
+    const double* x;                 /* [n_rows][2] */
+    const double* t;                 /* [n_rows]; read for time-dependent rows only */
+    int64_t n_rows;
+} pm_batch;
+
+/* mean, var: [n_rows] (var may be NULL); n_unexited: total capped Dirichlet
+ * paths (or NULL).  x, t, mean, var, n_unexited and the u pointers are device
+ * pointers with PM_DEVICE_PTRS, else host pointers.  Returns PM_OK,
+ * PM_WARN_UNEXITED, or an error. */
+int pm_forward_batched(pm_ctx* ctx, const pm_batch* batch, uint32_t flags, double* mean, double* var,
+                       int64_t* n_unexited);
+
+/* Graph capture and replay of pm_forward_batched: on (1, default) or off (0). */
+int pm_set_graph_mode(pm_ctx* ctx, int on);
+
+/* ---------------------------------------------------------------------------
  * Allocation-free variant (the paper has no counterpart; this is a library
  * convenience).
  *
@@ -237,6 +298,11 @@ float pm_last_kernel_ms(pm_ctx* ctx);
 
 /* Number of kernels the context has launched since it was created. */
 int64_t pm_launch_count(const pm_ctx* ctx);
+
+/* Euler steps taken by all paths of the last forward call on this context
+ * that synchronised (-1 after a PM_ASYNC call).  Dirichlet paths have
+ * data-dependent lengths; this is the count throughput figures use. */
+int64_t pm_last_step_count(const pm_ctx* ctx);
 
 #ifdef __cplusplus
 }

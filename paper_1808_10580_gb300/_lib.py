@@ -53,6 +53,22 @@ class pm_path_opts(C.Structure):
                 ("g_out", C.c_void_p), ("x_out", C.c_void_p)]
 
 
+PM_KIND_TIMEDEP = 0
+PM_KIND_DIRICHLET = 1
+
+
+class pm_instance(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("reserved", C.c_int32), ("u", C.c_void_p), ("kappa", C.c_double),
+                ("dt", C.c_double), ("drift_scale", C.c_double), ("max_steps", C.c_int64), ("row0", C.c_int64),
+                ("n_obs", C.c_int64), ("M", C.c_int64), ("seed", C.c_uint64)]
+
+
+class pm_batch(C.Structure):
+    _fields_ = [("K", C.c_int32), ("B", C.c_int32), ("inst", C.POINTER(pm_instance)),
+                ("theta0", C.POINTER(pm_fourier)), ("disk", C.POINTER(pm_dirichlet_data)), ("x", C.c_void_p),
+                ("t", C.c_void_p), ("n_rows", C.c_int64)]
+
+
 _lib = None
 
 
@@ -89,11 +105,15 @@ def load(build_if_missing: bool = True):
     L.pm_velocity.argtypes = [vp, C.POINTER(pm_field), vp, i64, vp, u32]
     L.pm_forward_timedep_noalloc.argtypes = [C.POINTER(pm_field), dbl, C.POINTER(pm_fourier), vp, vp, i64, i64,
                                              dbl, C.c_uint64, u32, vp, vp, vp]
+    L.pm_forward_batched.argtypes = [vp, C.POINTER(pm_batch), u32, vp, vp, vp]
+    L.pm_set_graph_mode.argtypes = [vp, C.c_int]
     L.pm_set_kernel_timing.argtypes = [vp, C.c_int]
     L.pm_last_kernel_ms.argtypes = [vp]
     L.pm_last_kernel_ms.restype = C.c_float
     L.pm_launch_count.argtypes = [vp]
     L.pm_launch_count.restype = i64
+    L.pm_last_step_count.argtypes = [vp]
+    L.pm_last_step_count.restype = i64
     _lib = L
     return L
 
@@ -191,6 +211,10 @@ def pm_launch_count(ctx):
     return int(load().pm_launch_count(ctx))
 
 
+def pm_last_step_count(ctx):
+    return int(load().pm_last_step_count(ctx))
+
+
 def _opts(path_offset=0, instance=0, g_out=None, x_out=None):
     return pm_path_opts(int(path_offset), int(instance), 0, _ptr(g_out), _ptr(x_out))
 
@@ -243,3 +267,37 @@ def pm_forward_timedep_noalloc(field: Field, kappa, theta0: Fourier, x, t, n_obs
     return _check(load().pm_forward_timedep_noalloc(C.byref(field.s), float(kappa), C.byref(theta0.s), _ptr(x),
                                                     _ptr(t), int(n_obs), int(M), float(dt), int(seed), int(flags),
                                                     _ptr(mean), _ptr(var), stream))
+
+
+class Batch:
+    """Keeps the arrays of a pm_batch alive.  ``instances`` is a list of dicts with
+    keys kind, u, kappa, dt, row0, n_obs, M, seed (and drift_scale, max_steps for
+    Dirichlet instances); u may be numpy (host) or CUDA tensors (device)."""
+
+    def __init__(self, K, instances, x, t, theta0: Fourier = None, disk: DirichletData = None):
+        self.keep = [x, t, theta0, disk]
+        arr = (pm_instance * len(instances))()
+        for q, d in enumerate(instances):
+            u = d["u"]
+            if not _is_torch(u):
+                u = np.ascontiguousarray(u, dtype=np.float64)
+            self.keep.append(u)
+            arr[q] = pm_instance(int(d["kind"]), 0, _ptr(u), float(d["kappa"]), float(d["dt"]),
+                                 float(d.get("drift_scale", 1.0)), int(d.get("max_steps", 0)), int(d["row0"]),
+                                 int(d["n_obs"]), int(d["M"]), int(d["seed"]))
+        self.arr = arr
+        self.device = _device(x, t, *[d["u"] for d in instances])
+        n_rows = (x.shape[0] if hasattr(x, "shape") else len(x))
+        self.s = pm_batch(int(K), len(instances), arr, C.pointer(theta0.s) if theta0 is not None else None,
+                          C.pointer(disk.s) if disk is not None else None, _ptr(x), _ptr(t), int(n_rows))
+
+
+def pm_forward_batched(ctx, batch: Batch, flags, mean, var=None, n_unexited=None):
+    if batch.device or _device(mean, var, n_unexited):
+        flags |= PM_DEVICE_PTRS
+    return _check(load().pm_forward_batched(ctx, C.byref(batch.s), int(flags), _ptr(mean), _ptr(var),
+                                            _ptr(n_unexited)))
+
+
+def pm_set_graph_mode(ctx, on):
+    return _check(load().pm_set_graph_mode(ctx, int(bool(on))))

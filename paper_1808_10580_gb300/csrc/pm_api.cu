@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/pm.h"
+#include "pm_internal.h"
 #include "pm_launch.h"
 
 using namespace pm;
@@ -19,7 +20,9 @@ using namespace pm;
 // ---------------------------------------------------------------------------
 namespace {
 thread_local char g_err[512] = "";
+}  // namespace
 
+namespace pm {
 int fail(int code, const char* fmt, ...)
 {
     va_list ap;
@@ -38,12 +41,6 @@ int cuda_fail(cudaError_t e, const char* what)
     return fail(PM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-#define PM_CUDA(call, what)                              \
-    do {                                                 \
-        cudaError_t e_ = (call);                         \
-        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
-    } while (0)
-
 bool supported_K(int K)
 {
     switch (K) {
@@ -51,6 +48,9 @@ bool supported_K(int K)
     default: return false;
     }
 }
+}  // namespace pm
+
+namespace {
 
 #define PM_K_LIST(X) X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(8) X(10) X(12) X(16)
 
@@ -135,6 +135,9 @@ std::vector<double> stage_coefficients(int K, const double* u)
     return tab;
 }
 
+}  // namespace
+
+namespace pm {
 bool finite_array(const double* p, int64_t n)
 {
     for (int64_t i = 0; i < n; ++i)
@@ -151,44 +154,15 @@ bool is_device_pointer(const void* p)
     }
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
-
-}  // namespace
+}  // namespace pm
 
 // Records a message for pm_last_error() from other translation units.
 int pm::set_error(int code, const char* msg) { return fail(code, "%s", msg); }
 
 // ---------------------------------------------------------------------------
-// Context
+// Context helpers (pm_internal.h)
 // ---------------------------------------------------------------------------
-struct pm_ctx {
-    int device = 0;
-    int sm_count = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    void* ws = nullptr;      // device workspace
-    size_t ws_size = 0;
-    void* host = nullptr;    // pinned staging
-    size_t host_size = 0;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    bool timing = false;
-    bool timed = false;
-    int64_t launches = 0;
-};
-
-namespace {
-
-struct Bump {
-    char* base;
-    size_t off = 0;
-    explicit Bump(void* b) : base((char*)b) {}
-    template <typename T> T* take(size_t count)
-    {
-        off = (off + 255) & ~(size_t)255;
-        T* p = (T*)(base ? base + off : nullptr);
-        off += count * sizeof(T);
-        return p;
-    }
-};
+namespace pm {
 
 int ensure_workspace(pm_ctx* c, size_t bytes)
 {
@@ -246,9 +220,9 @@ int check_ptrs(uint32_t flags, std::initializer_list<const void*> ptrs)
     return PM_OK;
 }
 
-void count_launch(pm_ctx* c, int n = 1) { c->launches += n; }
+void count_launch(pm_ctx* c, int n) { c->launches += n; }
 
-}  // namespace
+}  // namespace pm
 
 extern "C" {
 
@@ -295,6 +269,7 @@ void pm_destroy(pm_ctx* c)
     if (c->host) cudaFreeHost(c->host);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -319,6 +294,8 @@ float pm_last_kernel_ms(pm_ctx* c)
 }
 
 int64_t pm_launch_count(const pm_ctx* c) { return c ? c->launches : 0; }
+
+int64_t pm_last_step_count(const pm_ctx* c) { return c ? c->last_steps : -1; }
 
 // ---------------------------------------------------------------------------
 // Algorithm 1
@@ -360,8 +337,9 @@ int pm_forward_timedep(pm_ctx* c, const pm_field* field, double kappa, const pm_
     // Workspace layout.
     const bool sort = n_obs <= 8192;
     auto layout = [&](Bump& b) {
-        struct P { unsigned* err; ObsRec* rec; int32_t* order; double2* part; double *x, *t, *mean, *var, *g, *xo; } p{};
-        p.err = b.take<unsigned>(4);
+        struct P { unsigned* err; unsigned long long* steps; ObsRec* rec; int32_t* order; double2* part; double *x, *t, *mean, *var, *g, *xo; } p{};
+        p.err = b.take<unsigned>(64);     // error flag, then the step counter 128 bytes on
+        p.steps = (unsigned long long*)(p.err ? p.err + 32 : nullptr);
         p.rec = b.take<ObsRec>((size_t)n_obs);
         p.order = sort ? b.take<int32_t>((size_t)n_obs) : nullptr;
         p.part = b.take<double2>((size_t)(n_obs * chunks));
@@ -402,8 +380,10 @@ int pm_forward_timedep(pm_ctx* c, const pm_field* field, double kappa, const pm_
     }
 
     const std::vector<double> tab = stage_coefficients(field->K, field->u);
-    PM_CUDA(cudaMemsetAsync(W.err, 0, 16, c->stream), "clear flags");
-    PM_CUDA(launch_prep_timedep(dx, dtm, n_obs, dt, kappa, W.rec, W.order, W.err, c->stream), "prep kernel");
+    PM_CUDA(cudaMemsetAsync(W.err, 0, 256, c->stream), "clear flags");
+    PM_CUDA(launch_prep_timedep(dx, dtm, n_obs, dt, kappa, W.rec, W.order, W.err, c->stream, W.steps, M),
+            "prep kernel");
+    c->last_steps = -1;
     count_launch(c, sort ? 2 : 1);
 
     TimedepLaunch L{};
@@ -448,8 +428,11 @@ int pm_forward_timedep(pm_ctx* c, const pm_field* field, double kappa, const pm_
         if (g_out) { PM_CUDA(cudaMemcpyAsync(h + o, dg, (size_t)(n_obs * M) * 8, cudaMemcpyDeviceToHost, c->stream), "copy g"); o += (size_t)(n_obs * M); }
         if (x_out) { PM_CUDA(cudaMemcpyAsync(h + o, dxo, (size_t)(2 * n_obs * M) * 8, cudaMemcpyDeviceToHost, c->stream), "copy x_out"); }
     }
+    unsigned long long steps_taken = 0;
     PM_CUDA(cudaMemcpyAsync(&err_flag, W.err, 4, cudaMemcpyDeviceToHost, c->stream), "copy flags");
+    PM_CUDA(cudaMemcpyAsync(&steps_taken, W.steps, 8, cudaMemcpyDeviceToHost, c->stream), "copy step count");
     PM_CUDA(cudaStreamSynchronize(c->stream), "timedep");
+    c->last_steps = (int64_t)steps_taken;
     if (!dev) {
         const double* h = (const double*)c->host;
         size_t o = 0;
@@ -507,7 +490,7 @@ int pm_forward_dirichlet(pm_ctx* c, const pm_field* field, double drift_scale, d
 
     auto layout = [&](Bump& b) {
         struct P { unsigned long long* ctr; double *g, *x, *mean, *var, *xo; int32_t* es; } p{};
-        p.ctr = b.take<unsigned long long>(2);
+        p.ctr = b.take<unsigned long long>(3);  // next path, unexited, steps
         p.g = (dev && g_out) ? nullptr : b.take<double>((size_t)total);
         if (!dev) {
             p.x = b.take<double>((size_t)(2 * n_obs));
@@ -541,7 +524,8 @@ int pm_forward_dirichlet(pm_ctx* c, const pm_field* field, double drift_scale, d
         dxo = W.xo;
     }
     const std::vector<double> tab = stage_coefficients(field->K, field->u);
-    PM_CUDA(cudaMemsetAsync(W.ctr, 0, 16, c->stream), "clear counters");
+    PM_CUDA(cudaMemsetAsync(W.ctr, 0, 24, c->stream), "clear counters");
+    c->last_steps = -1;
 
     DirichletLaunch L{};
     L.coef = tab.data();
@@ -560,6 +544,7 @@ int pm_forward_dirichlet(pm_ctx* c, const pm_field* field, double drift_scale, d
     L.max_steps = max_steps;
     L.counter = W.ctr;
     L.n_unexited = W.ctr + 1;
+    L.steps = W.ctr + 2;
     L.g = dg;
     L.exit_step = des;
     L.x_out = dxo;
@@ -597,8 +582,11 @@ int pm_forward_dirichlet(pm_ctx* c, const pm_field* field, double drift_scale, d
         if (x_out) { PM_CUDA(cudaMemcpyAsync(h + o, dxo, (size_t)total * 16, cudaMemcpyDeviceToHost, c->stream), "copy x_out"); o += (size_t)total * 16; }
         if (exit_step) { PM_CUDA(cudaMemcpyAsync(h + o, des, (size_t)total * 4, cudaMemcpyDeviceToHost, c->stream), "copy exit steps"); }
     }
+    unsigned long long steps_taken = 0;
     PM_CUDA(cudaMemcpyAsync(&unexited, W.ctr + 1, 8, cudaMemcpyDeviceToHost, c->stream), "copy n_unexited");
+    PM_CUDA(cudaMemcpyAsync(&steps_taken, W.ctr + 2, 8, cudaMemcpyDeviceToHost, c->stream), "copy step count");
     PM_CUDA(cudaStreamSynchronize(c->stream), "dirichlet");
+    c->last_steps = (int64_t)steps_taken;
     if (!dev) {
         const char* h = (const char*)c->host;
         size_t o = 0;

@@ -106,10 +106,39 @@ __device__ __forceinline__ void fourier_powers(Real x, Real (&C)[K + 1], Real (&
     }
 }
 
-// P particles at once; `tab` yields coefficient t of the table (t a compile-time
-// index after unrolling, so a table in the kernel-parameter bank becomes an
-// FMA operand, and a table in shared memory becomes one broadcast load that
-// serves all P particles).
+template <typename Real>
+struct Quad { Real x, y, z, w; };
+
+// Coefficient sources.  `quad(i)` yields entries 4i .. 4i+3 of the table.
+// ParamTable: the table lives in the kernel-parameter bank; after unrolling
+// every index is a compile-time constant, so each coefficient becomes an FMA
+// operand and costs no instruction.
+template <typename Real, int K>
+struct ParamTable {
+    const FieldTable<Real, K>& f;
+    __device__ __forceinline__ Quad<Real> quad(int i) const
+    {
+        return Quad<Real>{f.c[4 * i], f.c[4 * i + 1], f.c[4 * i + 2], f.c[4 * i + 3]};
+    }
+};
+
+// SharedTable: the table lives in shared memory.  Each quad is one broadcast
+// 128-bit load, issued where it is used: the loads are volatile so that the
+// compiler cannot hoist all of them out of the path loop (which would need
+// one register per coefficient).
+struct SharedTable {
+    uint32_t base;  // shared-window address of entry 0 (16-byte aligned)
+    __device__ __forceinline__ Quad<float> quad(int i) const
+    {
+        Quad<float> q;
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(q.x), "=f"(q.y), "=f"(q.z), "=f"(q.w)
+                     : "r"(base + 16u * (uint32_t)i));
+        return q;
+    }
+};
+
+// P particles at once (each coefficient quad is fetched once and serves all P).
 template <typename Real, int K, int P, typename Tab>
 __device__ __forceinline__ void velocity(const Tab& tab, const Real (&x1)[P], const Real (&x2)[P],
                                          Real (&v1)[P], Real (&v2)[P])
@@ -125,9 +154,9 @@ __device__ __forceinline__ void velocity(const Tab& tab, const Real (&x1)[P], co
     // m = 0: only the v1 part (d1 of a function of x2 alone vanishes).
 #pragma unroll
     for (int n = 1; n <= K; ++n) {
-        const Real e0 = tab((0 * (K + 1) + n) * 8 + 0), e1 = tab((0 * (K + 1) + n) * 8 + 1);
+        const Quad<Real> E = tab.quad((0 * (K + 1) + n) * 2);
 #pragma unroll
-        for (int q = 0; q < P; ++q) v1[q] = fma_(e0, S2[q][n], fma_(e1, C2[q][n], v1[q]));
+        for (int q = 0; q < P; ++q) v1[q] = fma_(E.x, S2[q][n], fma_(E.y, C2[q][n], v1[q]));
     }
     Real C1m[P], S1m[P];
 #pragma unroll
@@ -135,6 +164,7 @@ __device__ __forceinline__ void velocity(const Tab& tab, const Real (&x1)[P], co
 #pragma unroll
     for (int m = 1; m <= K; ++m) {
         Real p1c[P], p1s[P], p2c[P], p2s[P];
+        const Quad<Real> F0 = tab.quad((m * (K + 1)) * 2 + 1);  // n = 0 column: f0 and f2
 #pragma unroll
         for (int q = 0; q < P; ++q) {
             const Real cn = C1m[q] * c1[q] - S1m[q] * s1[q];
@@ -143,20 +173,19 @@ __device__ __forceinline__ void velocity(const Tab& tab, const Real (&x1)[P], co
             // n = 0 column: C20 = 1, S20 = 0, and its v1 factor 2 pi n vanishes.
             p1c[q] = (Real)0;
             p1s[q] = (Real)0;
-            p2c[q] = tab((m * (K + 1)) * 8 + 4);
-            p2s[q] = tab((m * (K + 1)) * 8 + 6);
+            p2c[q] = F0.x;
+            p2s[q] = F0.z;
         }
 #pragma unroll
         for (int n = 1; n <= K; ++n) {
-            const int o = (m * (K + 1) + n) * 8;
-            const Real e0 = tab(o + 0), e1 = tab(o + 1), e2 = tab(o + 2), e3 = tab(o + 3);
-            const Real f0 = tab(o + 4), f1 = tab(o + 5), f2 = tab(o + 6), f3 = tab(o + 7);
+            const int o = (m * (K + 1) + n) * 2;
+            const Quad<Real> E = tab.quad(o), F = tab.quad(o + 1);
 #pragma unroll
             for (int q = 0; q < P; ++q) {
-                p1c[q] = fma_(e0, S2[q][n], fma_(e1, C2[q][n], p1c[q]));
-                p1s[q] = fma_(e2, S2[q][n], fma_(e3, C2[q][n], p1s[q]));
-                p2c[q] = fma_(f0, C2[q][n], fma_(f1, S2[q][n], p2c[q]));
-                p2s[q] = fma_(f2, C2[q][n], fma_(f3, S2[q][n], p2s[q]));
+                p1c[q] = fma_(E.x, S2[q][n], fma_(E.y, C2[q][n], p1c[q]));
+                p1s[q] = fma_(E.z, S2[q][n], fma_(E.w, C2[q][n], p1s[q]));
+                p2c[q] = fma_(F.x, C2[q][n], fma_(F.y, S2[q][n], p2c[q]));
+                p2s[q] = fma_(F.z, C2[q][n], fma_(F.w, S2[q][n], p2s[q]));
             }
         }
 #pragma unroll

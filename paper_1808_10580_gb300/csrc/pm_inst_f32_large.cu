@@ -1,5 +1,7 @@
 // Instantiations of the particle kernels: float paths, K in {12 16}.
-#include "pm_kernels.cuh"
+#include "pm_batched.cuh"
 
 PM_INSTANTIATE(float, 12)
 PM_INSTANTIATE(float, 16)
+PM_INSTANTIATE_BATCHED(12)
+PM_INSTANTIATE_BATCHED(16)

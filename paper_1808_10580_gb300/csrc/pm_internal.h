@@ -1,0 +1,67 @@
+// pm_internal.h -- the context object and host helpers shared by the C-ABI
+// translation units (pm_api.cu, pm_batched_api.cu).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <initializer_list>
+
+#include <cuda_runtime.h>
+
+#include "../../include/pm.h"
+
+struct pm_ctx {
+    int device = 0;
+    int sm_count = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void* ws = nullptr;      // device workspace (grows)
+    size_t ws_size = 0;
+    void* host = nullptr;    // pinned staging (grows)
+    size_t host_size = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool timing = false;
+    bool timed = false;
+    int64_t launches = 0;
+    int64_t last_steps = -1;     // Euler steps of the last synchronous forward call
+    // Batched map: the last captured CUDA graph and the key of the call shape it serves.
+    uint64_t graph_key = 0;
+    cudaGraphExec_t graph_exec = nullptr;
+    int64_t graph_launches = 0;  // kernels per replay
+    int graph_mode = 1;          // 1: capture and replay when the stream allows it
+};
+
+namespace pm {
+
+// Bump allocator over the workspace (256-byte aligned slices); a null base only measures.
+struct Bump {
+    char* base;
+    size_t off = 0;
+    explicit Bump(void* b) : base((char*)b) {}
+    template <typename T> T* take(size_t count)
+    {
+        off = (off + 255) & ~(size_t)255;
+        T* p = (T*)(base ? base + off : nullptr);
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+int fail(int code, const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+bool supported_K(int K);
+bool finite_array(const double* p, int64_t n);
+bool is_device_pointer(const void* p);
+int ensure_workspace(pm_ctx* c, size_t bytes);
+int ensure_host(pm_ctx* c, size_t bytes);
+int set_device(pm_ctx* c);
+int check_field(const pm_field* f);
+int check_ptrs(uint32_t flags, std::initializer_list<const void*> ptrs);
+void count_launch(pm_ctx* c, int n = 1);
+
+}  // namespace pm
+
+#define PM_CUDA(call, what)                                    \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return pm::cuda_fail(e_, what); \
+    } while (0)

@@ -7,15 +7,6 @@
 
 namespace pm {
 
-template <typename Real>
-struct Theta0Table {
-    int32_t n;
-    int32_t k1[kMaxTheta0];
-    int32_t k2[kMaxTheta0];
-    Real a[kMaxTheta0];
-    Real b[kMaxTheta0];
-};
-
 // Launch parameters travel in the kernel-parameter constant bank: the
 // velocity table is read as FMA operands at compile-time offsets, and every
 // launch carries its own copy (no shared constant symbol, so concurrent calls
@@ -113,7 +104,7 @@ __global__ void __launch_bounds__(BLOCK) timedep_kernel(const __grid_constant__ 
         const uint32_t pid = (uint32_t)(p.path_offset + i);
         const int N = o.nsteps;
         const Real h_last = (Real)o.h_last, s_last = (Real)o.s_last;
-        auto tab = [&](int t) { return p.field.c[t]; };
+        const ParamTable<Real, K> tab{p.field};
         for (int n = 0; n < N; n += 2) {
             const u32x4 r = philox4x32_10(u32x4{(uint32_t)(n >> 1), pid, (uint32_t)j, p.inst}, p.key0, p.key1);
             // One copy of the step body (kept rolled): the unrolled velocity sum is
@@ -198,6 +189,7 @@ struct DirichletParams {
     int64_t n_obs, M, total, max_steps, path_offset;
     unsigned long long* counter;
     unsigned long long* n_unexited;
+    unsigned long long* steps;   // total Euler steps taken (all paths)
     double* g;
     int32_t* exit_step;
     double* x_out;
@@ -236,11 +228,12 @@ __global__ void __launch_bounds__(kDirichletBlock) dirichlet_kernel(const __grid
 {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    auto tab = [&](int t) { return p.field.c[t]; };
+    const ParamTable<Real, K> tab{p.field};
     int64_t pid = -1;  // current path (global index j*M + i), -1 = none
     bool done = false;
     int64_t n = 0;
     uint32_t j = 0, i = 0;
+    unsigned long long lane_steps = 0;
     Coord<Real> X1, X2;
     X1.set(0.0);
     X2.set(0.0);
@@ -286,11 +279,13 @@ __global__ void __launch_bounds__(kDirichletBlock) dirichlet_kernel(const __grid
             const bool exited = radial_excess(X1, X2, p.R2hi, p.R2lo) >= (Real)0;
             if (exited || n >= p.max_steps) {
                 dirichlet_finish(p, pid, exited, n, X1, X2);
+                lane_steps += (unsigned long long)n;
                 pid = -1;
                 break;
             }
         }
     }
+    if (lane_steps) atomicAdd(p.steps, lane_steps);
 }
 
 template <typename Real, int K>
@@ -320,6 +315,7 @@ cudaError_t launch_dirichlet(const DirichletLaunch& L, cudaStream_t stream)
     p.path_offset = L.path_offset;
     p.counter = L.counter;
     p.n_unexited = L.n_unexited;
+    p.steps = L.steps;
     p.g = L.g;
     p.exit_step = L.exit_step;
     p.x_out = L.x_out;
@@ -355,7 +351,7 @@ __global__ void __launch_bounds__(128) velocity_kernel(const __grid_constant__ V
 {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= p.n) return;
-    auto tab = [&](int t) { return p.field.c[t]; };
+    const ParamTable<Real, K> tab{p.field};
     Coord<Real> X1, X2;
     X1.set(p.x[2 * q]);
     X2.set(p.x[2 * q + 1]);

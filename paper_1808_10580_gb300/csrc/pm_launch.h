@@ -20,7 +20,7 @@ struct ObsRec {
 };
 
 // Sizes of the velocity coefficient table for wave-number bound K.
-inline constexpr int table_size(int K) { return (K + 1) * (K + 1) * 8; }
+__host__ __device__ inline constexpr int table_size(int K) { return (K + 1) * (K + 1) * 8; }
 
 struct TimedepLaunch {
     const double* coef;  // host: pre-scaled product-basis table, table_size(K) entries
@@ -52,6 +52,7 @@ struct DirichletLaunch {
     int64_t max_steps;
     unsigned long long* counter;     // device, zero on entry: next unclaimed path
     unsigned long long* n_unexited;  // device, zero on entry
+    unsigned long long* steps;       // device, zero on entry: total Euler steps
     double* g;                       // device [n_obs * M] per-path values
     int32_t* exit_step;              // device [n_obs * M] or nullptr
     double* x_out;                   // device [n_obs * M * 2] or nullptr
@@ -76,7 +77,8 @@ int set_error(int code, const char* msg);
 
 // Support kernels (pm_support.cu).
 cudaError_t launch_prep_timedep(const double* x, const double* t, int64_t n_obs, double dt, double kappa,
-                                ObsRec* rec, int32_t* order, unsigned int* err, cudaStream_t s);
+                                ObsRec* rec, int32_t* order, unsigned int* err, cudaStream_t s,
+                                unsigned long long* steps = nullptr, int64_t M = 0);
 cudaError_t launch_reduce(const double2* part, int64_t n_obs, int32_t chunks, int64_t M, double* mean,
                           double* var, cudaStream_t s);
 cudaError_t launch_reduce_paths(const double* g, int64_t n_obs, int64_t M, double* mean, double* var,
@@ -85,5 +87,68 @@ cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, int64_t
                           cudaStream_t s);
 cudaError_t launch_normals(uint64_t seed, uint32_t b, uint32_t j, uint32_t i, int64_t n0, int64_t count,
                            double* out, bool fp64, cudaStream_t s);
+
+}  // namespace pm
+
+namespace pm {
+
+// ---- batched forward map (pm_batched.cuh, pm_batched_support.cu) ----
+template <typename Real>
+struct Theta0Table {
+    int32_t n;
+    int32_t k1[kMaxTheta0];
+    int32_t k2[kMaxTheta0];
+    Real a[kMaxTheta0];
+    Real b[kMaxTheta0];
+};
+
+struct BatchInstDev {
+    const double* u;      // device coefficients [2|H_K|]
+    int32_t kind;         // 0 time-dependent, 1 Dirichlet
+    int32_t n_obs;
+    int64_t M;
+    int64_t row0;         // first row of the batch arrays
+    int64_t path_base;    // path (j, i) of the instance is g[path_base + j*M + i]
+    int64_t n_paths;      // n_obs * M
+    int64_t max_steps;
+    double dt, kappa, drift_scale;
+    uint32_t key0, key1;
+};
+
+struct RowRec {
+    double x1, x2;
+    double h_last, s_last;
+    int32_t nsteps;
+    int32_t pad;
+};
+
+struct BatchKernelParams {
+    Theta0Table<float> th;
+    double ga[kMaxBoundary];
+    double gb[kMaxBoundary];
+    double R, quad, f_const;
+    int32_t n_ang;
+    float R2hi, R2lo;
+    const BatchInstDev* inst;
+    const RowRec* rows;
+    const float* tables;               // [B][table_size(K)]
+    unsigned long long* next_path;     // [B] per-instance path counters (zero on entry)
+    unsigned long long* n_unexited;
+    unsigned long long* steps;         // total Euler steps taken (all paths)
+    double* g;                         // per-path values
+    int32_t B;
+};
+
+template <int K> cudaError_t launch_batched(const BatchKernelParams& p, int grid, cudaStream_t s);
+template <int K> int batched_blocks_per_sm();
+// Velocity tables of all instances on the device (Eq. v_expand, the same fold
+// as the host staging): tables[b][table_size(K)] from inst[b].u.
+cudaError_t launch_stage_tables(const BatchInstDev* inst, int B, int K, float* tables, cudaStream_t s);
+// Per-row records (start point, step count, last step) of every instance.
+cudaError_t launch_prep_rows(const BatchInstDev* inst, int B, int max_obs, const double* x, const double* t,
+                             RowRec* rows, unsigned* err, cudaStream_t s);
+// Per-row mean and variance from the per-path values.
+cudaError_t launch_reduce_rows(const BatchInstDev* inst, int B, int max_obs, const double* g, double* mean,
+                               double* var, cudaStream_t s);
 
 }  // namespace pm

@@ -14,7 +14,8 @@ namespace pm {
 // times and step counts beyond int32 in *err.
 // ---------------------------------------------------------------------------
 __global__ void prep_timedep_kernel(const double* __restrict__ x, const double* __restrict__ t, int64_t n_obs,
-                                    double dt, double kappa, ObsRec* __restrict__ rec, unsigned int* err)
+                                    double dt, double kappa, ObsRec* __restrict__ rec, unsigned int* err,
+                                    unsigned long long* step_count, int64_t M)
 {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n_obs) return;
@@ -37,6 +38,7 @@ __global__ void prep_timedep_kernel(const double* __restrict__ x, const double* 
         r.nsteps = N;
         r.h_last = N > 0 ? __dsub_rn(tj, __dmul_rn((double)(N - 1), dt)) : 0.0;
         r.s_last = sqrt(__dmul_rn(__dmul_rn(2.0, kappa), r.h_last));
+        if (step_count) atomicAdd(step_count, (unsigned long long)N * (unsigned long long)M);
     }
     rec[j] = r;
 }
@@ -65,10 +67,11 @@ __global__ void order_kernel(const ObsRec* __restrict__ rec, int64_t n_obs, int3
 }
 
 cudaError_t launch_prep_timedep(const double* x, const double* t, int64_t n_obs, double dt, double kappa,
-                                ObsRec* rec, int32_t* order, unsigned int* err, cudaStream_t s)
+                                ObsRec* rec, int32_t* order, unsigned int* err, cudaStream_t s,
+                                unsigned long long* steps, int64_t M)
 {
     const unsigned grid = (unsigned)((n_obs + 255) / 256);
-    prep_timedep_kernel<<<grid, 256, 0, s>>>(x, t, n_obs, dt, kappa, rec, err);
+    prep_timedep_kernel<<<grid, 256, 0, s>>>(x, t, n_obs, dt, kappa, rec, err, steps, M);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || order == nullptr) return e;
     order_kernel<<<grid, 256, 0, s>>>(rec, n_obs, order);

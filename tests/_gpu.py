@@ -6,6 +6,7 @@ import pytest
 torch = pytest.importorskip("torch")
 
 import paper_1808_10580_gb300 as pm  # noqa: E402
+from paper_1808_10580_gb300 import inputs  # noqa: E402
 
 
 def ctx():
@@ -86,3 +87,50 @@ def dirichlet(c, w, flags=pm.PM_FP32, M=None, obs=None, device=True, want_paths=
         out["steps"] = es.reshape(n, M)
         out["g"] = g.reshape(n, M)
     return out
+
+
+def batch_from_workloads(ws, device=True):
+    """pm.Batch over a list of workloads (time-dependent ones share theta0, Dirichlet
+    ones share the disk data), rows laid out in list order."""
+    xs, ts, inst = [], [], []
+    row = 0
+    th = disk = None
+    for w in ws:
+        n = len(w.x)
+        xs.append(w.x)
+        if isinstance(w, inputs.TimedepWorkload):
+            ts.append(w.t)
+            th = th or pm.Fourier(w.theta0.k, w.theta0.a, w.theta0.b)
+            inst.append(dict(kind=pm.PM_KIND_TIMEDEP, u=w.u, kappa=w.kappa, dt=w.dt, row0=row, n_obs=n, M=w.M,
+                             seed=w.seed))
+        else:
+            ts.append(np.zeros(n))
+            disk = disk or pm.DirichletData(w.g.R, w.g.quad, w.g.f_const, w.g.a, w.g.b)
+            inst.append(dict(kind=pm.PM_KIND_DIRICHLET, u=w.u, kappa=w.kappa, dt=w.dt, row0=row, n_obs=n, M=w.M,
+                             seed=w.seed, drift_scale=w.drift_scale, max_steps=w.max_steps))
+        row += n
+    x = np.ascontiguousarray(np.concatenate(xs))
+    t = np.ascontiguousarray(np.concatenate(ts))
+    if device:
+        x = torch.from_numpy(x).cuda()
+        t = torch.from_numpy(t).cuda()
+        for d in inst:
+            d["u"] = torch.from_numpy(np.ascontiguousarray(d["u"])).cuda()
+    K = ws[0].K
+    return pm.Batch(K, inst, x, t, th, disk), row
+
+
+def batched(c, ws, device=True):
+    b, n_rows = batch_from_workloads(ws, device)
+    if device:
+        mean = torch.empty(n_rows, dtype=torch.float64, device="cuda")
+        var = torch.empty_like(mean)
+        nu = torch.zeros(1, dtype=torch.int64, device="cuda")
+        rc = pm.pm_forward_batched(c, b, pm.PM_FP32, mean, var, nu)
+        torch.cuda.synchronize()
+        return rc, mean.cpu().numpy(), var.cpu().numpy(), int(nu.item())
+    mean = np.empty(n_rows)
+    var = np.empty(n_rows)
+    nu = np.zeros(1, dtype=np.int64)
+    rc = pm.pm_forward_batched(c, b, pm.PM_FP32, mean, var, nu)
+    return rc, mean, var, int(nu[0])
