@@ -232,6 +232,65 @@ int pm_forward_batched(pm_ctx* ctx, const pm_batch* batch, uint32_t flags, doubl
 int pm_set_graph_mode(pm_ctx* ctx, int on);
 
 /* ---------------------------------------------------------------------------
+ * Learned surrogate of the forward map (the paper has no learned component;
+ * this serves the delayed-acceptance pre-screen of pCN MCMC proposals).
+ *
+ * A 3-layer ReLU network u -> relu(W1 u + b1) -> relu(W2 h1 + b2) -> W3 h2 + b3
+ * with weights [out][in], trained on (u, G(u)) pairs by Adam on an FP32 master
+ * copy; every matrix product runs on the tensor cores (tcgen05, BF16 operands,
+ * FP32 accumulation in tensor memory).  Loss: sum (y - target)^2 / (2 B n_out).
+ * n_hidden must be a multiple of 128.  The network object lives on the
+ * context's device; use it with one context at a time.
+ * ------------------------------------------------------------------------- */
+typedef struct pm_mlp pm_mlp;
+
+typedef struct pm_train_opts {
+    int32_t epochs;         /* passes over the data, >= 1 */
+    int32_t batch;          /* rows per Adam step, >= 1 */
+    float lr;               /* Adam step size */
+    float beta1, beta2;     /* moment decays in [0, 1) */
+    float eps;              /* > 0 */
+    uint64_t shuffle_seed;  /* seed of the per-epoch row shuffle */
+} pm_train_opts;
+
+/* Creates a network with seeded He-normal weights and zero biases. */
+int pm_surrogate_create(pm_ctx* ctx, pm_mlp** out, int32_t n_in, int32_t n_hidden, int32_t n_out, uint64_t seed);
+void pm_surrogate_destroy(pm_mlp* net);
+
+/* Host FP32 parameters, row-major [out][in]: W1 [n_hidden][n_in], b1 [n_hidden],
+ * W2 [n_hidden][n_hidden], b2, W3 [n_out][n_hidden], b3 [n_out].  Setting
+ * them resets the Adam state. */
+int pm_surrogate_set_params(pm_ctx* ctx, pm_mlp* net, const float* W1, const float* b1, const float* W2,
+                            const float* b2, const float* W3, const float* b3);
+int pm_surrogate_get_params(pm_ctx* ctx, const pm_mlp* net, float* W1, float* b1, float* W2, float* b2,
+                            float* W3, float* b3);
+
+/* One forward and backward pass on host arrays U [B][n_in], T [B][n_out]
+ * without an update: the loss and the gradients (host, same layouts as the
+ * parameters; any output may be NULL). */
+int pm_surrogate_gradients(pm_ctx* ctx, pm_mlp* net, const float* U, const float* T, int64_t B, float* loss,
+                           float* gW1, float* gb1, float* gW2, float* gb2, float* gW3, float* gb3);
+
+/* Adam training on U [N][n_in], Y [N][n_out] (device pointers with
+ * PM_DEVICE_PTRS); loss_history [epochs] receives each epoch's mean batch loss
+ * (or NULL). */
+int pm_surrogate_train(pm_ctx* ctx, pm_mlp* net, const float* U, const float* Y, int64_t N,
+                       const pm_train_opts* opts, uint32_t flags, float* loss_history);
+
+/* Y [B][n_out] = net(U [B][n_in]); pointers follow PM_DEVICE_PTRS. */
+int pm_surrogate_infer(pm_ctx* ctx, const pm_mlp* net, const float* U, int64_t B, float* Y, uint32_t flags);
+
+/* Parameters and Adam state to / from a binary file. */
+int pm_surrogate_save(pm_ctx* ctx, const pm_mlp* net, const char* path);
+int pm_surrogate_load(pm_ctx* ctx, pm_mlp** out, const char* path);
+
+/* Diagnostic: C[M][ldc] (FP32) = A[M][K] . B[N][K]^T for BF16 A (row pitch
+ * lda) and B (row pitch ldb), all device pointers, on the tensor-core GEMM
+ * the surrogate uses.  M % 128 == 0, N % 64 == 0, K % 64 == 0. */
+int pm_gemm_bf16(pm_ctx* ctx, const void* A, int32_t lda, const void* B, int32_t ldb, int32_t M, int32_t N,
+                 int32_t K, float* C, int32_t ldc);
+
+/* ---------------------------------------------------------------------------
  * Allocation-free variant (the paper has no counterpart; this is a library
  * convenience).
  *

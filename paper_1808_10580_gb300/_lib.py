@@ -301,3 +301,102 @@ def pm_forward_batched(ctx, batch: Batch, flags, mean, var=None, n_unexited=None
 
 def pm_set_graph_mode(ctx, on):
     return _check(load().pm_set_graph_mode(ctx, int(bool(on))))
+
+
+class pm_train_opts(C.Structure):
+    _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_float), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("eps", C.c_float), ("shuffle_seed", C.c_uint64)]
+
+
+def _declare_surrogate(L):
+    vp, i32, i64, u32 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32
+    L.pm_surrogate_create.argtypes = [vp, C.POINTER(vp), i32, i32, i32, C.c_uint64]
+    L.pm_surrogate_destroy.argtypes = [vp]
+    L.pm_surrogate_destroy.restype = None
+    L.pm_surrogate_set_params.argtypes = [vp, vp] + [vp] * 6
+    L.pm_surrogate_get_params.argtypes = [vp, vp] + [vp] * 6
+    L.pm_surrogate_gradients.argtypes = [vp, vp, vp, vp, i64, vp] + [vp] * 6
+    L.pm_surrogate_train.argtypes = [vp, vp, vp, vp, i64, C.POINTER(pm_train_opts), u32, vp]
+    L.pm_surrogate_infer.argtypes = [vp, vp, vp, i64, vp, u32]
+    L.pm_surrogate_save.argtypes = [vp, vp, C.c_char_p]
+    L.pm_surrogate_load.argtypes = [vp, C.POINTER(vp), C.c_char_p]
+    L.pm_gemm_bf16.argtypes = [vp, vp, i32, vp, i32, i32, i32, i32, vp, i32]
+
+
+def _slib():
+    L = load()
+    if not getattr(L, "_surrogate_declared", False):
+        _declare_surrogate(L)
+        L._surrogate_declared = True
+    return L
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def pm_surrogate_create(ctx, n_in, n_hidden, n_out, seed=0):
+    h = C.c_void_p()
+    _check(_slib().pm_surrogate_create(ctx, C.byref(h), int(n_in), int(n_hidden), int(n_out), int(seed)))
+    return h
+
+
+def pm_surrogate_destroy(net):
+    _slib().pm_surrogate_destroy(net)
+
+
+def pm_surrogate_set_params(ctx, net, W1, b1, W2, b2, W3, b3):
+    arrs = [_f32(a) for a in (W1, b1, W2, b2, W3, b3)]
+    return _check(_slib().pm_surrogate_set_params(ctx, net, *[a.ctypes.data for a in arrs]))
+
+
+def pm_surrogate_get_params(ctx, net, n_in, n_hidden, n_out):
+    out = [np.empty((n_hidden, n_in), np.float32), np.empty(n_hidden, np.float32),
+           np.empty((n_hidden, n_hidden), np.float32), np.empty(n_hidden, np.float32),
+           np.empty((n_out, n_hidden), np.float32), np.empty(n_out, np.float32)]
+    _check(_slib().pm_surrogate_get_params(ctx, net, *[a.ctypes.data for a in out]))
+    return out
+
+
+def pm_surrogate_gradients(ctx, net, U, T, n_in, n_hidden, n_out):
+    U, T = _f32(U), _f32(T)
+    loss = np.zeros(1, np.float32)
+    out = [np.empty((n_hidden, n_in), np.float32), np.empty(n_hidden, np.float32),
+           np.empty((n_hidden, n_hidden), np.float32), np.empty(n_hidden, np.float32),
+           np.empty((n_out, n_hidden), np.float32), np.empty(n_out, np.float32)]
+    _check(_slib().pm_surrogate_gradients(ctx, net, U.ctypes.data, T.ctypes.data, U.shape[0], loss.ctypes.data,
+                                          *[a.ctypes.data for a in out]))
+    return float(loss[0]), out
+
+
+def pm_surrogate_train(ctx, net, U, Y, epochs, batch, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, shuffle_seed=0):
+    dev = _device(U, Y)
+    if not dev:
+        U, Y = _f32(U), _f32(Y)
+    N = U.shape[0]
+    o = pm_train_opts(int(epochs), int(batch), float(lr), float(beta1), float(beta2), float(eps), int(shuffle_seed))
+    hist = np.zeros(int(epochs), np.float32)
+    _check(_slib().pm_surrogate_train(ctx, net, _ptr(U), _ptr(Y), int(N), C.byref(o),
+                                      PM_DEVICE_PTRS if dev else 0, hist.ctypes.data))
+    return hist
+
+
+def pm_surrogate_infer(ctx, net, U, Y, flags=0):
+    if _device(U, Y):
+        flags |= PM_DEVICE_PTRS
+    return _check(_slib().pm_surrogate_infer(ctx, net, _ptr(U), int(U.shape[0]), _ptr(Y), int(flags)))
+
+
+def pm_surrogate_save(ctx, net, path):
+    return _check(_slib().pm_surrogate_save(ctx, net, str(path).encode()))
+
+
+def pm_surrogate_load(ctx, path):
+    h = C.c_void_p()
+    _check(_slib().pm_surrogate_load(ctx, C.byref(h), str(path).encode()))
+    return h
+
+
+def pm_gemm_bf16(ctx, A, lda, B, ldb, M, N, K, C_out, ldc):
+    return _check(_slib().pm_gemm_bf16(ctx, _ptr(A), int(lda), _ptr(B), int(ldb), int(M), int(N), int(K),
+                                       _ptr(C_out), int(ldc)))

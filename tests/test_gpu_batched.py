@@ -23,9 +23,9 @@ def small_instances(B=6, M=256):
     ws = inputs.batched_instances(B=B, M=M)
     for w in ws:
         if isinstance(w, inputs.DirichletWorkload):
-            w.x = w.x[:20]
+            w.x = w.x[:20].copy()
         else:
-            w.x, w.t = w.x[::5], w.t[::5]
+            w.x, w.t = w.x[::5].copy(), w.t[::5].copy()
     return ws
 
 
