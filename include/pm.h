@@ -179,10 +179,12 @@ int pm_forward_dirichlet(pm_ctx* ctx, const pm_field* field, double drift_scale,
  * (time-dependent instances) and the disk data (Dirichlet instances).  The
  * observations of instance b are rows [row0, row0 + n_obs) of the batch's x
  * (and t); the rows of all instances must tile [0, n_rows) without overlap.
- * The RNG counter of instance b uses b as its instance word and the row's
- * offset j within the instance, so an instance gives the same estimate as
- * pm_forward_timedep / pm_forward_dirichlet with opts->instance = b and the
- * same seed (up to the float rounding of the coefficient table).
+ * The RNG counter of an instance uses its `stream` as the instance word and
+ * the row's offset j within the instance, so an instance gives the same
+ * estimate as pm_forward_timedep / pm_forward_dirichlet with opts->instance =
+ * stream and the same seed.  Giving several instances the same stream and
+ * seed makes them share their Brownian increments (common random numbers:
+ * the estimate is then a deterministic function of u alone).
  * Section 3.3 makes every path independent: one persistent kernel runs all
  * paths of all instances; each lane takes a new path of its warp's instance
  * as soon as its path ends, and warps move between instances as these run
@@ -198,7 +200,7 @@ int pm_forward_dirichlet(pm_ctx* ctx, const pm_field* field, double drift_scale,
 
 typedef struct pm_instance {
     int32_t kind;          /* PM_KIND_TIMEDEP or PM_KIND_DIRICHLET */
-    int32_t reserved;
+    uint32_t stream;       /* RNG instance word b of the counter {n/2, i, j, b} */
     const double* u;       /* 2|H_K| coefficients; host, or device with PM_DEVICE_PTRS */
     double kappa;          /* >= 0 */
     double dt;             /* > 0 */

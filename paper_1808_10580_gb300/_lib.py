@@ -58,7 +58,7 @@ PM_KIND_DIRICHLET = 1
 
 
 class pm_instance(C.Structure):
-    _fields_ = [("kind", C.c_int32), ("reserved", C.c_int32), ("u", C.c_void_p), ("kappa", C.c_double),
+    _fields_ = [("kind", C.c_int32), ("stream", C.c_uint32), ("u", C.c_void_p), ("kappa", C.c_double),
                 ("dt", C.c_double), ("drift_scale", C.c_double), ("max_steps", C.c_int64), ("row0", C.c_int64),
                 ("n_obs", C.c_int64), ("M", C.c_int64), ("seed", C.c_uint64)]
 
@@ -272,7 +272,8 @@ def pm_forward_timedep_noalloc(field: Field, kappa, theta0: Fourier, x, t, n_obs
 class Batch:
     """Keeps the arrays of a pm_batch alive.  ``instances`` is a list of dicts with
     keys kind, u, kappa, dt, row0, n_obs, M, seed (and drift_scale, max_steps for
-    Dirichlet instances); u may be numpy (host) or CUDA tensors (device)."""
+    Dirichlet instances; stream, default the instance's position); u may be numpy
+    (host) or CUDA tensors (device)."""
 
     def __init__(self, K, instances, x, t, theta0: Fourier = None, disk: DirichletData = None):
         self.keep = [x, t, theta0, disk]
@@ -282,7 +283,7 @@ class Batch:
             if not _is_torch(u):
                 u = np.ascontiguousarray(u, dtype=np.float64)
             self.keep.append(u)
-            arr[q] = pm_instance(int(d["kind"]), 0, _ptr(u), float(d["kappa"]), float(d["dt"]),
+            arr[q] = pm_instance(int(d["kind"]), int(d.get("stream", q)), _ptr(u), float(d["kappa"]), float(d["dt"]),
                                  float(d.get("drift_scale", 1.0)), int(d.get("max_steps", 0)), int(d["row0"]),
                                  int(d["n_obs"]), int(d["M"]), int(d["seed"]))
         self.arr = arr

@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(kBatchWarps * 32) batched_kernel(const __grid_
         if (pid < 0) continue;
 
         // ---- two Euler steps per Philox call ----------------------------------
-        const u32x4 r = philox4x32_10(u32x4{(uint32_t)(n >> 1), i, j, (uint32_t)b}, I.key0, I.key1);
+        const u32x4 r = philox4x32_10(u32x4{(uint32_t)(n >> 1), i, j, I.stream}, I.key0, I.key1);
 #pragma unroll 1
         for (int half = 0; half < 2; ++half) {
             float xi1, xi2;

@@ -192,6 +192,7 @@ extern "C" int pm_forward_batched(pm_ctx* c, const pm_batch* bt, uint32_t flags,
         d.drift_scale = I.kind == PM_KIND_DIRICHLET ? I.drift_scale : 1.0;
         d.key0 = (uint32_t)(I.seed & 0xffffffffu);
         d.key1 = (uint32_t)(I.seed >> 32);
+        d.stream = I.stream;
         Hs.inst[b] = d;
         if (!dev && NU > 0) memcpy(Hs.U + (size_t)b * NU, I.u, (size_t)NU * 8);
     }

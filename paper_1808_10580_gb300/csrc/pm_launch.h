@@ -113,6 +113,8 @@ struct BatchInstDev {
     int64_t max_steps;
     double dt, kappa, drift_scale;
     uint32_t key0, key1;
+    uint32_t stream;      // RNG instance word
+    uint32_t pad;
 };
 
 struct RowRec {

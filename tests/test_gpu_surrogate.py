@@ -79,10 +79,36 @@ def test_gradients_match_oracle(c):
     Y, cache = mlp.forward(P, U.astype(np.float64))
     ref = mlp.backward(P, cache, mlp.loss_grad(Y, T.astype(np.float64)))
     assert abs(loss - mlp.loss(Y, T)) <= 1e-2 * mlp.loss(Y, T)
+    # (1) Against the FP64 oracle.  The GPU stores activations and backward
+    # signals in BF16; a few pre-activations near 0 then change sign (ReLU mask
+    # flips), which moves the deeper gradients by a few percent: agreement in
+    # direction (cosine) and to 5 % in norm.
     for name, got in zip(("W1", "b1", "W2", "b2", "W3", "b3"), g):
-        assert rel(got, ref[name]) <= 2e-2, name
+        assert rel(got, ref[name]) <= 5e-2, name
         assert cosine(got.ravel(), ref[name].ravel()) >= 0.999, name
+    # (2) Against the oracle's own formulas with the GPU's storage roundings
+    # applied (BF16 after every layer and every backward signal, FP32 targets):
+    # the same algorithm, so agreement to FP32 accumulation order.
+    emu = bf16_step(P, U.astype(np.float64), T.astype(np.float64))
+    for name, got in zip(("W1", "b1", "W2", "b2", "W3", "b3"), g):
+        assert rel(got, emu[name]) <= 2e-3, name
     pm.pm_surrogate_destroy(net)
+
+
+def bf16_step(P, U, T):
+    """The oracle network's gradients (oracle/mlp.py formulas) with each stored
+    intermediate rounded to BF16 as the GPU kernels store them."""
+    H1 = bf16_round(np.maximum(U @ P["W1"].T + P["b1"], 0)).astype(np.float64)
+    H2 = bf16_round(np.maximum(H1 @ P["W2"].T + P["b2"], 0)).astype(np.float64)
+    Y = (H2 @ P["W3"].T + P["b3"]).astype(np.float32).astype(np.float64)
+    dYf = mlp.loss_grad(Y, T).astype(np.float32).astype(np.float64)
+    dY = bf16_round(dYf).astype(np.float64)
+    dH2f = (dY @ P["W3"]) * (H2 > 0)
+    dH2 = bf16_round(dH2f).astype(np.float64)
+    dH1f = (dH2 @ P["W2"]) * (H1 > 0)
+    dH1 = bf16_round(dH1f).astype(np.float64)
+    return {"W3": dY.T @ H2, "b3": dYf.sum(0), "W2": dH2.T @ H1, "b2": dH2f.sum(0), "W1": dH1.T @ U,
+            "b1": dH1f.sum(0)}
 
 
 def test_training_fits_a_smooth_map_and_saves(c, tmp_path):
