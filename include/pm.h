@@ -293,6 +293,63 @@ int pm_gemm_bf16(pm_ctx* ctx, const void* A, int32_t lda, const void* B, int32_t
                  int32_t K, float* C, int32_t ldc);
 
 /* ---------------------------------------------------------------------------
+ * pCN MCMC over the time-dependent map (Section 4.1: the paper samples its
+ * posteriors with preconditioned Crank-Nicolson), plain or with delayed
+ * acceptance (Christen & Fox 2005) through a surrogate network.
+ *
+ * Prior N(0, C) on the field coefficients with C = diag(|k_h|^-4); proposal
+ * u' = sqrt(1 - beta^2) u + beta C^{1/2} xi; Phi(u) = sum_j (y_j - G_j(u))^2 /
+ * (2 sigma^2).  Plain: accept with min(1, exp(Phi(u) - Phi(u'))).  Delayed
+ * acceptance: stage 1 with the surrogate's Phi~, stage 2 only for the stage-1
+ * survivors, accepting with min(1, exp(Phi(u) - Phi(u') - Phi~(u) + Phi~(u'))).
+ * G is the particle map of Algorithm 1 evaluated for all needed proposals in
+ * one batched launch with a single RNG stream and seed (so G is a
+ * deterministic function of u), or, for testing, a linear map A u.
+ * Randomness: proposal normals of chain c at step s from Philox counters
+ * {s, c, q, 0x4D43} (normals 4q..4q+3 from two Box-Muller pairs), stage-1 and
+ * stage-2 uniforms from {s, c, 0xFFFFFFFF, 1 or 2} (word 0), key = seed.
+ * Chain states, misfits and the running sum of states live on the device.
+ * ------------------------------------------------------------------------- */
+typedef struct pm_pcn pm_pcn;
+
+typedef struct pm_pcn_config {
+    int32_t n_chains;
+    int32_t K;                  /* field bound: n_u = (2K+1)^2 - 1 coefficients */
+    double beta;                /* pCN step in (0, 1] */
+    double sigma;               /* observation noise standard deviation */
+    uint64_t seed;              /* proposals and acceptance tests */
+    int64_t n_obs;
+    const double* y;            /* [n_obs] data (host) */
+    const double* A;            /* [n_obs][n_u] host: G(u) = A u (testing); NULL: particle map below */
+    double kappa, dt;           /* particle map: Algorithm 1 */
+    int64_t M;
+    uint64_t path_seed;
+    const pm_fourier* theta0;   /* host */
+    const double* x;            /* [n_obs][2] host */
+    const double* t;            /* [n_obs] host */
+} pm_pcn_config;
+
+typedef struct pm_pcn_stats {
+    int64_t steps;              /* pCN steps of every chain */
+    int64_t proposals;          /* steps x chains */
+    int64_t stage1_accepts;     /* proposals that passed the surrogate screen */
+    int64_t accepts;            /* accepted moves */
+    int64_t forward_evals;      /* particle-map evaluations (instances) */
+    double seconds;             /* device time of the run */
+} pm_pcn_stats;
+
+/* u0: [n_chains][n_u] host.  screen: NULL for plain pCN, else a surrogate
+ * with n_in = n_u and n_out = n_obs whose input is u * screen_scale
+ * (screen_scale [n_u] host, NULL = 1). */
+int pm_pcn_create(pm_ctx* ctx, pm_pcn** out, const pm_pcn_config* cfg, const double* u0, const pm_mlp* screen,
+                  const float* screen_scale);
+int pm_pcn_run(pm_ctx* ctx, pm_pcn* chains, int64_t n_steps, pm_pcn_stats* stats);
+/* Current states u [n_chains][n_u], misfits phi [n_chains], and the sum of all
+ * states visited so far sum_u [n_u] over n_summed = steps x chains (any may be NULL). */
+int pm_pcn_state(pm_ctx* ctx, const pm_pcn* chains, double* u, double* phi, double* sum_u, int64_t* n_summed);
+void pm_pcn_destroy(pm_pcn* chains);
+
+/* ---------------------------------------------------------------------------
  * Allocation-free variant (the paper has no counterpart; this is a library
  * convenience).
  *

@@ -401,3 +401,68 @@ def pm_surrogate_load(ctx, path):
 def pm_gemm_bf16(ctx, A, lda, B, ldb, M, N, K, C_out, ldc):
     return _check(_slib().pm_gemm_bf16(ctx, _ptr(A), int(lda), _ptr(B), int(ldb), int(M), int(N), int(K),
                                        _ptr(C_out), int(ldc)))
+
+
+class pm_pcn_config(C.Structure):
+    _fields_ = [("n_chains", C.c_int32), ("K", C.c_int32), ("beta", C.c_double), ("sigma", C.c_double),
+                ("seed", C.c_uint64), ("n_obs", C.c_int64), ("y", C.c_void_p), ("A", C.c_void_p),
+                ("kappa", C.c_double), ("dt", C.c_double), ("M", C.c_int64), ("path_seed", C.c_uint64),
+                ("theta0", C.POINTER(pm_fourier)), ("x", C.c_void_p), ("t", C.c_void_p)]
+
+
+class pm_pcn_stats(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("proposals", C.c_int64), ("stage1_accepts", C.c_int64),
+                ("accepts", C.c_int64), ("forward_evals", C.c_int64), ("seconds", C.c_double)]
+
+
+def _plib():
+    L = _slib()
+    if not getattr(L, "_pcn_declared", False):
+        vp = C.c_void_p
+        L.pm_pcn_create.argtypes = [vp, C.POINTER(vp), C.POINTER(pm_pcn_config), vp, vp, vp]
+        L.pm_pcn_run.argtypes = [vp, vp, C.c_int64, C.POINTER(pm_pcn_stats)]
+        L.pm_pcn_state.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.pm_pcn_destroy.argtypes = [vp]
+        L.pm_pcn_destroy.restype = None
+        L._pcn_declared = True
+    return L
+
+
+class PCN:
+    """pCN chains on the device (plain, or delayed acceptance when `screen` is given)."""
+
+    def __init__(self, ctx, K, u0, y, sigma, beta, seed, A=None, theta0: Fourier = None, x=None, t=None, kappa=0.0,
+                 dt=1e-3, M=1, path_seed=0, screen=None, screen_scale=None):
+        self.ctx = ctx
+        self.keep = [np.ascontiguousarray(y, dtype=np.float64), np.ascontiguousarray(u0, dtype=np.float64)]
+        self.C, self.n_u = self.keep[1].shape
+        A_ = np.ascontiguousarray(A, dtype=np.float64) if A is not None else None
+        x_ = np.ascontiguousarray(x, dtype=np.float64) if x is not None else None
+        t_ = np.ascontiguousarray(t, dtype=np.float64) if t is not None else None
+        sc = _f32(screen_scale) if screen_scale is not None else None
+        self.keep += [A_, x_, t_, sc, theta0]
+        cfg = pm_pcn_config(self.C, int(K), float(beta), float(sigma), int(seed), len(self.keep[0]),
+                            self.keep[0].ctypes.data, A_.ctypes.data if A_ is not None else None, float(kappa),
+                            float(dt), int(M), int(path_seed), C.pointer(theta0.s) if theta0 is not None else None,
+                            x_.ctypes.data if x_ is not None else None, t_.ctypes.data if t_ is not None else None)
+        self.h = C.c_void_p()
+        _check(_plib().pm_pcn_create(ctx, C.byref(self.h), C.byref(cfg), self.keep[1].ctypes.data, screen,
+                                     sc.ctypes.data if sc is not None else None))
+
+    def run(self, n_steps):
+        st = pm_pcn_stats()
+        _check(_plib().pm_pcn_run(self.ctx, self.h, int(n_steps), C.byref(st)))
+        return {k: getattr(st, k) for k, _ in pm_pcn_stats._fields_}
+
+    def state(self):
+        u = np.empty((self.C, self.n_u))
+        phi = np.empty(self.C)
+        s = np.empty(self.n_u)
+        n = C.c_int64()
+        _check(_plib().pm_pcn_state(self.ctx, self.h, u.ctypes.data, phi.ctypes.data, s.ctypes.data, C.byref(n)))
+        return u, phi, s, n.value
+
+    def close(self):
+        if self.h:
+            _plib().pm_pcn_destroy(self.h)
+            self.h = None

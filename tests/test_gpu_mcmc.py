@@ -1,0 +1,86 @@
+"""GPU pCN chains against the oracle sampler: step-by-step on a linear forward
+map, the posterior of delayed acceptance, and a short run over the particle map."""
+import numpy as np
+import pytest
+
+from oracle import mcmc
+from paper_1808_10580_gb300 import inputs
+from tests import _gpu
+
+pytestmark = pytest.mark.gpu
+pm = _gpu.pm
+torch = _gpu.torch
+
+
+@pytest.fixture(scope="module")
+def c():
+    h, s = _gpu.side_stream_ctx()
+    with torch.cuda.stream(s):
+        yield h
+    pm.pm_destroy(h)
+
+
+def toy(sigma=0.5, seed=0, n_obs=6, K=1):
+    std = mcmc.prior_std(K)
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((n_obs, len(std)))
+    y = A @ (std * rng.standard_normal(len(std))) + sigma * rng.standard_normal(n_obs)
+    return A, y, sigma, std
+
+
+def test_plain_chain_matches_oracle_step_by_step(c):
+    A, y, sigma, std = toy()
+    u0 = np.zeros((8, len(std)))
+    ch = pm.PCN(c, 1, u0, y, sigma, 0.3, seed=123, A=A)
+    st = ch.run(300)
+    U, phi, s, n = ch.state()
+    ch.close()
+    U_or, total, ost = mcmc.run(u0, lambda u: A @ u, y, sigma, 0.3, std, 300, seed=123)
+    assert st["accepts"] == ost["accepts"] and st["forward_evals"] == 8 * 300
+    assert np.abs(U - U_or).max() <= 1e-12
+    assert np.abs(s - total).max() <= 1e-10 * max(1.0, np.abs(total).max())
+    assert n == 8 * 300
+
+
+def test_delayed_acceptance_reaches_linear_posterior(c):
+    A, y, sigma, std = toy()
+    m, S = mcmc.linear_gaussian_posterior(A, y, sigma, std)
+    # a screen trained briefly on prior draws: close to, not equal to, A u
+    rng = np.random.default_rng(4)
+    Z = rng.standard_normal((4096, len(std)))
+    net = pm.pm_surrogate_create(c, len(std), 128, len(y), 9)
+    pm.pm_surrogate_train(c, net, Z.astype(np.float32), ((Z * std) @ A.T).astype(np.float32), epochs=40, batch=256,
+                          lr=3e-3)
+    ch = pm.PCN(c, 1, np.zeros((8, len(std))), y, sigma, 0.3, seed=77, A=A, screen=net, screen_scale=1.0 / std)
+    st = ch.run(6000)
+    U, phi, s, n = ch.state()
+    ch.close()
+    pm.pm_surrogate_destroy(net)
+    est = s / n
+    assert np.all(np.abs(est - m) <= 0.15 * np.sqrt(np.diag(S))), (est, m)
+    assert st["forward_evals"] == st["stage1_accepts"] < st["proposals"]
+    assert st["accepts"] <= st["stage1_accepts"]
+
+
+def test_particle_map_chains_run_and_screen_saves_evaluations(c):
+    w = inputs.plain_fp64_k2()
+    w.M = 256
+    # data from a prior draw through the particle map itself (same stream and seed)
+    u_true = inputs.prior_field(2, 55)
+    th = pm.Fourier(w.theta0.k, w.theta0.a, w.theta0.b)
+    y = np.empty(len(w.t))
+    pm.pm_forward_timedep(c, pm.Field(2, u_true), w.kappa, th, w.x, w.t, len(w.t), w.M, w.dt, 999, pm.PM_FP32, y)
+    kw = dict(theta0=th, x=w.x, t=w.t, kappa=w.kappa, dt=w.dt, M=w.M, path_seed=999)
+    std = mcmc.prior_std(2)
+    u0 = np.zeros((4, 24))
+    plain = pm.PCN(c, 2, u0, y, 0.05, 0.2, seed=5, **kw)
+    sp = plain.run(20)
+    _, phi_p, _, _ = plain.state()
+    plain.close()
+    assert sp["forward_evals"] == 80 and np.all(np.isfinite(phi_p))
+    net = pm.pm_surrogate_create(c, 24, 128, len(y), 2)     # untrained: a poor but valid screen
+    da = pm.PCN(c, 2, u0, y, 0.05, 0.2, seed=5, screen=net, screen_scale=1.0 / std, **kw)
+    sd = da.run(20)
+    da.close()
+    pm.pm_surrogate_destroy(net)
+    assert sd["forward_evals"] == sd["stage1_accepts"] <= sd["proposals"] == 80
