@@ -392,6 +392,43 @@ def run_aux(args):
     return 0
 
 
+def run_mcmc(args):
+    """Surrogate-screened pCN against plain pCN on the same GPU (auxiliary line):
+    64 chains started near the data-generating field, the same beta for both."""
+    import torch
+
+    import paper_1808_10580_gb300 as pm
+    from paper_1808_10580_gb300 import surrogate_mcmc as sm
+
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = pm.pm_create(0, stream.cuda_stream)
+    t0 = time.perf_counter()
+    prob = sm.make_data(ctx, sm.make_problem())
+    Z, G = sm.training_pairs(ctx, prob, args.train_pairs)
+    t_pairs = time.perf_counter() - t0
+    Zv, Gv = sm.training_pairs(ctx, prob, 1024, seed=7005)
+    t1 = time.perf_counter()
+    net, hist = sm.train_surrogate(ctx, prob, Z, G)
+    t_train = time.perf_counter() - t1
+    rmse = sm.surrogate_rmse(ctx, net, Zv, Gv)
+    u0 = sm.start_states(prob, 64, spread=0.0)
+    plain, _ = sm.run_chains(ctx, prob, u0, args.beta, args.plain_steps, seed=11)
+    da, _ = sm.run_chains(ctx, prob, u0, args.beta, args.da_steps, seed=11, net=net)
+    pm.pm_surrogate_destroy(net)
+    pm.pm_destroy(ctx)
+    line = {"metric": "accepted pCN proposals/s (64 chains)", "auxiliary": True, "data": "synthetic",
+            "value": da["accepted_per_s"], "unit": "accepted proposals/s",
+            "ratio_vs_plain": da["accepted_per_s"] / max(plain["accepted_per_s"], 1e-30),
+            "config": {"train_pairs": args.train_pairs, "M": prob.M, "n_obs": len(prob.t), "sigma": prob.sigma,
+                       "beta": args.beta, "chains": 64, "start": "data-generating field"},
+            "plain": plain, "delayed_acceptance": da,
+            "surrogate": {"val_rmse": rmse, "final_train_loss": float(hist[-1]), "train_seconds": t_train,
+                          "pair_generation_seconds": t_pairs}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -401,14 +438,20 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--M", type=int, default=0, help="particles per observation (default: the workload's own; "
                     "smaller values are for profiling captures only)")
-    ap.add_argument("--workload", default="timedep", choices=["timedep", "dirichlet", "batched"],
-                    help="timedep: the headline line; dirichlet / batched: auxiliary measurements")
+    ap.add_argument("--workload", default="timedep", choices=["timedep", "dirichlet", "batched", "mcmc"],
+                    help="timedep: the headline line; dirichlet / batched / mcmc: auxiliary measurements")
+    ap.add_argument("--train-pairs", type=int, default=1 << 16, help="mcmc: surrogate training pairs")
+    ap.add_argument("--beta", type=float, default=0.02, help="mcmc: pCN step, the same for both samplers")
+    ap.add_argument("--plain-steps", type=int, default=8, help="mcmc: steps of the plain sampler")
+    ap.add_argument("--da-steps", type=int, default=200, help="mcmc: steps of the delayed-acceptance sampler")
     ap.add_argument("--B", type=int, default=256, help="instances of the batched workload")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "mcmc":
+        return run_mcmc(args)
     if args.workload != "timedep":
         return run_aux(args)
     return run_gpu(args)
