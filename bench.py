@@ -404,12 +404,12 @@ def run_mcmc(args):
     torch.cuda.set_stream(stream)
     ctx = pm.pm_create(0, stream.cuda_stream)
     t0 = time.perf_counter()
-    prob = sm.make_data(ctx, sm.make_problem())
+    prob = sm.make_data(ctx, sm.make_problem(sigma=args.sigma))
     Z, G = sm.training_pairs(ctx, prob, args.train_pairs)
     t_pairs = time.perf_counter() - t0
     Zv, Gv = sm.training_pairs(ctx, prob, 1024, seed=7005)
     t1 = time.perf_counter()
-    net, hist = sm.train_surrogate(ctx, prob, Z, G)
+    net, hist = sm.train_surrogate(ctx, prob, Z, G, epochs=args.epochs)
     t_train = time.perf_counter() - t1
     rmse = sm.surrogate_rmse(ctx, net, Zv, Gv)
     u0 = sm.start_states(prob, 64, spread=0.0)
@@ -442,6 +442,8 @@ def main():
                     help="timedep: the headline line; dirichlet / batched / mcmc: auxiliary measurements")
     ap.add_argument("--train-pairs", type=int, default=1 << 16, help="mcmc: surrogate training pairs")
     ap.add_argument("--beta", type=float, default=0.02, help="mcmc: pCN step, the same for both samplers")
+    ap.add_argument("--sigma", type=float, default=0.01, help="mcmc: observation noise standard deviation")
+    ap.add_argument("--epochs", type=int, default=100, help="mcmc: surrogate training epochs")
     ap.add_argument("--plain-steps", type=int, default=8, help="mcmc: steps of the plain sampler")
     ap.add_argument("--da-steps", type=int, default=200, help="mcmc: steps of the delayed-acceptance sampler")
     ap.add_argument("--B", type=int, default=256, help="instances of the batched workload")

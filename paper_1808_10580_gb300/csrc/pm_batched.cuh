@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(kBatchWarps * 32) batched_kernel(const __grid_
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float* s_tab = s_tab_all + warp * TS;
-    const SharedTable tab{(uint32_t)__cvta_generic_to_shared(s_tab)};
+    const SharedTable tab{reinterpret_cast<const float4*>(s_tab)};
 
     const int gw = blockIdx.x * kBatchWarps + warp, nw = gridDim.x * kBatchWarps;
     int b = (int)(((long long)gw * p.B) / nw);   // spread warps over the instances
@@ -135,6 +135,7 @@ __global__ void __launch_bounds__(kBatchWarps * 32) batched_kernel(const __grid_
         const u32x4 r = philox4x32_10(u32x4{(uint32_t)(n >> 1), i, j, I.stream}, I.key0, I.key1);
 #pragma unroll 1
         for (int half = 0; half < 2; ++half) {
+            asm volatile("" ::: "memory");  // keeps the table loads inside the step
             float xi1, xi2;
             box_muller<float>(half ? r.z : r.x, half ? r.w : r.y, xi1, xi2);
             float x1[1] = {X1.val()}, x2[1] = {X2.val()}, v1[1], v2[1];

@@ -122,19 +122,17 @@ struct ParamTable {
     }
 };
 
-// SharedTable: the table lives in shared memory.  Each quad is one broadcast
-// 128-bit load, issued where it is used: the loads are volatile so that the
-// compiler cannot hoist all of them out of the path loop (which would need
-// one register per coefficient).
+// SharedTable: the table lives in shared memory; each quad is one broadcast
+// 128-bit load.  The kernel places a compiler barrier at the top of every step
+// so that these loads cannot be hoisted out of the path loop (which would need
+// one register per coefficient), while inside a step they can be scheduled
+// ahead of their uses.
 struct SharedTable {
-    uint32_t base;  // shared-window address of entry 0 (16-byte aligned)
+    const float4* base;
     __device__ __forceinline__ Quad<float> quad(int i) const
     {
-        Quad<float> q;
-        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-                     : "=f"(q.x), "=f"(q.y), "=f"(q.z), "=f"(q.w)
-                     : "r"(base + 16u * (uint32_t)i));
-        return q;
+        const float4 v = base[i];
+        return Quad<float>{v.x, v.y, v.z, v.w};
     }
 };
 
