@@ -205,7 +205,7 @@ def run_gpu(args):
     mean = torch.empty(n_obs, dtype=torch.float64, device=dev)
     var = torch.empty_like(mean)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    flags = pm.PM_FP32 | pm.PM_ASYNC
+    flags = pm.PM_FP32 | pm.PM_ASYNC | (pm.PM_TENSOR if args.tensor else 0)
 
     def step():
         pm.pm_forward_timedep(ctx, fld, w.kappa, th, x, t, n_obs, w.M, w.dt, w.seed, flags, mean, var,
@@ -257,8 +257,8 @@ def run_gpu(args):
     for k in range(max(2, min(args.steps, 5))):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        pm.pm_forward_timedep(ctx, fld, w.kappa, th, hx, ht, n_obs, w.M, w.dt, w.seed, pm.PM_FP32, hmean, hvar,
-                              instance=inst)
+        pm.pm_forward_timedep(ctx, fld, w.kappa, th, hx, ht, n_obs, w.M, w.dt, w.seed,
+                              pm.PM_FP32 | (pm.PM_TENSOR if args.tensor else 0), hmean, hvar, instance=inst)
         e2e_times.append(time.perf_counter() - t0)
     e2e_value = steps_per_eval * world / statistics.median(e2e_times)
 
@@ -284,7 +284,8 @@ def run_gpu(args):
                        "reductions": "f64", "mc_se_median": float(np.median(se)), "mc_se_max": float(se.max())},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                          "frac": achieved / peak_tflops, "traffic": traffic,
-                         "kernel": "timedep_kernel<float,10,128>", "kernel_ms": kern_mean_ms,
+                         "kernel": "timedep_tc_kernel<10>" if args.tensor else "timedep_kernel<float,10,128>",
+                         "kernel_ms": kern_mean_ms,
                          "flop_per_particle_step": flops_per_step(w.K),
                          "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 FLOP x sm_max_mhz "
                                        f"{peaks.get('sm_max_mhz', 2070.0)} ({peaks_kind})"},
@@ -297,8 +298,8 @@ def run_gpu(args):
         rate, threads, P, g_or, secs = oracle_sample(w)
         # pathwise check of the same sample against the GPU (same stream)
         gdev = torch.empty(n_obs * w.M, dtype=torch.float64, device=dev)
-        pm.pm_forward_timedep(ctx, fld, w.kappa, th, x, t, n_obs, w.M, w.dt, w.seed, pm.PM_FP32, mean, var,
-                              g_out=gdev)
+        pm.pm_forward_timedep(ctx, fld, w.kappa, th, x, t, n_obs, w.M, w.dt, w.seed,
+                              pm.PM_FP32 | (pm.PM_TENSOR if args.tensor else 0), mean, var, g_out=gdev)
         g_gpu = gdev.cpu().numpy().reshape(n_obs, w.M)[:, :P]
         d = (g_gpu - g_or).reshape(-1)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
@@ -447,6 +448,7 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=8, help="mcmc: steps of the plain sampler")
     ap.add_argument("--da-steps", type=int, default=200, help="mcmc: steps of the delayed-acceptance sampler")
     ap.add_argument("--B", type=int, default=256, help="instances of the batched workload")
+    ap.add_argument("--tensor", action="store_true", help="timedep: velocity sum on the tensor cores (PM_TENSOR)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

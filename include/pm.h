@@ -75,6 +75,10 @@ extern "C" {
 #define PM_FP64 1u
 #define PM_DEVICE_PTRS 2u
 #define PM_ASYNC 4u
+/* Time-dependent float paths only: evaluate the velocity sum on the tensor
+ * cores (tcgen05 TF32 with a three-term hi/lo split, about float accuracy);
+ * supported for K in {4, 5, 6, 8, 10, 12}, other K fall back to the FP32 pipes. */
+#define PM_TENSOR 8u
 
 #define PM_MAX_THETA0_MODES 64
 #define PM_MAX_BOUNDARY_MODES 32

@@ -26,6 +26,7 @@ PM_FP32 = 0
 PM_FP64 = 1
 PM_DEVICE_PTRS = 2
 PM_ASYNC = 4
+PM_TENSOR = 8
 
 
 class PMError(RuntimeError):

@@ -407,7 +407,20 @@ int pm_forward_timedep(pm_ctx* c, const pm_field* field, double kappa, const pm_
     L.key0 = (uint32_t)(seed & 0xffffffffu);
     L.key1 = (uint32_t)(seed >> 32);
     if (c->timing) PM_CUDA(cudaEventRecord(c->ev0, c->stream), "event");
-    cudaError_t e = fp64 ? dispatch_timedep<double>(field->K, L, c->stream) : dispatch_timedep<float>(field->K, L, c->stream);
+    cudaError_t e;
+    const int K = field->K;
+    if (!fp64 && (flags & PM_TENSOR) && (K == 4 || K == 5 || K == 6 || K == 8 || K == 10 || K == 12)) {
+        switch (K) {
+        case 4: e = tdtc::launch_timedep_tc<4>(L, W.err + 1, c->stream); break;
+        case 5: e = tdtc::launch_timedep_tc<5>(L, W.err + 1, c->stream); break;
+        case 6: e = tdtc::launch_timedep_tc<6>(L, W.err + 1, c->stream); break;
+        case 8: e = tdtc::launch_timedep_tc<8>(L, W.err + 1, c->stream); break;
+        case 10: e = tdtc::launch_timedep_tc<10>(L, W.err + 1, c->stream); break;
+        default: e = tdtc::launch_timedep_tc<12>(L, W.err + 1, c->stream); break;
+        }
+    } else {
+        e = fp64 ? dispatch_timedep<double>(K, L, c->stream) : dispatch_timedep<float>(K, L, c->stream);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "timedep kernel launch");
     if (c->timing) {
         PM_CUDA(cudaEventRecord(c->ev1, c->stream), "event");
@@ -429,6 +442,8 @@ int pm_forward_timedep(pm_ctx* c, const pm_field* field, double kappa, const pm_
         if (x_out) { PM_CUDA(cudaMemcpyAsync(h + o, dxo, (size_t)(2 * n_obs * M) * 8, cudaMemcpyDeviceToHost, c->stream), "copy x_out"); }
     }
     unsigned long long steps_taken = 0;
+    unsigned tc_flag = 0;
+    PM_CUDA(cudaMemcpyAsync(&tc_flag, W.err + 1, 4, cudaMemcpyDeviceToHost, c->stream), "copy flags");
     PM_CUDA(cudaMemcpyAsync(&err_flag, W.err, 4, cudaMemcpyDeviceToHost, c->stream), "copy flags");
     PM_CUDA(cudaMemcpyAsync(&steps_taken, W.steps, 8, cudaMemcpyDeviceToHost, c->stream), "copy step count");
     PM_CUDA(cudaStreamSynchronize(c->stream), "timedep");
@@ -443,6 +458,7 @@ int pm_forward_timedep(pm_ctx* c, const pm_field* field, double kappa, const pm_
         if (x_out) memcpy(x_out, h + o, (size_t)(2 * n_obs * M) * 8);
     }
     if (err_flag) return fail(PM_EINVAL, "observation points or times are not finite, a time is negative, or a step count exceeds 2^31");
+    if (tc_flag) return fail(PM_ETIMEOUT, "a tensor-core wait in the particle kernel timed out");
     return PM_OK;
 }
 

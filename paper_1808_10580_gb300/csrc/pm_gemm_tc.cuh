@@ -122,17 +122,22 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
     uint32_t r[32];
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+        "tcgen05.wait::ld.sync.aligned;"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
           "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
           "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
           "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        : "r"(taddr)
+        : "memory");
+    // (the wait is in the same statement: the outputs are valid when it ends)
 #pragma unroll
     for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
 }
 
+// The GEMM kernel itself is compiled in one translation unit only (pm_mlp.cu
+// defines PM_DEFINE_GEMM_KERNEL); other users of this header take the helpers.
+#ifdef PM_DEFINE_GEMM_KERNEL
 __global__ void __launch_bounds__(128, 1) gemm_bf16_tc_kernel(const __grid_constant__ GemmParams p)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -244,6 +249,7 @@ __global__ void __launch_bounds__(128, 1) gemm_bf16_tc_kernel(const __grid_const
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
     }
 }
+#endif  // PM_DEFINE_GEMM_KERNEL
 
 }  // namespace tc
 }  // namespace pm

@@ -153,4 +153,10 @@ cudaError_t launch_prep_rows(const BatchInstDev* inst, int B, int max_obs, const
 cudaError_t launch_reduce_rows(const BatchInstDev* inst, int B, int max_obs, const double* g, double* mean,
                                double* var, cudaStream_t s);
 
+// Time-dependent map with the velocity sum on the tensor cores (pm_timedep_tc.cuh);
+// *err is set when a bounded wait expires.
+namespace tdtc {
+template <int K> cudaError_t launch_timedep_tc(const TimedepLaunch& L, unsigned* err, cudaStream_t s);
+}
+
 }  // namespace pm

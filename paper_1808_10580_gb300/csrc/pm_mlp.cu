@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "../../include/pm.h"
+#define PM_DEFINE_GEMM_KERNEL
 #include "pm_gemm_tc.cuh"
 #include "pm_internal.h"
 

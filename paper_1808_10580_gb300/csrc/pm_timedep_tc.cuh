@@ -1,0 +1,310 @@
+// pm_timedep_tc.cuh -- Algorithm 1 with the velocity sum on the tensor cores.
+//
+// The velocity of the stream function (Eq. v_expand) in the product basis is
+//   v1 = P(0) + sum_{m>=1} C1m P1c(m) + S1m P1s(m),   v2 = sum_{m>=1} C1m P2c(m) + S1m P2s(m),
+// where every partial sum P(.)(m) is linear in the x2 harmonics
+//   a = (S2_1..S2_K, C2_1..C2_K, 1).
+// For the 128 particles of a CTA this is one matrix product per Euler step,
+//   P[128 x (4K+1)] = A[128 x (2K+1)] . W[(2K+1) x (4K+1)],
+// issued as tcgen05.mma kind::tf32 with the FP32 accumulator in tensor memory.
+// TF32 keeps 10 mantissa bits, so every operand is split x = hi + lo (hi = x
+// rounded to TF32, lo = (x - hi) rounded to TF32) and three products
+// hi.hi + lo.hi + hi.lo are accumulated (the lo.lo term, ~2^-22 relative, is
+// dropped): about float accuracy.  The remaining 4K+1 FMAs per particle, the
+// harmonics, the noise and the Euler step stay on the FP32 pipes.
+//
+// Per step: every thread writes its particle's row of A (hi and lo) into a
+// 128B-swizzled K-major tile, a CTA barrier hands the tile to the tensor core
+// (one thread issues 3 x ceil((2K+1)/8) MMAs and commits to an mbarrier), and
+// every thread reads its 4K+1 accumulator columns back with tcgen05.ld.
+#pragma once
+#include "pm_gemm_tc.cuh"
+#include "pm_kernels.cuh"
+
+namespace pm {
+namespace tdtc {
+
+template <int K>
+struct Shape {
+    static constexpr int KD = 2 * K + 1;              // A columns used
+    static constexpr int KS = (KD + 7) / 8;           // MMA k-steps (K = 8 per tf32 instruction)
+    static constexpr int NC = 4 * K + 1;              // accumulator columns used
+    static constexpr int NP = (NC + 15) / 16 * 16;    // MMA N (multiple of 16)
+    static constexpr int A_BYTES = 128 * 128;         // 128 rows x 32 tf32
+    static constexpr int B_BYTES = NP * 128;          // NP rows x 32 tf32
+    static constexpr int SMEM = 2 * A_BYTES + 2 * B_BYTES + 1024 + 64;
+    static_assert(KD <= 32, "one 128-byte atom of K");
+    static_assert(NP <= 64, "64 TMEM columns");
+};
+
+// Instruction descriptor, kind::tf32: FP32 accumulator, TF32 A and B, both K-major.
+template <int NP>
+__host__ __device__ constexpr uint32_t idesc_tf32() { return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NP >> 3) << 17) | ((uint32_t)(128 >> 4) << 24); }
+
+__device__ __forceinline__ float to_tf32(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// Byte offset of 16-byte chunk c of row r in a 128B-swizzled K-major tile.
+__device__ __forceinline__ uint32_t sw128(int r, int c) { return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4)); }
+
+template <int K>
+struct Params {
+    float W[Shape<K>::NP * 32];   // W^T: row nc (accumulator column), entry k (A column)
+    Theta0Table<float> th;
+    const ObsRec* obs;
+    const int32_t* order;
+    double2* part;
+    double* g_out;
+    double* x_out;
+    float dt, s_dt;
+    int64_t M, path_offset;
+    int32_t n_obs, chunks;
+    uint32_t inst, key0, key1;
+    unsigned* err;
+};
+
+template <int NP>
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc_tf32<NP>()), "r"(accumulate)
+        : "memory");
+}
+
+// 16 accumulator columns of this thread's lane; the wait is part of the same
+// statement, so the outputs are valid when it ends.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];\n"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+template <int K>
+__global__ void __launch_bounds__(128, 4) timedep_tc_kernel(const __grid_constant__ Params<K> p)
+{
+    using S = Shape<K>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* A_hi = smem;
+    uint8_t* A_lo = smem + S::A_BYTES;
+    uint8_t* B_hi = smem + 2 * S::A_BYTES;
+    uint8_t* B_lo = B_hi + S::B_BYTES;
+    uint64_t* bar = (uint64_t*)(B_lo + S::B_BYTES);
+    uint32_t* tmem_slot = (uint32_t*)(bar + 1);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t bar_a = tc::smem_u32(bar);
+
+    // Coefficient tiles (hi / lo) and zero padding of the particle tiles.
+    for (int q = tid; q < S::NP * 8; q += 128) {
+        const int r = q >> 3, c = q & 7;
+        float4 h, l;
+        float* hv = &h.x;
+        float* lv = &l.x;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float w = p.W[r * 32 + 4 * c + e];
+            hv[e] = to_tf32(w);
+            lv[e] = to_tf32(w - hv[e]);
+        }
+        *reinterpret_cast<float4*>(B_hi + sw128(r, c)) = h;
+        *reinterpret_cast<float4*>(B_lo + sw128(r, c)) = l;
+    }
+    for (int c = 0; c < 8; ++c) {
+        *reinterpret_cast<float4*>(A_hi + sw128(tid, c)) = make_float4(0.f, 0.f, 0.f, 0.f);
+        *reinterpret_cast<float4*>(A_lo + sw128(tid, c)) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (tid == 0) {
+        tc::mbar_init(bar_a, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(tmem_slot)),
+                     "r"(64u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t t_row = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint64_t dA_hi = tc::smem_desc_sw128(tc::smem_u32(A_hi)), dA_lo = tc::smem_desc_sw128(tc::smem_u32(A_lo));
+    const uint64_t dB_hi = tc::smem_desc_sw128(tc::smem_u32(B_hi)), dB_lo = tc::smem_desc_sw128(tc::smem_u32(B_lo));
+
+    const int slot = blockIdx.x / p.chunks;
+    const int cidx = blockIdx.x - slot * p.chunks;
+    const int j = p.order ? p.order[slot] : slot;
+    const int64_t i = (int64_t)cidx * 128 + tid;
+    const bool active = i < p.M;
+    const ObsRec o = p.obs[j];
+    Coord<float> X1, X2;
+    X1.set(o.x1);
+    X2.set(o.x2);
+    const uint32_t pid = (uint32_t)(p.path_offset + (active ? i : 0));
+    const int N = o.nsteps;
+    const float h_last = (float)o.h_last, s_last = (float)o.s_last;
+    bool failed = false;
+    u32x4 r{0, 0, 0, 0};
+
+    for (int n = 0; n < N; ++n) {
+        if ((n & 1) == 0) r = philox4x32_10(u32x4{(uint32_t)(n >> 1), pid, (uint32_t)j, p.inst}, p.key0, p.key1);
+        float xi1, xi2;
+        box_muller<float>((n & 1) ? r.z : r.x, (n & 1) ? r.w : r.y, xi1, xi2);
+        // Row of A: x2 harmonics (hi and lo).
+        {
+            float C2[K + 1], S2[K + 1];
+            fourier_powers<float, K>(X2.val(), C2, S2);
+            float a[32];
+#pragma unroll
+            for (int q = 0; q < 32; ++q) a[q] = 0.f;
+#pragma unroll
+            for (int q = 1; q <= K; ++q) { a[q - 1] = S2[q]; a[K + q - 1] = C2[q]; }
+            a[2 * K] = 1.f;
+#pragma unroll
+            for (int c = 0; c < (S::KD + 3) / 4; ++c) {
+                float4 h, l;
+                h.x = to_tf32(a[4 * c]);     l.x = to_tf32(a[4 * c] - h.x);
+                h.y = to_tf32(a[4 * c + 1]); l.y = to_tf32(a[4 * c + 1] - h.y);
+                h.z = to_tf32(a[4 * c + 2]); l.z = to_tf32(a[4 * c + 2] - h.z);
+                h.w = to_tf32(a[4 * c + 3]); l.w = to_tf32(a[4 * c + 3] - h.w);
+                *reinterpret_cast<float4*>(A_hi + sw128(tid, c)) = h;
+                *reinterpret_cast<float4*>(A_lo + sw128(tid, c)) = l;
+            }
+        }
+        // x1 harmonics stay in registers.
+        float C1[K + 1], S1[K + 1];
+        fourier_powers<float, K>(X1.val(), C1, S1);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, dA_hi + 2 * k, dB_hi + 2 * k, k > 0 ? 1u : 0u);
+#pragma unroll
+            for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, dA_lo + 2 * k, dB_hi + 2 * k, 1u);
+#pragma unroll
+            for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, dA_hi + 2 * k, dB_lo + 2 * k, 1u);
+            tc::mma_commit(bar_a);
+        }
+        const bool ok = tc::mbar_wait(bar_a, (uint32_t)(n & 1));
+        if (__syncthreads_or(!ok)) { failed = true; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        float acc[S::NP];
+#pragma unroll
+        for (int c0 = 0; c0 < S::NP; c0 += 16) tmem_ld16(t_row + (uint32_t)c0, acc + c0);
+        float v1 = acc[0], v2 = 0.f;
+#pragma unroll
+        for (int m = 1; m <= K; ++m) {
+            v1 = fmaf(C1[m], acc[m], fmaf(S1[m], acc[K + m], v1));
+            v2 = fmaf(C1[m], acc[2 * K + m], fmaf(S1[m], acc[3 * K + m], v2));
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        const bool last = (n == N - 1);
+        const float hh = last ? h_last : p.dt, ss = last ? s_last : p.s_dt;
+        em_update<float>(X1, v1, hh, ss, xi1);
+        em_update<float>(X2, v2, hh, ss, xi2);
+        X1.wrap();
+        X2.wrap();
+    }
+    double g = 0.0;
+    if (failed) {
+        if (tid == 0) atomicExch(p.err, 1u);
+    } else if (active) {
+        g = theta0_eval(p.th, X1, X2);
+        const int64_t w = (int64_t)j * p.M + i;
+        if (p.g_out) p.g_out[w] = g;
+        if (p.x_out) { p.x_out[2 * w] = X1.full(); p.x_out[2 * w + 1] = X2.full(); }
+    }
+    const double2 sum = block_sum2<128>(g, g * g);
+    if (tid == 0) p.part[(int64_t)j * p.chunks + cidx] = sum;
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64u) : "memory");
+    }
+}
+
+// W^T of the product-basis table t[(m (K+1) + n) 8 + q] (e0..e3, f0..f3).
+template <int K>
+void build_W(const double* t, float* W)
+{
+    using S = Shape<K>;
+    for (int q = 0; q < S::NP * 32; ++q) W[q] = 0.f;
+    auto T = [&](int m, int n, int q) { return t[(size_t)(m * (K + 1) + n) * 8 + q]; };
+    auto set = [&](int col, int row, double v) { W[col * 32 + row] = (float)v; };
+    const int rS = 0, rC = K, rOne = 2 * K;  // A columns: S2_n at n-1, C2_n at K+n-1, constant at 2K
+    for (int n = 1; n <= K; ++n) {  // m = 0: v1 only
+        set(0, rS + n - 1, T(0, n, 0));
+        set(0, rC + n - 1, T(0, n, 1));
+    }
+    for (int m = 1; m <= K; ++m) {
+        const int c1c = m, c1s = K + m, c2c = 2 * K + m, c2s = 3 * K + m;
+        for (int n = 1; n <= K; ++n) {
+            set(c1c, rS + n - 1, T(m, n, 0)); set(c1c, rC + n - 1, T(m, n, 1));
+            set(c1s, rS + n - 1, T(m, n, 2)); set(c1s, rC + n - 1, T(m, n, 3));
+            set(c2c, rC + n - 1, T(m, n, 4)); set(c2c, rS + n - 1, T(m, n, 5));
+            set(c2s, rC + n - 1, T(m, n, 6)); set(c2s, rS + n - 1, T(m, n, 7));
+        }
+        set(c2c, rOne, T(m, 0, 4));
+        set(c2s, rOne, T(m, 0, 6));
+    }
+}
+
+template <int K>
+cudaError_t launch_timedep_tc(const TimedepLaunch& L, unsigned* err, cudaStream_t stream)
+{
+    using S = Shape<K>;
+    Params<K> p;
+    build_W<K>(L.coef, p.W);
+    p.th.n = L.nq;
+    for (int q = 0; q < kMaxTheta0; ++q) {
+        const bool on = q < L.nq;
+        p.th.k1[q] = on ? L.qk[2 * q] : 0;
+        p.th.k2[q] = on ? L.qk[2 * q + 1] : 0;
+        p.th.a[q] = on ? (float)L.qa[q] : 0.f;
+        p.th.b[q] = on ? (float)L.qb[q] : 0.f;
+    }
+    p.obs = L.obs;
+    p.order = L.order;
+    p.part = L.part;
+    p.g_out = L.g_out;
+    p.x_out = L.x_out;
+    p.dt = (float)L.dt;
+    p.s_dt = (float)L.s_dt;
+    p.M = L.M;
+    p.path_offset = L.path_offset;
+    p.n_obs = L.n_obs;
+    p.chunks = L.chunks;
+    p.inst = L.inst;
+    p.key0 = L.key0;
+    p.key1 = L.key1;
+    p.err = err;
+    cudaError_t e = cudaFuncSetAttribute(timedep_tc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+    if (e != cudaSuccess) return e;
+    const int64_t grid = (int64_t)L.n_obs * L.chunks;
+    timedep_tc_kernel<K><<<(unsigned)grid, 128, S::SMEM, stream>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace tdtc
+}  // namespace pm
+
+#define PM_INSTANTIATE_TC(K) \
+    template cudaError_t pm::tdtc::launch_timedep_tc<K>(const pm::TimedepLaunch&, unsigned*, cudaStream_t);

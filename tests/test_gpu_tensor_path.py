@@ -1,0 +1,81 @@
+"""Parity of the time-dependent map with the velocity sum on the tensor cores
+(PM_TENSOR: tcgen05 TF32 with a three-term hi/lo split) against the FP64 oracle
+and against the FP32-pipe kernel."""
+import numpy as np
+import pytest
+
+from paper_1808_10580_gb300 import inputs
+from tests import _gpu
+
+pytestmark = pytest.mark.gpu
+pm = _gpu.pm
+torch = _gpu.torch
+
+
+@pytest.fixture(scope="module")
+def c():
+    h = _gpu.ctx()
+    yield h
+    pm.pm_destroy(h)
+
+
+@pytest.mark.parametrize("K", [4, 5, 6, 8, 10, 12])
+def test_one_step_positions_match_oracle(c, orc, K):
+    # One Euler step of length dt from 300 points: X1 - x = -v(x) dt + noise, so the
+    # end points expose the velocity the tensor-core path evaluated.
+    w = inputs.timedep_k10(M=128)
+    w.K = K
+    w.u = inputs.prior_field(K, 300 + K)
+    rng = np.random.default_rng(K)
+    w.x = rng.random((64, 2))
+    w.dt = 0.01
+    w.t = np.full(64, w.dt)
+    _, _, xe = _gpu.timedep(c, w, pm.PM_FP32 | pm.PM_TENSOR, x_out=True)
+    _, _, xs = _gpu.timedep(c, w, pm.PM_FP32, x_out=True)
+    _, xo = orc.timedep_paths(K, w.u, w.kappa, w.theta0, w.x, w.t, w.dt, w.seed, npaths=128, want_x=True)
+    modes = orc.half_modes(K).astype(float)
+    scale = float((2 * np.pi * np.sqrt((modes ** 2).sum(1)) * np.abs(w.u.reshape(-1, 2)).sum(1)).sum())
+    d_tc = xe - xo
+    d_tc -= np.round(d_tc)
+    d_sm = xs - xo
+    d_sm -= np.round(d_sm)
+    # 3xTF32 keeps ~21 bits per product: velocity error <= ~1e-6 of the term scale
+    assert np.abs(d_tc).max() <= w.dt * 4e-6 * scale + 1e-7, (np.abs(d_tc).max(), np.abs(d_sm).max())
+
+
+@pytest.mark.parametrize("field", ["zero", "shear"])
+def test_stable_fields_match_oracle_at_1e5(c, orc, field):
+    w = inputs.timedep_k10(M=4000)
+    if field == "zero":
+        w.u = np.zeros_like(w.u)
+    else:
+        modes = orc.half_modes(10)
+        h = [tuple(m) for m in modes].index((2, 3))
+        w.u = np.zeros_like(w.u)
+        w.u[2 * h], w.u[2 * h + 1] = 0.05, 0.02
+    obs = np.array([5, 120, 250])
+    mean, var = _gpu.timedep(c, w, pm.PM_FP32 | pm.PM_TENSOR, obs=obs)
+    g = orc.timedep_paths(10, w.u, w.kappa, w.theta0, w.x[obs], w.t[obs], w.dt, w.seed, npaths=w.M,
+                          obs_id=np.arange(3))
+    rm, rv, rse = orc.estimate(g)
+    assert np.abs(mean - rm).max() <= 1e-5
+
+
+def test_full_size_440_modes_in_distribution(c, orc):
+    w = inputs.timedep_k10()
+    mean, var, g = _gpu.timedep(c, w, pm.PM_FP32 | pm.PM_TENSOR, g_out=True)
+    ms, vs = _gpu.timedep(c, w, pm.PM_FP32)
+    P = 16
+    go = orc.timedep_paths(w.K, w.u, w.kappa, w.theta0, w.x, w.t, w.dt, w.seed, npaths=P)
+    d = (g[:, :P] - go).ravel()
+    assert abs(d.mean()) <= 5 * d.std(ddof=1) / np.sqrt(d.size)
+    # the two float kernels are two estimates with correlated early paths: within 5 SE of each other
+    se = np.sqrt((var + vs) / w.M)
+    assert np.mean(np.abs(mean - ms) <= 5 * se) >= 0.99
+
+
+def test_repeatable(c):
+    w = inputs.timedep_k10(M=512)
+    a = _gpu.timedep(c, w, pm.PM_FP32 | pm.PM_TENSOR)
+    b = _gpu.timedep(c, w, pm.PM_FP32 | pm.PM_TENSOR)
+    assert np.array_equal(a[0], b[0])
