@@ -395,7 +395,8 @@ def run_aux(args):
 
 def run_mcmc(args):
     """Surrogate-screened pCN against plain pCN on the same GPU (auxiliary line):
-    64 chains started near the data-generating field, the same beta for both."""
+    64 chains started at the data-generating field, the same beta for both
+    samplers; one line per beta in --betas."""
     import torch
 
     import paper_1808_10580_gb300 as pm
@@ -408,25 +409,28 @@ def run_mcmc(args):
     prob = sm.make_data(ctx, sm.make_problem(sigma=args.sigma))
     Z, G = sm.training_pairs(ctx, prob, args.train_pairs)
     t_pairs = time.perf_counter() - t0
-    Zv, Gv = sm.training_pairs(ctx, prob, 1024, seed=7005)
+    Zv, Gv = sm.training_pairs(ctx, prob, 2048, seed=7005)
     t1 = time.perf_counter()
     net, hist = sm.train_surrogate(ctx, prob, Z, G, epochs=args.epochs)
     t_train = time.perf_counter() - t1
     rmse = sm.surrogate_rmse(ctx, net, Zv, Gv)
+    rmse_train = sm.surrogate_rmse(ctx, net, Z[:2048], G[:2048])
     u0 = sm.start_states(prob, 64, spread=0.0)
-    plain, _ = sm.run_chains(ctx, prob, u0, args.beta, args.plain_steps, seed=11)
-    da, _ = sm.run_chains(ctx, prob, u0, args.beta, args.da_steps, seed=11, net=net)
+    for beta in [float(v) for v in args.betas.split(",")]:
+        plain, _ = sm.run_chains(ctx, prob, u0, beta, args.plain_steps, seed=11)
+        da, _ = sm.run_chains(ctx, prob, u0, beta, args.da_steps, seed=11, net=net)
+        line = {"metric": "accepted pCN proposals/s (64 chains)", "auxiliary": True, "data": "synthetic",
+                "value": da["accepted_per_s"], "unit": "accepted proposals/s",
+                "ratio_vs_plain": da["accepted_per_s"] / max(plain["accepted_per_s"], 1e-30),
+                "config": {"train_pairs": args.train_pairs, "epochs": args.epochs, "M": prob.M,
+                           "n_obs": len(prob.t), "sigma": prob.sigma, "beta": beta, "chains": 64,
+                           "start": "data-generating field"},
+                "plain": plain, "delayed_acceptance": da,
+                "surrogate": {"val_rmse": rmse, "train_rmse": rmse_train, "final_train_loss": float(hist[-1]),
+                              "train_seconds": t_train, "pair_generation_seconds": t_pairs}}
+        print(json.dumps(line), flush=True)
     pm.pm_surrogate_destroy(net)
     pm.pm_destroy(ctx)
-    line = {"metric": "accepted pCN proposals/s (64 chains)", "auxiliary": True, "data": "synthetic",
-            "value": da["accepted_per_s"], "unit": "accepted proposals/s",
-            "ratio_vs_plain": da["accepted_per_s"] / max(plain["accepted_per_s"], 1e-30),
-            "config": {"train_pairs": args.train_pairs, "M": prob.M, "n_obs": len(prob.t), "sigma": prob.sigma,
-                       "beta": args.beta, "chains": 64, "start": "data-generating field"},
-            "plain": plain, "delayed_acceptance": da,
-            "surrogate": {"val_rmse": rmse, "final_train_loss": float(hist[-1]), "train_seconds": t_train,
-                          "pair_generation_seconds": t_pairs}}
-    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -442,7 +446,7 @@ def main():
     ap.add_argument("--workload", default="timedep", choices=["timedep", "dirichlet", "batched", "mcmc"],
                     help="timedep: the headline line; dirichlet / batched / mcmc: auxiliary measurements")
     ap.add_argument("--train-pairs", type=int, default=1 << 16, help="mcmc: surrogate training pairs")
-    ap.add_argument("--beta", type=float, default=0.02, help="mcmc: pCN step, the same for both samplers")
+    ap.add_argument("--betas", default="0.03", help="mcmc: comma-separated pCN steps (each the same for both samplers)")
     ap.add_argument("--sigma", type=float, default=0.01, help="mcmc: observation noise standard deviation")
     ap.add_argument("--epochs", type=int, default=100, help="mcmc: surrogate training epochs")
     ap.add_argument("--plain-steps", type=int, default=8, help="mcmc: steps of the plain sampler")
