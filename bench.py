@@ -411,7 +411,8 @@ def run_mcmc(args):
     t_pairs = time.perf_counter() - t0
     Zv, Gv = sm.training_pairs(ctx, prob, 2048, seed=7005)
     t1 = time.perf_counter()
-    net, hist = sm.train_surrogate(ctx, prob, Z, G, epochs=args.epochs)
+    net, hist = sm.train_surrogate(ctx, prob, Z, G, epochs=args.epochs, weight_decay=args.weight_decay,
+                                   lr_decay=args.lr_decay)
     t_train = time.perf_counter() - t1
     rmse = sm.surrogate_rmse(ctx, net, Zv, Gv)
     rmse_train = sm.surrogate_rmse(ctx, net, Z[:2048], G[:2048])
@@ -449,6 +450,8 @@ def main():
     ap.add_argument("--betas", default="0.03", help="mcmc: comma-separated pCN steps (each the same for both samplers)")
     ap.add_argument("--sigma", type=float, default=0.01, help="mcmc: observation noise standard deviation")
     ap.add_argument("--epochs", type=int, default=100, help="mcmc: surrogate training epochs")
+    ap.add_argument("--weight-decay", type=float, default=0.0, help="mcmc: AdamW weight decay")
+    ap.add_argument("--lr-decay", type=float, default=1.0, help="mcmc: per-epoch step-size factor")
     ap.add_argument("--plain-steps", type=int, default=8, help="mcmc: steps of the plain sampler")
     ap.add_argument("--da-steps", type=int, default=200, help="mcmc: steps of the delayed-acceptance sampler")
     ap.add_argument("--B", type=int, default=256, help="instances of the batched workload")

@@ -256,6 +256,8 @@ typedef struct pm_train_opts {
     float lr;               /* Adam step size */
     float beta1, beta2;     /* moment decays in [0, 1) */
     float eps;              /* > 0 */
+    float weight_decay;     /* decoupled weight decay of the weight matrices (AdamW), >= 0 */
+    float lr_decay;         /* the step size is multiplied by this after every epoch, in (0, 1] */
     uint64_t shuffle_seed;  /* seed of the per-epoch row shuffle */
 } pm_train_opts;
 

@@ -307,7 +307,8 @@ def pm_set_graph_mode(ctx, on):
 
 class pm_train_opts(C.Structure):
     _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_float), ("beta1", C.c_float),
-                ("beta2", C.c_float), ("eps", C.c_float), ("shuffle_seed", C.c_uint64)]
+                ("beta2", C.c_float), ("eps", C.c_float), ("weight_decay", C.c_float), ("lr_decay", C.c_float),
+                ("shuffle_seed", C.c_uint64)]
 
 
 def _declare_surrogate(L):
@@ -371,12 +372,14 @@ def pm_surrogate_gradients(ctx, net, U, T, n_in, n_hidden, n_out):
     return float(loss[0]), out
 
 
-def pm_surrogate_train(ctx, net, U, Y, epochs, batch, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, shuffle_seed=0):
+def pm_surrogate_train(ctx, net, U, Y, epochs, batch, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, shuffle_seed=0,
+                       weight_decay=0.0, lr_decay=1.0):
     dev = _device(U, Y)
     if not dev:
         U, Y = _f32(U), _f32(Y)
     N = U.shape[0]
-    o = pm_train_opts(int(epochs), int(batch), float(lr), float(beta1), float(beta2), float(eps), int(shuffle_seed))
+    o = pm_train_opts(int(epochs), int(batch), float(lr), float(beta1), float(beta2), float(eps), float(weight_decay),
+                      float(lr_decay), int(shuffle_seed))
     hist = np.zeros(int(epochs), np.float32)
     _check(_slib().pm_surrogate_train(ctx, net, _ptr(U), _ptr(Y), int(N), C.byref(o),
                                       PM_DEVICE_PTRS if dev else 0, hist.ctypes.data))

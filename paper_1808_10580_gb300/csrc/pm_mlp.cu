@@ -183,10 +183,14 @@ __global__ void colsum_kernel(const float* __restrict__ X, int rows, int cols, i
     out[cidx] = (float)s;
 }
 
-// Adam on the whole parameter buffer.
+// Adam on the whole parameter buffer, with decoupled weight decay (AdamW,
+// Loshchilov & Hutter 2019) on the weight matrices; the three bias ranges
+// [bo_k, bo_k + bn_k) are not decayed.
+struct BiasRanges { int64_t o[3], n[3]; };
+
 __global__ void adam_kernel(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ m,
                             float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float c1,
-                            float c2)
+                            float c2, float wd, BiasRanges br)
 {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
@@ -196,7 +200,11 @@ __global__ void adam_kernel(float* __restrict__ P, const float* __restrict__ G, 
     m[q] = mq;
     v[q] = vq;
     const float mh = mq / c1, vh = vq / c2;
-    P[q] -= lr * mh / (sqrtf(vh) + eps);
+    bool bias = false;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) bias = bias || (q >= br.o[k] && q < br.o[k] + br.n[k]);
+    const float p = P[q];
+    P[q] = p - lr * (mh / (sqrtf(vh) + eps) + (bias ? 0.0f : wd * p));
 }
 
 // FP32 [rows][cols] -> BF16 row-major and transposed copies.
@@ -527,7 +535,8 @@ int pm_surrogate_train(pm_ctx* c, pm_mlp* n, const float* U, const float* Y, int
     if (!c || !n || !U || !Y || !o) return fail(PM_EINVAL, "NULL argument");
     if (N < 1) return fail(PM_EINVAL, "N < 1");
     if (o->epochs < 1 || o->batch < 1 || o->batch > (1 << 16)) return fail(PM_EINVAL, "bad epochs or batch");
-    if (!(o->lr > 0) || !(o->beta1 >= 0 && o->beta1 < 1) || !(o->beta2 >= 0 && o->beta2 < 1) || !(o->eps > 0))
+    if (!(o->lr > 0) || !(o->beta1 >= 0 && o->beta1 < 1) || !(o->beta2 >= 0 && o->beta2 < 1) || !(o->eps > 0) ||
+        !(o->weight_decay >= 0) || !(o->lr_decay > 0 && o->lr_decay <= 1))
         return fail(PM_EINVAL, "bad Adam settings");
     int rc = set_device(c);
     if (rc) return rc;
@@ -555,7 +564,9 @@ int pm_surrogate_train(pm_ctx* c, pm_mlp* n, const float* U, const float* Y, int
     uint64_t st = o->shuffle_seed;
     std::vector<float> step_loss((size_t)nb);
     PM_CUDA(cudaMemsetAsync(n->err, 0, 4, c->stream), "clear flag");
-    for (int ep = 0; ep < o->epochs; ++ep) {
+    const BiasRanges br{{n->ob1, n->ob2, n->ob3}, {n->H, n->H, n->Nout}};
+    float lr = o->lr;
+    for (int ep = 0; ep < o->epochs; ++ep, lr *= o->lr_decay) {
         for (int64_t i = N - 1; i > 0; --i) std::swap(perm[(size_t)i], perm[(size_t)(splitmix(st) % (uint64_t)(i + 1))]);
         PM_CUDA(cudaMemcpyAsync(dperm, perm.data(), pb, cudaMemcpyHostToDevice, c->stream), "copy permutation");
         double ep_loss = 0.0;
@@ -571,7 +582,8 @@ int pm_surrogate_train(pm_ctx* c, pm_mlp* n, const float* U, const float* Y, int
             n->step += 1;
             const float c1 = 1.0f - std::pow(o->beta1, (float)n->step), c2 = 1.0f - std::pow(o->beta2, (float)n->step);
             adam_kernel<<<(unsigned)((n->P + 255) / 256), 256, 0, c->stream>>>(n->params, n->grads, n->m, n->v, n->P,
-                                                                               o->lr, o->beta1, o->beta2, o->eps, c1, c2);
+                                                                               lr, o->beta1, o->beta2, o->eps, c1, c2,
+                                                                               o->weight_decay, br);
             PM_CUDA(cudaGetLastError(), "adam");
             count_launch(c);
             if ((rc = mlp_cast_weights(c, n))) return rc;

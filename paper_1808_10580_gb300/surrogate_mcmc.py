@@ -87,9 +87,11 @@ def training_pairs(ctx, prob: Problem, n: int, seed: int = 7004):
     return Z.astype(np.float32), G.astype(np.float32)
 
 
-def train_surrogate(ctx, prob: Problem, Z, G, hidden=512, epochs=20, batch=512, lr=1e-3, seed=8004):
+def train_surrogate(ctx, prob: Problem, Z, G, hidden=512, epochs=20, batch=512, lr=1e-3, seed=8004,
+                    weight_decay=0.0, lr_decay=1.0):
     net = pm.pm_surrogate_create(ctx, Z.shape[1], hidden, G.shape[1], seed)
-    hist = pm.pm_surrogate_train(ctx, net, Z, G, epochs=epochs, batch=batch, lr=lr, shuffle_seed=seed)
+    hist = pm.pm_surrogate_train(ctx, net, Z, G, epochs=epochs, batch=batch, lr=lr, shuffle_seed=seed,
+                                 weight_decay=weight_decay, lr_decay=lr_decay)
     return net, hist
 
 
