@@ -455,7 +455,10 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=8, help="mcmc: steps of the plain sampler")
     ap.add_argument("--da-steps", type=int, default=200, help="mcmc: steps of the delayed-acceptance sampler")
     ap.add_argument("--B", type=int, default=256, help="instances of the batched workload")
-    ap.add_argument("--tensor", action="store_true", help="timedep: velocity sum on the tensor cores (PM_TENSOR)")
+    ap.add_argument("--tensor", dest="tensor", action="store_true", default=True,
+                    help="timedep: velocity sum on the tensor cores (PM_TENSOR; the default)")
+    ap.add_argument("--no-tensor", dest="tensor", action="store_false",
+                    help="timedep: velocity sum on the FP32 pipes")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
