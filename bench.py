@@ -342,8 +342,9 @@ def run_aux(args):
 
         def step():
             pm.pm_forward_dirichlet(ctx, fld, w.drift_scale, w.kappa, gd, x, len(w.x), w.M, w.dt, w.max_steps,
-                                    w.seed, pm.PM_FP32, mean, var)
-        name, cfg = w.name, {"n_obs": len(w.x), "M": w.M, "dt": w.dt, "kappa": w.kappa, "drift_scale": w.drift_scale}
+                                    w.seed, pm.PM_FP32 | (pm.PM_TENSOR if args.tensor else 0), mean, var)
+        name, cfg = w.name, {"n_obs": len(w.x), "M": w.M, "dt": w.dt, "kappa": w.kappa, "drift_scale": w.drift_scale,
+                             "tensor_cores": bool(args.tensor)}
     else:
         ws = inputs.batched_instances(B=args.B, M=args.M or 4096)
         xs, ts, inst = [], [], []

@@ -506,7 +506,7 @@ int pm_forward_dirichlet(pm_ctx* c, const pm_field* field, double drift_scale, d
 
     auto layout = [&](Bump& b) {
         struct P { unsigned long long* ctr; double *g, *x, *mean, *var, *xo; int32_t* es; } p{};
-        p.ctr = b.take<unsigned long long>(3);  // next path, unexited, steps
+        p.ctr = b.take<unsigned long long>(4);  // next path, unexited, steps, tensor-core error flag
         p.g = (dev && g_out) ? nullptr : b.take<double>((size_t)total);
         if (!dev) {
             p.x = b.take<double>((size_t)(2 * n_obs));
@@ -540,7 +540,7 @@ int pm_forward_dirichlet(pm_ctx* c, const pm_field* field, double drift_scale, d
         dxo = W.xo;
     }
     const std::vector<double> tab = stage_coefficients(field->K, field->u);
-    PM_CUDA(cudaMemsetAsync(W.ctr, 0, 24, c->stream), "clear counters");
+    PM_CUDA(cudaMemsetAsync(W.ctr, 0, 32, c->stream), "clear counters");
     c->last_steps = -1;
 
     DirichletLaunch L{};
@@ -568,13 +568,40 @@ int pm_forward_dirichlet(pm_ctx* c, const pm_field* field, double drift_scale, d
     L.inst = opts ? opts->instance : 0u;
     L.key0 = (uint32_t)(seed & 0xffffffffu);
     L.key1 = (uint32_t)(seed >> 32);
-    const int per_sm = fp64 ? dispatch_dirichlet_occupancy<double>(field->K) : dispatch_dirichlet_occupancy<float>(field->K);
+    const int Kd = field->K;
+    const bool use_tc = !fp64 && (flags & PM_TENSOR) && (Kd == 4 || Kd == 5 || Kd == 6 || Kd == 8 || Kd == 10 || Kd == 12);
+    int per_sm = 1;
+    if (use_tc) {
+        switch (Kd) {
+        case 4: per_sm = tdtc::dirichlet_tc_blocks_per_sm<4>(); break;
+        case 5: per_sm = tdtc::dirichlet_tc_blocks_per_sm<5>(); break;
+        case 6: per_sm = tdtc::dirichlet_tc_blocks_per_sm<6>(); break;
+        case 8: per_sm = tdtc::dirichlet_tc_blocks_per_sm<8>(); break;
+        case 10: per_sm = tdtc::dirichlet_tc_blocks_per_sm<10>(); break;
+        default: per_sm = tdtc::dirichlet_tc_blocks_per_sm<12>(); break;
+        }
+    } else {
+        per_sm = fp64 ? dispatch_dirichlet_occupancy<double>(Kd) : dispatch_dirichlet_occupancy<float>(Kd);
+    }
     int64_t grid = (int64_t)per_sm * c->sm_count;
     const int64_t need = (total + kDirichletBlock - 1) / kDirichletBlock;
     if (grid > need) grid = need;
     L.grid = (int)(grid > 0 ? grid : 1);
     if (c->timing) PM_CUDA(cudaEventRecord(c->ev0, c->stream), "event");
-    cudaError_t e = fp64 ? dispatch_dirichlet<double>(field->K, L, c->stream) : dispatch_dirichlet<float>(field->K, L, c->stream);
+    cudaError_t e;
+    unsigned* tc_err = (unsigned*)(W.ctr + 3);
+    if (use_tc) {
+        switch (Kd) {
+        case 4: e = tdtc::launch_dirichlet_tc<4>(L, tc_err, c->stream); break;
+        case 5: e = tdtc::launch_dirichlet_tc<5>(L, tc_err, c->stream); break;
+        case 6: e = tdtc::launch_dirichlet_tc<6>(L, tc_err, c->stream); break;
+        case 8: e = tdtc::launch_dirichlet_tc<8>(L, tc_err, c->stream); break;
+        case 10: e = tdtc::launch_dirichlet_tc<10>(L, tc_err, c->stream); break;
+        default: e = tdtc::launch_dirichlet_tc<12>(L, tc_err, c->stream); break;
+        }
+    } else {
+        e = fp64 ? dispatch_dirichlet<double>(Kd, L, c->stream) : dispatch_dirichlet<float>(Kd, L, c->stream);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "dirichlet kernel launch");
     if (c->timing) {
         PM_CUDA(cudaEventRecord(c->ev1, c->stream), "event");
@@ -601,6 +628,8 @@ int pm_forward_dirichlet(pm_ctx* c, const pm_field* field, double drift_scale, d
     unsigned long long steps_taken = 0;
     PM_CUDA(cudaMemcpyAsync(&unexited, W.ctr + 1, 8, cudaMemcpyDeviceToHost, c->stream), "copy n_unexited");
     PM_CUDA(cudaMemcpyAsync(&steps_taken, W.ctr + 2, 8, cudaMemcpyDeviceToHost, c->stream), "copy step count");
+    unsigned tc_flag = 0;
+    PM_CUDA(cudaMemcpyAsync(&tc_flag, tc_err, 4, cudaMemcpyDeviceToHost, c->stream), "copy flag");
     PM_CUDA(cudaStreamSynchronize(c->stream), "dirichlet");
     c->last_steps = (int64_t)steps_taken;
     if (!dev) {
@@ -614,6 +643,7 @@ int pm_forward_dirichlet(pm_ctx* c, const pm_field* field, double drift_scale, d
         if (exit_step) memcpy(exit_step, h + o, (size_t)total * 4);
         if (n_unexited) *n_unexited = (int64_t)unexited;
     }
+    if (tc_flag) return fail(PM_ETIMEOUT, "a tensor-core wait in the particle kernel timed out");
     return unexited ? PM_WARN_UNEXITED : PM_OK;
 }
 

@@ -1,0 +1,295 @@
+// pm_dirichlet_tc.cuh -- Algorithm 2 (walks to the first exit from the disk)
+// with the velocity sum on the tensor cores, in a persistent kernel.
+//
+// Same per-lane refill as dirichlet_kernel (each lane takes the next unclaimed
+// path as soon as its path exits; one atomic per warp per refill), but the 128
+// lanes of a CTA step together: every Euler step is one CTA-wide matrix
+// product of the lanes' x2 harmonics with the coefficient matrix (see
+// pm_timedep_tc.cuh), so a lane without a path still supplies a row (whose
+// result is ignored).  The CTA leaves when every lane has found the path
+// counter exhausted.
+#pragma once
+#include "pm_timedep_tc.cuh"
+
+namespace pm {
+namespace tdtc {
+
+template <int K>
+struct DirParams {
+    float W[Shape<K>::NP * 32];
+    double ga[kMaxBoundary];
+    double gb[kMaxBoundary];
+    double R, quad, f_const, dt;
+    int32_t n_ang;
+    float drift_dt, s_dt, R2hi, R2lo;
+    const double* x;
+    int64_t n_obs, M, total, max_steps, path_offset;
+    unsigned long long* counter;
+    unsigned long long* n_unexited;
+    unsigned long long* steps;
+    double* g;
+    int32_t* exit_step;
+    double* x_out;
+    uint32_t inst, key0, key1;
+    unsigned* err;
+};
+
+template <int K>
+__device__ __forceinline__ void dir_finish(const DirParams<K>& p, int64_t pid, bool exited, int64_t n,
+                                           const Coord<float>& X1, const Coord<float>& X2)
+{
+    double g = 0.0;
+    if (exited) {
+        const double y1 = X1.full(), y2 = X2.full();
+        const double rr = sqrt(y1 * y1 + y2 * y2);
+        const double c1 = y1 / rr, s1 = y2 / rr;
+        g = p.quad * (p.R * p.R) * (c1 * c1 - s1 * s1);
+        double cm = 1.0, sm = 0.0;
+        for (int m = 1; m <= p.n_ang; ++m) {
+            const double cn = cm * c1 - sm * s1;
+            sm = sm * c1 + cm * s1;
+            cm = cn;
+            g += p.ga[m - 1] * cm + p.gb[m - 1] * sm;
+        }
+        g -= p.f_const * ((double)n * p.dt);
+    } else {
+        atomicAdd(p.n_unexited, 1ull);
+    }
+    p.g[pid] = g;
+    if (p.exit_step) p.exit_step[pid] = exited ? (int32_t)n : -1;
+    if (p.x_out) { p.x_out[2 * pid] = X1.full(); p.x_out[2 * pid + 1] = X2.full(); }
+}
+
+template <int K>
+__global__ void __launch_bounds__(128, 4) dirichlet_tc_kernel(const __grid_constant__ DirParams<K> p)
+{
+    using S = Shape<K>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* A_hi = smem;
+    uint8_t* A_lo = smem + S::A_BYTES;
+    uint8_t* B_hi = smem + 2 * S::A_BYTES;
+    uint8_t* B_lo = B_hi + S::B_BYTES;
+    uint64_t* bar = (uint64_t*)(B_lo + S::B_BYTES);
+    uint32_t* tmem_slot = (uint32_t*)(bar + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const unsigned full = 0xffffffffu;
+    const uint32_t bar_a = tc::smem_u32(bar);
+
+    for (int q = tid; q < S::NP * 8; q += 128) {
+        const int r = q >> 3, c = q & 7;
+        float4 h, l;
+        float* hv = &h.x;
+        float* lv = &l.x;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float w = p.W[r * 32 + 4 * c + e];
+            hv[e] = to_tf32(w);
+            lv[e] = to_tf32(w - hv[e]);
+        }
+        *reinterpret_cast<float4*>(B_hi + sw128(r, c)) = h;
+        *reinterpret_cast<float4*>(B_lo + sw128(r, c)) = l;
+    }
+    for (int c = 0; c < 8; ++c) {
+        *reinterpret_cast<float4*>(A_hi + sw128(tid, c)) = make_float4(0.f, 0.f, 0.f, 0.f);
+        *reinterpret_cast<float4*>(A_lo + sw128(tid, c)) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (tid == 0) {
+        tc::mbar_init(bar_a, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(tmem_slot)),
+                     "r"(64u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t t_row = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint64_t dA_hi = tc::smem_desc_sw128(tc::smem_u32(A_hi)), dA_lo = tc::smem_desc_sw128(tc::smem_u32(A_lo));
+    const uint64_t dB_hi = tc::smem_desc_sw128(tc::smem_u32(B_hi)), dB_lo = tc::smem_desc_sw128(tc::smem_u32(B_lo));
+
+    int64_t pid = -1;
+    bool done = false;
+    int64_t n = 0;
+    uint32_t j = 0, i = 0;
+    unsigned long long lane_steps = 0;
+    uint32_t phase = 0;
+    bool failed = false;
+    Coord<float> X1, X2;
+    X1.set(0.0);
+    X2.set(0.0);
+
+    for (;;) {
+        // Refill (per warp).
+        const bool need = !done && pid < 0;
+        const unsigned mask = __ballot_sync(full, need);
+        if (mask) {
+            unsigned long long base = 0;
+            const int leader = __ffs(mask) - 1;
+            if (lane == leader) base = atomicAdd(p.counter, (unsigned long long)__popc(mask));
+            base = __shfl_sync(full, base, leader);
+            if (need) {
+                const int64_t cand = (int64_t)base + __popc(mask & ((1u << lane) - 1u));
+                if (cand < p.total) {
+                    pid = cand;
+                    j = (uint32_t)(cand / p.M);
+                    i = (uint32_t)(cand - (int64_t)j * p.M + p.path_offset);
+                    X1.set(p.x[2 * (int64_t)j]);
+                    X2.set(p.x[2 * (int64_t)j + 1]);
+                    n = 0;
+                    if (radial_excess(X1, X2, p.R2hi, p.R2lo) >= 0.f) {  // starts outside
+                        dir_finish(p, pid, true, 0, X1, X2);
+                        pid = -1;
+                    }
+                } else {
+                    done = true;
+                }
+            }
+        }
+        // Leave when every lane of the CTA is out of work; step while any lane has a path.
+        if (!__syncthreads_or(pid >= 0)) {
+            if (__syncthreads_and(done)) break;
+            continue;
+        }
+        u32x4 r{0, 0, 0, 0};
+        if (pid >= 0) r = philox4x32_10(u32x4{(uint32_t)(n >> 1), i, j, p.inst}, p.key0, p.key1);
+#pragma unroll 1
+        for (int half = 0; half < 2; ++half) {
+            float xi1, xi2;
+            box_muller<float>(half ? r.z : r.x, half ? r.w : r.y, xi1, xi2);
+            {
+                float C2[K + 1], S2[K + 1];
+                fourier_powers<float, K>(X2.val(), C2, S2);
+                float a[32];
+#pragma unroll
+                for (int q = 0; q < 32; ++q) a[q] = 0.f;
+#pragma unroll
+                for (int q = 1; q <= K; ++q) { a[q - 1] = S2[q]; a[K + q - 1] = C2[q]; }
+                a[2 * K] = 1.f;
+#pragma unroll
+                for (int c = 0; c < (S::KD + 3) / 4; ++c) {
+                    float4 h, l;
+                    h.x = to_tf32(a[4 * c]);     l.x = to_tf32(a[4 * c] - h.x);
+                    h.y = to_tf32(a[4 * c + 1]); l.y = to_tf32(a[4 * c + 1] - h.y);
+                    h.z = to_tf32(a[4 * c + 2]); l.z = to_tf32(a[4 * c + 2] - h.z);
+                    h.w = to_tf32(a[4 * c + 3]); l.w = to_tf32(a[4 * c + 3] - h.w);
+                    *reinterpret_cast<float4*>(A_hi + sw128(tid, c)) = h;
+                    *reinterpret_cast<float4*>(A_lo + sw128(tid, c)) = l;
+                }
+            }
+            float C1[K + 1], S1[K + 1];
+            fourier_powers<float, K>(X1.val(), C1, S1);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+            if (tid == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+                for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, dA_hi + 2 * k, dB_hi + 2 * k, k > 0 ? 1u : 0u);
+#pragma unroll
+                for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, dA_lo + 2 * k, dB_hi + 2 * k, 1u);
+#pragma unroll
+                for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, dA_hi + 2 * k, dB_lo + 2 * k, 1u);
+                tc::mma_commit(bar_a);
+            }
+            const bool ok = tc::mbar_wait(bar_a, phase);
+            phase ^= 1u;
+            if (__syncthreads_or(!ok)) { failed = true; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            float acc[S::NP];
+#pragma unroll
+            for (int c0 = 0; c0 < S::NP; c0 += 16) tmem_ld16(t_row + (uint32_t)c0, acc + c0);
+            float v1 = acc[0], v2 = 0.f;
+#pragma unroll
+            for (int m = 1; m <= K; ++m) {
+                v1 = fmaf(C1[m], acc[m], fmaf(S1[m], acc[K + m], v1));
+                v2 = fmaf(C1[m], acc[2 * K + m], fmaf(S1[m], acc[3 * K + m], v2));
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            if (pid >= 0) {
+                em_update<float>(X1, v1, p.drift_dt, p.s_dt, xi1);
+                em_update<float>(X2, v2, p.drift_dt, p.s_dt, xi2);
+                ++n;
+                const bool exited = radial_excess(X1, X2, p.R2hi, p.R2lo) >= 0.f;
+                if (exited || n >= p.max_steps) {
+                    dir_finish(p, pid, exited, n, X1, X2);
+                    lane_steps += (unsigned long long)n;
+                    pid = -1;
+                }
+            }
+        }
+        if (failed) break;
+    }
+    if (failed && tid == 0) atomicExch(p.err, 1u);
+    if (lane_steps) atomicAdd(p.steps, lane_steps);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64u) : "memory");
+    }
+}
+
+template <int K>
+cudaError_t launch_dirichlet_tc(const DirichletLaunch& L, unsigned* err, cudaStream_t stream)
+{
+    using S = Shape<K>;
+    DirParams<K> p;
+    build_W<K>(L.coef, p.W);
+    for (int m = 0; m < kMaxBoundary; ++m) {
+        p.ga[m] = m < L.n_ang ? L.ga[m] : 0.0;
+        p.gb[m] = m < L.n_ang ? L.gb[m] : 0.0;
+    }
+    p.R = L.R;
+    p.quad = L.quad;
+    p.f_const = L.f_const;
+    p.dt = L.dt;
+    p.n_ang = L.n_ang;
+    p.drift_dt = (float)(L.drift_scale * L.dt);
+    p.s_dt = (float)L.s_dt;
+    const double R2 = L.R * L.R;
+    p.R2hi = (float)R2;
+    p.R2lo = (float)(R2 - (double)p.R2hi);
+    p.x = L.x;
+    p.n_obs = L.n_obs;
+    p.M = L.M;
+    p.total = L.n_obs * L.M;
+    p.max_steps = L.max_steps;
+    p.path_offset = L.path_offset;
+    p.counter = L.counter;
+    p.n_unexited = L.n_unexited;
+    p.steps = L.steps;
+    p.g = L.g;
+    p.exit_step = L.exit_step;
+    p.x_out = L.x_out;
+    p.inst = L.inst;
+    p.key0 = L.key0;
+    p.key1 = L.key1;
+    p.err = err;
+    cudaError_t e = cudaFuncSetAttribute(dirichlet_tc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+    if (e != cudaSuccess) return e;
+    dirichlet_tc_kernel<K><<<L.grid, 128, S::SMEM, stream>>>(p);
+    return cudaGetLastError();
+}
+
+template <int K>
+int dirichlet_tc_blocks_per_sm()
+{
+    using S = Shape<K>;
+    int nb = 0;
+    cudaFuncSetAttribute(dirichlet_tc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dirichlet_tc_kernel<K>, 128, S::SMEM) != cudaSuccess) return 1;
+    return nb > 0 ? nb : 1;
+}
+
+}  // namespace tdtc
+}  // namespace pm
+
+#define PM_INSTANTIATE_DIR_TC(K)                                                                                 \
+    template cudaError_t pm::tdtc::launch_dirichlet_tc<K>(const pm::DirichletLaunch&, unsigned*, cudaStream_t); \
+    template int pm::tdtc::dirichlet_tc_blocks_per_sm<K>();

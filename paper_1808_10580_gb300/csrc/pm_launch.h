@@ -157,6 +157,8 @@ cudaError_t launch_reduce_rows(const BatchInstDev* inst, int B, int max_obs, con
 // *err is set when a bounded wait expires.
 namespace tdtc {
 template <int K> cudaError_t launch_timedep_tc(const TimedepLaunch& L, unsigned* err, cudaStream_t s);
+template <int K> cudaError_t launch_dirichlet_tc(const DirichletLaunch& L, unsigned* err, cudaStream_t s);
+template <int K> int dirichlet_tc_blocks_per_sm();
 }
 
 }  // namespace pm

@@ -79,3 +79,28 @@ def test_repeatable(c):
     a = _gpu.timedep(c, w, pm.PM_FP32 | pm.PM_TENSOR)
     b = _gpu.timedep(c, w, pm.PM_FP32 | pm.PM_TENSOR)
     assert np.array_equal(a[0], b[0])
+
+
+def test_dirichlet_zero_drift_exit_steps(c, orc):
+    from tests.test_gpu_dirichlet import zero_drift_workload
+    w = zero_drift_workload(M=2000)
+    r = _gpu.dirichlet(c, w, pm.PM_FP32 | pm.PM_TENSOR, want_paths=True)
+    g, st = orc.dirichlet_paths(0, np.zeros(0), 0.0, w.kappa, w.g, w.x, w.dt, w.max_steps, w.seed, npaths=w.M)
+    assert np.mean(r["steps"] == st) >= 0.999
+    rm, rv, rse = orc.estimate(g)
+    assert np.all(np.abs(r["mean"] - rm) <= 3 * np.sqrt(2) * rse)
+
+
+def test_dirichlet_drift_full_size(c, orc):
+    w = inputs.dirichlet_disk_k10()
+    r = _gpu.dirichlet(c, w, pm.PM_FP32 | pm.PM_TENSOR, want_paths=True)
+    s = _gpu.dirichlet(c, w, pm.PM_FP32)
+    assert r["rc"] == 0 and r["unexited"] == 0
+    P = 3
+    go, so = orc.dirichlet_paths(w.K, w.u, w.drift_scale, w.kappa, w.g, w.x, w.dt, w.max_steps, w.seed, npaths=P)
+    d = (r["g"][:, :P] - go).ravel()
+    assert abs(d.mean()) <= 5 * d.std(ddof=1) / np.sqrt(d.size)
+    early = so < 2000
+    assert np.mean(r["steps"][:, :P][early] == so[early]) >= 0.99
+    se = np.sqrt((r["var"] + s["var"]) / w.M)
+    assert np.mean(np.abs(r["mean"] - s["mean"]) <= 5 * se) >= 0.98
