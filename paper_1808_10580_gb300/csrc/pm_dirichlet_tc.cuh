@@ -113,6 +113,9 @@ __global__ void __launch_bounds__(128, 4) dirichlet_tc_kernel(const __grid_const
     const uint64_t dA_hi = tc::smem_desc_sw128(tc::smem_u32(A_hi)), dA_lo = tc::smem_desc_sw128(tc::smem_u32(A_lo));
     const uint64_t dB_hi = tc::smem_desc_sw128(tc::smem_u32(B_hi)), dB_lo = tc::smem_desc_sw128(tc::smem_u32(B_lo));
 
+    uint32_t row_off[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) row_off[c] = sw128(tid, c);
     int64_t pid = -1;
     bool done = false;
     int64_t n = 0;
@@ -171,16 +174,7 @@ __global__ void __launch_bounds__(128, 4) dirichlet_tc_kernel(const __grid_const
 #pragma unroll
                 for (int q = 1; q <= K; ++q) { a[q - 1] = S2[q]; a[K + q - 1] = C2[q]; }
                 a[2 * K] = 1.f;
-#pragma unroll
-                for (int c = 0; c < (S::KD + 3) / 4; ++c) {
-                    float4 h, l;
-                    h.x = to_tf32(a[4 * c]);     l.x = to_tf32(a[4 * c] - h.x);
-                    h.y = to_tf32(a[4 * c + 1]); l.y = to_tf32(a[4 * c + 1] - h.y);
-                    h.z = to_tf32(a[4 * c + 2]); l.z = to_tf32(a[4 * c + 2] - h.z);
-                    h.w = to_tf32(a[4 * c + 3]); l.w = to_tf32(a[4 * c + 3] - h.w);
-                    *reinterpret_cast<float4*>(A_hi + sw128(tid, c)) = h;
-                    *reinterpret_cast<float4*>(A_lo + sw128(tid, c)) = l;
-                }
+                write_row<S::KD>(A_hi, A_lo, row_off, a);
             }
             float C1[K + 1], S1[K + 1];
             fourier_powers<float, K>(X1.val(), C1, S1);
@@ -202,8 +196,7 @@ __global__ void __launch_bounds__(128, 4) dirichlet_tc_kernel(const __grid_const
             if (__syncthreads_or(!ok)) { failed = true; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             float acc[S::NP];
-#pragma unroll
-            for (int c0 = 0; c0 < S::NP; c0 += 16) tmem_ld16(t_row + (uint32_t)c0, acc + c0);
+            tmem_ld_row<S::NP>(t_row, acc);
             float v1 = acc[0], v2 = 0.f;
 #pragma unroll
             for (int m = 1; m <= K; ++m) {

@@ -7,10 +7,11 @@
 // For the 128 particles of a CTA this is one matrix product per Euler step,
 //   P[128 x (4K+1)] = A[128 x (2K+1)] . W[(2K+1) x (4K+1)],
 // issued as tcgen05.mma kind::tf32 with the FP32 accumulator in tensor memory.
-// TF32 keeps 10 mantissa bits, so every operand is split x = hi + lo (hi = x
-// rounded to TF32, lo = (x - hi) rounded to TF32) and three products
-// hi.hi + lo.hi + hi.lo are accumulated (the lo.lo term, ~2^-22 relative, is
-// dropped): about float accuracy.  The remaining 4K+1 FMAs per particle, the
+// TF32 keeps 10 mantissa bits, so every operand is split x = hi + lo (the
+// coefficients: hi = x rounded to TF32, lo = (x - hi) rounded; the particle
+// harmonics, every step: hi = x with its low 13 bits cleared, lo = x - hi) and
+// three products hi.hi + lo.hi + hi.lo are accumulated (the lo.lo term and
+// the reduction of lo, ~2^-20 relative, are dropped): close to float accuracy.  The remaining 4K+1 FMAs per particle, the
 // harmonics, the noise and the Euler step stay on the FP32 pipes.
 //
 // Per step: every thread writes its particle's row of A (hi and lo) into a
@@ -93,6 +94,76 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v)
     for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
 }
 
+// hi = a with its 13 low mantissa bits cleared (exact in TF32), lo = a - hi
+// (exact in float); the tensor core reduces lo to TF32 itself, an error of at
+// most 2^-20 |a|.
+__device__ __forceinline__ void split_tf32(float a, float& hi, float& lo)
+{
+    hi = __uint_as_float(__float_as_uint(a) & 0xFFFFE000u);
+    lo = a - hi;
+}
+
+// All NP accumulator columns of this thread's lane, loads and one wait in a
+// single statement (the outputs are valid when it ends).
+template <int NP> __device__ __forceinline__ void tmem_ld_row(uint32_t taddr, float* v);
+
+template <> __device__ __forceinline__ void tmem_ld_row<32>(uint32_t taddr, float* v)
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+template <> __device__ __forceinline__ void tmem_ld_row<48>(uint32_t taddr, float* v)
+{
+    uint32_t r[48];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%48];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47}, [%49];\n"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47])
+        : "r"(taddr), "r"(taddr + 32u)
+        : "memory");
+#pragma unroll
+    for (int q = 0; q < 48; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+template <> __device__ __forceinline__ void tmem_ld_row<64>(uint32_t taddr, float* v)
+{
+    uint32_t r[64];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%64];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%65];\n"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+        : "r"(taddr), "r"(taddr + 32u)
+        : "memory");
+#pragma unroll
+    for (int q = 0; q < 64; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+// This thread's row of the particle tiles: harmonics a[0..KD) split into hi / lo.
+template <int KD>
+__device__ __forceinline__ void write_row(uint8_t* A_hi, uint8_t* A_lo, const uint32_t (&off)[8], const float (&a)[32])
+{
+#pragma unroll
+    for (int c = 0; c < (KD + 3) / 4; ++c) {
+        float4 h, l;
+        split_tf32(a[4 * c], h.x, l.x);
+        split_tf32(a[4 * c + 1], h.y, l.y);
+        split_tf32(a[4 * c + 2], h.z, l.z);
+        split_tf32(a[4 * c + 3], h.w, l.w);
+        *reinterpret_cast<float4*>(A_hi + off[c]) = h;
+        *reinterpret_cast<float4*>(A_lo + off[c]) = l;
+    }
+}
+
 template <int K>
 __global__ void __launch_bounds__(128, 4) timedep_tc_kernel(const __grid_constant__ Params<K> p)
 {
@@ -146,6 +217,9 @@ __global__ void __launch_bounds__(128, 4) timedep_tc_kernel(const __grid_constan
     const uint64_t dA_hi = tc::smem_desc_sw128(tc::smem_u32(A_hi)), dA_lo = tc::smem_desc_sw128(tc::smem_u32(A_lo));
     const uint64_t dB_hi = tc::smem_desc_sw128(tc::smem_u32(B_hi)), dB_lo = tc::smem_desc_sw128(tc::smem_u32(B_lo));
 
+    uint32_t row_off[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) row_off[c] = sw128(tid, c);
     const int slot = blockIdx.x / p.chunks;
     const int cidx = blockIdx.x - slot * p.chunks;
     const int j = p.order ? p.order[slot] : slot;
@@ -175,16 +249,7 @@ __global__ void __launch_bounds__(128, 4) timedep_tc_kernel(const __grid_constan
 #pragma unroll
             for (int q = 1; q <= K; ++q) { a[q - 1] = S2[q]; a[K + q - 1] = C2[q]; }
             a[2 * K] = 1.f;
-#pragma unroll
-            for (int c = 0; c < (S::KD + 3) / 4; ++c) {
-                float4 h, l;
-                h.x = to_tf32(a[4 * c]);     l.x = to_tf32(a[4 * c] - h.x);
-                h.y = to_tf32(a[4 * c + 1]); l.y = to_tf32(a[4 * c + 1] - h.y);
-                h.z = to_tf32(a[4 * c + 2]); l.z = to_tf32(a[4 * c + 2] - h.z);
-                h.w = to_tf32(a[4 * c + 3]); l.w = to_tf32(a[4 * c + 3] - h.w);
-                *reinterpret_cast<float4*>(A_hi + sw128(tid, c)) = h;
-                *reinterpret_cast<float4*>(A_lo + sw128(tid, c)) = l;
-            }
+            write_row<S::KD>(A_hi, A_lo, row_off, a);
         }
         // x1 harmonics stay in registers.
         float C1[K + 1], S1[K + 1];
@@ -206,8 +271,7 @@ __global__ void __launch_bounds__(128, 4) timedep_tc_kernel(const __grid_constan
         if (__syncthreads_or(!ok)) { failed = true; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         float acc[S::NP];
-#pragma unroll
-        for (int c0 = 0; c0 < S::NP; c0 += 16) tmem_ld16(t_row + (uint32_t)c0, acc + c0);
+        tmem_ld_row<S::NP>(t_row, acc);
         float v1 = acc[0], v2 = 0.f;
 #pragma unroll
         for (int m = 1; m <= K; ++m) {
