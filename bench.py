@@ -368,8 +368,9 @@ def run_aux(args):
         var = torch.empty_like(mean)
 
         def step():
-            pm.pm_forward_batched(ctx, batch, pm.PM_FP32, mean, var)
-        name, cfg = f"batched_{args.B}x100obs_M{args.M or 4096}", {"B": args.B, "rows": row}
+            pm.pm_forward_batched(ctx, batch, pm.PM_FP32 | (pm.PM_TENSOR if args.tensor else 0), mean, var)
+        name, cfg = f"batched_{args.B}x100obs_M{args.M or 4096}", {"B": args.B, "rows": row,
+                                                                    "tensor_cores": bool(args.tensor)}
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize(dev)

@@ -28,6 +28,28 @@ cudaError_t launch_batched_K(int K, const BatchKernelParams& p, int grid, cudaSt
     return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_batched_tc_K(int K, const BatchKernelParams& p, int grid, cudaStream_t s)
+{
+    switch (K) {
+#define PM_CASE(k) case k: return tdtc::launch_batched_tc<k>(p, grid, s);
+        PM_CASE(4) PM_CASE(5) PM_CASE(6) PM_CASE(8) PM_CASE(10) PM_CASE(12)
+#undef PM_CASE
+    }
+    return cudaErrorInvalidValue;
+}
+
+int blocks_per_sm_tc_K(int K)
+{
+    switch (K) {
+#define PM_CASE(k) case k: return tdtc::batched_tc_blocks_per_sm<k>();
+        PM_CASE(4) PM_CASE(5) PM_CASE(6) PM_CASE(8) PM_CASE(10) PM_CASE(12)
+#undef PM_CASE
+    }
+    return 1;
+}
+
+bool tc_supported(int K) { return K == 4 || K == 5 || K == 6 || K == 8 || K == 10 || K == 12; }
+
 int blocks_per_sm_K(int K)
 {
     switch (K) {
@@ -141,7 +163,7 @@ extern "C" int pm_forward_batched(pm_ctx* c, const pm_batch* bt, uint32_t flags,
         w.inst = bp.take<BatchInstDev>((size_t)B);
         w.tables = bp.take<float>((size_t)B * TS);
         w.rows = bp.take<RowRec>((size_t)n_rows);
-        w.ctr = bp.take<unsigned long long>((size_t)B + 3);  // next_path[B], unexited, error flag, steps
+        w.ctr = bp.take<unsigned long long>((size_t)B + 4);  // next_path[B], unexited, error flag, steps, tc flag
         w.g = bp.take<double>((size_t)total);
         if (!dev) {
             w.U = bp.take<double>((size_t)(B * std::max<int64_t>(NU, 1)));
@@ -164,7 +186,7 @@ extern "C" int pm_forward_batched(pm_ctx* c, const pm_batch* bt, uint32_t flags,
             h.xt = bp.take<double>((size_t)(3 * n_rows));
             h.out = bp.take<double>((size_t)(2 * n_rows));
         }
-        h.flags = bp.take<unsigned long long>(3);
+        h.flags = bp.take<unsigned long long>(4);
         return h;
     };
     Bump hprobe(nullptr);
@@ -226,9 +248,11 @@ extern "C" int pm_forward_batched(pm_ctx* c, const pm_batch* bt, uint32_t flags,
     p.next_path = W.ctr;
     p.n_unexited = W.ctr + B;
     p.steps = W.ctr + B + 2;
+    p.tc_err = (unsigned*)(W.ctr + B + 3);
+    const bool use_tc = (flags & PM_TENSOR) && tc_supported(K);
     p.g = W.g;
     p.B = B;
-    const int per_sm = blocks_per_sm_K(K);  // also sets the kernel's shared-memory attribute
+    const int per_sm = use_tc ? blocks_per_sm_tc_K(K) : blocks_per_sm_K(K);  // also sets the shared-memory attribute
     int64_t grid = (int64_t)per_sm * c->sm_count;
     const int64_t need = (total + kBatchWarpsHost * 32 - 1) / (kBatchWarpsHost * 32);
     grid = std::max<int64_t>(1, std::min(grid, need));
@@ -245,10 +269,10 @@ extern "C" int pm_forward_batched(pm_ctx* c, const pm_batch* bt, uint32_t flags,
         if (e == cudaSuccess && !dev && NU > 0)
             e = cudaMemcpyAsync(W.U, Hs.U, (size_t)(B * NU) * 8, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess && !dev) e = cudaMemcpyAsync(W.xt, Hs.xt, (size_t)n_rows * 24, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(W.ctr, 0, sizeof(unsigned long long) * ((size_t)B + 3), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(W.ctr, 0, sizeof(unsigned long long) * ((size_t)B + 4), s);
         if (e == cudaSuccess) e = launch_stage_tables(W.inst, B, K, W.tables, s);
         if (e == cudaSuccess) e = launch_prep_rows(W.inst, B, (int)max_obs, dx, any_td ? dt_ : dx, W.rows, derr, s);
-        if (e == cudaSuccess) e = launch_batched_K(K, p, (int)grid, s);
+        if (e == cudaSuccess) e = use_tc ? launch_batched_tc_K(K, p, (int)grid, s) : launch_batched_K(K, p, (int)grid, s);
         if (e == cudaSuccess) e = launch_reduce_rows(W.inst, B, (int)max_obs, W.g, dmean, dvar, s);
         if (e == cudaSuccess && !dev) {
             e = cudaMemcpyAsync(Hs.out, W.mean, (size_t)n_rows * 8, cudaMemcpyDeviceToHost, s);
@@ -256,7 +280,7 @@ extern "C" int pm_forward_batched(pm_ctx* c, const pm_batch* bt, uint32_t flags,
         }
         if (e == cudaSuccess && dev && n_unexited)
             e = cudaMemcpyAsync(n_unexited, W.ctr + B, 8, cudaMemcpyDeviceToDevice, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(Hs.flags, W.ctr + B, 24, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(Hs.flags, W.ctr + B, 32, cudaMemcpyDeviceToHost, s);
         return e;
     };
     // prep_rows reads t only for time-dependent instances; when there are none
@@ -269,6 +293,7 @@ extern "C" int pm_forward_batched(pm_ctx* c, const pm_batch* bt, uint32_t flags,
     key = fnv_val(key, (const void*)bt->x); key = fnv_val(key, (const void*)bt->t);
     key = fnv_val(key, (const void*)mean); key = fnv_val(key, (const void*)var); key = fnv_val(key, (const void*)n_unexited);
     key = fnv(key, &p, sizeof p);
+    key = fnv_val(key, use_tc);
     for (int b = 0; b < B; ++b) {
         const pm_instance& I = bt->inst[b];
         key = fnv_val(key, I.kind); key = fnv_val(key, I.row0); key = fnv_val(key, I.n_obs); key = fnv_val(key, I.M);
@@ -305,5 +330,6 @@ extern "C" int pm_forward_batched(pm_ctx* c, const pm_batch* bt, uint32_t flags,
     }
     if (Hs.flags[1] & 0xffffffffull)
         return fail(PM_EINVAL, "observation points or times are not finite, a time is negative, or a step count exceeds 2^31");
+    if (Hs.flags[3] & 0xffffffffull) return fail(PM_ETIMEOUT, "a tensor-core wait in the batched kernel timed out");
     return Hs.flags[0] ? PM_WARN_UNEXITED : PM_OK;
 }

@@ -1,0 +1,301 @@
+// pm_batched_tc.cuh -- the batched persistent map (many instances u_b, mixed
+// time-dependent and Dirichlet) with the velocity sum on the tensor cores.
+//
+// A CTA works on one instance at a time: that instance's coefficient matrix
+// W_b is the B operand of the per-step MMA (see pm_timedep_tc.cuh), kept as
+// TF32 hi / lo tiles in shared memory.  Its lanes take paths of the instance
+// from the instance's path counter (one atomic per warp per refill) and step
+// together; when the instance has no unclaimed paths left and every lane of
+// the CTA has finished, the CTA moves to the next instance with work and
+// rebuilds its tiles.  Results are stored per path, so the estimates do not
+// depend on which CTA ran which path.
+#pragma once
+#include "pm_batched.cuh"
+#include "pm_timedep_tc.cuh"
+
+namespace pm {
+namespace tdtc {
+
+// Entry W[k][nc] of the coefficient matrix from the product-basis table
+// tab[(m (K+1) + n) 8 + q] (e0..e3, f0..f3): A column k holds S2_{k+1}
+// (k < K), C2_{k-K+1} (K <= k < 2K) or the constant 1 (k = 2K); accumulator
+// column nc is P1c(nc) for nc <= K, P1s(nc-K), P2c(nc-2K), P2s(nc-3K) above.
+template <int K>
+__device__ __forceinline__ float w_entry(const float* tab, int nc, int k)
+{
+    int n = 0, type = 0;  // type 0: S2_n, 1: C2_n, 2: constant
+    if (k < K) { n = k + 1; type = 0; }
+    else if (k < 2 * K) { n = k - K + 1; type = 1; }
+    else if (k == 2 * K) { type = 2; }
+    else return 0.f;
+    auto T = [&](int m, int nn, int q) { return tab[(m * (K + 1) + nn) * 8 + q]; };
+    if (nc <= K) {  // P1c(m), m = nc (m = 0 included)
+        const int m = nc;
+        return type == 0 ? T(m, n, 0) : type == 1 ? T(m, n, 1) : 0.f;
+    }
+    if (nc <= 2 * K) {  // P1s(m)
+        const int m = nc - K;
+        return type == 0 ? T(m, n, 2) : type == 1 ? T(m, n, 3) : 0.f;
+    }
+    if (nc <= 3 * K) {  // P2c(m)
+        const int m = nc - 2 * K;
+        return type == 1 ? T(m, n, 4) : type == 0 ? T(m, n, 5) : T(m, 0, 4);
+    }
+    if (nc <= 4 * K) {  // P2s(m)
+        const int m = nc - 3 * K;
+        return type == 1 ? T(m, n, 6) : type == 0 ? T(m, n, 7) : T(m, 0, 6);
+    }
+    return 0.f;
+}
+
+template <int K>
+__global__ void __launch_bounds__(128, 4) batched_tc_kernel(const __grid_constant__ BatchKernelParams p)
+{
+    using S = Shape<K>;
+    constexpr int TS = table_size(K);
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* A_hi = smem;
+    uint8_t* A_lo = smem + S::A_BYTES;
+    uint8_t* B_hi = smem + 2 * S::A_BYTES;
+    uint8_t* B_lo = B_hi + S::B_BYTES;
+    uint64_t* bar = (uint64_t*)(B_lo + S::B_BYTES);
+    uint32_t* tmem_slot = (uint32_t*)(bar + 1);
+    int* s_next = (int*)(tmem_slot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const unsigned full = 0xffffffffu;
+    const uint32_t bar_a = tc::smem_u32(bar);
+
+    for (int c = 0; c < 8; ++c) {
+        *reinterpret_cast<float4*>(A_hi + sw128(tid, c)) = make_float4(0.f, 0.f, 0.f, 0.f);
+        *reinterpret_cast<float4*>(A_lo + sw128(tid, c)) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (tid == 0) {
+        tc::mbar_init(bar_a, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(tmem_slot)),
+                     "r"(64u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t t_row = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint64_t dA_hi = tc::smem_desc_sw128(tc::smem_u32(A_hi)), dA_lo = tc::smem_desc_sw128(tc::smem_u32(A_lo));
+    const uint64_t dB_hi = tc::smem_desc_sw128(tc::smem_u32(B_hi)), dB_lo = tc::smem_desc_sw128(tc::smem_u32(B_lo));
+    uint32_t row_off[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) row_off[c] = sw128(tid, c);
+
+    int b = (int)(((long long)blockIdx.x * p.B) / gridDim.x);  // spread CTAs over the instances
+    bool have_inst = false;
+    bool exhausted = true;  // warp-uniform: no unclaimed paths left in b for this warp
+    BatchInstDev I{};
+    float s_dt = 0.f, drift_dt = 0.f, dt = 0.f;
+    int64_t pid = -1, n = 0;
+    int32_t N = 0;
+    float h_last = 0.f, s_last = 0.f;
+    uint32_t j = 0, i = 0;
+    unsigned long long lane_steps = 0;
+    uint32_t phase = 0;
+    bool failed = false;
+    Coord<float> X1, X2;
+    X1.set(0.0);
+    X2.set(0.0);
+
+    for (;;) {
+        // ---- refill idle lanes of this warp from the CTA's instance --------------
+        if (!exhausted) {
+            const bool need = pid < 0;
+            const unsigned mask = __ballot_sync(full, need);
+            if (mask) {
+                unsigned long long base = 0;
+                const int leader = __ffs(mask) - 1;
+                if (lane == leader) base = atomicAdd(&p.next_path[b], (unsigned long long)__popc(mask));
+                base = __shfl_sync(full, base, leader);
+                if ((int64_t)(base + __popc(mask)) >= I.n_paths) exhausted = true;
+                if (need) {
+                    const int64_t cand = (int64_t)base + __popc(mask & ((1u << lane) - 1u));
+                    if (cand < I.n_paths) {
+                        pid = cand;
+                        j = (uint32_t)(cand / I.M);
+                        i = (uint32_t)(cand - (int64_t)j * I.M);
+                        const RowRec rr = p.rows[I.row0 + j];
+                        X1.set(rr.x1);
+                        X2.set(rr.x2);
+                        n = 0;
+                        N = rr.nsteps;
+                        h_last = (float)rr.h_last;
+                        s_last = (float)rr.s_last;
+                        if (I.kind == 0 && N == 0) {
+                            p.g[I.path_base + pid] = theta0_eval(p.th, X1, X2);
+                            pid = -1;
+                        } else if (I.kind == 1 && radial_excess(X1, X2, p.R2hi, p.R2lo) >= 0.f) {
+                            p.g[I.path_base + pid] =
+                                boundary_value(p.ga, p.gb, p.n_ang, p.R, p.quad, X1.full(), X2.full());
+                            pid = -1;
+                        }
+                    }
+                }
+            }
+        }
+        // ---- no lane of the CTA has a path: refill again, or change instance ------
+        if (!__syncthreads_or(pid >= 0)) {
+            if (!__syncthreads_and(exhausted)) continue;
+            if (warp == 0) {
+                int found = -1;
+                const int start = have_inst ? b + 1 : b;
+                for (int base = 0; base < p.B && found < 0; base += 32) {
+                    const int q = base + lane;
+                    bool ok = false;
+                    int cand_b = 0;
+                    if (q < p.B) {
+                        cand_b = (start + q) % p.B;
+                        ok = (int64_t)(*(volatile unsigned long long*)&p.next_path[cand_b]) < p.inst[cand_b].n_paths;
+                    }
+                    const unsigned m2 = __ballot_sync(full, ok);
+                    if (m2) found = __shfl_sync(full, cand_b, __ffs(m2) - 1);
+                }
+                if (lane == 0) *s_next = found;
+            }
+            __syncthreads();
+            const int found = *s_next;
+            if (found < 0) break;
+            b = found;
+            I = p.inst[b];
+            have_inst = true;
+            exhausted = false;
+            dt = (float)I.dt;
+            s_dt = (float)sqrt(2.0 * I.kappa * I.dt);
+            drift_dt = (float)(I.drift_scale * I.dt);
+            // coefficient tiles of the new instance (the previous MMA has completed)
+            const float* tab = p.tables + (size_t)b * TS;
+            for (int q = tid; q < S::NP * 32; q += 128) {
+                const int nc = q >> 5, k = q & 31;
+                const float w = w_entry<K>(tab, nc, k);
+                const float hi = to_tf32(w);
+                const uint32_t off = sw128(nc, k >> 2) + 4u * (uint32_t)(k & 3);
+                *reinterpret_cast<float*>(B_hi + off) = hi;
+                *reinterpret_cast<float*>(B_lo + off) = to_tf32(w - hi);
+            }
+            __syncthreads();
+            continue;
+        }
+
+        // ---- two Euler steps per Philox call, one MMA per step ----------------------
+        u32x4 r{0, 0, 0, 0};
+        if (pid >= 0) r = philox4x32_10(u32x4{(uint32_t)(n >> 1), i, j, I.stream}, I.key0, I.key1);
+#pragma unroll 1
+        for (int half = 0; half < 2; ++half) {
+            float xi1, xi2;
+            box_muller<float>(half ? r.z : r.x, half ? r.w : r.y, xi1, xi2);
+            {
+                float C2[K + 1], S2[K + 1];
+                fourier_powers<float, K>(X2.val(), C2, S2);
+                float a[32];
+#pragma unroll
+                for (int q = 0; q < 32; ++q) a[q] = 0.f;
+#pragma unroll
+                for (int q = 1; q <= K; ++q) { a[q - 1] = S2[q]; a[K + q - 1] = C2[q]; }
+                a[2 * K] = 1.f;
+                write_row<S::KD>(A_hi, A_lo, row_off, a);
+            }
+            float C1[K + 1], S1[K + 1];
+            fourier_powers<float, K>(X1.val(), C1, S1);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+            if (tid == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+                for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, dA_hi + 2 * k, dB_hi + 2 * k, k > 0 ? 1u : 0u);
+#pragma unroll
+                for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, dA_lo + 2 * k, dB_hi + 2 * k, 1u);
+#pragma unroll
+                for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, dA_hi + 2 * k, dB_lo + 2 * k, 1u);
+                tc::mma_commit(bar_a);
+            }
+            const bool ok = tc::mbar_wait(bar_a, phase);
+            phase ^= 1u;
+            if (__syncthreads_or(!ok)) { failed = true; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            float acc[S::NP];
+            tmem_ld_row<S::NP>(t_row, acc);
+            float v1 = acc[0], v2 = 0.f;
+#pragma unroll
+            for (int m = 1; m <= K; ++m) {
+                v1 = fmaf(C1[m], acc[m], fmaf(S1[m], acc[K + m], v1));
+                v2 = fmaf(C1[m], acc[2 * K + m], fmaf(S1[m], acc[3 * K + m], v2));
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            if (pid < 0) continue;
+            if (I.kind == 0) {
+                const bool last = (n == N - 1);
+                const float h = last ? h_last : dt, s = last ? s_last : s_dt;
+                em_update<float>(X1, v1, h, s, xi1);
+                em_update<float>(X2, v2, h, s, xi2);
+                X1.wrap();
+                X2.wrap();
+                ++n;
+                if (n >= N) {
+                    p.g[I.path_base + pid] = theta0_eval(p.th, X1, X2);
+                    lane_steps += (unsigned long long)n;
+                    pid = -1;
+                }
+            } else {
+                em_update<float>(X1, v1, drift_dt, s_dt, xi1);
+                em_update<float>(X2, v2, drift_dt, s_dt, xi2);
+                ++n;
+                const bool exited = radial_excess(X1, X2, p.R2hi, p.R2lo) >= 0.f;
+                if (exited || n >= I.max_steps) {
+                    double gv = 0.0;
+                    if (exited) gv = boundary_value(p.ga, p.gb, p.n_ang, p.R, p.quad, X1.full(), X2.full()) -
+                                     p.f_const * ((double)n * I.dt);
+                    else atomicAdd(p.n_unexited, 1ull);
+                    p.g[I.path_base + pid] = gv;
+                    lane_steps += (unsigned long long)n;
+                    pid = -1;
+                }
+            }
+        }
+        if (failed) break;
+    }
+    if (failed && tid == 0 && p.tc_err) atomicExch(p.tc_err, 1u);
+    if (lane_steps) atomicAdd(p.steps, lane_steps);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64u) : "memory");
+    }
+}
+
+template <int K>
+cudaError_t launch_batched_tc(const BatchKernelParams& p, int grid, cudaStream_t s)
+{
+    batched_tc_kernel<K><<<grid, 128, Shape<K>::SMEM + 64, s>>>(p);
+    return cudaGetLastError();
+}
+
+// Also sets the kernel's dynamic shared-memory limit (call outside any capture).
+template <int K>
+int batched_tc_blocks_per_sm()
+{
+    int nb = 0;
+    const int smem = Shape<K>::SMEM + 64;
+    cudaFuncSetAttribute(batched_tc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batched_tc_kernel<K>, 128, smem) != cudaSuccess) return 1;
+    return nb > 0 ? nb : 1;
+}
+
+}  // namespace tdtc
+}  // namespace pm
+
+#define PM_INSTANTIATE_BATCHED_TC(K)                                                                        \
+    template cudaError_t pm::tdtc::launch_batched_tc<K>(const pm::BatchKernelParams&, int, cudaStream_t); \
+    template int pm::tdtc::batched_tc_blocks_per_sm<K>();

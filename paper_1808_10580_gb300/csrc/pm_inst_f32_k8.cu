@@ -1,8 +1,10 @@
 // Instantiations of the particle kernels: float paths, K in {8}.
 #include "pm_batched.cuh"
 #include "pm_dirichlet_tc.cuh"
+#include "pm_batched_tc.cuh"
 
 PM_INSTANTIATE(float, 8)
 PM_INSTANTIATE_BATCHED(8)
 PM_INSTANTIATE_TC(8)
 PM_INSTANTIATE_DIR_TC(8)
+PM_INSTANTIATE_BATCHED_TC(8)

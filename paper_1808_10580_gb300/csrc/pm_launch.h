@@ -138,6 +138,7 @@ struct BatchKernelParams {
     unsigned long long* n_unexited;
     unsigned long long* steps;         // total Euler steps taken (all paths)
     double* g;                         // per-path values
+    unsigned* tc_err;                  // set when a tensor-core wait expires (tensor-core kernel)
     int32_t B;
 };
 
@@ -159,6 +160,8 @@ namespace tdtc {
 template <int K> cudaError_t launch_timedep_tc(const TimedepLaunch& L, unsigned* err, cudaStream_t s);
 template <int K> cudaError_t launch_dirichlet_tc(const DirichletLaunch& L, unsigned* err, cudaStream_t s);
 template <int K> int dirichlet_tc_blocks_per_sm();
+template <int K> cudaError_t launch_batched_tc(const BatchKernelParams& p, int grid, cudaStream_t s);
+template <int K> int batched_tc_blocks_per_sm();
 }
 
 }  // namespace pm

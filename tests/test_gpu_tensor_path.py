@@ -104,3 +104,33 @@ def test_dirichlet_drift_full_size(c, orc):
     assert np.mean(r["steps"][:, :P][early] == so[early]) >= 0.99
     se = np.sqrt((r["var"] + s["var"]) / w.M)
     assert np.mean(np.abs(r["mean"] - s["mean"]) <= 5 * se) >= 0.98
+
+
+def test_batched_tensor_equals_single_instance_tensor_calls():
+    from tests.test_gpu_batched import small_instances
+    h, s = _gpu.side_stream_ctx()
+    try:
+        with torch.cuda.stream(s):
+            ws = small_instances(B=6, M=256)
+            b, n_rows = _gpu.batch_from_workloads(ws, device=True)
+            mean = torch.empty(n_rows, dtype=torch.float64, device="cuda")
+            var = torch.empty_like(mean)
+            rc = pm.pm_forward_batched(h, b, pm.PM_FP32 | pm.PM_TENSOR, mean, var)
+            torch.cuda.synchronize()
+            got = mean.cpu().numpy()
+            ref = []
+            for k, w in enumerate(ws):
+                n = len(w.x)
+                m = np.empty(n)
+                if isinstance(w, inputs.TimedepWorkload):
+                    pm.pm_forward_timedep(h, pm.Field(w.K, w.u), w.kappa, pm.Fourier(w.theta0.k, w.theta0.a, w.theta0.b),
+                                          w.x, w.t, n, w.M, w.dt, w.seed, pm.PM_FP32 | pm.PM_TENSOR, m, instance=k)
+                else:
+                    pm.pm_forward_dirichlet(h, pm.Field(w.K, w.u), w.drift_scale, w.kappa,
+                                            pm.DirichletData(w.g.R, w.g.quad, w.g.f_const, w.g.a, w.g.b), w.x, n, w.M,
+                                            w.dt, w.max_steps, w.seed, pm.PM_FP32 | pm.PM_TENSOR, m, instance=k)
+                ref.append(m)
+        assert rc == 0
+        np.testing.assert_allclose(got, np.concatenate(ref), rtol=0, atol=1e-12)
+    finally:
+        pm.pm_destroy(h)
