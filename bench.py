@@ -56,10 +56,17 @@ def measured_peaks():
     return {"sm_max_mhz": 2070.0}, "fallback"
 
 
-def profile_traffic():
+def tensor_flops_per_step(K: int) -> int:
+    """FLOP per particle-step of the tensor-core path: the per-step contraction
+    P = A W with A one row of (2K+1) basis values and W the (2K+1) x (4K+1)
+    coefficient matrix, done as three TF32 products (hi.hi, lo.hi, hi.lo)."""
+    return 3 * 2 * (2 * K + 1) * (4 * K + 1)
+
+
+def profile_traffic(name="timedep_k10_kernel.md"):
     """DRAM bytes per launch of the particle kernel from the committed ncu summary
     (line 'traffic_bytes_per_launch: <int>'), or None."""
-    p = os.path.join(ROOT, "profiles", "timedep_k10_kernel.md")
+    p = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(p):
         return None
     for line in open(p):
@@ -269,10 +276,34 @@ def run_gpu(args):
     if rank == 0:
         peaks, peaks_kind = measured_peaks()
         sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-        peak_tflops = sm_count * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        fp32_peak = sm_count * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
         kern_mean_ms = statistics.mean(kern_ms)
-        achieved = steps_per_eval * flops_per_step(w.K) / (kern_mean_ms / 1e3) / 1e12
-        traffic = profile_traffic()
+        simt_rate = steps_per_eval * flops_per_step(w.K) / (kern_mean_ms / 1e3) / 1e12
+        if args.tensor:
+            # TF32 dense peak = measured bf16 dense peak x (1.1 / 2.25), the nominal ratio.
+            bf16 = float(peaks.get("bf16_tflops", 1900.0))
+            peak_tflops = bf16 * 1.1 / 2.25
+            achieved = steps_per_eval * tensor_flops_per_step(w.K) / (kern_mean_ms / 1e3) / 1e12
+            roof = {"bound": "tensor", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                    "frac": achieved / peak_tflops, "traffic": profile_traffic("timedep_k10_tc_kernel.md"),
+                    "kernel": f"timedep_tc_kernel<{w.K}>", "kernel_ms": kern_mean_ms,
+                    "flop_per_particle_step": tensor_flops_per_step(w.K),
+                    "peak_basis": f"TF32 dense = bf16_tflops {bf16} ({peaks_kind}, burst) x 1.1/2.25",
+                    "single_product_frac": achieved / 3 / peak_tflops,
+                    "fp32_equivalent": {"achieved": simt_rate, "peak": fp32_peak,
+                                        "flop_per_particle_step": flops_per_step(w.K),
+                                        "note": "the same steps counted as FP32 direct-sum work, against "
+                                                "the FP32 pipe peak; above 1 because the sum runs on "
+                                                "the tensor cores"}}
+        else:
+            peak_tflops = fp32_peak
+            achieved = simt_rate
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                    "frac": achieved / peak_tflops, "traffic": profile_traffic(),
+                    "kernel": f"timedep_kernel<float,{w.K},128>", "kernel_ms": kern_mean_ms,
+                    "flop_per_particle_step": flops_per_step(w.K),
+                    "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 FLOP x sm_max_mhz "
+                                  f"{peaks.get('sm_max_mhz', 2070.0)} ({peaks_kind})"}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
@@ -282,13 +313,7 @@ def run_gpu(args):
                        "forward_map_evals_per_s": value / steps_per_eval,
                        "l2": "flushed between timed steps (256 MiB write, outside the timed events)",
                        "reductions": "f64", "mc_se_median": float(np.median(se)), "mc_se_max": float(se.max())},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                         "frac": achieved / peak_tflops, "traffic": traffic,
-                         "kernel": "timedep_tc_kernel<10>" if args.tensor else "timedep_kernel<float,10,128>",
-                         "kernel_ms": kern_mean_ms,
-                         "flop_per_particle_step": flops_per_step(w.K),
-                         "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 FLOP x sm_max_mhz "
-                                       f"{peaks.get('sm_max_mhz', 2070.0)} ({peaks_kind})"},
+            "roofline": roof,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n_obs * 24,
                     "d2h_bytes_per_step": n_obs * 16},
             "gpu_launches": int(launches),
@@ -390,6 +415,19 @@ def run_aux(args):
             "config": dict(workload=name, particle_steps_per_call=steps[-1], **cfg)}
     if args.workload == "dirichlet":
         line["kernel_ms"] = pm.pm_last_kernel_ms(ctx)
+        # Exit-step distribution of the same call (outside the timed region): the
+        # longest path bounds the call from below at one path's step latency.
+        es = torch.empty(len(w.x) * w.M, dtype=torch.int32, device=dev)
+        pm.pm_forward_dirichlet(ctx, fld, w.drift_scale, w.kappa, gd, x, len(w.x), w.M, w.dt, w.max_steps,
+                                w.seed, pm.PM_FP32 | (pm.PM_TENSOR if args.tensor else 0), mean, var, exit_step=es)
+        e = es.cpu().numpy().astype(np.int64)
+        ex = e[e >= 0]
+        q = np.quantile(ex, [0.5, 0.99, 0.999, 0.99999]) if ex.size else [0, 0, 0, 0]
+        line["exit_steps"] = {"mean": float(ex.mean()) if ex.size else 0.0, "p50": float(q[0]), "p99": float(q[1]),
+                              "p99.9": float(q[2]), "p99.999": float(q[3]), "max": int(ex.max()) if ex.size else 0,
+                              "capped": int((e < 0).sum()),
+                              "ms_per_step_of_longest_path": line["kernel_ms"] / max(int(ex.max()), 1)
+                              if ex.size else None}
     print(json.dumps(line), flush=True)
     pm.pm_destroy(ctx)
     return 0
