@@ -413,6 +413,7 @@ def run_aux(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "dtype": "f32", "data": "synthetic", "auxiliary": True,
             "config": dict(workload=name, particle_steps_per_call=steps[-1], **cfg)}
+    line["config"]["grid"] = pm.pm_last_grid(ctx)
     if args.workload == "dirichlet":
         line["kernel_ms"] = pm.pm_last_kernel_ms(ctx)
         # Exit-step distribution of the same call (outside the timed region): the

@@ -428,6 +428,11 @@ int64_t pm_launch_count(const pm_ctx* ctx);
  * data-dependent lengths; this is the count throughput figures use. */
 int64_t pm_last_step_count(const pm_ctx* ctx);
 
+/* CTAs of the main particle kernel of the last forward call on this context
+ * (persistent kernels: resident CTAs per SM x SMs, capped by the work), 0
+ * before the first call. */
+int64_t pm_last_grid(const pm_ctx* ctx);
+
 #ifdef __cplusplus
 }
 #endif

@@ -115,6 +115,8 @@ def load(build_if_missing: bool = True):
     L.pm_launch_count.restype = i64
     L.pm_last_step_count.argtypes = [vp]
     L.pm_last_step_count.restype = i64
+    L.pm_last_grid.argtypes = [vp]
+    L.pm_last_grid.restype = i64
     _lib = L
     return L
 
@@ -214,6 +216,10 @@ def pm_launch_count(ctx):
 
 def pm_last_step_count(ctx):
     return int(load().pm_last_step_count(ctx))
+
+
+def pm_last_grid(ctx):
+    return int(load().pm_last_grid(ctx))
 
 
 def _opts(path_offset=0, instance=0, g_out=None, x_out=None):

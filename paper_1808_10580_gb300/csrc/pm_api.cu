@@ -297,6 +297,8 @@ int64_t pm_launch_count(const pm_ctx* c) { return c ? c->launches : 0; }
 
 int64_t pm_last_step_count(const pm_ctx* c) { return c ? c->last_steps : -1; }
 
+int64_t pm_last_grid(const pm_ctx* c) { return c ? c->last_grid : 0; }
+
 // ---------------------------------------------------------------------------
 // Algorithm 1
 // ---------------------------------------------------------------------------
@@ -403,6 +405,7 @@ int pm_forward_timedep(pm_ctx* c, const pm_field* field, double kappa, const pm_
     L.path_offset = off;
     L.n_obs = (int32_t)n_obs;
     L.chunks = chunks;
+    c->last_grid = n_obs * (int64_t)chunks;
     L.inst = opts ? opts->instance : 0u;
     L.key0 = (uint32_t)(seed & 0xffffffffu);
     L.key1 = (uint32_t)(seed >> 32);
@@ -587,6 +590,7 @@ int pm_forward_dirichlet(pm_ctx* c, const pm_field* field, double drift_scale, d
     const int64_t need = (total + kDirichletBlock - 1) / kDirichletBlock;
     if (grid > need) grid = need;
     L.grid = (int)(grid > 0 ? grid : 1);
+    c->last_grid = L.grid;
     if (c->timing) PM_CUDA(cudaEventRecord(c->ev0, c->stream), "event");
     cudaError_t e;
     unsigned* tc_err = (unsigned*)(W.ctr + 3);

@@ -256,6 +256,7 @@ extern "C" int pm_forward_batched(pm_ctx* c, const pm_batch* bt, uint32_t flags,
     int64_t grid = (int64_t)per_sm * c->sm_count;
     const int64_t need = (total + kBatchWarpsHost * 32 - 1) / (kBatchWarpsHost * 32);
     grid = std::max<int64_t>(1, std::min(grid, need));
+    c->last_grid = grid;
 
     const double* dx = dev ? bt->x : W.xt;
     const double* dt_ = dev ? bt->t : W.xt + 2 * n_rows;

@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(128, 4) batched_tc_kernel(const __grid_constan
     uint32_t j = 0, i = 0;
     unsigned long long lane_steps = 0;
     uint32_t phase = 0;
-    bool failed = false;
+    bool failed = false, stop = false;
     Coord<float> X1, X2;
     X1.set(0.0);
     X2.set(0.0);
@@ -192,8 +192,6 @@ __global__ void __launch_bounds__(128, 4) batched_tc_kernel(const __grid_constan
         if (pid >= 0) r = philox4x32_10(u32x4{(uint32_t)(n >> 1), i, j, I.stream}, I.key0, I.key1);
 #pragma unroll 1
         for (int half = 0; half < 2; ++half) {
-            float xi1, xi2;
-            box_muller<float>(half ? r.z : r.x, half ? r.w : r.y, xi1, xi2);
             {
                 float C2[K + 1], S2[K + 1];
                 fourier_powers<float, K>(X2.val(), C2, S2);
@@ -205,11 +203,11 @@ __global__ void __launch_bounds__(128, 4) batched_tc_kernel(const __grid_constan
                 a[2 * K] = 1.f;
                 write_row<S::KD>(A_hi, A_lo, row_off, a);
             }
-            float C1[K + 1], S1[K + 1];
-            fourier_powers<float, K>(X1.val(), C1, S1);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncthreads();
+            // One barrier per step: the rows are in place, and a wait that gave
+            // up in the previous step (any thread) stops the whole CTA.
+            if (__syncthreads_or(failed)) { stop = true; break; }
             if (tid == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
@@ -220,9 +218,13 @@ __global__ void __launch_bounds__(128, 4) batched_tc_kernel(const __grid_constan
                 for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, dA_hi + 2 * k, dB_lo + 2 * k, 1u);
                 tc::mma_commit(bar_a);
             }
-            const bool ok = tc::mbar_wait(bar_a, phase);
+            // While the product runs: the Brownian increment and the x1 harmonics.
+            float xi1, xi2;
+            box_muller<float>(half ? r.z : r.x, half ? r.w : r.y, xi1, xi2);
+            float C1[K + 1], S1[K + 1];
+            fourier_powers<float, K>(X1.val(), C1, S1);
+            failed = !tc::mbar_wait(bar_a, phase);
             phase ^= 1u;
-            if (__syncthreads_or(!ok)) { failed = true; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             float acc[S::NP];
             tmem_ld_row<S::NP>(t_row, acc);
@@ -263,9 +265,9 @@ __global__ void __launch_bounds__(128, 4) batched_tc_kernel(const __grid_constan
                 }
             }
         }
-        if (failed) break;
+        if (stop) break;
     }
-    if (failed && tid == 0 && p.tc_err) atomicExch(p.tc_err, 1u);
+    if (failed && p.tc_err) atomicExch(p.tc_err, 1u);
     if (lane_steps) atomicAdd(p.steps, lane_steps);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -286,11 +288,9 @@ cudaError_t launch_batched_tc(const BatchKernelParams& p, int grid, cudaStream_t
 template <int K>
 int batched_tc_blocks_per_sm()
 {
-    int nb = 0;
     const int smem = Shape<K>::SMEM + 64;
     cudaFuncSetAttribute(batched_tc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batched_tc_kernel<K>, 128, smem) != cudaSuccess) return 1;
-    return nb > 0 ? nb : 1;
+    return resident_ctas((const void*)batched_tc_kernel<K>, 128, smem, 64);
 }
 
 }  // namespace tdtc

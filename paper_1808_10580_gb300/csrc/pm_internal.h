@@ -23,6 +23,7 @@ struct pm_ctx {
     bool timed = false;
     int64_t launches = 0;
     int64_t last_steps = -1;     // Euler steps of the last synchronous forward call
+    int64_t last_grid = 0;       // CTAs of the last particle-kernel launch
     // Batched map: the last captured CUDA graph and the key of the call shape it serves.
     uint64_t graph_key = 0;
     cudaGraphExec_t graph_exec = nullptr;

@@ -19,6 +19,7 @@
 // (one thread issues 3 x ceil((2K+1)/8) MMAs and commits to an mbarrier), and
 // every thread reads its 4K+1 accumulator columns back with tcgen05.ld.
 #pragma once
+#include <algorithm>
 #include "pm_gemm_tc.cuh"
 #include "pm_kernels.cuh"
 
@@ -51,6 +52,34 @@ __device__ __forceinline__ float to_tf32(float x)
 
 // Byte offset of 16-byte chunk c of row r in a 128B-swizzled K-major tile.
 __device__ __forceinline__ uint32_t sw128(int r, int c) { return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4)); }
+
+// CTAs of a tensor-core kernel that fit on one SM at once, from its register
+// count, its shared memory and the 512 tensor-memory columns (each CTA
+// allocates tmem_cols).  Persistent grids are this many CTAs per SM.
+inline int resident_ctas(const void* fn, int threads, int dyn_smem, int tmem_cols)
+{
+    int dev = 0;
+    cudaFuncAttributes fa{};
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    int regs_sm = 65536, smem_sm = 0, max_blocks = 32, max_thr = 2048, reserved = 0;
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&max_blocks, cudaDevAttrMaxBlocksPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&max_thr, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    const int warps = (threads + 31) / 32;
+    const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;  // allocated per warp in units of 256
+    int nb = regs_warp > 0 ? regs_sm / (regs_warp * warps) : max_blocks;
+    const int smem_cta = dyn_smem + (int)fa.sharedSizeBytes + reserved;
+    if (smem_cta > 0 && smem_sm > 0) nb = std::min(nb, smem_sm / smem_cta);
+    nb = std::min(nb, max_thr / threads);
+    nb = std::min(nb, max_blocks);
+    nb = std::min(nb, 512 / tmem_cols);
+    return std::max(nb, 1);
+}
 
 template <int K>
 struct Params {
@@ -236,9 +265,6 @@ __global__ void __launch_bounds__(128, 4) timedep_tc_kernel(const __grid_constan
     u32x4 r{0, 0, 0, 0};
 
     for (int n = 0; n < N; ++n) {
-        if ((n & 1) == 0) r = philox4x32_10(u32x4{(uint32_t)(n >> 1), pid, (uint32_t)j, p.inst}, p.key0, p.key1);
-        float xi1, xi2;
-        box_muller<float>((n & 1) ? r.z : r.x, (n & 1) ? r.w : r.y, xi1, xi2);
         // Row of A: x2 harmonics (hi and lo).
         {
             float C2[K + 1], S2[K + 1];
@@ -251,12 +277,11 @@ __global__ void __launch_bounds__(128, 4) timedep_tc_kernel(const __grid_constan
             a[2 * K] = 1.f;
             write_row<S::KD>(A_hi, A_lo, row_off, a);
         }
-        // x1 harmonics stay in registers.
-        float C1[K + 1], S1[K + 1];
-        fourier_powers<float, K>(X1.val(), C1, S1);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
+        // One barrier per step: the rows are in place, and a wait that gave up
+        // in the previous step (any thread) ends the loop for the whole CTA.
+        if (__syncthreads_or(failed)) break;
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
@@ -267,8 +292,13 @@ __global__ void __launch_bounds__(128, 4) timedep_tc_kernel(const __grid_constan
             for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, dA_hi + 2 * k, dB_lo + 2 * k, 1u);
             tc::mma_commit(bar_a);
         }
-        const bool ok = tc::mbar_wait(bar_a, (uint32_t)(n & 1));
-        if (__syncthreads_or(!ok)) { failed = true; break; }
+        // While the product runs: the Brownian increment and the x1 harmonics.
+        if ((n & 1) == 0) r = philox4x32_10(u32x4{(uint32_t)(n >> 1), pid, (uint32_t)j, p.inst}, p.key0, p.key1);
+        float xi1, xi2;
+        box_muller<float>((n & 1) ? r.z : r.x, (n & 1) ? r.w : r.y, xi1, xi2);
+        float C1[K + 1], S1[K + 1];
+        fourier_powers<float, K>(X1.val(), C1, S1);
+        failed = !tc::mbar_wait(bar_a, (uint32_t)(n & 1));
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         float acc[S::NP];
         tmem_ld_row<S::NP>(t_row, acc);
@@ -286,6 +316,7 @@ __global__ void __launch_bounds__(128, 4) timedep_tc_kernel(const __grid_constan
         X1.wrap();
         X2.wrap();
     }
+    failed = __syncthreads_or(failed);
     double g = 0.0;
     if (failed) {
         if (tid == 0) atomicExch(p.err, 1u);

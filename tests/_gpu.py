@@ -120,17 +120,17 @@ def batch_from_workloads(ws, device=True):
     return pm.Batch(K, inst, x, t, th, disk), row
 
 
-def batched(c, ws, device=True):
+def batched(c, ws, device=True, flags=pm.PM_FP32):
     b, n_rows = batch_from_workloads(ws, device)
     if device:
         mean = torch.empty(n_rows, dtype=torch.float64, device="cuda")
         var = torch.empty_like(mean)
         nu = torch.zeros(1, dtype=torch.int64, device="cuda")
-        rc = pm.pm_forward_batched(c, b, pm.PM_FP32, mean, var, nu)
+        rc = pm.pm_forward_batched(c, b, flags, mean, var, nu)
         torch.cuda.synchronize()
         return rc, mean.cpu().numpy(), var.cpu().numpy(), int(nu.item())
     mean = np.empty(n_rows)
     var = np.empty(n_rows)
     nu = np.zeros(1, dtype=np.int64)
-    rc = pm.pm_forward_batched(c, b, pm.PM_FP32, mean, var, nu)
+    rc = pm.pm_forward_batched(c, b, flags, mean, var, nu)
     return rc, mean, var, int(nu[0])

@@ -134,3 +134,19 @@ def test_batched_tensor_equals_single_instance_tensor_calls():
         np.testing.assert_allclose(got, np.concatenate(ref), rtol=0, atol=1e-12)
     finally:
         pm.pm_destroy(h)
+
+
+def test_persistent_tensor_grids_fill_every_sm(c):
+    # The persistent tensor-core kernels run several CTAs per SM (registers,
+    # shared memory and tensor memory allow 4 at K = 10), not one.
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    w = inputs.dirichlet_disk_k10(M=4096)
+    w.max_steps = 2000
+    _gpu.dirichlet(c, w, pm.PM_FP32 | pm.PM_TENSOR)
+    g_dir = pm.pm_last_grid(c)
+    from tests.test_gpu_batched import small_instances
+    ws = small_instances(B=8, M=4096)
+    _gpu.batched(c, ws, flags=pm.PM_FP32 | pm.PM_TENSOR)
+    g_bat = pm.pm_last_grid(c)
+    assert g_dir % sms == 0 and g_dir >= 2 * sms, (g_dir, sms)
+    assert g_bat % sms == 0 and g_bat >= 2 * sms, (g_bat, sms)
