@@ -448,25 +448,29 @@ def run_mcmc(args):
     ctx = pm.pm_create(0, stream.cuda_stream)
     t0 = time.perf_counter()
     prob = sm.make_data(ctx, sm.make_problem(sigma=args.sigma))
-    Z, G = sm.training_pairs(ctx, prob, args.train_pairs)
+    u0 = sm.start_states(prob, 64, spread=0.0)
+    centers = u0 if args.train_spread > 0 else None
+    spread = args.train_spread if args.train_spread > 0 else 1.0
+    Z, G = sm.training_pairs(ctx, prob, args.train_pairs, centers=centers, spread=spread, tensor=args.tensor)
     t_pairs = time.perf_counter() - t0
-    Zv, Gv = sm.training_pairs(ctx, prob, 2048, seed=7005)
+    Zv, Gv = sm.training_pairs(ctx, prob, 2048, seed=7005, centers=centers, spread=spread, tensor=args.tensor)
     t1 = time.perf_counter()
     net, hist = sm.train_surrogate(ctx, prob, Z, G, epochs=args.epochs, weight_decay=args.weight_decay,
                                    lr_decay=args.lr_decay)
     t_train = time.perf_counter() - t1
     rmse = sm.surrogate_rmse(ctx, net, Zv, Gv)
     rmse_train = sm.surrogate_rmse(ctx, net, Z[:2048], G[:2048])
-    u0 = sm.start_states(prob, 64, spread=0.0)
     for beta in [float(v) for v in args.betas.split(",")]:
-        plain, _ = sm.run_chains(ctx, prob, u0, beta, args.plain_steps, seed=11)
-        da, _ = sm.run_chains(ctx, prob, u0, beta, args.da_steps, seed=11, net=net)
+        plain, _ = sm.run_chains(ctx, prob, u0, beta, args.plain_steps, seed=11, tensor=args.tensor)
+        da, _ = sm.run_chains(ctx, prob, u0, beta, args.da_steps, seed=11, net=net, tensor=args.tensor)
         line = {"metric": "accepted pCN proposals/s (64 chains)", "auxiliary": True, "data": "synthetic",
                 "value": da["accepted_per_s"], "unit": "accepted proposals/s",
                 "ratio_vs_plain": da["accepted_per_s"] / max(plain["accepted_per_s"], 1e-30),
                 "config": {"train_pairs": args.train_pairs, "epochs": args.epochs, "M": prob.M,
                            "n_obs": len(prob.t), "sigma": prob.sigma, "beta": beta, "chains": 64,
-                           "start": "data-generating field"},
+                           "start": "data-generating field", "tensor_cores": bool(args.tensor),
+                           "training_inputs": (f"local: start state + {args.train_spread} x prior std x N(0, I)"
+                                               if args.train_spread > 0 else "prior draws")},
                 "plain": plain, "delayed_acceptance": da,
                 "surrogate": {"val_rmse": rmse, "train_rmse": rmse_train, "final_train_loss": float(hist[-1]),
                               "train_seconds": t_train, "pair_generation_seconds": t_pairs}}
@@ -489,8 +493,13 @@ def main():
                     help="timedep: the headline line; dirichlet / batched / mcmc: auxiliary measurements")
     ap.add_argument("--train-pairs", type=int, default=1 << 16, help="mcmc: surrogate training pairs")
     ap.add_argument("--betas", default="0.03", help="mcmc: comma-separated pCN steps (each the same for both samplers)")
-    ap.add_argument("--sigma", type=float, default=0.01, help="mcmc: observation noise standard deviation")
+    ap.add_argument("--sigma", type=float, default=0.1,
+                    help="mcmc: observation noise standard deviation (0.01 is below the map's Monte Carlo noise "
+                         "at M = 4096 and no chain moves)")
     ap.add_argument("--epochs", type=int, default=100, help="mcmc: surrogate training epochs")
+    ap.add_argument("--train-spread", type=float, default=0.1,
+                    help="mcmc: training inputs local to the start states with this spread (prior-std units); "
+                         "0: prior draws")
     ap.add_argument("--weight-decay", type=float, default=0.0, help="mcmc: AdamW weight decay")
     ap.add_argument("--lr-decay", type=float, default=1.0, help="mcmc: per-epoch step-size factor")
     ap.add_argument("--plain-steps", type=int, default=8, help="mcmc: steps of the plain sampler")

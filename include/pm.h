@@ -333,6 +333,7 @@ typedef struct pm_pcn_config {
     const pm_fourier* theta0;   /* host */
     const double* x;            /* [n_obs][2] host */
     const double* t;            /* [n_obs] host */
+    uint32_t map_flags;         /* particle map: 0 (FP32 pipes) or PM_TENSOR; other bits rejected */
 } pm_pcn_config;
 
 typedef struct pm_pcn_stats {

@@ -417,7 +417,7 @@ class pm_pcn_config(C.Structure):
     _fields_ = [("n_chains", C.c_int32), ("K", C.c_int32), ("beta", C.c_double), ("sigma", C.c_double),
                 ("seed", C.c_uint64), ("n_obs", C.c_int64), ("y", C.c_void_p), ("A", C.c_void_p),
                 ("kappa", C.c_double), ("dt", C.c_double), ("M", C.c_int64), ("path_seed", C.c_uint64),
-                ("theta0", C.POINTER(pm_fourier)), ("x", C.c_void_p), ("t", C.c_void_p)]
+                ("theta0", C.POINTER(pm_fourier)), ("x", C.c_void_p), ("t", C.c_void_p), ("map_flags", C.c_uint32)]
 
 
 class pm_pcn_stats(C.Structure):
@@ -442,7 +442,7 @@ class PCN:
     """pCN chains on the device (plain, or delayed acceptance when `screen` is given)."""
 
     def __init__(self, ctx, K, u0, y, sigma, beta, seed, A=None, theta0: Fourier = None, x=None, t=None, kappa=0.0,
-                 dt=1e-3, M=1, path_seed=0, screen=None, screen_scale=None):
+                 dt=1e-3, M=1, path_seed=0, screen=None, screen_scale=None, tensor=False):
         self.ctx = ctx
         self.keep = [np.ascontiguousarray(y, dtype=np.float64), np.ascontiguousarray(u0, dtype=np.float64)]
         self.C, self.n_u = self.keep[1].shape
@@ -454,7 +454,8 @@ class PCN:
         cfg = pm_pcn_config(self.C, int(K), float(beta), float(sigma), int(seed), len(self.keep[0]),
                             self.keep[0].ctypes.data, A_.ctypes.data if A_ is not None else None, float(kappa),
                             float(dt), int(M), int(path_seed), C.pointer(theta0.s) if theta0 is not None else None,
-                            x_.ctypes.data if x_ is not None else None, t_.ctypes.data if t_ is not None else None)
+                            x_.ctypes.data if x_ is not None else None, t_.ctypes.data if t_ is not None else None,
+                            PM_TENSOR if tensor else 0)
         self.h = C.c_void_p()
         _check(_plib().pm_pcn_create(ctx, C.byref(self.h), C.byref(cfg), self.keep[1].ctypes.data, screen,
                                      sc.ctypes.data if sc is not None else None))

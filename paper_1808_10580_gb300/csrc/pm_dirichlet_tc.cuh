@@ -61,11 +61,11 @@ __device__ __forceinline__ void dir_finish(const DirParams<K>& p, int64_t pid, b
 }
 
 template <int K>
-__global__ void __launch_bounds__(128, 4) dirichlet_tc_kernel(const __grid_constant__ DirParams<K> p)
+__global__ void __launch_bounds__(128, 6) dirichlet_tc_kernel(const __grid_constant__ DirParams<K> p)
 {
     using S = Shape<K>;
     extern __shared__ uint8_t smem_raw[];
-    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     uint8_t* A_hi = smem;
     uint8_t* A_lo = smem + S::A_BYTES;
     uint8_t* B_hi = smem + 2 * S::A_BYTES;
@@ -76,8 +76,8 @@ __global__ void __launch_bounds__(128, 4) dirichlet_tc_kernel(const __grid_const
     const unsigned full = 0xffffffffu;
     const uint32_t bar_a = tc::smem_u32(bar);
 
-    for (int q = tid; q < S::NP * 8; q += 128) {
-        const int r = q >> 3, c = q & 7;
+    for (int q = tid; q < S::NP * S::KC; q += 128) {
+        const int r = q / S::KC, c = q - r * S::KC;
         float4 h, l;
         float* hv = &h.x;
         float* lv = &l.x;
@@ -87,12 +87,12 @@ __global__ void __launch_bounds__(128, 4) dirichlet_tc_kernel(const __grid_const
             hv[e] = to_tf32(w);
             lv[e] = to_tf32(w - hv[e]);
         }
-        *reinterpret_cast<float4*>(B_hi + sw128(r, c)) = h;
-        *reinterpret_cast<float4*>(B_lo + sw128(r, c)) = l;
+        *reinterpret_cast<float4*>(B_hi + tile_off<S::KC>(r, c)) = h;
+        *reinterpret_cast<float4*>(B_lo + tile_off<S::KC>(r, c)) = l;
     }
-    for (int c = 0; c < 8; ++c) {
-        *reinterpret_cast<float4*>(A_hi + sw128(tid, c)) = make_float4(0.f, 0.f, 0.f, 0.f);
-        *reinterpret_cast<float4*>(A_lo + sw128(tid, c)) = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int c = 0; c < S::KC; ++c) {
+        *reinterpret_cast<float4*>(A_hi + tile_off<S::KC>(tid, c)) = make_float4(0.f, 0.f, 0.f, 0.f);
+        *reinterpret_cast<float4*>(A_lo + tile_off<S::KC>(tid, c)) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     if (tid == 0) {
         tc::mbar_init(bar_a, 1);
@@ -110,12 +110,12 @@ __global__ void __launch_bounds__(128, 4) dirichlet_tc_kernel(const __grid_const
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
     const uint32_t t_row = tmem + ((uint32_t)(warp * 32) << 16);
-    const uint64_t dA_hi = tc::smem_desc_sw128(tc::smem_u32(A_hi)), dA_lo = tc::smem_desc_sw128(tc::smem_u32(A_lo));
-    const uint64_t dB_hi = tc::smem_desc_sw128(tc::smem_u32(B_hi)), dB_lo = tc::smem_desc_sw128(tc::smem_u32(B_lo));
+    const uint64_t dA_hi = tile_desc<S::SBO>(tc::smem_u32(A_hi)), dA_lo = tile_desc<S::SBO>(tc::smem_u32(A_lo));
+    const uint64_t dB_hi = tile_desc<S::SBO>(tc::smem_u32(B_hi)), dB_lo = tile_desc<S::SBO>(tc::smem_u32(B_lo));
 
     uint32_t row_off[8];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) row_off[c] = sw128(tid, c);
+    for (int c = 0; c < S::KC; ++c) row_off[c] = tile_off<S::KC>(tid, c);
     int64_t pid = -1;
     bool done = false;
     int64_t n = 0;
@@ -182,11 +182,11 @@ __global__ void __launch_bounds__(128, 4) dirichlet_tc_kernel(const __grid_const
             if (tid == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-                for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, dA_hi + 2 * k, dB_hi + 2 * k, k > 0 ? 1u : 0u);
+                for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, dA_hi + kKStep * k, dB_hi + kKStep * k, k > 0 ? 1u : 0u);
 #pragma unroll
-                for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, dA_lo + 2 * k, dB_hi + 2 * k, 1u);
+                for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, dA_lo + kKStep * k, dB_hi + kKStep * k, 1u);
 #pragma unroll
-                for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, dA_hi + 2 * k, dB_lo + 2 * k, 1u);
+                for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, dA_hi + kKStep * k, dB_lo + kKStep * k, 1u);
                 tc::mma_commit(bar_a);
             }
             // While the product runs: the Brownian increment and the x1 harmonics.
@@ -197,14 +197,8 @@ __global__ void __launch_bounds__(128, 4) dirichlet_tc_kernel(const __grid_const
             failed = !tc::mbar_wait(bar_a, phase);
             phase ^= 1u;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            float acc[S::NP];
-            tmem_ld_row<S::NP>(t_row, acc);
-            float v1 = acc[0], v2 = 0.f;
-#pragma unroll
-            for (int m = 1; m <= K; ++m) {
-                v1 = fmaf(C1[m], acc[m], fmaf(S1[m], acc[K + m], v1));
-                v2 = fmaf(C1[m], acc[2 * K + m], fmaf(S1[m], acc[3 * K + m], v2));
-            }
+            float v1, v2;
+            velocity_from_tmem<K>(t_row, C1, S1, v1, v2);
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             if (pid >= 0) {
                 em_update<float>(X1, v1, p.drift_dt, p.s_dt, xi1);

@@ -152,6 +152,7 @@ struct pm_pcn {
     double kappa = 0, dt = 0;
     int64_t M = 0;
     uint64_t path_seed = 0;
+    uint32_t map_flags = 0;     // PM_TENSOR or 0
     std::vector<int32_t> qk;
     std::vector<double> qa, qb;
     // screen
@@ -206,7 +207,7 @@ int forward_listed(pm_ctx* c, pm_pcn* p, const std::vector<int>& idx_h)
     b.x = p->x_rep;
     b.t = p->t_rep;
     b.n_rows = (int64_t)n * p->n_obs;
-    int rc = pm_forward_batched(c, &b, PM_DEVICE_PTRS, p->G, nullptr, nullptr);
+    int rc = pm_forward_batched(c, &b, PM_DEVICE_PTRS | p->map_flags, p->G, nullptr, nullptr);
     return rc < 0 ? rc : PM_OK;
 }
 
@@ -223,6 +224,7 @@ int pm_pcn_create(pm_ctx* c, pm_pcn** out, const pm_pcn_config* cfg, const doubl
     if (!supported_K(cfg->K) || cfg->K < 1) return fail(PM_EINVAL, "unsupported K");
     if (!(cfg->beta > 0 && cfg->beta <= 1) || !(cfg->sigma > 0)) return fail(PM_EINVAL, "need 0 < beta <= 1, sigma > 0");
     if (cfg->n_obs < 1 || !cfg->y) return fail(PM_EINVAL, "observations missing");
+    if (cfg->map_flags & ~(uint32_t)PM_TENSOR) return fail(PM_EINVAL, "map_flags: only PM_TENSOR");
     const bool linear = cfg->A != nullptr;
     if (!linear) {
         if (!cfg->theta0 || !cfg->x || !cfg->t || cfg->M < 1 || !(cfg->dt > 0) || !(cfg->kappa >= 0))
@@ -241,6 +243,7 @@ int pm_pcn_create(pm_ctx* c, pm_pcn** out, const pm_pcn_config* cfg, const doubl
     p->rho = std::sqrt(1.0 - cfg->beta * cfg->beta);
     p->sigma = cfg->sigma;
     p->seed = cfg->seed;
+    p->map_flags = cfg->map_flags;
     p->linear = linear;
     p->screen = screen;
     if (!linear) {

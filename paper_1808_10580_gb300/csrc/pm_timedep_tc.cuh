@@ -15,7 +15,7 @@
 // harmonics, the noise and the Euler step stay on the FP32 pipes.
 //
 // Per step: every thread writes its particle's row of A (hi and lo) into a
-// 128B-swizzled K-major tile, a CTA barrier hands the tile to the tensor core
+// K-major tile (layout at tile_off), a CTA barrier hands the tile to the tensor core
 // (one thread issues 3 x ceil((2K+1)/8) MMAs and commits to an mbarrier), and
 // every thread reads its 4K+1 accumulator columns back with tcgen05.ld.
 #pragma once
@@ -30,12 +30,14 @@ template <int K>
 struct Shape {
     static constexpr int KD = 2 * K + 1;              // A columns used
     static constexpr int KS = (KD + 7) / 8;           // MMA k-steps (K = 8 per tf32 instruction)
+    static constexpr int KC = 2 * KS;                 // 16-byte chunks (4 tf32) per tile row
     static constexpr int NC = 4 * K + 1;              // accumulator columns used
     static constexpr int NP = (NC + 15) / 16 * 16;    // MMA N (multiple of 16)
-    static constexpr int A_BYTES = 128 * 128;         // 128 rows x 32 tf32
-    static constexpr int B_BYTES = NP * 128;          // NP rows x 32 tf32
-    static constexpr int SMEM = 2 * A_BYTES + 2 * B_BYTES + 1024 + 64;
-    static_assert(KD <= 32, "one 128-byte atom of K");
+    static constexpr int SBO = KC * 128;              // bytes between 8-row groups of a tile
+    static constexpr int A_BYTES = 128 * KC * 16;     // 128 rows x 8 KS tf32
+    static constexpr int B_BYTES = NP * KC * 16;      // NP rows x 8 KS tf32
+    static constexpr int SMEM = 2 * A_BYTES + 2 * B_BYTES + 128 + 64;
+    static_assert(KD <= 4 * KC, "A columns fit the k-steps");
     static_assert(NP <= 64, "64 TMEM columns");
 };
 
@@ -50,8 +52,30 @@ __device__ __forceinline__ float to_tf32(float x)
     return __uint_as_float(r);
 }
 
-// Byte offset of 16-byte chunk c of row r in a 128B-swizzled K-major tile.
-__device__ __forceinline__ uint32_t sw128(int r, int c) { return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4)); }
+// Tiles are K-major without swizzling: 8 x 16-byte core matrices (8 rows x 4
+// tf32, 128 contiguous bytes), the KC core matrices of an 8-row group side by
+// side (128 B apart along K), 8-row groups SBO = KC x 128 B apart.  One MMA
+// k-step (8 tf32) spans two core matrices along K.
+// Byte offset of 16-byte chunk c of row r.
+template <int KC>
+__device__ __forceinline__ uint32_t tile_off(int r, int c) { return (uint32_t)((r >> 3) * (KC * 128) + (r & 7) * 16 + c * 128); }
+
+// Shared-memory matrix descriptor of such a tile: leading-dimension (K) byte
+// offset 128 B between core matrices, stride-dimension byte offset SBO
+// between 8-row groups, no swizzle.
+template <int SBO>
+__device__ __forceinline__ uint64_t tile_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(128 >> 4) << 16;
+    d |= (uint64_t)(SBO >> 4) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version
+    return d;                // swizzle mode 0
+}
+
+// Descriptor start-address units (16 B) per k-step: two core matrices.
+constexpr uint64_t kKStep = 256 >> 4;
 
 // CTAs of a tensor-core kernel that fit on one SM at once, from its register
 // count, its shared memory and the 512 tensor-memory columns (each CTA
@@ -177,6 +201,41 @@ template <> __device__ __forceinline__ void tmem_ld_row<64>(uint32_t taddr, floa
     for (int q = 0; q < 64; ++q) v[q] = __uint_as_float(r[q]);
 }
 
+// The velocity from this lane's accumulator row, read 32 columns at a time:
+//   v1 = P(0) + sum_m C1m P1c(m) + S1m P1s(m)      (columns 0 .. 2K, all < 32),
+//   v2 = sum_m C1m P2c(m)  +  sum_m S1m P2s(m)      (columns 2K+1 .. 4K).
+template <int K>
+__device__ __forceinline__ void velocity_from_tmem(uint32_t t_row, const float (&C1)[K + 1], const float (&S1)[K + 1],
+                                                   float& v1, float& v2)
+{
+    constexpr int NP = Shape<K>::NP;
+    static_assert(2 * K < 32, "v1 columns in the first 32");
+    float v2c = 0.f, v2s = 0.f;
+    {
+        float a[32];
+        tmem_ld_row<32>(t_row, a);
+        v1 = a[0];
+#pragma unroll
+        for (int m = 1; m <= K; ++m) v1 = fmaf(C1[m], a[m], fmaf(S1[m], a[K + m], v1));
+#pragma unroll
+        for (int m = 1; m <= K; ++m) {
+            if (2 * K + m < 32) v2c = fmaf(C1[m], a[(2 * K + m) & 31], v2c);
+            if (3 * K + m < 32) v2s = fmaf(S1[m], a[(3 * K + m) & 31], v2s);
+        }
+    }
+    if constexpr (NP > 32) {
+        float b[NP - 32];
+        if constexpr (NP - 32 == 16) tmem_ld16(t_row + 32u, b);
+        else tmem_ld_row<32>(t_row + 32u, b);
+#pragma unroll
+        for (int m = 1; m <= K; ++m) {
+            if (2 * K + m >= 32) v2c = fmaf(C1[m], b[(2 * K + m - 32) & (NP - 33)], v2c);
+            if (3 * K + m >= 32) v2s = fmaf(S1[m], b[(3 * K + m - 32) & (NP - 33)], v2s);
+        }
+    }
+    v2 = v2c + v2s;
+}
+
 // This thread's row of the particle tiles: harmonics a[0..KD) split into hi / lo.
 template <int KD>
 __device__ __forceinline__ void write_row(uint8_t* A_hi, uint8_t* A_lo, const uint32_t (&off)[8], const float (&a)[32])
@@ -194,11 +253,11 @@ __device__ __forceinline__ void write_row(uint8_t* A_hi, uint8_t* A_lo, const ui
 }
 
 template <int K>
-__global__ void __launch_bounds__(128, 4) timedep_tc_kernel(const __grid_constant__ Params<K> p)
+__global__ void __launch_bounds__(128, 6) timedep_tc_kernel(const __grid_constant__ Params<K> p)
 {
     using S = Shape<K>;
     extern __shared__ uint8_t smem_raw[];
-    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     uint8_t* A_hi = smem;
     uint8_t* A_lo = smem + S::A_BYTES;
     uint8_t* B_hi = smem + 2 * S::A_BYTES;
@@ -209,8 +268,8 @@ __global__ void __launch_bounds__(128, 4) timedep_tc_kernel(const __grid_constan
     const uint32_t bar_a = tc::smem_u32(bar);
 
     // Coefficient tiles (hi / lo) and zero padding of the particle tiles.
-    for (int q = tid; q < S::NP * 8; q += 128) {
-        const int r = q >> 3, c = q & 7;
+    for (int q = tid; q < S::NP * S::KC; q += 128) {
+        const int r = q / S::KC, c = q - r * S::KC;
         float4 h, l;
         float* hv = &h.x;
         float* lv = &l.x;
@@ -220,12 +279,12 @@ __global__ void __launch_bounds__(128, 4) timedep_tc_kernel(const __grid_constan
             hv[e] = to_tf32(w);
             lv[e] = to_tf32(w - hv[e]);
         }
-        *reinterpret_cast<float4*>(B_hi + sw128(r, c)) = h;
-        *reinterpret_cast<float4*>(B_lo + sw128(r, c)) = l;
+        *reinterpret_cast<float4*>(B_hi + tile_off<S::KC>(r, c)) = h;
+        *reinterpret_cast<float4*>(B_lo + tile_off<S::KC>(r, c)) = l;
     }
-    for (int c = 0; c < 8; ++c) {
-        *reinterpret_cast<float4*>(A_hi + sw128(tid, c)) = make_float4(0.f, 0.f, 0.f, 0.f);
-        *reinterpret_cast<float4*>(A_lo + sw128(tid, c)) = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int c = 0; c < S::KC; ++c) {
+        *reinterpret_cast<float4*>(A_hi + tile_off<S::KC>(tid, c)) = make_float4(0.f, 0.f, 0.f, 0.f);
+        *reinterpret_cast<float4*>(A_lo + tile_off<S::KC>(tid, c)) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     if (tid == 0) {
         tc::mbar_init(bar_a, 1);
@@ -243,12 +302,12 @@ __global__ void __launch_bounds__(128, 4) timedep_tc_kernel(const __grid_constan
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
     const uint32_t t_row = tmem + ((uint32_t)(warp * 32) << 16);
-    const uint64_t dA_hi = tc::smem_desc_sw128(tc::smem_u32(A_hi)), dA_lo = tc::smem_desc_sw128(tc::smem_u32(A_lo));
-    const uint64_t dB_hi = tc::smem_desc_sw128(tc::smem_u32(B_hi)), dB_lo = tc::smem_desc_sw128(tc::smem_u32(B_lo));
+    const uint64_t dA_hi = tile_desc<S::SBO>(tc::smem_u32(A_hi)), dA_lo = tile_desc<S::SBO>(tc::smem_u32(A_lo));
+    const uint64_t dB_hi = tile_desc<S::SBO>(tc::smem_u32(B_hi)), dB_lo = tile_desc<S::SBO>(tc::smem_u32(B_lo));
 
     uint32_t row_off[8];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) row_off[c] = sw128(tid, c);
+    for (int c = 0; c < S::KC; ++c) row_off[c] = tile_off<S::KC>(tid, c);
     const int slot = blockIdx.x / p.chunks;
     const int cidx = blockIdx.x - slot * p.chunks;
     const int j = p.order ? p.order[slot] : slot;
@@ -285,11 +344,11 @@ __global__ void __launch_bounds__(128, 4) timedep_tc_kernel(const __grid_constan
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-            for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, dA_hi + 2 * k, dB_hi + 2 * k, k > 0 ? 1u : 0u);
+            for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, dA_hi + kKStep * k, dB_hi + kKStep * k, k > 0 ? 1u : 0u);
 #pragma unroll
-            for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, dA_lo + 2 * k, dB_hi + 2 * k, 1u);
+            for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, dA_lo + kKStep * k, dB_hi + kKStep * k, 1u);
 #pragma unroll
-            for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, dA_hi + 2 * k, dB_lo + 2 * k, 1u);
+            for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, dA_hi + kKStep * k, dB_lo + kKStep * k, 1u);
             tc::mma_commit(bar_a);
         }
         // While the product runs: the Brownian increment and the x1 harmonics.
@@ -300,14 +359,8 @@ __global__ void __launch_bounds__(128, 4) timedep_tc_kernel(const __grid_constan
         fourier_powers<float, K>(X1.val(), C1, S1);
         failed = !tc::mbar_wait(bar_a, (uint32_t)(n & 1));
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        float acc[S::NP];
-        tmem_ld_row<S::NP>(t_row, acc);
-        float v1 = acc[0], v2 = 0.f;
-#pragma unroll
-        for (int m = 1; m <= K; ++m) {
-            v1 = fmaf(C1[m], acc[m], fmaf(S1[m], acc[K + m], v1));
-            v2 = fmaf(C1[m], acc[2 * K + m], fmaf(S1[m], acc[3 * K + m], v2));
-        }
+        float v1, v2;
+        velocity_from_tmem<K>(t_row, C1, S1, v1, v2);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         const bool last = (n == N - 1);
         const float hh = last ? h_last : p.dt, ss = last ? s_last : p.s_dt;

@@ -8,8 +8,8 @@ Workflow, all on the GPU through the library's C ABI:
      every evaluation on one RNG stream and seed, so G is a deterministic
      function of u (common random numbers);
   2. data y = G(u_true) + N(0, sigma^2 I), u_true a prior draw;
-  3. training pairs (u, G(u)) with u from the prior, evaluated 256 at a time
-     by the batched map;
+  3. training pairs (u, G(u)) with u from the prior, or local to the chains'
+     start states, evaluated 256 at a time by the batched map;
   4. the surrogate network trained on (u / prior std, G(u));
   5. pCN chains, plain and with delayed acceptance through the surrogate, with
      the same beta, compared by accepted proposals per second.
@@ -52,8 +52,9 @@ def make_problem(M: int = 4096, sigma: float = 0.01, seed_true: int = 5004, seed
                    std=prior_std(w.K), sigma=sigma)
 
 
-def forward_many(ctx, prob: Problem, U: np.ndarray, chunk: int = 256) -> np.ndarray:
-    """G(u) for every row of U [N, n_u] with the batched map (one stream, one seed)."""
+def forward_many(ctx, prob: Problem, U: np.ndarray, chunk: int = 256, tensor: bool = True) -> np.ndarray:
+    """G(u) for every row of U [N, n_u] with the batched map (one stream, one seed);
+    the velocity sum on the tensor cores unless tensor=False."""
     n_obs = len(prob.t)
     out = np.empty((U.shape[0], n_obs))
     th = pm.Fourier(prob.theta0.k, prob.theta0.a, prob.theta0.b)
@@ -66,7 +67,7 @@ def forward_many(ctx, prob: Problem, U: np.ndarray, chunk: int = 256) -> np.ndar
         t = np.ascontiguousarray(np.tile(prob.t, B))
         batch = pm.Batch(prob.K, inst, x, t, th, None)
         mean = np.empty(B * n_obs)
-        pm.pm_forward_batched(ctx, batch, pm.PM_FP32, mean)
+        pm.pm_forward_batched(ctx, batch, pm.PM_FP32 | (pm.PM_TENSOR if tensor else 0), mean)
         out[s:s + B] = mean.reshape(B, n_obs)
     return out
 
@@ -80,10 +81,17 @@ def make_data(ctx, prob: Problem, seed_true: int = 5004, seed_noise: int = 6004)
     return prob
 
 
-def training_pairs(ctx, prob: Problem, n: int, seed: int = 7004):
+def training_pairs(ctx, prob: Problem, n: int, seed: int = 7004, centers: np.ndarray = None, spread: float = 1.0,
+                   tensor: bool = True):
+    """n pairs (z, G(std * z)).  Without centers z is a prior draw (standard
+    normal); with centers [C, n_u] (fields u) z = centers[c] / std + spread * xi
+    for a random c per pair: pairs local to the region the chains sample."""
     rng = np.random.Generator(np.random.PCG64(seed))
     Z = rng.standard_normal((n, len(prob.std)))
-    G = forward_many(ctx, prob, Z * prob.std)
+    if centers is not None:
+        zc = np.asarray(centers, dtype=np.float64) / prob.std[None, :]
+        Z = zc[rng.integers(0, len(zc), n)] + spread * Z
+    G = forward_many(ctx, prob, Z * prob.std, tensor=tensor)
     return Z.astype(np.float32), G.astype(np.float32)
 
 
@@ -106,11 +114,11 @@ def start_states(prob: Problem, n_chains: int, spread: float = 0.0, seed: int = 
     return prob.u_true[None, :] + spread * prob.std[None, :] * rng.standard_normal((n_chains, len(prob.std)))
 
 
-def run_chains(ctx, prob: Problem, u0, beta, n_steps, seed, net=None):
+def run_chains(ctx, prob: Problem, u0, beta, n_steps, seed, net=None, tensor: bool = True):
     th = pm.Fourier(prob.theta0.k, prob.theta0.a, prob.theta0.b)
     ch = pm.PCN(ctx, prob.K, u0, prob.y, prob.sigma, beta, seed, theta0=th, x=prob.x, t=prob.t, kappa=prob.kappa,
                 dt=prob.dt, M=prob.M, path_seed=prob.path_seed, screen=net,
-                screen_scale=(1.0 / prob.std) if net is not None else None)
+                screen_scale=(1.0 / prob.std) if net is not None else None, tensor=tensor)
     t0 = time.perf_counter()
     st = ch.run(n_steps)
     st["wall_seconds"] = time.perf_counter() - t0

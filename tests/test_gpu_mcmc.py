@@ -84,3 +84,28 @@ def test_particle_map_chains_run_and_screen_saves_evaluations(c):
     da.close()
     pm.pm_surrogate_destroy(net)
     assert sd["forward_evals"] == sd["stage1_accepts"] <= sd["proposals"] == 80
+
+
+def test_tensor_map_chains_start_from_the_tensor_map_misfit(c):
+    # map_flags = PM_TENSOR: the chains' initial misfits are those of the
+    # batched tensor-core map on the same stream and seed (stream 0 for all).
+    w = inputs.batched_instances(B=1, M=256)[0]
+    x, t = w.x[:20].copy(), w.t[:20].copy()
+    th = pm.Fourier(w.theta0.k, w.theta0.a, w.theta0.b)
+    u0 = np.stack([inputs.prior_field(10, 70 + k) for k in range(3)])
+    y = np.linspace(-0.2, 0.2, len(t))
+    sigma = 0.1
+    ch = pm.PCN(c, 10, u0, y, sigma, 0.1, seed=3, theta0=th, x=x, t=t, kappa=w.kappa, dt=w.dt, M=256,
+                path_seed=w.seed, tensor=True)
+    _, phi, _, _ = ch.state()
+    ch.close()
+    inst = [dict(kind=pm.PM_KIND_TIMEDEP, u=u0[b], kappa=w.kappa, dt=w.dt, row0=b * len(t), n_obs=len(t), M=256,
+                 seed=w.seed, stream=0) for b in range(3)]
+    batch = pm.Batch(10, inst, np.ascontiguousarray(np.tile(x, (3, 1))), np.ascontiguousarray(np.tile(t, 3)), th, None)
+    G = np.empty(3 * len(t))
+    pm.pm_forward_batched(c, batch, pm.PM_FP32 | pm.PM_TENSOR, G)
+    phi_ref = ((y[None, :] - G.reshape(3, -1)) ** 2).sum(1) / (2 * sigma ** 2)
+    np.testing.assert_allclose(phi, phi_ref, rtol=1e-12, atol=0)
+    G_simt = np.empty(3 * len(t))
+    pm.pm_forward_batched(c, batch, pm.PM_FP32, G_simt)
+    assert not np.array_equal(G, G_simt)   # the flag reached the map
