@@ -434,6 +434,51 @@ def run_aux(args):
     return 0
 
 
+def run_sweep(args):
+    """Cost against the number of real coefficients N_u (the scaling the paper
+    plots for its GPU code, Section 4): the time-dependent workload's 300
+    observations x M paths with a prior field of each K, on the FP32 pipes and
+    on the tensor cores where the tensor path has the K (auxiliary line)."""
+    import torch
+
+    import paper_1808_10580_gb300 as pm
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    ctx = pm.pm_create(0, stream.cuda_stream)
+    pm.pm_set_kernel_timing(ctx, 1)
+    w = inputs.timedep_k10(M=args.M or 10_000)
+    th = pm.Fourier(w.theta0.k, w.theta0.a, w.theta0.b)
+    x = torch.from_numpy(w.x).to(dev)
+    t = torch.from_numpy(w.t).to(dev)
+    mean = torch.empty(len(w.t), dtype=torch.float64, device=dev)
+    steps = particle_steps(w)
+    rows = []
+    for K in (2, 3, 4, 5, 6, 8, 10, 12, 16):
+        fld = pm.Field(K, inputs.prior_field(K, 1001))
+        row = {"K": K, "n_u": (2 * K + 1) ** 2 - 1}
+        for name, flags in (("fp32_ms", pm.PM_FP32), ("tensor_ms", pm.PM_FP32 | pm.PM_TENSOR)):
+            if name == "tensor_ms" and K not in (4, 5, 6, 8, 10, 12):
+                continue
+            ms = []
+            for k in range(args.warmup + args.steps):
+                pm.pm_forward_timedep(ctx, fld, w.kappa, th, x, t, len(w.t), w.M, w.dt, w.seed, flags, mean)
+                if k >= args.warmup:
+                    ms.append(pm.pm_last_kernel_ms(ctx))
+            row[name] = statistics.median(ms)
+        rows.append(row)
+    fp32 = np.array([[r["n_u"], r["fp32_ms"]] for r in rows if r["K"] >= 4])
+    slope, icpt = np.polyfit(fp32[:, 0], fp32[:, 1], 1)
+    line = {"metric": "particle-map kernel time vs N_u", "auxiliary": True, "data": "synthetic",
+            "unit": "ms per evaluation", "value": None, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "config": {"workload": f"{w.name} with a prior field of each K", "particle_steps_per_eval": steps},
+            "rows": rows, "fp32_linear_fit": {"ms_per_coefficient": slope, "ms_at_zero": icpt}}
+    print(json.dumps(line), flush=True)
+    pm.pm_destroy(ctx)
+    return 0
+
+
 def run_mcmc(args):
     """Surrogate-screened pCN against plain pCN on the same GPU (auxiliary line):
     64 chains started at the data-generating field, the same beta for both
@@ -447,7 +492,7 @@ def run_mcmc(args):
     torch.cuda.set_stream(stream)
     ctx = pm.pm_create(0, stream.cuda_stream)
     t0 = time.perf_counter()
-    prob = sm.make_data(ctx, sm.make_problem(sigma=args.sigma))
+    prob = sm.make_data(ctx, sm.make_problem(M=args.M or 4096, sigma=args.sigma))
     u0 = sm.start_states(prob, 64, spread=0.0)
     centers = u0 if args.train_spread > 0 else None
     spread = args.train_spread if args.train_spread > 0 else 1.0
@@ -489,7 +534,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--M", type=int, default=0, help="particles per observation (default: the workload's own; "
                     "smaller values are for profiling captures only)")
-    ap.add_argument("--workload", default="timedep", choices=["timedep", "dirichlet", "batched", "mcmc"],
+    ap.add_argument("--workload", default="timedep", choices=["timedep", "dirichlet", "batched", "mcmc", "sweep"],
                     help="timedep: the headline line; dirichlet / batched / mcmc: auxiliary measurements")
     ap.add_argument("--train-pairs", type=int, default=1 << 16, help="mcmc: surrogate training pairs")
     ap.add_argument("--betas", default="0.03", help="mcmc: comma-separated pCN steps (each the same for both samplers)")
@@ -516,6 +561,8 @@ def main():
         return run_reference(args)
     if args.workload == "mcmc":
         return run_mcmc(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
     if args.workload != "timedep":
         return run_aux(args)
     return run_gpu(args)
