@@ -137,17 +137,19 @@ def dist_setup(n_gpus):
     return rank, world, local
 
 
-def oracle_sample(w, budget_s=12.0, max_paths=512):
+def oracle_sample(w, budget_s=12.0, max_paths=512, obs_id=None):
     """Times the FP64 oracle on paths [0, P) of every observation, P sized so the
-    run takes about budget_s.  Returns (steps/s, threads, P, per-path g, seconds)."""
+    run takes about budget_s.  Returns (steps/s, threads, P, per-path g, seconds).
+    obs_id: the RNG stream of each observation (shared paths), default its index."""
     import oracle
     oracle.lib()
+    ids = None if obs_id is None else np.asarray(obs_id, dtype=np.int64)
     t0 = time.perf_counter()
-    g1 = oracle.timedep_paths(w.K, w.u, w.kappa, w.theta0, w.x, w.t, w.dt, w.seed, npaths=1)
+    g1 = oracle.timedep_paths(w.K, w.u, w.kappa, w.theta0, w.x, w.t, w.dt, w.seed, npaths=1, obs_id=ids)
     t1 = time.perf_counter() - t0
     P = int(max(1, min(max_paths, budget_s / max(t1, 1e-3))))
     t0 = time.perf_counter()
-    g = oracle.timedep_paths(w.K, w.u, w.kappa, w.theta0, w.x, w.t, w.dt, w.seed, npaths=P)
+    g = oracle.timedep_paths(w.K, w.u, w.kappa, w.theta0, w.x, w.t, w.dt, w.seed, npaths=P, obs_id=ids)
     secs = time.perf_counter() - t0
     steps = particle_steps(w) // w.M * P
     threads = os.cpu_count() or 1
@@ -202,6 +204,11 @@ def run_gpu(args):
     n_obs = len(w.t)
     inst = rank                                   # each rank evaluates its own instance (weak scaling)
     steps_per_eval = particle_steps(w)
+    stream_of = None
+    if args.share_paths:
+        # one path per point and path index, stopped at every time of that point
+        _, stream_of, _, steps_per_path = pm.pm_path_groups(w.x, w.t, w.dt)
+        steps_per_eval = steps_per_path * w.M
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
     ctx = pm.pm_create(local, stream.cuda_stream)
@@ -212,7 +219,8 @@ def run_gpu(args):
     mean = torch.empty(n_obs, dtype=torch.float64, device=dev)
     var = torch.empty_like(mean)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    flags = pm.PM_FP32 | pm.PM_ASYNC | (pm.PM_TENSOR if args.tensor else 0)
+    mode = (pm.PM_TENSOR if args.tensor else 0) | (pm.PM_SHARE_PATHS if args.share_paths else 0)
+    flags = pm.PM_FP32 | pm.PM_ASYNC | mode
 
     def step():
         pm.pm_forward_timedep(ctx, fld, w.kappa, th, x, t, n_obs, w.M, w.dt, w.seed, flags, mean, var,
@@ -265,7 +273,7 @@ def run_gpu(args):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         pm.pm_forward_timedep(ctx, fld, w.kappa, th, hx, ht, n_obs, w.M, w.dt, w.seed,
-                              pm.PM_FP32 | (pm.PM_TENSOR if args.tensor else 0), hmean, hvar, instance=inst)
+                              pm.PM_FP32 | mode, hmean, hvar, instance=inst)
         e2e_times.append(time.perf_counter() - t0)
     e2e_value = steps_per_eval * world / statistics.median(e2e_times)
 
@@ -310,6 +318,8 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "K": w.K, "n_u": (2 * w.K + 1) ** 2 - 1, "n_obs": n_obs, "M": w.M,
                        "dt": w.dt, "kappa": w.kappa, "particle_steps_per_eval": steps_per_eval,
+                       "shared_paths": bool(args.share_paths),
+                       "independent_path_steps_per_eval": particle_steps(w),
                        "forward_map_evals_per_s": value / steps_per_eval,
                        "l2": "flushed between timed steps (256 MiB write, outside the timed events)",
                        "reductions": "f64", "mc_se_median": float(np.median(se)), "mc_se_max": float(se.max())},
@@ -320,11 +330,11 @@ def run_gpu(args):
             "clocks": clock,
         }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, threads, P, g_or, secs = oracle_sample(w)
+        rate, threads, P, g_or, secs = oracle_sample(w, obs_id=stream_of)
         # pathwise check of the same sample against the GPU (same stream)
         gdev = torch.empty(n_obs * w.M, dtype=torch.float64, device=dev)
         pm.pm_forward_timedep(ctx, fld, w.kappa, th, x, t, n_obs, w.M, w.dt, w.seed,
-                              pm.PM_FP32 | (pm.PM_TENSOR if args.tensor else 0), mean, var, g_out=gdev)
+                              pm.PM_FP32 | mode, mean, var, g_out=gdev)
         g_gpu = gdev.cpu().numpy().reshape(n_obs, w.M)[:, :P]
         d = (g_gpu - g_or).reshape(-1)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
@@ -494,11 +504,16 @@ def run_mcmc(args):
     t0 = time.perf_counter()
     prob = sm.make_data(ctx, sm.make_problem(M=args.M or 4096, sigma=args.sigma))
     u0 = sm.start_states(prob, 64, spread=0.0)
-    centers = u0 if args.train_spread > 0 else None
+    center = u0[0] if args.train_spread > 0 else None
     spread = args.train_spread if args.train_spread > 0 else 1.0
-    Z, G = sm.training_pairs(ctx, prob, args.train_pairs, centers=centers, spread=spread, tensor=args.tensor)
+    # network input: prior coordinates u / std (--screen-coords prior), or
+    # coordinates centred on the start state (local)
+    coords = sm.screen_coords(prob, center, spread) if args.screen_coords == "local" else sm.screen_coords(prob)
+    Z, G = sm.training_pairs(ctx, prob, args.train_pairs, center=center, spread=spread, tensor=args.tensor,
+                             coords=coords)
     t_pairs = time.perf_counter() - t0
-    Zv, Gv = sm.training_pairs(ctx, prob, 2048, seed=7005, centers=centers, spread=spread, tensor=args.tensor)
+    Zv, Gv = sm.training_pairs(ctx, prob, 2048, seed=7005, center=center, spread=spread, tensor=args.tensor,
+                               coords=coords)
     t1 = time.perf_counter()
     net, hist = sm.train_surrogate(ctx, prob, Z, G, epochs=args.epochs, weight_decay=args.weight_decay,
                                    lr_decay=args.lr_decay)
@@ -507,7 +522,8 @@ def run_mcmc(args):
     rmse_train = sm.surrogate_rmse(ctx, net, Z[:2048], G[:2048])
     for beta in [float(v) for v in args.betas.split(",")]:
         plain, _ = sm.run_chains(ctx, prob, u0, beta, args.plain_steps, seed=11, tensor=args.tensor)
-        da, _ = sm.run_chains(ctx, prob, u0, beta, args.da_steps, seed=11, net=net, tensor=args.tensor)
+        da, _ = sm.run_chains(ctx, prob, u0, beta, args.da_steps, seed=11, net=net, tensor=args.tensor,
+                              coords=coords)
         line = {"metric": "accepted pCN proposals/s (64 chains)", "auxiliary": True, "data": "synthetic",
                 "value": da["accepted_per_s"], "unit": "accepted proposals/s",
                 "ratio_vs_plain": da["accepted_per_s"] / max(plain["accepted_per_s"], 1e-30),
@@ -515,7 +531,8 @@ def run_mcmc(args):
                            "n_obs": len(prob.t), "sigma": prob.sigma, "beta": beta, "chains": 64,
                            "start": "data-generating field", "tensor_cores": bool(args.tensor),
                            "training_inputs": (f"local: start state + {args.train_spread} x prior std x N(0, I)"
-                                               if args.train_spread > 0 else "prior draws")},
+                                               if args.train_spread > 0 else "prior draws"),
+                           "screen_coords": args.screen_coords},
                 "plain": plain, "delayed_acceptance": da,
                 "surrogate": {"val_rmse": rmse, "train_rmse": rmse_train, "final_train_loss": float(hist[-1]),
                               "train_seconds": t_train, "pair_generation_seconds": t_pairs}}
@@ -542,6 +559,8 @@ def main():
                     help="mcmc: observation noise standard deviation (0.01 is below the map's Monte Carlo noise "
                          "at M = 4096 and no chain moves)")
     ap.add_argument("--epochs", type=int, default=100, help="mcmc: surrogate training epochs")
+    ap.add_argument("--screen-coords", default="prior", choices=["prior", "local"],
+                    help="mcmc: surrogate input u / prior std, or (u - start) / (spread x prior std)")
     ap.add_argument("--train-spread", type=float, default=0.1,
                     help="mcmc: training inputs local to the start states with this spread (prior-std units); "
                          "0: prior draws")
@@ -554,6 +573,9 @@ def main():
                     help="timedep: velocity sum on the tensor cores (PM_TENSOR; the default)")
     ap.add_argument("--no-tensor", dest="tensor", action="store_false",
                     help="timedep: velocity sum on the FP32 pipes")
+    ap.add_argument("--share-paths", action="store_true",
+                    help="timedep: observations at one point share their paths (PM_SHARE_PATHS, tensor path); "
+                         "value counts the steps taken, forward_map_evals_per_s the evaluations")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -79,6 +79,18 @@ extern "C" {
  * cores (tcgen05 TF32 with a three-term hi/lo split, about float accuracy);
  * supported for K in {4, 5, 6, 8, 10, 12}, other K fall back to the FP32 pipes. */
 #define PM_TENSOR 8u
+/* pm_forward_timedep with PM_TENSOR: observations at bit-identical points x
+ * share their paths (Theorem 3.1: the value at t_j needs the path only up to
+ * time t_j, so one path serves every t_j at the same x).  Such a group
+ * draws its noise from the RNG stream of its
+ * lowest observation index j0 (counter word j = j0 for every member); one path
+ * i runs to the largest step count of the group and every member j records
+ * theta0 where its own path ends (after N_j - 1 full steps and its last step
+ * of length t_j - (N_j - 1) dt, with the noise of that step).  Each member's
+ * estimate has the law it has without the flag, members of a group are
+ * correlated, and a group costs max N_j steps per path instead of sum N_j.
+ * With PM_DEVICE_PTRS the call copies x and t to the host to form the groups. */
+#define PM_SHARE_PATHS 16u
 
 #define PM_MAX_THETA0_MODES 64
 #define PM_MAX_BOUNDARY_MODES 32
@@ -151,13 +163,29 @@ typedef struct pm_path_opts {
  *   M       particles per observation, 1 <= M, path_offset + M <= 2^32
  *   dt      Euler-Maruyama step > 0
  *   seed    64-bit Philox key
- *   flags   PM_FP32 | PM_FP64, PM_DEVICE_PTRS, PM_ASYNC
+ *   flags   PM_FP32 | PM_FP64, PM_DEVICE_PTRS, PM_ASYNC, PM_TENSOR, PM_SHARE_PATHS
+ *           (PM_SHARE_PATHS needs PM_TENSOR, float paths and a tensor-core K)
  *   mean    [n_obs] output; var [n_obs] output or NULL
  * n_obs == 0 is a no-op.  Returns PM_OK or an error. */
 int pm_forward_timedep(pm_ctx* ctx, const pm_field* field, double kappa, const pm_fourier* theta0,
                        const double* x, const double* t, int64_t n_obs, int64_t M, double dt,
                        uint64_t seed, uint32_t flags, double* mean, double* var,
                        const pm_path_opts* opts);
+
+/* The groups PM_SHARE_PATHS forms, computed on the host (no device, no
+ * context): x [n_obs][2], t [n_obs] host arrays as for pm_forward_timedep.
+ *   group_of[j]   group of observation j, numbered in launch order (groups
+ *                 sorted by their largest step count, longest first, then by
+ *                 stream); may be NULL
+ *   stream_of[j]  RNG observation index its paths use (lowest index of its
+ *                 group); may be NULL
+ *   n_groups      number of groups; may be NULL
+ *   steps_per_path  Euler steps one path index takes over all groups (sum of
+ *                 the groups' largest N_j); may be NULL
+ * Returns PM_OK, or PM_EINVAL for NULL x / t, n_obs < 0, dt <= 0, or a time
+ * that is negative, not finite or needs more than 2^31 - 2 steps. */
+int pm_path_groups(const double* x, const double* t, int64_t n_obs, double dt, int32_t* group_of,
+                   int32_t* stream_of, int64_t* n_groups, int64_t* steps_per_path);
 
 /* Algorithm 2 (Section 3.2): Dirichlet map G_j(u) = theta(x_j) in the disk.
  *   drift_scale  multiplies v_u (the drift is -drift_scale v_u)
@@ -334,6 +362,8 @@ typedef struct pm_pcn_config {
     const double* x;            /* [n_obs][2] host */
     const double* t;            /* [n_obs] host */
     uint32_t map_flags;         /* particle map: 0 (FP32 pipes) or PM_TENSOR; other bits rejected */
+    uint32_t reserved;
+    const double* screen_shift; /* [n_u] host or NULL (= 0): the surrogate input is (u - shift) * scale */
 } pm_pcn_config;
 
 typedef struct pm_pcn_stats {
@@ -346,8 +376,8 @@ typedef struct pm_pcn_stats {
 } pm_pcn_stats;
 
 /* u0: [n_chains][n_u] host.  screen: NULL for plain pCN, else a surrogate
- * with n_in = n_u and n_out = n_obs whose input is u * screen_scale
- * (screen_scale [n_u] host, NULL = 1). */
+ * with n_in = n_u and n_out = n_obs whose input is (u - cfg->screen_shift) *
+ * screen_scale (screen_scale [n_u] host, NULL = 1). */
 int pm_pcn_create(pm_ctx* ctx, pm_pcn** out, const pm_pcn_config* cfg, const double* u0, const pm_mlp* screen,
                   const float* screen_scale);
 int pm_pcn_run(pm_ctx* ctx, pm_pcn* chains, int64_t n_steps, pm_pcn_stats* stats);

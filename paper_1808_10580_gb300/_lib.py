@@ -27,6 +27,7 @@ PM_FP64 = 1
 PM_DEVICE_PTRS = 2
 PM_ASYNC = 4
 PM_TENSOR = 8
+PM_SHARE_PATHS = 16
 
 
 class PMError(RuntimeError):
@@ -117,6 +118,7 @@ def load(build_if_missing: bool = True):
     L.pm_last_step_count.restype = i64
     L.pm_last_grid.argtypes = [vp]
     L.pm_last_grid.restype = i64
+    L.pm_path_groups.argtypes = [vp, vp, i64, C.c_double, vp, vp, vp, vp]
     _lib = L
     return L
 
@@ -220,6 +222,24 @@ def pm_last_step_count(ctx):
 
 def pm_last_grid(ctx):
     return int(load().pm_last_grid(ctx))
+
+
+def pm_path_groups(x, t, dt):
+    """The observation groups PM_SHARE_PATHS forms (host only) ->
+    (group_of [n_obs], stream_of [n_obs], n_groups, steps_per_path)."""
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 2)
+    t = np.ascontiguousarray(t, dtype=np.float64).reshape(-1)
+    n = len(t)
+    assert x.shape[0] == n
+    gof = np.empty(n, dtype=np.int32)
+    sof = np.empty(n, dtype=np.int32)
+    ng = C.c_int64()
+    sp = C.c_int64()
+    rc = load().pm_path_groups(x.ctypes.data, t.ctypes.data, n, float(dt), gof.ctypes.data, sof.ctypes.data,
+                               C.byref(ng), C.byref(sp))
+    if rc < 0:
+        raise PMError(rc, "pm_path_groups: invalid arguments")
+    return gof, sof, int(ng.value), int(sp.value)
 
 
 def _opts(path_offset=0, instance=0, g_out=None, x_out=None):
@@ -417,7 +437,8 @@ class pm_pcn_config(C.Structure):
     _fields_ = [("n_chains", C.c_int32), ("K", C.c_int32), ("beta", C.c_double), ("sigma", C.c_double),
                 ("seed", C.c_uint64), ("n_obs", C.c_int64), ("y", C.c_void_p), ("A", C.c_void_p),
                 ("kappa", C.c_double), ("dt", C.c_double), ("M", C.c_int64), ("path_seed", C.c_uint64),
-                ("theta0", C.POINTER(pm_fourier)), ("x", C.c_void_p), ("t", C.c_void_p), ("map_flags", C.c_uint32)]
+                ("theta0", C.POINTER(pm_fourier)), ("x", C.c_void_p), ("t", C.c_void_p), ("map_flags", C.c_uint32),
+                ("reserved", C.c_uint32), ("screen_shift", C.c_void_p)]
 
 
 class pm_pcn_stats(C.Structure):
@@ -442,7 +463,7 @@ class PCN:
     """pCN chains on the device (plain, or delayed acceptance when `screen` is given)."""
 
     def __init__(self, ctx, K, u0, y, sigma, beta, seed, A=None, theta0: Fourier = None, x=None, t=None, kappa=0.0,
-                 dt=1e-3, M=1, path_seed=0, screen=None, screen_scale=None, tensor=False):
+                 dt=1e-3, M=1, path_seed=0, screen=None, screen_scale=None, tensor=False, screen_shift=None):
         self.ctx = ctx
         self.keep = [np.ascontiguousarray(y, dtype=np.float64), np.ascontiguousarray(u0, dtype=np.float64)]
         self.C, self.n_u = self.keep[1].shape
@@ -450,12 +471,13 @@ class PCN:
         x_ = np.ascontiguousarray(x, dtype=np.float64) if x is not None else None
         t_ = np.ascontiguousarray(t, dtype=np.float64) if t is not None else None
         sc = _f32(screen_scale) if screen_scale is not None else None
-        self.keep += [A_, x_, t_, sc, theta0]
+        sh = np.ascontiguousarray(screen_shift, dtype=np.float64) if screen_shift is not None else None
+        self.keep += [A_, x_, t_, sc, theta0, sh]
         cfg = pm_pcn_config(self.C, int(K), float(beta), float(sigma), int(seed), len(self.keep[0]),
                             self.keep[0].ctypes.data, A_.ctypes.data if A_ is not None else None, float(kappa),
                             float(dt), int(M), int(path_seed), C.pointer(theta0.s) if theta0 is not None else None,
                             x_.ctypes.data if x_ is not None else None, t_.ctypes.data if t_ is not None else None,
-                            PM_TENSOR if tensor else 0)
+                            PM_TENSOR if tensor else 0, 0, sh.ctypes.data if sh is not None else None)
         self.h = C.c_void_p()
         _check(_plib().pm_pcn_create(ctx, C.byref(self.h), C.byref(cfg), self.keep[1].ctypes.data, screen,
                                      sc.ctypes.data if sc is not None else None))

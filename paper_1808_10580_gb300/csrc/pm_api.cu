@@ -2,6 +2,7 @@
 // staging, workspace management and kernel sequencing.  Every arithmetic step
 // of the forward maps runs in the CUDA kernels (pm_kernels.cuh,
 // pm_support.cu); the host only validates, stages and copies.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -300,6 +301,90 @@ int64_t pm_last_step_count(const pm_ctx* c) { return c ? c->last_steps : -1; }
 int64_t pm_last_grid(const pm_ctx* c) { return c ? c->last_grid : 0; }
 
 // ---------------------------------------------------------------------------
+// Observation groups that share paths (PM_SHARE_PATHS): observations at
+// bit-identical x, members sorted by step count then index, the RNG stream
+// the lowest member index; groups in launch order (largest step count first,
+// then by stream).  Step counts as the prep kernel forms them.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct PathGroups {
+    std::vector<int4> groups;      // {m0, m1, stream, nmax}
+    std::vector<int32_t> members;  // observation indices, group by group
+    int64_t steps_per_path = 0;    // sum of nmax
+};
+
+int make_path_groups(const double* x, const double* t, int64_t n, double dt, PathGroups& G)
+{
+    std::vector<int32_t> N((size_t)n);
+    for (int64_t j = 0; j < n; ++j) {
+        const double tj = t[j];
+        if (!std::isfinite(tj) || tj < 0.0 || !std::isfinite(x[2 * j]) || !std::isfinite(x[2 * j + 1])) return PM_EINVAL;
+        const double steps = tj > 0.0 ? std::ceil(tj / dt - 1e-9) : 0.0;
+        if (steps > 2147483646.0) return PM_EINVAL;
+        N[(size_t)j] = (int32_t)steps;
+    }
+    auto bits = [&](int64_t j, int c) {
+        uint64_t b;
+        memcpy(&b, &x[2 * j + c], 8);
+        return b;
+    };
+    std::vector<int32_t> idx((size_t)n);
+    for (int64_t j = 0; j < n; ++j) idx[(size_t)j] = (int32_t)j;
+    std::sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) {
+        const uint64_t a1 = bits(a, 0), b1 = bits(b, 0);
+        if (a1 != b1) return a1 < b1;
+        const uint64_t a2 = bits(a, 1), b2 = bits(b, 1);
+        if (a2 != b2) return a2 < b2;
+        if (N[(size_t)a] != N[(size_t)b]) return N[(size_t)a] < N[(size_t)b];
+        return a < b;
+    });
+    std::vector<int4> runs;  // m0, m1 over idx, stream, nmax
+    for (size_t s = 0; s < (size_t)n;) {
+        size_t e = s + 1;
+        while (e < (size_t)n && bits(idx[e], 0) == bits(idx[s], 0) && bits(idx[e], 1) == bits(idx[s], 1)) ++e;
+        int32_t stream = idx[s];
+        for (size_t k = s; k < e; ++k) stream = std::min(stream, idx[k]);
+        runs.push_back(make_int4((int)s, (int)e, stream, N[(size_t)idx[e - 1]]));
+        s = e;
+    }
+    std::stable_sort(runs.begin(), runs.end(), [](const int4& a, const int4& b) {
+        if (a.w != b.w) return a.w > b.w;
+        return a.z < b.z;
+    });
+    G.groups.clear();
+    G.members.clear();
+    G.steps_per_path = 0;
+    for (const int4& r : runs) {
+        const int m0 = (int)G.members.size();
+        for (int k = r.x; k < r.y; ++k) G.members.push_back(idx[(size_t)k]);
+        G.groups.push_back(make_int4(m0, (int)G.members.size(), r.z, r.w));
+        G.steps_per_path += r.w;
+    }
+    return PM_OK;
+}
+
+}  // namespace
+
+int pm_path_groups(const double* x, const double* t, int64_t n_obs, double dt, int32_t* group_of, int32_t* stream_of,
+                   int64_t* n_groups, int64_t* steps_per_path)
+{
+    if (!x || !t || n_obs < 0 || !(std::isfinite(dt) && dt > 0)) return PM_EINVAL;
+    PathGroups G;
+    const int rc = make_path_groups(x, t, n_obs, dt, G);
+    if (rc) return rc;
+    for (size_t g = 0; g < G.groups.size(); ++g)
+        for (int m = G.groups[g].x; m < G.groups[g].y; ++m) {
+            const int32_t j = G.members[(size_t)m];
+            if (group_of) group_of[j] = (int32_t)g;
+            if (stream_of) stream_of[j] = G.groups[g].z;
+        }
+    if (n_groups) *n_groups = (int64_t)G.groups.size();
+    if (steps_per_path) *steps_per_path = G.steps_per_path;
+    return PM_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Algorithm 1
 // ---------------------------------------------------------------------------
 int pm_forward_timedep(pm_ctx* c, const pm_field* field, double kappa, const pm_fourier* th, const double* x,
@@ -334,17 +419,41 @@ int pm_forward_timedep(pm_ctx* c, const pm_field* field, double kappa, const pm_
     const int64_t chunks64 = (M + kTimedepBlock - 1) / kTimedepBlock;
     if (n_obs * chunks64 > 0x7fffffffLL) return fail(PM_EINVAL, "n_obs * ceil(M/%d) exceeds the grid limit", kTimedepBlock);
     const int32_t chunks = (int32_t)chunks64;
+    const int K = field->K;
+    const bool tc = !fp64 && (flags & PM_TENSOR) && (K == 4 || K == 5 || K == 6 || K == 8 || K == 10 || K == 12);
+    const bool share = flags & PM_SHARE_PATHS;
+    if (share && !tc) return fail(PM_EINVAL, "PM_SHARE_PATHS needs PM_TENSOR, float paths and K in {4,5,6,8,10,12}");
     if ((rc = set_device(c))) return rc;
 
+    // Shared paths: the groups, from host copies of x and t.
+    PathGroups PG;
+    if (share) {
+        std::vector<double> hx, ht;
+        const double *gx = x, *gt = t;
+        if (dev) {
+            hx.resize((size_t)(2 * n_obs));
+            ht.resize((size_t)n_obs);
+            PM_CUDA(cudaMemcpyAsync(hx.data(), x, (size_t)n_obs * 16, cudaMemcpyDeviceToHost, c->stream), "copy x");
+            PM_CUDA(cudaMemcpyAsync(ht.data(), t, (size_t)n_obs * 8, cudaMemcpyDeviceToHost, c->stream), "copy t");
+            PM_CUDA(cudaStreamSynchronize(c->stream), "copy x, t");
+            gx = hx.data();
+            gt = ht.data();
+        }
+        if (make_path_groups(gx, gt, n_obs, dt, PG))
+            return fail(PM_EINVAL, "observation points or times are not finite, a time is negative, or a step count exceeds 2^31");
+    }
+
     // Workspace layout.
-    const bool sort = n_obs <= 8192;
+    const bool sort = n_obs <= 8192 && !share;
     auto layout = [&](Bump& b) {
-        struct P { unsigned* err; unsigned long long* steps; ObsRec* rec; int32_t* order; double2* part; double *x, *t, *mean, *var, *g, *xo; } p{};
+        struct P { unsigned* err; unsigned long long* steps; ObsRec* rec; int32_t* order; double2* part; int4* grp; int32_t* mem; double *x, *t, *mean, *var, *g, *xo; } p{};
         p.err = b.take<unsigned>(64);     // error flag, then the step counter 128 bytes on
         p.steps = (unsigned long long*)(p.err ? p.err + 32 : nullptr);
         p.rec = b.take<ObsRec>((size_t)n_obs);
         p.order = sort ? b.take<int32_t>((size_t)n_obs) : nullptr;
         p.part = b.take<double2>((size_t)(n_obs * chunks));
+        p.grp = share ? b.take<int4>(PG.groups.size()) : nullptr;
+        p.mem = share ? b.take<int32_t>((size_t)n_obs) : nullptr;
         if (!dev) {
             p.x = b.take<double>((size_t)(3 * n_obs));  // x then t, one copy
             p.t = p.x + 2 * n_obs;
@@ -383,10 +492,17 @@ int pm_forward_timedep(pm_ctx* c, const pm_field* field, double kappa, const pm_
 
     const std::vector<double> tab = stage_coefficients(field->K, field->u);
     PM_CUDA(cudaMemsetAsync(W.err, 0, 256, c->stream), "clear flags");
-    PM_CUDA(launch_prep_timedep(dx, dtm, n_obs, dt, kappa, W.rec, W.order, W.err, c->stream, W.steps, M),
+    PM_CUDA(launch_prep_timedep(dx, dtm, n_obs, dt, kappa, W.rec, W.order, W.err, c->stream, share ? nullptr : W.steps, M),
             "prep kernel");
     c->last_steps = -1;
     count_launch(c, sort ? 2 : 1);
+    if (share) {
+        PM_CUDA(cudaMemcpyAsync(W.grp, PG.groups.data(), PG.groups.size() * sizeof(int4), cudaMemcpyHostToDevice, c->stream),
+                "copy groups");
+        PM_CUDA(cudaMemcpyAsync(W.mem, PG.members.data(), PG.members.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                c->stream),
+                "copy group members");
+    }
 
     TimedepLaunch L{};
     L.coef = tab.data();
@@ -405,14 +521,16 @@ int pm_forward_timedep(pm_ctx* c, const pm_field* field, double kappa, const pm_
     L.path_offset = off;
     L.n_obs = (int32_t)n_obs;
     L.chunks = chunks;
-    c->last_grid = n_obs * (int64_t)chunks;
+    L.groups = share ? W.grp : nullptr;
+    L.members = share ? W.mem : nullptr;
+    L.n_groups = (int32_t)PG.groups.size();
+    c->last_grid = (share ? (int64_t)PG.groups.size() : n_obs) * (int64_t)chunks;
     L.inst = opts ? opts->instance : 0u;
     L.key0 = (uint32_t)(seed & 0xffffffffu);
     L.key1 = (uint32_t)(seed >> 32);
     if (c->timing) PM_CUDA(cudaEventRecord(c->ev0, c->stream), "event");
     cudaError_t e;
-    const int K = field->K;
-    if (!fp64 && (flags & PM_TENSOR) && (K == 4 || K == 5 || K == 6 || K == 8 || K == 10 || K == 12)) {
+    if (tc) {
         switch (K) {
         case 4: e = tdtc::launch_timedep_tc<4>(L, W.err + 1, c->stream); break;
         case 5: e = tdtc::launch_timedep_tc<5>(L, W.err + 1, c->stream); break;
@@ -450,7 +568,7 @@ int pm_forward_timedep(pm_ctx* c, const pm_field* field, double kappa, const pm_
     PM_CUDA(cudaMemcpyAsync(&err_flag, W.err, 4, cudaMemcpyDeviceToHost, c->stream), "copy flags");
     PM_CUDA(cudaMemcpyAsync(&steps_taken, W.steps, 8, cudaMemcpyDeviceToHost, c->stream), "copy step count");
     PM_CUDA(cudaStreamSynchronize(c->stream), "timedep");
-    c->last_steps = (int64_t)steps_taken;
+    c->last_steps = share ? PG.steps_per_path * M : (int64_t)steps_taken;
     if (!dev) {
         const double* h = (const double*)c->host;
         size_t o = 0;

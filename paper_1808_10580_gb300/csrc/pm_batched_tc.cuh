@@ -86,11 +86,8 @@ __global__ void __launch_bounds__(128, 6) batched_tc_kernel(const __grid_constan
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
     const uint32_t t_row = tmem + ((uint32_t)(warp * 32) << 16);
-    const uint64_t dA_hi = tile_desc<S::SBO>(tc::smem_u32(A_hi)), dA_lo = tile_desc<S::SBO>(tc::smem_u32(A_lo));
-    const uint64_t dB_hi = tile_desc<S::SBO>(tc::smem_u32(B_hi)), dB_lo = tile_desc<S::SBO>(tc::smem_u32(B_lo));
-    uint32_t row_off[8];
-#pragma unroll
-    for (int c = 0; c < S::KC; ++c) row_off[c] = tile_off<S::KC>(tid, c);
+    const uint32_t row = tile_off<S::KC>(tid, 0);
+    const uint32_t sb = tc::smem_u32(A_hi);  // A_hi, A_lo, B_hi, B_lo back to back
 
     int b = (int)(((long long)blockIdx.x * p.B) / gridDim.x);  // spread CTAs over the instances
     bool have_inst = false;
@@ -201,23 +198,14 @@ __global__ void __launch_bounds__(128, 6) batched_tc_kernel(const __grid_constan
 #pragma unroll
                 for (int q = 1; q <= K; ++q) { a[q - 1] = S2[q]; a[K + q - 1] = C2[q]; }
                 a[2 * K] = 1.f;
-                write_row<S::KD>(A_hi, A_lo, row_off, a);
+                write_row<K>(sb + row, a);
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             // One barrier per step: the rows are in place, and a wait that gave
             // up in the previous step (any thread) stops the whole CTA.
             if (__syncthreads_or(failed)) { stop = true; break; }
-            if (tid == 0) {
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-                for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, dA_hi + kKStep * k, dB_hi + kKStep * k, k > 0 ? 1u : 0u);
-#pragma unroll
-                for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, dA_lo + kKStep * k, dB_hi + kKStep * k, 1u);
-#pragma unroll
-                for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, dA_hi + kKStep * k, dB_lo + kKStep * k, 1u);
-                tc::mma_commit(bar_a);
-            }
+            if (tid == 0) issue_step_mma<K>(tmem, sb, bar_a);
             // While the product runs: the Brownian increment and the x1 harmonics.
             float xi1, xi2;
             box_muller<float>(half ? r.z : r.x, half ? r.w : r.y, xi1, xi2);

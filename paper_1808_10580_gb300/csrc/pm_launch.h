@@ -37,6 +37,12 @@ struct TimedepLaunch {
     int64_t M, path_offset;
     int32_t n_obs, chunks;
     uint32_t inst, key0, key1;
+    // Shared paths (PM_SHARE_PATHS): n_groups records {m0, m1, stream, nmax}
+    // (members[m0..m1) sorted by step count), in launch order; nullptr: one
+    // observation per CTA row of the grid (order[] or identity).
+    const int4* groups = nullptr;  // device [n_groups]
+    const int32_t* members = nullptr;  // device [n_obs]
+    int32_t n_groups = 0;
 };
 
 struct DirichletLaunch {

@@ -51,12 +51,12 @@ __global__ void propose_kernel(const double* __restrict__ U, double* __restrict_
     }
 }
 
-__global__ void screen_input_kernel(const double* __restrict__ Up, const float* __restrict__ scale, int C, int n_u,
-                                    float* __restrict__ X)
+__global__ void screen_input_kernel(const double* __restrict__ Up, const double* __restrict__ shift,
+                                    const float* __restrict__ scale, int C, int n_u, float* __restrict__ X)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)C * n_u) return;
-    X[t] = (float)(Up[t] * (double)scale[t % n_u]);
+    X[t] = (float)((Up[t] - shift[t % n_u]) * (double)scale[t % n_u]);
 }
 
 __device__ double misfit(const double* __restrict__ y, const float* __restrict__ Gf, const double* __restrict__ Gd,
@@ -161,6 +161,7 @@ struct pm_pcn {
     void* buf = nullptr;
     double *U, *Up, *stdv, *y, *A, *Phi, *PhiS, *PhiS_new, *G, *sum_u, *x_rep, *t_rep;
     float *scale, *X, *Gs;
+    double* shift;              // surrogate input (u - shift) * scale
     int *pass, *idx;
     unsigned long long* accepts;
     int64_t n_summed = 0;
@@ -268,6 +269,7 @@ int pm_pcn_create(pm_ctx* c, pm_pcn** out, const pm_pcn_config* cfg, const doubl
         p->x_rep = linear ? nullptr : b.take<double>((size_t)(2 * C * n_obs));
         p->t_rep = linear ? nullptr : b.take<double>((size_t)(C * n_obs));
         p->scale = b.take<float>((size_t)n_u); p->X = b.take<float>((size_t)C * n_u);
+        p->shift = b.take<double>((size_t)n_u);
         p->Gs = b.take<float>((size_t)(C * n_obs));
         p->pass = b.take<int>((size_t)C); p->idx = b.take<int>((size_t)C);
         p->accepts = b.take<unsigned long long>(4);
@@ -291,6 +293,8 @@ int pm_pcn_create(pm_ctx* c, pm_pcn** out, const pm_pcn_config* cfg, const doubl
     }
     std::vector<float> sc((size_t)n_u, 1.0f);
     if (screen_scale) memcpy(sc.data(), screen_scale, sizeof(float) * (size_t)n_u);
+    std::vector<double> sh((size_t)n_u, 0.0);
+    if (cfg->screen_shift) memcpy(sh.data(), cfg->screen_shift, sizeof(double) * (size_t)n_u);
     cudaError_t e = cudaMemcpyAsync(p->U, u0, sizeof(double) * (size_t)C * n_u, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->Up, u0, sizeof(double) * (size_t)C * n_u, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->stdv, sd.data(), sizeof(double) * (size_t)n_u, cudaMemcpyHostToDevice, c->stream);
@@ -298,6 +302,7 @@ int pm_pcn_create(pm_ctx* c, pm_pcn** out, const pm_pcn_config* cfg, const doubl
     if (e == cudaSuccess && linear)
         e = cudaMemcpyAsync(p->A, cfg->A, sizeof(double) * (size_t)(n_obs * n_u), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->scale, sc.data(), sizeof(float) * (size_t)n_u, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->shift, sh.data(), sizeof(double) * (size_t)n_u, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->sum_u, 0, sizeof(double) * (size_t)n_u, c->stream);
     if (e == cudaSuccess && !linear) {
         std::vector<double> xr((size_t)(2 * C * n_obs)), tr((size_t)(C * n_obs));
@@ -317,7 +322,7 @@ int pm_pcn_create(pm_ctx* c, pm_pcn** out, const pm_pcn_config* cfg, const doubl
     if ((rc = forward_listed(c, p, all))) { pm_pcn_destroy(p); return rc; }
     misfit_all_kernel<<<blocks(C, 128), 128, 0, c->stream>>>(p->y, p->G, nullptr, C, (int)n_obs, inv2s2, p->Phi);
     if (screen) {
-        screen_input_kernel<<<blocks((int64_t)C * n_u, 256), 256, 0, c->stream>>>(p->Up, p->scale, C, n_u, p->X);
+        screen_input_kernel<<<blocks((int64_t)C * n_u, 256), 256, 0, c->stream>>>(p->Up, p->shift, p->scale, C, n_u, p->X);
         if ((rc = pm_surrogate_infer(c, screen, p->X, C, p->Gs, PM_DEVICE_PTRS))) { pm_pcn_destroy(p); return rc; }
         misfit_all_kernel<<<blocks(C, 128), 128, 0, c->stream>>>(p->y, nullptr, p->Gs, C, (int)n_obs, inv2s2, p->PhiS);
     }
@@ -360,7 +365,7 @@ int pm_pcn_run(pm_ctx* c, pm_pcn* p, int64_t n_steps, pm_pcn_stats* st)
         count_launch(c);
         idx_h.clear();
         if (da) {
-            screen_input_kernel<<<blocks((int64_t)C * n_u, 256), 256, 0, c->stream>>>(p->Up, p->scale, C, n_u, p->X);
+            screen_input_kernel<<<blocks((int64_t)C * n_u, 256), 256, 0, c->stream>>>(p->Up, p->shift, p->scale, C, n_u, p->X);
             PM_CUDA(cudaGetLastError(), "screen input");
             count_launch(c);
             if ((rc = pm_surrogate_infer(c, p->screen, p->X, C, p->Gs, PM_DEVICE_PTRS | PM_ASYNC))) return rc;

@@ -119,6 +119,8 @@ struct Params {
     int32_t n_obs, chunks;
     uint32_t inst, key0, key1;
     unsigned* err;
+    const int4* groups;       // shared paths: {m0, m1, stream, nmax} per grid row, or nullptr
+    const int32_t* members;   // [n_obs] observation indices of the groups
 };
 
 template <int NP>
@@ -201,55 +203,74 @@ template <> __device__ __forceinline__ void tmem_ld_row<64>(uint32_t taddr, floa
     for (int q = 0; q < 64; ++q) v[q] = __uint_as_float(r[q]);
 }
 
-// The velocity from this lane's accumulator row, read 32 columns at a time:
-//   v1 = P(0) + sum_m C1m P1c(m) + S1m P1s(m)      (columns 0 .. 2K, all < 32),
+// The velocity from this lane's accumulator row, read 16 columns at a time:
+//   v1 = P(0) + sum_m C1m P1c(m) + S1m P1s(m)      (columns 0 .. 2K),
 //   v2 = sum_m C1m P2c(m)  +  sum_m S1m P2s(m)      (columns 2K+1 .. 4K).
+// Terms are added in the order of their columns within each sum.
 template <int K>
 __device__ __forceinline__ void velocity_from_tmem(uint32_t t_row, const float (&C1)[K + 1], const float (&S1)[K + 1],
                                                    float& v1, float& v2)
 {
     constexpr int NP = Shape<K>::NP;
-    static_assert(2 * K < 32, "v1 columns in the first 32");
-    float v2c = 0.f, v2s = 0.f;
-    {
-        float a[32];
-        tmem_ld_row<32>(t_row, a);
-        v1 = a[0];
+    float v1c = 0.f, v1s = 0.f, v2c = 0.f, v2s = 0.f, p0 = 0.f;
 #pragma unroll
-        for (int m = 1; m <= K; ++m) v1 = fmaf(C1[m], a[m], fmaf(S1[m], a[K + m], v1));
+    for (int q = 0; q < NP / 16; ++q) {
+        float a[16];
+        tmem_ld16(t_row + 16u * q, a);
 #pragma unroll
-        for (int m = 1; m <= K; ++m) {
-            if (2 * K + m < 32) v2c = fmaf(C1[m], a[(2 * K + m) & 31], v2c);
-            if (3 * K + m < 32) v2s = fmaf(S1[m], a[(3 * K + m) & 31], v2s);
+        for (int e = 0; e < 16; ++e) {
+            const int col = 16 * q + e;
+            if (col == 0) p0 = a[e];
+            else if (col <= K) v1c = fmaf(C1[col], a[e], v1c);
+            else if (col <= 2 * K) v1s = fmaf(S1[col - K], a[e], v1s);
+            else if (col <= 3 * K) v2c = fmaf(C1[col - 2 * K], a[e], v2c);
+            else if (col <= 4 * K) v2s = fmaf(S1[col - 3 * K], a[e], v2s);
         }
     }
-    if constexpr (NP > 32) {
-        float b[NP - 32];
-        if constexpr (NP - 32 == 16) tmem_ld16(t_row + 32u, b);
-        else tmem_ld_row<32>(t_row + 32u, b);
-#pragma unroll
-        for (int m = 1; m <= K; ++m) {
-            if (2 * K + m >= 32) v2c = fmaf(C1[m], b[(2 * K + m - 32) & (NP - 33)], v2c);
-            if (3 * K + m >= 32) v2s = fmaf(S1[m], b[(3 * K + m - 32) & (NP - 33)], v2s);
-        }
-    }
+    v1 = p0 + (v1c + v1s);
     v2 = v2c + v2s;
 }
 
-// This thread's row of the particle tiles: harmonics a[0..KD) split into hi / lo.
-template <int KD>
-__device__ __forceinline__ void write_row(uint8_t* A_hi, uint8_t* A_lo, const uint32_t (&off)[8], const float (&a)[32])
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, const float4& v)
 {
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w) : "memory");
+}
+
+// Tiles at shared address sb: A_hi, A_lo (A_BYTES each), then B_hi, B_lo.
+// This thread's row of the particle tiles (row = sb + tile_off(r, 0); chunk c
+// 128 c bytes further): harmonics a[0..KD) split into hi / lo.
+template <int K>
+__device__ __forceinline__ void write_row(uint32_t row, const float (&a)[32])
+{
+    using S = Shape<K>;
 #pragma unroll
-    for (int c = 0; c < (KD + 3) / 4; ++c) {
+    for (int c = 0; c < (S::KD + 3) / 4; ++c) {
         float4 h, l;
         split_tf32(a[4 * c], h.x, l.x);
         split_tf32(a[4 * c + 1], h.y, l.y);
         split_tf32(a[4 * c + 2], h.z, l.z);
         split_tf32(a[4 * c + 3], h.w, l.w);
-        *reinterpret_cast<float4*>(A_hi + off[c]) = h;
-        *reinterpret_cast<float4*>(A_lo + off[c]) = l;
+        st_shared_v4(row + 128u * c, h);
+        st_shared_v4(row + (uint32_t)S::A_BYTES + 128u * c, l);
     }
+}
+
+// One Euler step's product, issued by one thread: P = A_hi W_hi + A_lo W_hi +
+// A_hi W_lo over the KS k-steps, then a commit to the step's mbarrier.
+template <int K>
+__device__ __forceinline__ void issue_step_mma(uint32_t tmem, uint32_t sb, uint32_t bar)
+{
+    using S = Shape<K>;
+    const uint64_t ah = tile_desc<S::SBO>(sb), al = tile_desc<S::SBO>(sb + S::A_BYTES);
+    const uint64_t bh = tile_desc<S::SBO>(sb + 2 * S::A_BYTES), bl = tile_desc<S::SBO>(sb + 2 * S::A_BYTES + S::B_BYTES);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, ah + kKStep * k, bh + kKStep * k, k > 0 ? 1u : 0u);
+#pragma unroll
+    for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, al + kKStep * k, bh + kKStep * k, 1u);
+#pragma unroll
+    for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, ah + kKStep * k, bl + kKStep * k, 1u);
+    tc::mma_commit(bar);
 }
 
 template <int K>
@@ -302,24 +323,54 @@ __global__ void __launch_bounds__(128, 6) timedep_tc_kernel(const __grid_constan
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
     const uint32_t t_row = tmem + ((uint32_t)(warp * 32) << 16);
-    const uint64_t dA_hi = tile_desc<S::SBO>(tc::smem_u32(A_hi)), dA_lo = tile_desc<S::SBO>(tc::smem_u32(A_lo));
-    const uint64_t dB_hi = tile_desc<S::SBO>(tc::smem_u32(B_hi)), dB_lo = tile_desc<S::SBO>(tc::smem_u32(B_lo));
 
-    uint32_t row_off[8];
-#pragma unroll
-    for (int c = 0; c < S::KC; ++c) row_off[c] = tile_off<S::KC>(tid, c);
+    const uint32_t row = tile_off<S::KC>(tid, 0);
+    const uint32_t sb = tc::smem_u32(A_hi);  // A_hi, A_lo, B_hi, B_lo back to back
     const int slot = blockIdx.x / p.chunks;
     const int cidx = blockIdx.x - slot * p.chunks;
-    const int j = p.order ? p.order[slot] : slot;
+    // The observations this grid row serves: a group at one point x whose
+    // members (sorted by step count) share the paths, or one observation.
+    int m0, m1, stream;
+    if (p.groups) {
+        const int4 G = p.groups[slot];
+        m0 = G.x;
+        m1 = G.y;
+        stream = G.z;
+    } else {
+        stream = p.order ? p.order[slot] : slot;
+        m0 = stream;
+        m1 = stream + 1;
+    }
+    auto member = [&](int m) { return p.groups ? p.members[m] : m; };
     const int64_t i = (int64_t)cidx * 128 + tid;
     const bool active = i < p.M;
-    const ObsRec o = p.obs[j];
     Coord<float> X1, X2;
-    X1.set(o.x1);
-    X2.set(o.x2);
+    {
+        const ObsRec o = p.obs[member(m0)];
+        X1.set(o.x1);
+        X2.set(o.x2);
+    }
     const uint32_t pid = (uint32_t)(p.path_offset + (active ? i : 0));
-    const int N = o.nsteps;
-    const float h_last = (float)o.h_last, s_last = (float)o.s_last;
+    // Member m's path ends at (Y1, Y2): theta0, per-path outputs, and the CTA's
+    // (sum, sum of squares) for that observation.  Uniform over the CTA.
+    auto finish = [&](int m, const Coord<float>& Y1, const Coord<float>& Y2, bool ok) {
+        const int jm = member(m);
+        double g = 0.0;
+        if (ok && active) {
+            g = theta0_eval(p.th, Y1, Y2);
+            const int64_t w = (int64_t)jm * p.M + i;
+            if (p.g_out) p.g_out[w] = g;
+            if (p.x_out) { p.x_out[2 * w] = Y1.full(); p.x_out[2 * w + 1] = Y2.full(); }
+        }
+        const double2 sum = block_sum2<128>(g, g * g);
+        if (tid == 0) p.part[(int64_t)jm * p.chunks + cidx] = sum;
+        __syncthreads();  // block_sum2's scratch is reused by the next member
+    };
+    auto steps_of = [&](int m) { return m < m1 ? p.obs[member(m)].nsteps : -1; };
+    int m = m0;  // next member to finish
+    while (steps_of(m) == 0) finish(m++, X1, X2, true);
+    const int N = m < m1 ? steps_of(m1 - 1) : 0;
+    int stop = steps_of(m) - 1;  // the step at which member m takes its last step
     bool failed = false;
     u32x4 r{0, 0, 0, 0};
 
@@ -334,25 +385,16 @@ __global__ void __launch_bounds__(128, 6) timedep_tc_kernel(const __grid_constan
 #pragma unroll
             for (int q = 1; q <= K; ++q) { a[q - 1] = S2[q]; a[K + q - 1] = C2[q]; }
             a[2 * K] = 1.f;
-            write_row<S::KD>(A_hi, A_lo, row_off, a);
+            write_row<K>(sb + row, a);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         // One barrier per step: the rows are in place, and a wait that gave up
         // in the previous step (any thread) ends the loop for the whole CTA.
-        if (__syncthreads_or(failed)) break;
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-            for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, dA_hi + kKStep * k, dB_hi + kKStep * k, k > 0 ? 1u : 0u);
-#pragma unroll
-            for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, dA_lo + kKStep * k, dB_hi + kKStep * k, 1u);
-#pragma unroll
-            for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, dA_hi + kKStep * k, dB_lo + kKStep * k, 1u);
-            tc::mma_commit(bar_a);
-        }
+        if (__syncthreads_or(failed)) { failed = true; break; }
+        if (tid == 0) issue_step_mma<K>(tmem, sb, bar_a);
         // While the product runs: the Brownian increment and the x1 harmonics.
-        if ((n & 1) == 0) r = philox4x32_10(u32x4{(uint32_t)(n >> 1), pid, (uint32_t)j, p.inst}, p.key0, p.key1);
+        if ((n & 1) == 0) r = philox4x32_10(u32x4{(uint32_t)(n >> 1), pid, (uint32_t)stream, p.inst}, p.key0, p.key1);
         float xi1, xi2;
         box_muller<float>((n & 1) ? r.z : r.x, (n & 1) ? r.w : r.y, xi1, xi2);
         float C1[K + 1], S1[K + 1];
@@ -362,25 +404,28 @@ __global__ void __launch_bounds__(128, 6) timedep_tc_kernel(const __grid_constan
         float v1, v2;
         velocity_from_tmem<K>(t_row, C1, S1, v1, v2);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        const bool last = (n == N - 1);
-        const float hh = last ? h_last : p.dt, ss = last ? s_last : p.s_dt;
-        em_update<float>(X1, v1, hh, ss, xi1);
-        em_update<float>(X2, v2, hh, ss, xi2);
-        X1.wrap();
-        X2.wrap();
+        // Members whose last step is this one take it with their own length.
+        while (n == stop) {
+            const ObsRec o = p.obs[member(m)];
+            const float hh = (float)o.h_last, ss = (float)o.s_last;
+            Coord<float> Y1 = X1, Y2 = X2;
+            em_update<float>(Y1, v1, hh, ss, xi1);
+            em_update<float>(Y2, v2, hh, ss, xi2);
+            Y1.wrap();
+            Y2.wrap();
+            finish(m++, Y1, Y2, true);
+            stop = steps_of(m) - 1;
+        }
+        if (n + 1 < N) {
+            em_update<float>(X1, v1, p.dt, p.s_dt, xi1);
+            em_update<float>(X2, v2, p.dt, p.s_dt, xi2);
+            X1.wrap();
+            X2.wrap();
+        }
     }
     failed = __syncthreads_or(failed);
-    double g = 0.0;
-    if (failed) {
-        if (tid == 0) atomicExch(p.err, 1u);
-    } else if (active) {
-        g = theta0_eval(p.th, X1, X2);
-        const int64_t w = (int64_t)j * p.M + i;
-        if (p.g_out) p.g_out[w] = g;
-        if (p.x_out) { p.x_out[2 * w] = X1.full(); p.x_out[2 * w + 1] = X2.full(); }
-    }
-    const double2 sum = block_sum2<128>(g, g * g);
-    if (tid == 0) p.part[(int64_t)j * p.chunks + cidx] = sum;
+    if (failed && tid == 0) atomicExch(p.err, 1u);
+    while (m < m1) finish(m++, X1, X2, false);  // only after a failed wait
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
@@ -444,9 +489,11 @@ cudaError_t launch_timedep_tc(const TimedepLaunch& L, unsigned* err, cudaStream_
     p.key0 = L.key0;
     p.key1 = L.key1;
     p.err = err;
+    p.groups = L.groups;
+    p.members = L.members;
     cudaError_t e = cudaFuncSetAttribute(timedep_tc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
     if (e != cudaSuccess) return e;
-    const int64_t grid = (int64_t)L.n_obs * L.chunks;
+    const int64_t grid = (int64_t)(L.groups ? L.n_groups : L.n_obs) * L.chunks;
     timedep_tc_kernel<K><<<(unsigned)grid, 128, S::SMEM, stream>>>(p);
     return cudaGetLastError();
 }

@@ -9,8 +9,9 @@ Workflow, all on the GPU through the library's C ABI:
      function of u (common random numbers);
   2. data y = G(u_true) + N(0, sigma^2 I), u_true a prior draw;
   3. training pairs (u, G(u)) with u from the prior, or local to the chains'
-     start states, evaluated 256 at a time by the batched map;
-  4. the surrogate network trained on (u / prior std, G(u));
+     start state, evaluated 256 at a time by the batched map;
+  4. the surrogate network trained on (standardised u, G(u)): u / prior std,
+     or (u - start) / (spread * prior std) for local pairs;
   5. pCN chains, plain and with delayed acceptance through the surrogate, with
      the same beta, compared by accepted proposals per second.
 """
@@ -81,18 +82,27 @@ def make_data(ctx, prob: Problem, seed_true: int = 5004, seed_noise: int = 6004)
     return prob
 
 
-def training_pairs(ctx, prob: Problem, n: int, seed: int = 7004, centers: np.ndarray = None, spread: float = 1.0,
-                   tensor: bool = True):
-    """n pairs (z, G(std * z)).  Without centers z is a prior draw (standard
-    normal); with centers [C, n_u] (fields u) z = centers[c] / std + spread * xi
-    for a random c per pair: pairs local to the region the chains sample."""
+def training_pairs(ctx, prob: Problem, n: int, seed: int = 7004, center: np.ndarray = None, spread: float = 1.0,
+                   tensor: bool = True, coords=None):
+    """n pairs (network input, G(u)) with u = center + spread * std * z,
+    z ~ N(0, I) (center None: 0, so spread 1 gives prior draws).  The network
+    input is (u - shift) * scale for coords = (shift, scale); the default is
+    the prior coordinates u / std."""
     rng = np.random.Generator(np.random.PCG64(seed))
     Z = rng.standard_normal((n, len(prob.std)))
-    if centers is not None:
-        zc = np.asarray(centers, dtype=np.float64) / prob.std[None, :]
-        Z = zc[rng.integers(0, len(zc), n)] + spread * Z
-    G = forward_many(ctx, prob, Z * prob.std, tensor=tensor)
-    return Z.astype(np.float32), G.astype(np.float32)
+    c = np.zeros(len(prob.std)) if center is None else np.asarray(center, dtype=np.float64)
+    U = c[None, :] + spread * prob.std[None, :] * Z
+    G = forward_many(ctx, prob, U, tensor=tensor)
+    shift, scale = coords if coords is not None else screen_coords(prob)
+    X = (U - shift[None, :]) * scale.astype(np.float64)[None, :]
+    return X.astype(np.float32), G.astype(np.float32)
+
+
+def screen_coords(prob: Problem, center: np.ndarray = None, spread: float = 1.0):
+    """(shift, scale) of the network input (u - shift) * scale: by default the
+    prior coordinates u / std; with a center, (u - center) / (spread * std)."""
+    shift = np.zeros(len(prob.std)) if center is None else np.asarray(center, dtype=np.float64)
+    return shift, (1.0 / (spread * prob.std)).astype(np.float32)
 
 
 def train_surrogate(ctx, prob: Problem, Z, G, hidden=512, epochs=20, batch=512, lr=1e-3, seed=8004,
@@ -114,11 +124,14 @@ def start_states(prob: Problem, n_chains: int, spread: float = 0.0, seed: int = 
     return prob.u_true[None, :] + spread * prob.std[None, :] * rng.standard_normal((n_chains, len(prob.std)))
 
 
-def run_chains(ctx, prob: Problem, u0, beta, n_steps, seed, net=None, tensor: bool = True):
+def run_chains(ctx, prob: Problem, u0, beta, n_steps, seed, net=None, tensor: bool = True, coords=None):
+    """coords: (shift, scale) of the network input (default: prior coordinates u / std)."""
     th = pm.Fourier(prob.theta0.k, prob.theta0.a, prob.theta0.b)
+    shift, scale = coords if coords is not None else screen_coords(prob)
     ch = pm.PCN(ctx, prob.K, u0, prob.y, prob.sigma, beta, seed, theta0=th, x=prob.x, t=prob.t, kappa=prob.kappa,
                 dt=prob.dt, M=prob.M, path_seed=prob.path_seed, screen=net,
-                screen_scale=(1.0 / prob.std) if net is not None else None, tensor=tensor)
+                screen_scale=scale if net is not None else None,
+                screen_shift=shift if net is not None else None, tensor=tensor)
     t0 = time.perf_counter()
     st = ch.run(n_steps)
     st["wall_seconds"] = time.perf_counter() - t0

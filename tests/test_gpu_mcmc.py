@@ -109,3 +109,23 @@ def test_tensor_map_chains_start_from_the_tensor_map_misfit(c):
     G_simt = np.empty(3 * len(t))
     pm.pm_forward_batched(c, batch, pm.PM_FP32, G_simt)
     assert not np.array_equal(G, G_simt)   # the flag reached the map
+
+
+def test_screen_shift_zero_equals_no_shift(c):
+    A, y, sigma, std = toy(sigma=0.5, seed=3, n_obs=6, K=1)
+    net = pm.pm_surrogate_create(c, len(std), 128, len(y), 9)
+    runs = []
+    for shift in (None, np.zeros(len(std))):
+        ch = pm.PCN(c, 1, np.zeros((8, len(std))), y, sigma, 0.3, seed=21, A=A, screen=net, screen_scale=1.0 / std,
+                    screen_shift=shift)
+        runs.append(ch.run(200))
+        ch.close()
+    # a shift moves the screen's inputs, so its stage-1 decisions change
+    ch = pm.PCN(c, 1, np.zeros((8, len(std))), y, sigma, 0.3, seed=21, A=A, screen=net, screen_scale=1.0 / std,
+                screen_shift=np.full(len(std), 3.0))
+    shifted = ch.run(200)
+    ch.close()
+    pm.pm_surrogate_destroy(net)
+    keys = ("proposals", "stage1_accepts", "accepts", "forward_evals")
+    assert all(runs[0][k] == runs[1][k] for k in keys)
+    assert shifted["stage1_accepts"] != runs[0]["stage1_accepts"]
