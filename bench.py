@@ -406,6 +406,14 @@ def run_aux(args):
             pm.pm_forward_batched(ctx, batch, pm.PM_FP32 | (pm.PM_TENSOR if args.tensor else 0), mean, var)
         name, cfg = f"batched_{args.B}x100obs_M{args.M or 4096}", {"B": args.B, "rows": row,
                                                                     "tensor_cores": bool(args.tensor)}
+    tuned = None
+    if args.autotune:
+        flags = pm.PM_FP32 | (pm.PM_TENSOR if args.tensor else 0)
+        if args.workload == "dirichlet":
+            tuned = pm.pm_autotune_dirichlet(ctx, fld, w.drift_scale, w.kappa, gd, x, len(w.x), w.M, w.dt,
+                                             w.max_steps, w.seed, flags)
+        else:
+            tuned = pm.pm_autotune_batched(ctx, batch, flags)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize(dev)
@@ -424,6 +432,7 @@ def run_aux(args):
             "dtype": "f32", "data": "synthetic", "auxiliary": True,
             "config": dict(workload=name, particle_steps_per_call=steps[-1], **cfg)}
     line["config"]["grid"] = pm.pm_last_grid(ctx)
+    line["config"]["autotuned_ctas_per_sm"] = tuned
     if args.workload == "dirichlet":
         line["kernel_ms"] = pm.pm_last_kernel_ms(ctx)
         # Exit-step distribution of the same call (outside the timed region): the
@@ -489,6 +498,65 @@ def run_sweep(args):
     return 0
 
 
+def run_surrogate(args):
+    """Training and inference throughput of the surrogate network (auxiliary
+    line): 440 -> 512 -> 512 -> 100, BF16 operands with FP32 accumulation on
+    the tensor cores, Adam, batch 512, on 2^16 synthetic pairs resident on the
+    device; inference at batch 64."""
+    import torch
+
+    import paper_1808_10580_gb300 as pm
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    ctx = pm.pm_create(0, stream.cuda_stream)
+    n_in, h, n_out, N, batch = 440, 512, 100, 1 << 16, 512
+    g = torch.Generator(device="cpu").manual_seed(12)
+    U = torch.randn(N, n_in, generator=g).to(dev)
+    Y = torch.tanh(U[:, :n_out] * 0.5 + 0.1 * U[:, n_out:2 * n_out]).contiguous()
+    net = pm.pm_surrogate_create(ctx, n_in, h, n_out, 12)
+    epochs = max(1, args.steps)
+    pm.pm_surrogate_train(ctx, net, U, Y, epochs=1, batch=batch)          # warm-up epoch
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    hist = pm.pm_surrogate_train(ctx, net, U, Y, epochs=epochs, batch=batch)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    train_s = e0.elapsed_time(e1) / 1e3
+    fwd = 2 * (n_in * h + h * h + h * n_out)
+    step_flop = fwd + fwd + 2 * (h * h + h * n_out)        # forward, weight gradients, input gradients of layers 2-3
+    samples = epochs * (N // batch) * batch
+    Ui = U[:64].contiguous()
+    Yi = torch.empty(64, n_out, device=dev)
+    for _ in range(10):
+        pm.pm_surrogate_infer(ctx, net, Ui, Yi)
+    torch.cuda.synchronize(dev)
+    reps = 200
+    e0.record(stream)
+    for _ in range(reps):
+        pm.pm_surrogate_infer(ctx, net, Ui, Yi)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    infer_ms = e0.elapsed_time(e1) / reps
+    peaks, kind = measured_peaks()
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    achieved = samples * step_flop / train_s / 1e12
+    line = {"metric": "surrogate training samples/s", "auxiliary": True, "data": "synthetic",
+            "value": samples / train_s, "unit": "samples/s", "n_gpus": 1, "steps": epochs, "warmup": 1,
+            "dtype": "bf16", "config": {"workload": "mlp_440_512_512_100_batch512_2^16pairs", "epochs": epochs,
+                                        "final_loss": float(hist[-1])},
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "flop_per_sample": step_flop,
+                         "peak_basis": f"bf16_tflops ({kind}, burst)"},
+            "inference_batch64_ms": infer_ms}
+    print(json.dumps(line), flush=True)
+    pm.pm_surrogate_destroy(net)
+    pm.pm_destroy(ctx)
+    return 0
+
+
 def run_mcmc(args):
     """Surrogate-screened pCN against plain pCN on the same GPU (auxiliary line):
     64 chains started at the data-generating field, the same beta for both
@@ -527,6 +595,9 @@ def run_mcmc(args):
         line = {"metric": "accepted pCN proposals/s (64 chains)", "auxiliary": True, "data": "synthetic",
                 "value": da["accepted_per_s"], "unit": "accepted proposals/s",
                 "ratio_vs_plain": da["accepted_per_s"] / max(plain["accepted_per_s"], 1e-30),
+                "sq_jump_per_s": {"plain": plain["sq_jump_per_s"], "delayed_acceptance": da["sq_jump_per_s"],
+                                  "ratio": da["sq_jump_per_s"] / max(plain["sq_jump_per_s"], 1e-30),
+                                  "note": "squared prior-whitened jump distance of accepted moves per second"},
                 "config": {"train_pairs": args.train_pairs, "epochs": args.epochs, "M": prob.M,
                            "n_obs": len(prob.t), "sigma": prob.sigma, "beta": beta, "chains": 64,
                            "start": "data-generating field", "tensor_cores": bool(args.tensor),
@@ -551,7 +622,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--M", type=int, default=0, help="particles per observation (default: the workload's own; "
                     "smaller values are for profiling captures only)")
-    ap.add_argument("--workload", default="timedep", choices=["timedep", "dirichlet", "batched", "mcmc", "sweep"],
+    ap.add_argument("--workload", default="timedep", choices=["timedep", "dirichlet", "batched", "mcmc", "sweep", "surrogate"],
                     help="timedep: the headline line; dirichlet / batched / mcmc: auxiliary measurements")
     ap.add_argument("--train-pairs", type=int, default=1 << 16, help="mcmc: surrogate training pairs")
     ap.add_argument("--betas", default="0.03", help="mcmc: comma-separated pCN steps (each the same for both samplers)")
@@ -573,6 +644,8 @@ def main():
                     help="timedep: velocity sum on the tensor cores (PM_TENSOR; the default)")
     ap.add_argument("--no-tensor", dest="tensor", action="store_false",
                     help="timedep: velocity sum on the FP32 pipes")
+    ap.add_argument("--autotune", action="store_true",
+                    help="dirichlet / batched: pick the persistent grid with the autotuner first")
     ap.add_argument("--share-paths", action="store_true",
                     help="timedep: observations at one point share their paths (PM_SHARE_PATHS, tensor path); "
                          "value counts the steps taken, forward_map_evals_per_s the evaluations")
@@ -585,6 +658,8 @@ def main():
         return run_mcmc(args)
     if args.workload == "sweep":
         return run_sweep(args)
+    if args.workload == "surrogate":
+        return run_surrogate(args)
     if args.workload != "timedep":
         return run_aux(args)
     return run_gpu(args)

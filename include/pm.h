@@ -265,6 +265,38 @@ int pm_forward_batched(pm_ctx* ctx, const pm_batch* batch, uint32_t flags, doubl
 /* Graph capture and replay of pm_forward_batched: on (1, default) or off (0). */
 int pm_set_graph_mode(pm_ctx* ctx, int on);
 
+/* ------------------------------------------------------------------------- *
+ * Autotuner of the persistent launches (the batching pattern's block and
+ * chunk shapes).  The Dirichlet and batched kernels run a persistent grid of
+ * (CTAs per SM) x SMs whose lanes claim paths from counters; every path's
+ * value is stored and reduced in path order, so results do not depend on
+ * the grid and its one free shape is the number of CTAs per SM.
+ *
+ * pm_autotune_dirichlet / pm_autotune_batched time two forward calls (the
+ * second measured) with the caller's problem and flags for every candidate
+ * from 1 to the kernel's occupancy limit, keep the fastest in the context
+ * for (kernel, K, PM_FP64 and PM_TENSOR bits) and store it in
+ * *best_ctas_per_sm (may be NULL).  Arguments are those of the forward call
+ * (PM_ASYNC is ignored; outputs go to scratch the call allocates and frees).
+ * When the environment variable PM_AUTOTUNE_CACHE names a file, pm_create
+ * reads this device's choices from it (a flat JSON object
+ * {"<device name>|<kind>|<K>|<flags>": ctas_per_sm}) and the autotuners write
+ * theirs back.  PM_AUTOTUNE=0 makes every launch use the occupancy limit.
+ * Returns PM_OK or the error of the failing forward call.
+ * ------------------------------------------------------------------------- */
+#define PM_TUNE_DIRICHLET 0
+#define PM_TUNE_BATCHED 1
+
+int pm_autotune_dirichlet(pm_ctx* ctx, const pm_field* field, double drift_scale, double kappa,
+                          const pm_dirichlet_data* g, const double* x, int64_t n_obs, int64_t M, double dt,
+                          int64_t max_steps, uint64_t seed, uint32_t flags, int32_t* best_ctas_per_sm);
+int pm_autotune_batched(pm_ctx* ctx, const pm_batch* batch, uint32_t flags, int32_t* best_ctas_per_sm);
+
+/* Sets the CTAs per SM used for (kind, K, flags & (PM_FP64 | PM_TENSOR));
+ * values above the occupancy limit are clamped to it, <= 0 removes the
+ * setting.  kind: PM_TUNE_DIRICHLET or PM_TUNE_BATCHED. */
+int pm_set_ctas_per_sm(pm_ctx* ctx, int32_t kind, int32_t K, uint32_t flags, int32_t ctas_per_sm);
+
 /* ---------------------------------------------------------------------------
  * Learned surrogate of the forward map (the paper has no learned component;
  * this serves the delayed-acceptance pre-screen of pCN MCMC proposals).
@@ -373,6 +405,7 @@ typedef struct pm_pcn_stats {
     int64_t accepts;            /* accepted moves */
     int64_t forward_evals;      /* particle-map evaluations (instances) */
     double seconds;             /* device time of the run */
+    double sq_jump;             /* sum over accepted moves of |(u' - u) / prior std|^2 (an efficiency measure) */
 } pm_pcn_stats;
 
 /* u0: [n_chains][n_u] host.  screen: NULL for plain pCN, else a surrogate

@@ -67,14 +67,16 @@ def phi(y, G, sigma):
 def run(u0, G, y, sigma, beta, std, n_steps, seed, Gs=None, step0=0):
     """Chains u0 [C, n] for n_steps pCN steps (delayed acceptance when the cheap
     map Gs is given).  Returns the final states, the running sum of states over
-    all steps (for posterior means) and counters."""
+    all steps (for posterior means) and counters; sq_jump sums the squared
+    prior-whitened jumps |(u' - u) / std|^2 of accepted moves (the expected
+    squared jump distance, a standard efficiency measure of a sampler)."""
     U = np.array(u0, dtype=np.float64, copy=True)
     C, n = U.shape
     rho = math.sqrt(1.0 - beta * beta)
     Phi = np.array([phi(y, G(U[c]), sigma) for c in range(C)])
     PhiS = np.array([phi(y, Gs(U[c]), sigma) for c in range(C)]) if Gs else np.zeros(C)
     total = np.zeros(n)
-    stats = dict(stage1=0, accepts=0, evals=0)
+    stats = dict(stage1=0, accepts=0, evals=0, sq_jump=0.0)
     for s in range(step0, step0 + n_steps):
         for c in range(C):
             up = rho * U[c] + beta * std * proposal_normals(seed, s, c, n)
@@ -87,12 +89,14 @@ def run(u0, G, y, sigma, beta, std, n_steps, seed, Gs=None, step0=0):
                 stats["evals"] += 1
                 a = PhiS[c] - phs  # log of the stage-1 ratio
                 if accept_uniform(seed, s, c, 2) < math.exp(min(0.0, (Phi[c] - ph) - a)):
+                    stats["sq_jump"] += float((((up - U[c]) / std) ** 2).sum())
                     U[c], Phi[c], PhiS[c] = up, ph, phs
                     stats["accepts"] += 1
             else:
                 ph = phi(y, G(up), sigma)
                 stats["evals"] += 1
                 if accept_uniform(seed, s, c, 2) < math.exp(min(0.0, Phi[c] - ph)):
+                    stats["sq_jump"] += float((((up - U[c]) / std) ** 2).sum())
                     U[c], Phi[c] = up, ph
                     stats["accepts"] += 1
         total += U.sum(0)

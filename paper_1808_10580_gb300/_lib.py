@@ -28,6 +28,8 @@ PM_DEVICE_PTRS = 2
 PM_ASYNC = 4
 PM_TENSOR = 8
 PM_SHARE_PATHS = 16
+PM_TUNE_DIRICHLET = 0
+PM_TUNE_BATCHED = 1
 
 
 class PMError(RuntimeError):
@@ -108,6 +110,9 @@ def load(build_if_missing: bool = True):
     L.pm_forward_timedep_noalloc.argtypes = [C.POINTER(pm_field), dbl, C.POINTER(pm_fourier), vp, vp, i64, i64,
                                              dbl, C.c_uint64, u32, vp, vp, vp]
     L.pm_forward_batched.argtypes = [vp, C.POINTER(pm_batch), u32, vp, vp, vp]
+    L.pm_autotune_batched.argtypes = [vp, C.POINTER(pm_batch), u32, vp]
+    L.pm_autotune_dirichlet.argtypes = [vp, C.POINTER(pm_field), dbl, dbl, C.POINTER(pm_dirichlet_data), vp, i64,
+                                        i64, dbl, i64, C.c_uint64, u32, vp]
     L.pm_set_graph_mode.argtypes = [vp, C.c_int]
     L.pm_set_kernel_timing.argtypes = [vp, C.c_int]
     L.pm_last_kernel_ms.argtypes = [vp]
@@ -119,6 +124,7 @@ def load(build_if_missing: bool = True):
     L.pm_last_grid.argtypes = [vp]
     L.pm_last_grid.restype = i64
     L.pm_path_groups.argtypes = [vp, vp, i64, C.c_double, vp, vp, vp, vp]
+    L.pm_set_ctas_per_sm.argtypes = [vp, C.c_int32, C.c_int32, C.c_uint32, C.c_int32]
     _lib = L
     return L
 
@@ -331,6 +337,31 @@ def pm_set_graph_mode(ctx, on):
     return _check(load().pm_set_graph_mode(ctx, int(bool(on))))
 
 
+def pm_autotune_batched(ctx, batch: Batch, flags):
+    """Times the batched call for every CTAs-per-SM candidate; returns the fastest (kept in ctx)."""
+    if batch.device:
+        flags |= PM_DEVICE_PTRS
+    best = C.c_int32()
+    _check(load().pm_autotune_batched(ctx, C.byref(batch.s), int(flags), C.byref(best)))
+    return best.value
+
+
+def pm_autotune_dirichlet(ctx, field: Field, drift_scale, kappa, g: DirichletData, x, n_obs, M, dt, max_steps, seed,
+                          flags):
+    """Times the Dirichlet call for every CTAs-per-SM candidate; returns the fastest (kept in ctx)."""
+    if _device(x):
+        flags |= PM_DEVICE_PTRS
+    best = C.c_int32()
+    _check(load().pm_autotune_dirichlet(ctx, C.byref(field.s), float(drift_scale), float(kappa), C.byref(g.s), _ptr(x),
+                                        int(n_obs), int(M), float(dt), int(max_steps), int(seed), int(flags),
+                                        C.byref(best)))
+    return best.value
+
+
+def pm_set_ctas_per_sm(ctx, kind, K, flags, ctas_per_sm):
+    return _check(load().pm_set_ctas_per_sm(ctx, int(kind), int(K), int(flags), int(ctas_per_sm)))
+
+
 class pm_train_opts(C.Structure):
     _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_float), ("beta1", C.c_float),
                 ("beta2", C.c_float), ("eps", C.c_float), ("weight_decay", C.c_float), ("lr_decay", C.c_float),
@@ -443,7 +474,8 @@ class pm_pcn_config(C.Structure):
 
 class pm_pcn_stats(C.Structure):
     _fields_ = [("steps", C.c_int64), ("proposals", C.c_int64), ("stage1_accepts", C.c_int64),
-                ("accepts", C.c_int64), ("forward_evals", C.c_int64), ("seconds", C.c_double)]
+                ("accepts", C.c_int64), ("forward_evals", C.c_int64), ("seconds", C.c_double),
+                ("sq_jump", C.c_double)]
 
 
 def _plib():

@@ -253,10 +253,14 @@ int pm_create(pm_ctx** out, int device, void* cuda_stream)
     }
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+    cudaDeviceProp prop{};
+    if (e == cudaSuccess) e = cudaGetDeviceProperties(&prop, device);
     if (e != cudaSuccess) {
         pm_destroy(c);
         return cuda_fail(e, "pm_create");
     }
+    c->device_name = prop.name;
+    load_tune_cache(c);
     *out = c;
     return PM_OK;
 }
@@ -583,6 +587,30 @@ int pm_forward_timedep(pm_ctx* c, const pm_field* field, double kappa, const pm_
     return PM_OK;
 }
 
+// Dirichlet launch shape: the tensor-core kernel for float paths with
+// PM_TENSOR at K in {4,5,6,8,10,12}; resident CTAs per SM of the kernel used.
+namespace {
+bool dirichlet_uses_tc(int K, uint32_t flags)
+{
+    return !(flags & PM_FP64) && (flags & PM_TENSOR) && (K == 4 || K == 5 || K == 6 || K == 8 || K == 10 || K == 12);
+}
+
+int dirichlet_resident(int K, bool fp64, bool use_tc)
+{
+    if (use_tc) {
+        switch (K) {
+        case 4: return tdtc::dirichlet_tc_blocks_per_sm<4>();
+        case 5: return tdtc::dirichlet_tc_blocks_per_sm<5>();
+        case 6: return tdtc::dirichlet_tc_blocks_per_sm<6>();
+        case 8: return tdtc::dirichlet_tc_blocks_per_sm<8>();
+        case 10: return tdtc::dirichlet_tc_blocks_per_sm<10>();
+        default: return tdtc::dirichlet_tc_blocks_per_sm<12>();
+        }
+    }
+    return fp64 ? dispatch_dirichlet_occupancy<double>(K) : dispatch_dirichlet_occupancy<float>(K);
+}
+}  // namespace
+
 // ---------------------------------------------------------------------------
 // Algorithm 2
 // ---------------------------------------------------------------------------
@@ -690,20 +718,9 @@ int pm_forward_dirichlet(pm_ctx* c, const pm_field* field, double drift_scale, d
     L.key0 = (uint32_t)(seed & 0xffffffffu);
     L.key1 = (uint32_t)(seed >> 32);
     const int Kd = field->K;
-    const bool use_tc = !fp64 && (flags & PM_TENSOR) && (Kd == 4 || Kd == 5 || Kd == 6 || Kd == 8 || Kd == 10 || Kd == 12);
-    int per_sm = 1;
-    if (use_tc) {
-        switch (Kd) {
-        case 4: per_sm = tdtc::dirichlet_tc_blocks_per_sm<4>(); break;
-        case 5: per_sm = tdtc::dirichlet_tc_blocks_per_sm<5>(); break;
-        case 6: per_sm = tdtc::dirichlet_tc_blocks_per_sm<6>(); break;
-        case 8: per_sm = tdtc::dirichlet_tc_blocks_per_sm<8>(); break;
-        case 10: per_sm = tdtc::dirichlet_tc_blocks_per_sm<10>(); break;
-        default: per_sm = tdtc::dirichlet_tc_blocks_per_sm<12>(); break;
-        }
-    } else {
-        per_sm = fp64 ? dispatch_dirichlet_occupancy<double>(Kd) : dispatch_dirichlet_occupancy<float>(Kd);
-    }
+    const bool use_tc = dirichlet_uses_tc(Kd, flags);
+    int per_sm = dirichlet_resident(Kd, fp64, use_tc);
+    per_sm = tuned_ctas_per_sm(c, PM_TUNE_DIRICHLET, Kd, flags & (PM_FP64 | (use_tc ? PM_TENSOR : 0u)), per_sm);
     int64_t grid = (int64_t)per_sm * c->sm_count;
     const int64_t need = (total + kDirichletBlock - 1) / kDirichletBlock;
     if (grid > need) grid = need;
@@ -863,3 +880,38 @@ int pm_velocity(pm_ctx* c, const pm_field* field, const double* x, int64_t npts,
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Autotuning of the Dirichlet kernel's persistent grid (pm_autotune.cu)
+// ---------------------------------------------------------------------------
+int pm_autotune_dirichlet(pm_ctx* c, const pm_field* field, double drift_scale, double kappa,
+                          const pm_dirichlet_data* g, const double* x, int64_t n_obs, int64_t M, double dt,
+                          int64_t max_steps, uint64_t seed, uint32_t flags, int32_t* best_ctas_per_sm)
+{
+    if (!c) return fail(PM_EINVAL, "ctx is NULL");
+    int rc = check_field(field);
+    if (rc) return rc;
+    if (n_obs < 1 || M < 1) return fail(PM_EINVAL, "autotuning needs n_obs >= 1 and M >= 1");
+    if ((rc = set_device(c))) return rc;
+    flags &= ~PM_ASYNC;
+    const bool dev = flags & PM_DEVICE_PTRS;
+    const int K = field->K;
+    const bool use_tc = dirichlet_uses_tc(K, flags);
+    const int resident = dirichlet_resident(K, flags & PM_FP64, use_tc);
+    std::vector<double> hmean;
+    double* mean = nullptr;
+    if (dev) {
+        PM_CUDA(cudaMalloc(&mean, (size_t)n_obs * 8), "autotune output");
+    } else {
+        hmean.resize((size_t)n_obs);
+        mean = hmean.data();
+    }
+    auto run = [&]() {
+        return pm_forward_dirichlet(c, field, drift_scale, kappa, g, x, n_obs, M, dt, max_steps, seed, flags, mean,
+                                    nullptr, nullptr, nullptr, nullptr);
+    };
+    rc = autotune_loop(c, PM_TUNE_DIRICHLET, K, flags & (PM_FP64 | (use_tc ? PM_TENSOR : 0u)), resident, run,
+                       best_ctas_per_sm);
+    if (dev) cudaFree(mean);
+    return rc;
+}

@@ -252,7 +252,8 @@ extern "C" int pm_forward_batched(pm_ctx* c, const pm_batch* bt, uint32_t flags,
     const bool use_tc = (flags & PM_TENSOR) && tc_supported(K);
     p.g = W.g;
     p.B = B;
-    const int per_sm = use_tc ? blocks_per_sm_tc_K(K) : blocks_per_sm_K(K);  // also sets the shared-memory attribute
+    const int resident = use_tc ? blocks_per_sm_tc_K(K) : blocks_per_sm_K(K);  // also sets the shared-memory attribute
+    const int per_sm = tuned_ctas_per_sm(c, PM_TUNE_BATCHED, K, use_tc ? PM_TENSOR : 0u, resident);
     int64_t grid = (int64_t)per_sm * c->sm_count;
     const int64_t need = (total + kBatchWarpsHost * 32 - 1) / (kBatchWarpsHost * 32);
     grid = std::max<int64_t>(1, std::min(grid, need));
@@ -333,4 +334,31 @@ extern "C" int pm_forward_batched(pm_ctx* c, const pm_batch* bt, uint32_t flags,
         return fail(PM_EINVAL, "observation points or times are not finite, a time is negative, or a step count exceeds 2^31");
     if (Hs.flags[3] & 0xffffffffull) return fail(PM_ETIMEOUT, "a tensor-core wait in the batched kernel timed out");
     return Hs.flags[0] ? PM_WARN_UNEXITED : PM_OK;
+}
+
+// Autotuning of the batched kernel's persistent grid (pm_autotune.cu).
+extern "C" int pm_autotune_batched(pm_ctx* c, const pm_batch* bt, uint32_t flags, int32_t* best_ctas_per_sm)
+{
+    if (!c || !bt) return fail(PM_EINVAL, "ctx or batch is NULL");
+    if (bt->n_rows < 1 || bt->B < 1) return fail(PM_EINVAL, "autotuning needs a non-empty batch");
+    if (!supported_K(bt->K)) return fail(PM_EINVAL, "unsupported K %d", bt->K);
+    int rc = set_device(c);
+    if (rc) return rc;
+    flags &= ~PM_ASYNC;
+    const bool dev = flags & PM_DEVICE_PTRS;
+    const int K = bt->K;
+    const bool use_tc = (flags & PM_TENSOR) && tc_supported(K);
+    const int resident = use_tc ? blocks_per_sm_tc_K(K) : blocks_per_sm_K(K);
+    std::vector<double> hmean;
+    double* mean = nullptr;
+    if (dev) {
+        PM_CUDA(cudaMalloc(&mean, (size_t)bt->n_rows * 8), "autotune output");
+    } else {
+        hmean.resize((size_t)bt->n_rows);
+        mean = hmean.data();
+    }
+    auto run = [&]() { return pm_forward_batched(c, bt, flags, mean, nullptr, nullptr); };
+    rc = autotune_loop(c, PM_TUNE_BATCHED, K, use_tc ? PM_TENSOR : 0u, resident, run, best_ctas_per_sm);
+    if (dev) cudaFree(mean);
+    return rc;
 }

@@ -3,7 +3,10 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <functional>
 #include <initializer_list>
+#include <map>
+#include <string>
 
 #include <cuda_runtime.h>
 
@@ -29,6 +32,9 @@ struct pm_ctx {
     cudaGraphExec_t graph_exec = nullptr;
     int64_t graph_launches = 0;  // kernels per replay
     int graph_mode = 1;          // 1: capture and replay when the stream allows it
+    // Autotuned resident CTAs per SM of the persistent kernels, by tune_key().
+    std::map<uint64_t, int> ctas_per_sm;
+    std::string device_name;
 };
 
 namespace pm {
@@ -58,6 +64,17 @@ int set_device(pm_ctx* c);
 int check_field(const pm_field* f);
 int check_ptrs(uint32_t flags, std::initializer_list<const void*> ptrs);
 void count_launch(pm_ctx* c, int n = 1);
+
+// Autotuner (pm_autotune.cu).  kind: PM_TUNE_DIRICHLET or PM_TUNE_BATCHED.
+uint64_t tune_key(int kind, int K, uint32_t flags);
+// CTAs per SM for a persistent launch: the tuned value (at most `resident`)
+// unless PM_AUTOTUNE=0 or none is known, else `resident`.
+int tuned_ctas_per_sm(pm_ctx* c, int kind, int K, uint32_t flags, int resident);
+// Reads this device's entries of the PM_AUTOTUNE_CACHE file into the context.
+void load_tune_cache(pm_ctx* c);
+// Runs the timing sweep over CTAs per SM in [1, resident] (see pm_autotune.cu).
+int autotune_loop(pm_ctx* c, int kind, int K, uint32_t flags, int resident, const std::function<int()>& run,
+                  int32_t* best);
 
 }  // namespace pm
 

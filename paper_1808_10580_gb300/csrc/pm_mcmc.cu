@@ -102,7 +102,8 @@ __global__ void accept_kernel(const int* __restrict__ idx, int n, const double* 
                               const double* __restrict__ G, int n_obs, double inv2s2, int da, double* __restrict__ Phi,
                               double* __restrict__ PhiS, const double* __restrict__ PhiS_new, double* __restrict__ U,
                               const double* __restrict__ Up, int n_u, uint32_t k0, uint32_t k1, uint32_t step,
-                              unsigned long long* __restrict__ accepts)
+                              unsigned long long* __restrict__ accepts, const double* __restrict__ std_,
+                              double* __restrict__ jump)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
@@ -114,7 +115,13 @@ __global__ void accept_kernel(const int* __restrict__ idx, int n, const double* 
     if (uniform_d(r.x) < exp(fmin(0.0, a))) {
         Phi[c] = ph;
         if (da) PhiS[c] = PhiS_new[c];
-        for (int h = 0; h < n_u; ++h) U[(size_t)c * n_u + h] = Up[(size_t)c * n_u + h];
+        double sq = 0.0;  // squared jump in prior-whitened coordinates
+        for (int h = 0; h < n_u; ++h) {
+            const double d = (Up[(size_t)c * n_u + h] - U[(size_t)c * n_u + h]) / std_[h];
+            sq += d * d;
+            U[(size_t)c * n_u + h] = Up[(size_t)c * n_u + h];
+        }
+        jump[c] += sq;
         atomicAdd(accepts, 1ull);
     }
 }
@@ -162,6 +169,7 @@ struct pm_pcn {
     double *U, *Up, *stdv, *y, *A, *Phi, *PhiS, *PhiS_new, *G, *sum_u, *x_rep, *t_rep;
     float *scale, *X, *Gs;
     double* shift;              // surrogate input (u - shift) * scale
+    double* jump;               // per chain: squared prior-whitened jumps of accepted moves in the current run
     int *pass, *idx;
     unsigned long long* accepts;
     int64_t n_summed = 0;
@@ -270,6 +278,7 @@ int pm_pcn_create(pm_ctx* c, pm_pcn** out, const pm_pcn_config* cfg, const doubl
         p->t_rep = linear ? nullptr : b.take<double>((size_t)(C * n_obs));
         p->scale = b.take<float>((size_t)n_u); p->X = b.take<float>((size_t)C * n_u);
         p->shift = b.take<double>((size_t)n_u);
+        p->jump = b.take<double>((size_t)C);
         p->Gs = b.take<float>((size_t)(C * n_obs));
         p->pass = b.take<int>((size_t)C); p->idx = b.take<int>((size_t)C);
         p->accepts = b.take<unsigned long long>(4);
@@ -353,6 +362,7 @@ int pm_pcn_run(pm_ctx* c, pm_pcn* p, int64_t n_steps, pm_pcn_stats* st)
     idx_h.reserve((size_t)C);
     pm_pcn_stats s{};
     PM_CUDA(cudaMemsetAsync(p->accepts, 0, 8, c->stream), "clear counter");
+    PM_CUDA(cudaMemsetAsync(p->jump, 0, sizeof(double) * (size_t)C, c->stream), "clear jumps");
     cudaEvent_t e0, e1;
     PM_CUDA(cudaEventCreate(&e0), "event");
     PM_CUDA(cudaEventCreate(&e1), "event");
@@ -386,7 +396,7 @@ int pm_pcn_run(pm_ctx* c, pm_pcn* p, int64_t n_steps, pm_pcn_stats* st)
             s.forward_evals += (int64_t)idx_h.size();
             accept_kernel<<<blocks((int64_t)idx_h.size(), 128), 128, 0, c->stream>>>(
                 p->idx, (int)idx_h.size(), p->y, p->G, n_obs, inv2s2, da ? 1 : 0, p->Phi, p->PhiS, p->PhiS_new, p->U,
-                p->Up, n_u, k0, k1, step, p->accepts);
+                p->Up, n_u, k0, k1, step, p->accepts, p->stdv, p->jump);
             PM_CUDA(cudaGetLastError(), "accept");
             count_launch(c);
         }
@@ -400,8 +410,12 @@ int pm_pcn_run(pm_ctx* c, pm_pcn* p, int64_t n_steps, pm_pcn_stats* st)
     }
     PM_CUDA(cudaEventRecord(e1, c->stream), "event");
     unsigned long long acc = 0;
+    std::vector<double> jump_h((size_t)C);
     PM_CUDA(cudaMemcpyAsync(&acc, p->accepts, 8, cudaMemcpyDeviceToHost, c->stream), "copy accepts");
+    PM_CUDA(cudaMemcpyAsync(jump_h.data(), p->jump, sizeof(double) * (size_t)C, cudaMemcpyDeviceToHost, c->stream),
+            "copy jumps");
     PM_CUDA(cudaStreamSynchronize(c->stream), "pcn");
+    for (int q = 0; q < C; ++q) s.sq_jump += jump_h[(size_t)q];
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);

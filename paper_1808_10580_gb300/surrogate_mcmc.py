@@ -139,5 +139,6 @@ def run_chains(ctx, prob: Problem, u0, beta, n_steps, seed, net=None, tensor: bo
     ch.close()
     st["mean_phi"] = float(np.mean(phi))
     st["accepted_per_s"] = st["accepts"] / st["wall_seconds"]
+    st["sq_jump_per_s"] = st["sq_jump"] / st["wall_seconds"]
     st["samples_per_s"] = st["proposals"] / st["wall_seconds"]
     return st, s / max(n, 1)

@@ -37,6 +37,7 @@ def test_plain_chain_matches_oracle_step_by_step(c):
     ch.close()
     U_or, total, ost = mcmc.run(u0, lambda u: A @ u, y, sigma, 0.3, std, 300, seed=123)
     assert st["accepts"] == ost["accepts"] and st["forward_evals"] == 8 * 300
+    assert abs(st["sq_jump"] - ost["sq_jump"]) <= 1e-10 * ost["sq_jump"]
     assert np.abs(U - U_or).max() <= 1e-12
     assert np.abs(s - total).max() <= 1e-10 * max(1.0, np.abs(total).max())
     assert n == 8 * 300
@@ -129,3 +130,33 @@ def test_screen_shift_zero_equals_no_shift(c):
     keys = ("proposals", "stage1_accepts", "accepts", "forward_evals")
     assert all(runs[0][k] == runs[1][k] for k in keys)
     assert shifted["stage1_accepts"] != runs[0]["stage1_accepts"]
+
+
+def test_trained_screen_gains_over_plain_pcn(c):
+    # What the trained network buys: at a large pCN step most proposals are
+    # rejected; the screen rejects them without a forward evaluation, so the
+    # chain spends far fewer evaluations per accepted move than plain pCN,
+    # and both reach the posterior mean.
+    A, y, sigma, std = toy(sigma=0.2, seed=5, n_obs=6, K=1)
+    m, S = mcmc.linear_gaussian_posterior(A, y, sigma, std)
+    rng = np.random.default_rng(6)
+    Z = rng.standard_normal((8192, len(std)))
+    net = pm.pm_surrogate_create(c, len(std), 128, len(y), 3)
+    pm.pm_surrogate_train(c, net, Z.astype(np.float32), ((Z * std) @ A.T).astype(np.float32), epochs=60, batch=256,
+                          lr=3e-3)
+    beta, steps = 0.8, 4000
+    runs = {}
+    for name, screen in (("plain", None), ("da", net)):
+        ch = pm.PCN(c, 1, np.zeros((16, len(std))), y, sigma, beta, seed=31, A=A, screen=screen,
+                    screen_scale=(1.0 / std) if screen is not None else None)
+        st = ch.run(steps)
+        _, _, s, n = ch.state()
+        ch.close()
+        runs[name] = (st, s / n)
+    pm.pm_surrogate_destroy(net)
+    (sp, mp), (sd, md) = runs["plain"], runs["da"]
+    evals_per_accept_plain = sp["forward_evals"] / sp["accepts"]
+    evals_per_accept_da = sd["forward_evals"] / sd["accepts"]
+    assert evals_per_accept_da <= 0.5 * evals_per_accept_plain, (evals_per_accept_plain, evals_per_accept_da)
+    for est in (mp, md):
+        assert np.all(np.abs(est - m) <= 0.2 * np.sqrt(np.diag(S))), (est, m)

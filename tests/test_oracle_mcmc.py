@@ -53,3 +53,22 @@ def test_delayed_acceptance_with_exact_screen_equals_plain_chain():
     u0 = np.zeros((2, len(std)))
     U1, t1, _ = mcmc.run(u0, G, y, sigma, 0.3, std, 200, seed=5, Gs=G)
     assert np.all(np.isfinite(U1)) and np.abs(t1).sum() > 0
+
+
+def test_sq_jump_counts_the_moves_of_accepted_proposals():
+    # The squared-jump statistic equals the squared prior-whitened distance
+    # between successive states, recomputed here one step at a time from the
+    # states themselves.
+    rng = np.random.default_rng(2)
+    std = mcmc.prior_std(1)
+    A = rng.standard_normal((4, len(std)))
+    y = rng.standard_normal(4)
+    U = np.zeros((3, len(std)))
+    _, _, st = mcmc.run(U, lambda u: A @ u, y, 0.5, 0.4, std, 40, seed=9)
+    total = 0.0
+    for s in range(40):
+        V, _, _ = mcmc.run(U, lambda u: A @ u, y, 0.5, 0.4, std, 1, seed=9, step0=s)
+        total += float((((V - U) / std) ** 2).sum())
+        U = V
+    assert st["accepts"] > 0
+    assert abs(st["sq_jump"] - total) <= 1e-12 * total
