@@ -21,7 +21,7 @@
  * Per-path values are returned; the estimator mean/variance are formed by the
  * caller with plain numpy (mean, unbiased variance).
  *
- * Readings of points where the paper is silent (each is listed in the design doc):
+ * Readings of points where the paper is silent (the same on both sides):
  *   stream-function parameterisation and half-mode order; RNG counter layout
  *   and 23-bit uniforms; step count and last step; periodic wrap; exit test
  *   |X|^2 >= R^2 with radial projection; left-point integral of f; unexited

@@ -654,8 +654,9 @@ int pm_forward_dirichlet(pm_ctx* c, const pm_field* field, double drift_scale, d
     const int64_t total = n_obs * M;
 
     auto layout = [&](Bump& b) {
-        struct P { unsigned long long* ctr; double *g, *x, *mean, *var, *xo; int32_t* es; } p{};
+        struct P { unsigned long long* ctr; double *g, *x, *mean, *var, *xo; int32_t* es; double2* rpart; } p{};
         p.ctr = b.take<unsigned long long>(4);  // next path, unexited, steps, tensor-core error flag
+        p.rpart = b.take<double2>((size_t)(n_obs * (int64_t)reduce_path_chunks(M)));
         p.g = (dev && g_out) ? nullptr : b.take<double>((size_t)total);
         if (!dev) {
             p.x = b.take<double>((size_t)(2 * n_obs));
@@ -747,8 +748,8 @@ int pm_forward_dirichlet(pm_ctx* c, const pm_field* field, double drift_scale, d
         c->timed = true;
     }
     count_launch(c);
-    PM_CUDA(launch_reduce_paths(dg, n_obs, M, dmean, dvar, c->stream), "reduce kernel");
-    count_launch(c);
+    PM_CUDA(launch_reduce_paths(dg, n_obs, M, dmean, dvar, c->stream, W.rpart), "reduce kernel");
+    count_launch(c, reduce_path_chunks(M) > 0 ? 2 : 1);
     if (dev && n_unexited)
         PM_CUDA(cudaMemcpyAsync(n_unexited, W.ctr + 1, 8, cudaMemcpyDeviceToDevice, c->stream), "copy n_unexited");
     if (dev && (flags & PM_ASYNC)) return PM_OK;

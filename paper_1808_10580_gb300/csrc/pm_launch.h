@@ -87,8 +87,13 @@ cudaError_t launch_prep_timedep(const double* x, const double* t, int64_t n_obs,
                                 unsigned long long* steps = nullptr, int64_t M = 0);
 cudaError_t launch_reduce(const double2* part, int64_t n_obs, int32_t chunks, int64_t M, double* mean,
                           double* var, cudaStream_t s);
+// Per-path values g [n_obs][M] -> mean, var.  For M > kReducePathChunk the
+// reduction runs in two passes through `part` ([n_obs][reduce_path_chunks(M)]
+// scratch); with part == nullptr, or shorter rows, one CTA per observation.
+constexpr int64_t kReducePathChunk = 2048;
+int32_t reduce_path_chunks(int64_t M);
 cudaError_t launch_reduce_paths(const double* g, int64_t n_obs, int64_t M, double* mean, double* var,
-                                cudaStream_t s);
+                                cudaStream_t s, double2* part = nullptr);
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, int64_t n, uint32_t* out,
                           cudaStream_t s);
 cudaError_t launch_normals(uint64_t seed, uint32_t b, uint32_t j, uint32_t i, int64_t n0, int64_t count,

@@ -167,10 +167,50 @@ __global__ void reduce_paths_kernel(const double* __restrict__ g, int64_t M, dou
     }
 }
 
-cudaError_t launch_reduce_paths(const double* g, int64_t n_obs, int64_t M, double* mean, double* var, cudaStream_t s)
+// Long rows (M > kReducePathChunk): first one CTA per (observation, chunk of
+// kReducePathChunk paths) forms the chunk's compensated (sum, sum of squares)
+// in the same fixed order, then reduce_chunks_kernel combines the chunks in
+// chunk order.  Enough CTAs to stream the per-path array at HBM speed.
+__global__ void reduce_path_chunks_kernel(const double* __restrict__ g, int64_t M, int32_t chunks,
+                                          double2* __restrict__ part)
 {
-    reduce_paths_kernel<<<(unsigned)n_obs, 256, 0, s>>>(g, M, mean, var);
-    return cudaGetLastError();
+    const int64_t j = blockIdx.y;
+    const int64_t i0 = (int64_t)blockIdx.x * kReducePathChunk;
+    const int64_t i1 = (i0 + kReducePathChunk < M) ? i0 + kReducePathChunk : M;
+    const double* gj = g + j * M;
+    Kahan a, b;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const double v = gj[i];
+        a.add(v);
+        b.add(v * v);
+    }
+    warp_combine(a);
+    warp_combine(b);
+    __shared__ double sa[8], sca[8], sb[8], scb[8];
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { sa[w] = a.s; sca[w] = a.c; sb[w] = b.s; scb[w] = b.c; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Kahan A, B;
+        for (int k = 0; k < 8; ++k) { A.add(sa[k]); A.c += sca[k]; B.add(sb[k]); B.c += scb[k]; }
+        part[j * chunks + blockIdx.x] = make_double2(A.value(), B.value());
+    }
+}
+
+int32_t reduce_path_chunks(int64_t M) { return M > kReducePathChunk ? (int32_t)((M + kReducePathChunk - 1) / kReducePathChunk) : 0; }
+
+cudaError_t launch_reduce_paths(const double* g, int64_t n_obs, int64_t M, double* mean, double* var, cudaStream_t s,
+                                double2* part)
+{
+    const int32_t chunks = reduce_path_chunks(M);
+    if (chunks == 0 || part == nullptr) {
+        reduce_paths_kernel<<<(unsigned)n_obs, 256, 0, s>>>(g, M, mean, var);
+        return cudaGetLastError();
+    }
+    reduce_path_chunks_kernel<<<dim3((unsigned)chunks, (unsigned)n_obs), 256, 0, s>>>(g, M, chunks, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_reduce(part, n_obs, chunks, M, mean, var, s);
 }
 
 // ---------------------------------------------------------------------------

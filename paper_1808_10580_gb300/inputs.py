@@ -8,8 +8,8 @@ Every draw uses numpy's PCG64 generator with a fixed seed, so a workload is a
 pure function of its name.  Shapes follow Section 4 of the paper: about 100
 observations (Example 1), a Fourier stream function over a square lattice of
 wave numbers (Eq. v_expand) with a |k|^-4 prior on each real coefficient,
-Dirichlet data on a disk.  The concrete recipe of each workload is listed in
-DESIGN.md under "Input recipe".
+Dirichlet data on a disk.  The concrete recipe of each workload is in its
+function's docstring below.
 
 Layout conventions (the library's input format, shared by both sides):
   * ``u``: float64 array of length 2H, pairs (a_h, b_h) over the half-plane

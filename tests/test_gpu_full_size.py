@@ -1,7 +1,8 @@
 """Parity at the full workload sizes, in the launch configurations the benchmark
 times.  The FP64 oracle computes a sample of the per-path values one path at a
 time; the GPU run is the full one.  On the 440-mode field float and double paths
-decorrelate (the design doc r12), so the comparison is paired and in distribution:
+decorrelate (a chaotic flow: a rounding-size change grows to O(1) by t ~ 0.8),
+so the comparison is paired and in distribution:
 the mean per-path difference must vanish within 5 standard errors, and paths
 that finish early (before the flow separates them) must agree closely."""
 import numpy as np

@@ -150,3 +150,42 @@ def test_persistent_tensor_grids_fill_every_sm(c):
     g_bat = pm.pm_last_grid(c)
     assert g_dir % sms == 0 and g_dir >= 2 * sms, (g_dir, sms)
     assert g_bat % sms == 0 and g_bat >= 2 * sms, (g_bat, sms)
+
+
+def shear_field(orc, w):
+    modes = orc.half_modes(10)
+    h = [tuple(m) for m in modes].index((2, 3))
+    u = np.zeros_like(w.u)
+    u[2 * h], u[2 * h + 1] = 0.05, 0.02
+    return u
+
+
+def test_tensor_path_shards_equal_one_call(c):
+    # Paths are keyed by their index, and a tile row's result depends on its
+    # own particle only: shards at any path offset reproduce the single call.
+    w = inputs.timedep_k10(M=384)
+    obs = np.array([3, 150, 299])
+    _, _, g = _gpu.timedep(c, w, pm.PM_FP32 | pm.PM_TENSOR, obs=obs, g_out=True)
+    _, _, g1 = _gpu.timedep(c, w, pm.PM_FP32 | pm.PM_TENSOR, obs=obs, M=200, g_out=True)
+    _, _, g2 = _gpu.timedep(c, w, pm.PM_FP32 | pm.PM_TENSOR, obs=obs, M=184, g_out=True, path_offset=200)
+    assert np.array_equal(np.concatenate([g1, g2], axis=1), g)
+
+
+@pytest.mark.parametrize("M", [1, 129])
+def test_tensor_path_zero_horizon_and_ragged_tiles(c, orc, M):
+    w = inputs.timedep_k10(M=M)
+    w.u = shear_field(orc, w)
+    w.x, w.t = w.x[:4].copy(), np.array([0.0, 0.001, 0.0105, 0.3])
+    mean, var, g = _gpu.timedep(c, w, pm.PM_FP32 | pm.PM_TENSOR, g_out=True)
+    go = orc.timedep_paths(10, w.u, w.kappa, w.theta0, w.x, w.t, w.dt, w.seed, npaths=M)
+    assert np.abs(g - go).max() <= 5e-5
+    # t = 0: every path is theta0 at the observation point
+    assert np.ptp(g[0]) == 0.0 and np.abs(g[0] - go[0]).max() <= 1e-6
+
+
+@pytest.mark.parametrize("device", [False, True])
+def test_tensor_path_host_and_device_pointers_agree(c, device):
+    w = inputs.timedep_k10(M=256)
+    a = _gpu.timedep(c, w, pm.PM_FP32 | pm.PM_TENSOR, device=True)
+    b = _gpu.timedep(c, w, pm.PM_FP32 | pm.PM_TENSOR, device=device)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])

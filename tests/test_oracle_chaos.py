@@ -1,4 +1,5 @@
-"""Evidence for the parity reading of the design doc r12, from the oracle alone: on
+"""Evidence for reading the parity bound per observation rather than per path
+(float and double paths separate on the 440-mode field), from the oracle alone: on
 the 440-mode field a rounding-size change of a path's start grows to macroscopic
 size within the observation horizon (chaotic advection), while on the fields used
 for pathwise parity (zero drift, one stream mode) it does not."""
