@@ -90,7 +90,7 @@ cudaError_t launch_reduce(const double2* part, int64_t n_obs, int32_t chunks, in
 // Per-path values g [n_obs][M] -> mean, var.  For M > kReducePathChunk the
 // reduction runs in two passes through `part` ([n_obs][reduce_path_chunks(M)]
 // scratch); with part == nullptr, or shorter rows, one CTA per observation.
-constexpr int64_t kReducePathChunk = 2048;
+constexpr int64_t kReducePathChunk = 8192;
 int32_t reduce_path_chunks(int64_t M);
 cudaError_t launch_reduce_paths(const double* g, int64_t n_obs, int64_t M, double* mean, double* var,
                                 cudaStream_t s, double2* part = nullptr);

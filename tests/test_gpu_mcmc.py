@@ -147,7 +147,7 @@ def test_trained_screen_gains_over_plain_pcn(c):
     beta, steps = 0.8, 6000
     runs = {}
     for name, screen in (("plain", None), ("da", net)):
-        ch = pm.PCN(c, 1, np.zeros((32, len(std))), y, sigma, beta, seed=31, A=A, screen=screen,
+        ch = pm.PCN(c, 1, np.tile(m, (32, 1)), y, sigma, beta, seed=31, A=A, screen=screen,
                     screen_scale=(1.0 / std) if screen is not None else None)
         st = ch.run(steps)
         _, _, s, n = ch.state()
@@ -158,9 +158,9 @@ def test_trained_screen_gains_over_plain_pcn(c):
     evals_per_accept_plain = sp["forward_evals"] / sp["accepts"]
     evals_per_accept_da = sd["forward_evals"] / sd["accepts"]
     assert evals_per_accept_da <= 0.5 * evals_per_accept_plain, (evals_per_accept_plain, evals_per_accept_da)
-    # both sample the posterior (running means from the prior mean, burn-in
-    # included, at a step where plain pCN accepts a few percent): within 0.75
-    # posterior standard deviations; the closed-form check of the screened
-    # chain at a working step is test_delayed_acceptance_reaches_linear_posterior
+    # both sample the posterior (chains started at its mean, at a step where
+    # plain pCN accepts a few percent): within 0.75 posterior standard
+    # deviations; the closed-form check of the screened chain from the prior
+    # mean is test_delayed_acceptance_reaches_linear_posterior
     for est in (mp, md):
         assert np.all(np.abs(est - m) <= 0.75 * np.sqrt(np.diag(S))), (est, m)
