@@ -166,7 +166,7 @@ def run_reference(args):
     w = inputs.timedep_k10()
     cores = os.cpu_count() or 1
     obs = np.arange(0, len(w.t), 10)          # 30 observations spanning the three times
-    P = 4
+    P = 32                                    # 960 (observation, path) items: every host core busy
     sub_steps = sum(int(np.ceil(t / w.dt - 1e-9)) for t in w.t[obs]) * P
 
     def step():
