@@ -55,6 +55,10 @@ def lib():
                                          C.c_int64, C.c_double, C.c_int64, C.c_uint64, C.c_uint32,
                                          i64, C.c_int32, d, i64, d]
         L.or_dirichlet_paths.restype = C.c_int32
+        L.or_square_bvp_paths.argtypes = [d, C.c_double, C.c_int32, d, C.c_double, C.c_double, C.c_double, d,
+                                          C.c_int64, C.c_int64, C.c_int64, C.c_double, C.c_int64, C.c_uint64,
+                                          C.c_uint32, i64, C.c_int32, d, i64]
+        L.or_square_bvp_paths.restype = C.c_int32
         _lib = L
     return _lib
 
@@ -180,6 +184,27 @@ def dirichlet_paths(K, u, drift_scale, kappa, gd, x, dt, max_steps, seed, i0=0, 
     if nt < 0:
         raise MemoryError("oracle allocation failed")
     return (g, st, xe) if want_x else (g, st)
+
+
+def square_bvp_paths(prob, x, dt, max_steps, seed, i0=0, npaths=1, inst=0, nthreads=0, obs_id=None):
+    """Per-path values of the optimal-forcing problem in the unit square
+    (Section 4, Eq. bvp:ex1, by Algorithm 2 / Theorem 3.2) -> (out [n_obs,
+    n_src + 1, npaths]: g(X_tau) then the time integrals of each source
+    profile, exit steps [n_obs, npaths])."""
+    x = _f64(x).reshape(-1, 2)
+    c = _f64(prob.c).reshape(-1, 2)
+    b = _f64(prob.b).reshape(2)
+    n_obs, n_src = x.shape[0], c.shape[0]
+    out = np.empty((n_obs, n_src + 1, npaths))
+    st = np.empty((n_obs, npaths), dtype=np.int64)
+    ids = _ids(obs_id, n_obs)
+    nt = lib().or_square_bvp_paths(_p(b, C.c_double), prob.kappa, n_src, _p(c, C.c_double), prob.w, prob.g_cos,
+                                   prob.g_quad, _p(x, C.c_double), n_obs, i0, npaths, dt, max_steps, seed, inst,
+                                   _p(ids, C.c_int64) if ids is not None else None, nthreads, _p(out, C.c_double),
+                                   _p(st, C.c_int64))
+    if nt < 0:
+        raise ValueError("oracle: at most 16 sources")
+    return out, st
 
 
 def estimate(g):

@@ -446,3 +446,109 @@ int32_t or_dirichlet_paths(int32_t K, const double* u, double drift_scale, doubl
     field_free(&J.field);
     return nt;
 }
+
+/* ------------------------------------------------------------------------ */
+/* The optimal-forcing boundary-value problem of Section 4 (Eq. bvp:ex1),    */
+/* by Algorithm 2 / Theorem 3.2 in the unit square:                          */
+/*   -b . grad theta + kappa Laplace theta = sum_q F_q phi_q(x),             */
+/*   phi_q(x) = exp(-w |x - c_q|^2),  theta = g on the boundary,             */
+/*   g(y) = g_cos (cos(pi y1 / 2) + cos(pi y2 / 2)) / 2 + g_quad (y1^2 - y2^2).*/
+/* theta(x; F) = E[g(X_tau)] - sum_q F_q E[int_0^tau phi_q(X_s) ds] with     */
+/* dX = -b ds + sqrt(2 kappa) dW.  One path returns the n_src + 1 values     */
+/* (g(X_tau), sum_m phi_1(X_m) dt, ..., sum_m phi_n(X_m) dt), m < n_exit.    */
+/* Exit: the first step with X outside the open square; X_tau is the exit    */
+/* position clamped to the square.  A path that reaches max_steps returns    */
+/* zeros (the chi_{tau < infinity} of Theorem 3.2) and exit step -1.         */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    double b[2], kappa, w, g_cos, g_quad;
+    int32_t n_src;
+    const double* c;
+    const double* x;
+    int64_t n_obs, i0, npaths;
+    double dt;
+    int64_t max_steps;
+    uint64_t seed;
+    uint32_t inst;
+    double* out;         /* [n_obs][n_src + 1][npaths] */
+    int64_t* exit_step;  /* [n_obs][npaths] */
+    const int64_t* jid;
+    int64_t next;
+    pthread_mutex_t lock;
+} sq_job_t;
+
+static int outside_unit_square(const double X[2])
+{
+    return X[0] <= 0.0 || X[0] >= 1.0 || X[1] <= 0.0 || X[1] >= 1.0;
+}
+
+static void sq_path(const sq_job_t* J, int64_t j, int64_t i, int64_t w)
+{
+    const int64_t nf = J->n_src + 1, P = J->npaths, p = w % P;
+    double* o = J->out + (j * nf) * P + p;  /* value q at o[q * P] */
+    double X[2] = {J->x[2 * j], J->x[2 * j + 1]};
+    double sums[16];
+    for (int q = 0; q < J->n_src; ++q) sums[q] = 0.0;
+    const double sq = sqrt(2.0 * J->kappa * J->dt);
+    int64_t n = 0;
+    int exited = outside_unit_square(X);
+    while (!exited && n < J->max_steps) {
+        for (int q = 0; q < J->n_src; ++q) {  /* left-point rule: phi at X_n */
+            const double d0 = X[0] - J->c[2 * q], d1 = X[1] - J->c[2 * q + 1];
+            sums[q] += exp(-J->w * (d0 * d0 + d1 * d1)) * J->dt;
+        }
+        double xi[2];
+        or_step_normals(J->seed, J->inst, (uint32_t)(J->jid ? J->jid[j] : j), (uint32_t)i, n, xi);
+        X[0] = X[0] - J->b[0] * J->dt + sq * xi[0];
+        X[1] = X[1] - J->b[1] * J->dt + sq * xi[1];
+        ++n;
+        exited = outside_unit_square(X);
+    }
+    if (!exited) {
+        for (int64_t q = 0; q < nf; ++q) o[q * P] = 0.0;
+        J->exit_step[j * P + p] = -1;
+        return;
+    }
+    const double y0 = X[0] < 0.0 ? 0.0 : (X[0] > 1.0 ? 1.0 : X[0]);
+    const double y1 = X[1] < 0.0 ? 0.0 : (X[1] > 1.0 ? 1.0 : X[1]);
+    const double pi = 3.14159265358979323846;
+    o[0] = J->g_cos * 0.5 * (cos(0.5 * pi * y0) + cos(0.5 * pi * y1)) + J->g_quad * (y0 * y0 - y1 * y1);
+    for (int q = 0; q < J->n_src; ++q) o[(q + 1) * P] = sums[q];
+    J->exit_step[j * P + p] = n;
+}
+
+static void* sq_worker(void* arg)
+{
+    sq_job_t* J = (sq_job_t*)arg;
+    const int64_t total = J->n_obs * J->npaths;
+    const int64_t grain = 16;
+    for (;;) {
+        const int64_t w0 = job_take(&J->next, &J->lock, total, grain);
+        if (w0 >= total) break;
+        const int64_t w1 = w0 + grain < total ? w0 + grain : total;
+        for (int64_t w = w0; w < w1; ++w) sq_path(J, w / J->npaths, J->i0 + w % J->npaths, w);
+    }
+    return NULL;
+}
+
+int32_t or_square_bvp_paths(const double* b, double kappa, int32_t n_src, const double* c, double w,
+                            double g_cos, double g_quad, const double* x, int64_t n_obs, int64_t i0,
+                            int64_t npaths, double dt, int64_t max_steps, uint64_t seed, uint32_t inst,
+                            const int64_t* obs_id, int32_t nthreads, double* out, int64_t* exit_step)
+{
+    if (n_src < 0 || n_src > 16) return -1;
+    sq_job_t J;
+    J.b[0] = b[0]; J.b[1] = b[1]; J.kappa = kappa; J.w = w; J.g_cos = g_cos; J.g_quad = g_quad;
+    J.n_src = n_src; J.c = c; J.x = x; J.n_obs = n_obs; J.i0 = i0; J.npaths = npaths; J.dt = dt;
+    J.max_steps = max_steps; J.seed = seed; J.inst = inst; J.out = out; J.exit_step = exit_step;
+    J.jid = obs_id; J.next = 0;
+    pthread_mutex_init(&J.lock, NULL);
+    const int nt = resolve_threads(nthreads);
+    pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)nt);
+    for (int k = 0; k < nt; ++k) pthread_create(&th[k], NULL, sq_worker, &J);
+    for (int k = 0; k < nt; ++k) pthread_join(th[k], NULL);
+    free(th);
+    pthread_mutex_destroy(&J.lock);
+    return nt;
+}

@@ -121,6 +121,45 @@ class DirichletWorkload:
     seed: int
 
 
+@dataclass
+class SquareBVP:
+    """The optimal-forcing boundary-value problem in the unit square (the
+    example of Section 4, Eq. bvp:ex1): constant drift b, diffusion kappa,
+    Gaussian source profiles exp(-w |x - c_q|^2) at c [n_src, 2], boundary
+    data g_cos (cos(pi x1 / 2) + cos(pi x2 / 2)) / 2 + g_quad (x1^2 - x2^2)."""
+    b: np.ndarray
+    kappa: float
+    c: np.ndarray
+    w: float
+    g_cos: float = 1.0
+    g_quad: float = 0.0
+
+
+@dataclass
+class SquareBVPWorkload:
+    name: str
+    prob: SquareBVP
+    x: np.ndarray          # [n_obs, 2] observation points
+    y: np.ndarray          # [n_obs] target data
+    M: int
+    dt: float
+    max_steps: int
+    seed: int
+
+
+def optimal_forcing(M: int = 1_000_000) -> SquareBVPWorkload:
+    """The paper's optimal-forcing example: b = (1, 1), kappa = 0.282, three
+    sources exp(-4 |x - c_q|^2), the paper's boundary data, data y = (0, 0, 0)
+    at three observation points.  The paper shows its source and observation
+    locations only in a figure; these stand in for them (sources near three
+    corners of the square's interior, observations between them).  dt = 1e-4,
+    M paths per observation, path seed 4005."""
+    prob = SquareBVP(b=np.array([1.0, 1.0]), kappa=0.282,
+                     c=np.array([[0.25, 0.25], [0.75, 0.35], [0.4, 0.8]]), w=4.0)
+    x = np.array([[0.3, 0.55], [0.65, 0.6], [0.55, 0.25]])
+    return SquareBVPWorkload("optimal_forcing_square_3src_3obs", prob, x, np.zeros(3), M, 1e-4, 10_000_000, 4005)
+
+
 def plain_fp64_k2() -> TimedepWorkload:
     """K=2 (24 reals), kappa=0.05, theta0 = sin 2pi x1 sin 2pi x2, 3x3 grid, t=1, M=1000, dt=0.01."""
     th = Fourier(k=np.array([[1, -1], [1, 1]], dtype=np.int32),
