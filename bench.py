@@ -574,6 +574,53 @@ def run_surrogate(args):
     return 0
 
 
+def run_bvp(args):
+    """The optimal-forcing example (auxiliary line): the particle functionals of
+    the square-domain boundary-value problem (3 observations x M paths, the
+    paper's drift, diffusion, sources and boundary data), timed, then the
+    Nelder-Mead search for the forcing on those functionals."""
+    import torch
+
+    import paper_1808_10580_gb300 as pm
+    from paper_1808_10580_gb300 import optimal_forcing as of
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    ctx = pm.pm_create(0, stream.cuda_stream)
+    pm.pm_set_kernel_timing(ctx, 1)
+    w = inputs.optimal_forcing(M=args.M or 1_000_000)
+    flags = pm.PM_FP32
+    for _ in range(args.warmup):
+        E, se = of.functionals(ctx, w, flags)
+    times, steps = [], []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        E, se = of.functionals(ctx, w, flags)
+        times.append(time.perf_counter() - t0)
+        steps.append(pm.pm_last_step_count(ctx))
+    kern_ms = pm.pm_last_kernel_ms(ctx)
+    t0 = time.perf_counter()
+    r = of.solve(E, w.y, xtol=1e-12, ftol=1e-16)
+    t_nm = time.perf_counter() - t0
+    per_call = statistics.median(times)
+    line = {"metric": METRIC, "value": steps[-1] / per_call, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * per_call, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic", "auxiliary": True,
+            "config": {"workload": w.name, "n_obs": len(w.x), "M": w.M, "dt": w.dt, "kappa": w.prob.kappa,
+                       "b": w.prob.b.tolist(), "sources": w.prob.c.tolist(), "particle_steps_per_call": steps[-1],
+                       "grid": pm.pm_last_grid(ctx)},
+            "kernel_ms": kern_ms,
+            "functionals": {"E": E.tolist(), "se": se.tolist()},
+            "nelder_mead": {"F": r.x.tolist(), "cost": r.fun, "evaluations": r.evaluations,
+                            "iterations": r.iterations, "seconds": t_nm,
+                            "G_evaluations_per_s": r.evaluations / (per_call + t_nm),
+                            "note": "G(F) is affine in F (Theorem 3.2), so one set of paths serves every evaluation"}}
+    print(json.dumps(line), flush=True)
+    pm.pm_destroy(ctx)
+    return 0
+
+
 def run_mcmc(args):
     """Surrogate-screened pCN against plain pCN on the same GPU (auxiliary line):
     64 chains started at the data-generating field, the same beta for both
@@ -639,7 +686,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--M", type=int, default=0, help="particles per observation (default: the workload's own; "
                     "smaller values are for profiling captures only)")
-    ap.add_argument("--workload", default="timedep", choices=["timedep", "dirichlet", "batched", "mcmc", "sweep", "surrogate"],
+    ap.add_argument("--workload", default="timedep", choices=["timedep", "dirichlet", "batched", "mcmc", "sweep", "surrogate", "bvp"],
                     help="timedep: the headline line; dirichlet / batched / mcmc: auxiliary measurements")
     ap.add_argument("--train-pairs", type=int, default=1 << 16, help="mcmc: surrogate training pairs")
     ap.add_argument("--betas", default="0.03", help="mcmc: comma-separated pCN steps (each the same for both samplers)")
@@ -677,6 +724,8 @@ def main():
         return run_sweep(args)
     if args.workload == "surrogate":
         return run_surrogate(args)
+    if args.workload == "bvp":
+        return run_bvp(args)
     if args.workload != "timedep":
         return run_aux(args)
     return run_gpu(args)

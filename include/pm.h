@@ -172,6 +172,43 @@ int pm_forward_timedep(pm_ctx* ctx, const pm_field* field, double kappa, const p
                        uint64_t seed, uint32_t flags, double* mean, double* var,
                        const pm_path_opts* opts);
 
+/* ------------------------------------------------------------------------- *
+ * The optimal-forcing boundary-value problem of Section 4 (Eq. bvp:ex1) by
+ * Algorithm 2 and Theorem 3.2: in the unit square (0,1)^2,
+ *   -b . grad theta + kappa Laplace theta = sum_q F_q phi_q,
+ *   phi_q(x) = exp(-w |x - c_q|^2),      theta = g on the boundary,
+ *   g(y) = g_cos (cos(pi y1 / 2) + cos(pi y2 / 2)) / 2 + g_quad (y1^2 - y2^2)
+ * (the paper's data: g_cos = 1, g_quad = 0).  Theorem 3.2 with dX = -b ds +
+ * sqrt(2 kappa) dW gives theta(x; F) = E[g(X_tau)] - sum_q F_q E[int_0^tau
+ * phi_q(X_s) ds], affine in F: one set of paths yields, per observation, the
+ * n_src + 1 functionals from which theta(x; F) follows for every F.
+ * Paths: Euler-Maruyama steps of length dt, noise as for pm_forward_dirichlet
+ * (counter {n/2, i, j, instance}); the integrals by the left-point rule
+ * sum_{m < n} phi_q(X_m) dt; exit at the first step outside the open square,
+ * X_tau = that position clamped to the square; a path that reaches max_steps
+ * contributes zeros and is counted in *n_unexited.
+ * ------------------------------------------------------------------------- */
+#define PM_MAX_SOURCES 8
+
+typedef struct pm_square_bvp {
+    double b[2];        /* constant drift (the paper: (1, 1)) */
+    double kappa;       /* >= 0 */
+    double w;           /* source width parameter (the paper: 4), >= 0 */
+    double g_cos, g_quad;
+    int32_t n_src;      /* 0 .. PM_MAX_SOURCES */
+    int32_t reserved;
+    const double* c;    /* [n_src][2] source centres (host) */
+} pm_square_bvp;
+
+/* mean, var: [n_obs][n_src + 1] (var may be NULL): for observation j, entry 0
+ * is E[g(X_tau)] and entry q + 1 is E[int phi_q]; opts->g_out, if set,
+ * receives the per-path values [n_obs][n_src + 1][M]; opts->x_out is not
+ * used.  x: [n_obs][2].  Pointers follow PM_DEVICE_PTRS; PM_FP64 selects
+ * double paths.  Returns PM_OK, PM_WARN_UNEXITED or an error. */
+int pm_forward_square_bvp(pm_ctx* ctx, const pm_square_bvp* prob, const double* x, int64_t n_obs, int64_t M,
+                          double dt, int64_t max_steps, uint64_t seed, uint32_t flags, double* mean, double* var,
+                          int32_t* exit_step, int64_t* n_unexited, const pm_path_opts* opts);
+
 /* The groups PM_SHARE_PATHS forms, computed on the host (no device, no
  * context): x [n_obs][2], t [n_obs] host arrays as for pm_forward_timedep.
  *   group_of[j]   group of observation j, numbered in launch order (groups

@@ -124,6 +124,8 @@ def load(build_if_missing: bool = True):
     L.pm_last_grid.argtypes = [vp]
     L.pm_last_grid.restype = i64
     L.pm_path_groups.argtypes = [vp, vp, i64, C.c_double, vp, vp, vp, vp]
+    L.pm_forward_square_bvp.argtypes = [vp, vp, vp, i64, i64, C.c_double, i64, C.c_uint64, u32, vp, vp, vp, vp,
+                                        C.POINTER(pm_path_opts)]
     L.pm_set_ctas_per_sm.argtypes = [vp, C.c_int32, C.c_int32, C.c_uint32, C.c_int32]
     _lib = L
     return L
@@ -272,6 +274,31 @@ def pm_forward_dirichlet(ctx, field: Field, drift_scale, kappa, g: DirichletData
                                               _ptr(x), int(n_obs), int(M), float(dt), int(max_steps), int(seed),
                                               int(flags), _ptr(mean), _ptr(var), _ptr(exit_step), _ptr(n_unexited),
                                               C.byref(o)))
+
+
+class pm_square_bvp(C.Structure):
+    _fields_ = [("b", C.c_double * 2), ("kappa", C.c_double), ("w", C.c_double), ("g_cos", C.c_double),
+                ("g_quad", C.c_double), ("n_src", C.c_int32), ("reserved", C.c_int32), ("c", C.c_void_p)]
+
+
+class SquareBVP:
+    """Host description of the optimal-forcing problem (keeps its arrays alive)."""
+
+    def __init__(self, b, kappa, c, w, g_cos=1.0, g_quad=0.0):
+        self.c = np.ascontiguousarray(np.asarray(c, dtype=np.float64).reshape(-1, 2))
+        b = np.asarray(b, dtype=np.float64).reshape(2)
+        self.s = pm_square_bvp((C.c_double * 2)(b[0], b[1]), float(kappa), float(w), float(g_cos), float(g_quad),
+                               int(self.c.shape[0]), 0, self.c.ctypes.data if self.c.size else None)
+
+
+def pm_forward_square_bvp(ctx, prob: SquareBVP, x, n_obs, M, dt, max_steps, seed, flags, mean, var=None,
+                          exit_step=None, n_unexited=None, path_offset=0, instance=0, g_out=None):
+    if _device(x, mean, var, exit_step, n_unexited, g_out):
+        flags |= PM_DEVICE_PTRS
+    o = _opts(path_offset, instance, g_out, None)
+    return _check(load().pm_forward_square_bvp(ctx, C.byref(prob.s), _ptr(x), int(n_obs), int(M), float(dt),
+                                               int(max_steps), int(seed), int(flags), _ptr(mean), _ptr(var),
+                                               _ptr(exit_step), _ptr(n_unexited), C.byref(o)))
 
 
 def pm_philox(ctx, ctr, key0, key1, n, out, flags=0):
