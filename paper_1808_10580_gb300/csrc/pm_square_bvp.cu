@@ -51,10 +51,31 @@ __device__ __forceinline__ bool outside01(const Coord<double>& X) { return X.hi 
 __device__ __forceinline__ float exp_(float a) { return expf(a); }
 __device__ __forceinline__ double exp_(double a) { return exp(a); }
 
+// Running time integral of one source profile along a path.  Float paths
+// keep a compensated (Kahan) float sum, so the step loop stays off the
+// double-precision pipe; double paths add in double.
+template <typename Real> struct PathSum;
+template <> struct PathSum<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v)
+    {
+        const float y = v - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+template <> struct PathSum<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double v) { s += v; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
 template <typename Real>
 __device__ __forceinline__ void square_finish(const SquareParams<Real>& p, int64_t pid, bool exited, int64_t n,
                                               const Coord<Real>& X1, const Coord<Real>& X2,
-                                              const double (&sums)[PM_MAX_SOURCES])
+                                              const PathSum<Real> (&sums)[PM_MAX_SOURCES])
 {
     const int64_t nf = p.n_src + 1;
     const int64_t j = pid / p.M, i = pid - j * p.M;
@@ -65,7 +86,7 @@ __device__ __forceinline__ void square_finish(const SquareParams<Real>& p, int64
         o[0] = p.g_cos * 0.5 * (cos(h * y1) + cos(h * y2)) + p.g_quad * (y1 * y1 - y2 * y2);
 #pragma unroll
         for (int q = 0; q < PM_MAX_SOURCES; ++q)
-            if (q < p.n_src) o[(q + 1) * p.M] = sums[q];
+            if (q < p.n_src) o[(q + 1) * p.M] = sums[q].value();
     } else {
         for (int64_t q = 0; q < nf; ++q) o[q * p.M] = 0.0;
         atomicAdd(p.n_unexited, 1ull);
@@ -83,7 +104,7 @@ __global__ void __launch_bounds__(kSquareBlock) square_bvp_kernel(const __grid_c
     int64_t n = 0;
     uint32_t j = 0, i = 0;
     unsigned long long lane_steps = 0;
-    double sums[PM_MAX_SOURCES];
+    PathSum<Real> sums[PM_MAX_SOURCES];
     Coord<Real> X1, X2;
     X1.set(0.0);
     X2.set(0.0);
@@ -105,7 +126,7 @@ __global__ void __launch_bounds__(kSquareBlock) square_bvp_kernel(const __grid_c
                     X2.set(p.x[2 * (int64_t)j + 1]);
                     n = 0;
 #pragma unroll
-                    for (int q = 0; q < PM_MAX_SOURCES; ++q) sums[q] = 0.0;
+                    for (int q = 0; q < PM_MAX_SOURCES; ++q) sums[q] = PathSum<Real>{};
                     if (outside01(X1) || outside01(X2)) {  // starts on or outside the boundary
                         square_finish(p, pid, true, 0, X1, X2, sums);
                         pid = -1;
@@ -126,7 +147,7 @@ __global__ void __launch_bounds__(kSquareBlock) square_bvp_kernel(const __grid_c
             for (int q = 0; q < PM_MAX_SOURCES; ++q) {
                 if (q < p.n_src) {
                     const Real d1 = x1 - p.c1[q], d2 = x2 - p.c2[q];
-                    sums[q] += (double)(exp_(-p.w * (d1 * d1 + d2 * d2)) * p.dt_r);
+                    sums[q].add(exp_(-p.w * (d1 * d1 + d2 * d2)) * p.dt_r);
                 }
             }
             Real xi1, xi2;
