@@ -433,6 +433,22 @@ def run_aux(args):
             "config": dict(workload=name, particle_steps_per_call=steps[-1], **cfg)}
     line["config"]["grid"] = pm.pm_last_grid(ctx)
     line["config"]["autotuned_ctas_per_sm"] = tuned
+    if args.workload == "batched":
+        # CUDA-graph replay against direct launches of the same call (the
+        # difference is the launch overhead the graph removes)
+        def timed():
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            return e0.elapsed_time(e1)
+        replay = timed()
+        pm.pm_set_graph_mode(ctx, 0)
+        step()
+        direct = timed()
+        pm.pm_set_graph_mode(ctx, 1)
+        line["graph"] = {"replay_ms": replay, "direct_ms": direct, "launches_per_call": 4}
     if args.workload == "dirichlet":
         line["kernel_ms"] = pm.pm_last_kernel_ms(ctx)
         # Exit-step distribution of the same call (outside the timed region): the

@@ -72,3 +72,22 @@ def test_repeated_calls_are_bit_identical(c):
     a = _gpu.dirichlet(c, w, pm.PM_FP32)
     b = _gpu.dirichlet(c, w, pm.PM_FP32)
     assert np.array_equal(a["mean"], b["mean"]) and np.array_equal(a["var"], b["var"])
+
+
+@pytest.mark.parametrize("M", [5000, 20000])
+def test_reduction_equals_exact_sums_of_the_path_values(c, M):
+    # The per-observation mean and variance (one pass, or two passes through
+    # chunk partials when M > 8192) against exactly rounded sums (math.fsum)
+    # of the same per-path values.
+    import math
+    w = inputs.dirichlet_disk_k10(M=M)
+    w.x = w.x[:4].copy()
+    w.max_steps = 20000
+    r = _gpu.dirichlet(c, w, pm.PM_FP32, want_paths=True)
+    g = r["g"]
+    for j in range(g.shape[0]):
+        s = math.fsum(g[j])
+        m = s / M
+        v = (math.fsum(g[j] * g[j]) - s * m) / (M - 1)
+        assert abs(r["mean"][j] - m) <= 1e-15 * max(1.0, abs(m))
+        assert abs(r["var"][j] - v) <= 1e-12 * max(1.0, v)
