@@ -280,6 +280,19 @@ def run_gpu(args):
     # Monte Carlo standard error of the timed estimate.
     se = np.sqrt(var.cpu().numpy() / w.M)
 
+    # The plain FP64 path on the same GPU and workload (one evaluation, kernel
+    # time by events): the metric's point of comparison.
+    fp64 = None
+    if not args.no_fp64_compare:
+        m64 = torch.empty_like(mean)
+        pm.pm_forward_timedep(ctx, fld, w.kappa, th, x, t, n_obs, w.M, w.dt, w.seed, pm.PM_FP64, m64,
+                              instance=inst)
+        ms64 = pm.pm_last_kernel_ms(ctx)
+        fp64 = {"kernel_ms": ms64, "particle_steps_per_s": particle_steps(w) / (ms64 / 1e3),
+                "evaluation_speedup": ms64 / statistics.mean(kern_ms),
+                "max_abs_mean_diff": float((m64 - mean).abs().max().item()),
+                "note": "timedep_kernel<double,10,128> on the same observations, paths and streams"}
+
     line = None
     if rank == 0:
         peaks, peaks_kind = measured_peaks()
@@ -328,6 +341,7 @@ def run_gpu(args):
                     "d2h_bytes_per_step": n_obs * 16},
             "gpu_launches": int(launches),
             "clocks": clock,
+            "plain_fp64_gpu": fp64,
         }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, threads, P, g_or, secs = oracle_sample(w, obs_id=stream_of)
@@ -700,6 +714,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true",
+                    help="timedep: skip the one FP64-path evaluation reported beside the line")
     ap.add_argument("--M", type=int, default=0, help="particles per observation (default: the workload's own; "
                     "smaller values are for profiling captures only)")
     ap.add_argument("--workload", default="timedep", choices=["timedep", "dirichlet", "batched", "mcmc", "sweep", "surrogate", "bvp"],
