@@ -34,7 +34,7 @@ using bf16 = __nv_bfloat16;
 namespace {
 
 // ---------------------------------------------------------------------------
-// Tensor maps (the driver's encoder, fetched once through the runtime)
+// Tensor maps (the CUDA driver API's encoder, fetched once through the runtime)
 // ---------------------------------------------------------------------------
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,

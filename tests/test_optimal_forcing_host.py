@@ -1,4 +1,4 @@
-"""Host logic of the optimal-forcing driver (no GPU): the Nelder-Mead search
+"""Host logic of the optimal-forcing search (no GPU): the Nelder-Mead method
 against known minima, and the affine structure of G(F)."""
 import numpy as np
 import pytest
