@@ -46,3 +46,18 @@ def test_create_without_gpu_fails_cleanly():
     import paper_1808_10580_gb300 as pm
     with pytest.raises(pm.PMError):
         pm.pm_create(0)
+
+
+def test_header_is_plain_c():
+    # The boundary is a C ABI: the header must compile as C11 on its own (no
+    # C++ types, references, default arguments or overloads).  The source goes
+    # to the compiler on standard input, so nothing is written.
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = '#include "pm.h"\nint main(void) { pm_ctx* c = 0; (void)c; return pm_version() > 0 ? 0 : 1; }\n'
+    r = subprocess.run([cc, "-std=c11", "-Wall", "-Werror", "-pedantic", "-fsyntax-only",
+                        "-I", os.path.join(ROOT, "include"), "-x", "c", "-"], input=src, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
