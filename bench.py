@@ -508,7 +508,7 @@ def run_sweep(args):
         fld = pm.Field(K, inputs.prior_field(K, 1001))
         row = {"K": K, "n_u": (2 * K + 1) ** 2 - 1}
         for name, flags in (("fp32_ms", pm.PM_FP32), ("tensor_ms", pm.PM_FP32 | pm.PM_TENSOR)):
-            if name == "tensor_ms" and K not in (4, 5, 6, 8, 10, 12):
+            if name == "tensor_ms" and K not in (4, 5, 6, 8, 10, 12, 16):
                 continue
             ms = []
             for k in range(args.warmup + args.steps):

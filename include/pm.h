@@ -77,7 +77,7 @@ extern "C" {
 #define PM_ASYNC 4u
 /* Time-dependent float paths only: evaluate the velocity sum on the tensor
  * cores (tcgen05 TF32 with a three-term hi/lo split, about float accuracy);
- * supported for K in {4, 5, 6, 8, 10, 12}, other K fall back to the FP32 pipes. */
+ * supported for K in {4, 5, 6, 8, 10, 12, 16}, other K fall back to the FP32 pipes. */
 #define PM_TENSOR 8u
 /* pm_forward_timedep with PM_TENSOR: observations at bit-identical points x
  * share their paths (Theorem 3.1: the value at t_j needs the path only up to

@@ -424,9 +424,9 @@ int pm_forward_timedep(pm_ctx* c, const pm_field* field, double kappa, const pm_
     if (n_obs * chunks64 > 0x7fffffffLL) return fail(PM_EINVAL, "n_obs * ceil(M/%d) exceeds the grid limit", kTimedepBlock);
     const int32_t chunks = (int32_t)chunks64;
     const int K = field->K;
-    const bool tc = !fp64 && (flags & PM_TENSOR) && (K == 4 || K == 5 || K == 6 || K == 8 || K == 10 || K == 12);
+    const bool tc = !fp64 && (flags & PM_TENSOR) && (K == 4 || K == 5 || K == 6 || K == 8 || K == 10 || K == 12 || K == 16);
     const bool share = flags & PM_SHARE_PATHS;
-    if (share && !tc) return fail(PM_EINVAL, "PM_SHARE_PATHS needs PM_TENSOR, float paths and K in {4,5,6,8,10,12}");
+    if (share && !tc) return fail(PM_EINVAL, "PM_SHARE_PATHS needs PM_TENSOR, float paths and K in {4,5,6,8,10,12,16}");
     if ((rc = set_device(c))) return rc;
 
     // Shared paths: the groups, from host copies of x and t.
@@ -541,7 +541,8 @@ int pm_forward_timedep(pm_ctx* c, const pm_field* field, double kappa, const pm_
         case 6: e = tdtc::launch_timedep_tc<6>(L, W.err + 1, c->stream); break;
         case 8: e = tdtc::launch_timedep_tc<8>(L, W.err + 1, c->stream); break;
         case 10: e = tdtc::launch_timedep_tc<10>(L, W.err + 1, c->stream); break;
-        default: e = tdtc::launch_timedep_tc<12>(L, W.err + 1, c->stream); break;
+        case 12: e = tdtc::launch_timedep_tc<12>(L, W.err + 1, c->stream); break;
+        default: e = tdtc::launch_timedep_tc<16>(L, W.err + 1, c->stream); break;
         }
     } else {
         e = fp64 ? dispatch_timedep<double>(K, L, c->stream) : dispatch_timedep<float>(K, L, c->stream);
@@ -588,11 +589,11 @@ int pm_forward_timedep(pm_ctx* c, const pm_field* field, double kappa, const pm_
 }
 
 // Dirichlet launch shape: the tensor-core kernel for float paths with
-// PM_TENSOR at K in {4,5,6,8,10,12}; resident CTAs per SM of the kernel used.
+// PM_TENSOR at K in {4,5,6,8,10,12,16}; resident CTAs per SM of the kernel used.
 namespace {
 bool dirichlet_uses_tc(int K, uint32_t flags)
 {
-    return !(flags & PM_FP64) && (flags & PM_TENSOR) && (K == 4 || K == 5 || K == 6 || K == 8 || K == 10 || K == 12);
+    return !(flags & PM_FP64) && (flags & PM_TENSOR) && (K == 4 || K == 5 || K == 6 || K == 8 || K == 10 || K == 12 || K == 16);
 }
 
 int dirichlet_resident(int K, bool fp64, bool use_tc)
@@ -604,7 +605,8 @@ int dirichlet_resident(int K, bool fp64, bool use_tc)
         case 6: return tdtc::dirichlet_tc_blocks_per_sm<6>();
         case 8: return tdtc::dirichlet_tc_blocks_per_sm<8>();
         case 10: return tdtc::dirichlet_tc_blocks_per_sm<10>();
-        default: return tdtc::dirichlet_tc_blocks_per_sm<12>();
+        case 12: return tdtc::dirichlet_tc_blocks_per_sm<12>();
+        default: return tdtc::dirichlet_tc_blocks_per_sm<16>();
         }
     }
     return fp64 ? dispatch_dirichlet_occupancy<double>(K) : dispatch_dirichlet_occupancy<float>(K);
@@ -737,7 +739,8 @@ int pm_forward_dirichlet(pm_ctx* c, const pm_field* field, double drift_scale, d
         case 6: e = tdtc::launch_dirichlet_tc<6>(L, tc_err, c->stream); break;
         case 8: e = tdtc::launch_dirichlet_tc<8>(L, tc_err, c->stream); break;
         case 10: e = tdtc::launch_dirichlet_tc<10>(L, tc_err, c->stream); break;
-        default: e = tdtc::launch_dirichlet_tc<12>(L, tc_err, c->stream); break;
+        case 12: e = tdtc::launch_dirichlet_tc<12>(L, tc_err, c->stream); break;
+        default: e = tdtc::launch_dirichlet_tc<16>(L, tc_err, c->stream); break;
         }
     } else {
         e = fp64 ? dispatch_dirichlet<double>(Kd, L, c->stream) : dispatch_dirichlet<float>(Kd, L, c->stream);

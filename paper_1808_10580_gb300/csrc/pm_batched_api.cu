@@ -32,7 +32,7 @@ cudaError_t launch_batched_tc_K(int K, const BatchKernelParams& p, int grid, cud
 {
     switch (K) {
 #define PM_CASE(k) case k: return tdtc::launch_batched_tc<k>(p, grid, s);
-        PM_CASE(4) PM_CASE(5) PM_CASE(6) PM_CASE(8) PM_CASE(10) PM_CASE(12)
+        PM_CASE(4) PM_CASE(5) PM_CASE(6) PM_CASE(8) PM_CASE(10) PM_CASE(12) PM_CASE(16)
 #undef PM_CASE
     }
     return cudaErrorInvalidValue;
@@ -42,13 +42,13 @@ int blocks_per_sm_tc_K(int K)
 {
     switch (K) {
 #define PM_CASE(k) case k: return tdtc::batched_tc_blocks_per_sm<k>();
-        PM_CASE(4) PM_CASE(5) PM_CASE(6) PM_CASE(8) PM_CASE(10) PM_CASE(12)
+        PM_CASE(4) PM_CASE(5) PM_CASE(6) PM_CASE(8) PM_CASE(10) PM_CASE(12) PM_CASE(16)
 #undef PM_CASE
     }
     return 1;
 }
 
-bool tc_supported(int K) { return K == 4 || K == 5 || K == 6 || K == 8 || K == 10 || K == 12; }
+bool tc_supported(int K) { return K == 4 || K == 5 || K == 6 || K == 8 || K == 10 || K == 12 || K == 16; }
 
 int blocks_per_sm_K(int K)
 {

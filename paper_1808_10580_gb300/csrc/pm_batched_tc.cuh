@@ -49,7 +49,7 @@ __device__ __forceinline__ float w_entry(const float* tab, int nc, int k)
 }
 
 template <int K>
-__global__ void __launch_bounds__(128, 6) batched_tc_kernel(const __grid_constant__ BatchKernelParams p)
+__global__ void __launch_bounds__(128, Shape<K>::MIN_CTAS) batched_tc_kernel(const __grid_constant__ BatchKernelParams p)
 {
     using S = Shape<K>;
     constexpr int TS = table_size(K);
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(128, 6) batched_tc_kernel(const __grid_constan
     __syncwarp();
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(tmem_slot)),
-                     "r"(64u)
+                     "r"(S::TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -192,9 +192,9 @@ __global__ void __launch_bounds__(128, 6) batched_tc_kernel(const __grid_constan
             {
                 float C2[K + 1], S2[K + 1];
                 fourier_powers<float, K>(X2.val(), C2, S2);
-                float a[32];
+                float a[4 * S::KC];
 #pragma unroll
-                for (int q = 0; q < 32; ++q) a[q] = 0.f;
+                for (int q = 0; q < 4 * S::KC; ++q) a[q] = 0.f;
 #pragma unroll
                 for (int q = 1; q <= K; ++q) { a[q - 1] = S2[q]; a[K + q - 1] = C2[q]; }
                 a[2 * K] = 1.f;
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(128, 6) batched_tc_kernel(const __grid_constan
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64u) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Shape<K>::TMEM_COLS) : "memory");
     }
 }
 
@@ -272,7 +272,7 @@ int batched_tc_blocks_per_sm()
 {
     const int smem = Shape<K>::SMEM + 64;
     cudaFuncSetAttribute(batched_tc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    return resident_ctas((const void*)batched_tc_kernel<K>, 128, smem, 64);
+    return resident_ctas((const void*)batched_tc_kernel<K>, 128, smem, (int)Shape<K>::TMEM_COLS);
 }
 
 }  // namespace tdtc

@@ -16,7 +16,7 @@ namespace tdtc {
 
 template <int K>
 struct DirParams {
-    float W[Shape<K>::NP * 32];
+    float W[Shape<K>::NP * Shape<K>::WS];
     double ga[kMaxBoundary];
     double gb[kMaxBoundary];
     double R, quad, f_const, dt;
@@ -61,7 +61,7 @@ __device__ __forceinline__ void dir_finish(const DirParams<K>& p, int64_t pid, b
 }
 
 template <int K>
-__global__ void __launch_bounds__(128, 6) dirichlet_tc_kernel(const __grid_constant__ DirParams<K> p)
+__global__ void __launch_bounds__(128, Shape<K>::MIN_CTAS) dirichlet_tc_kernel(const __grid_constant__ DirParams<K> p)
 {
     using S = Shape<K>;
     extern __shared__ uint8_t smem_raw[];
@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(128, 6) dirichlet_tc_kernel(const __grid_const
         float* lv = &l.x;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const float w = p.W[r * 32 + 4 * c + e];
+            const float w = p.W[r * S::WS + 4 * c + e];
             hv[e] = to_tf32(w);
             lv[e] = to_tf32(w - hv[e]);
         }
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(128, 6) dirichlet_tc_kernel(const __grid_const
     __syncwarp();
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(tmem_slot)),
-                     "r"(64u)
+                     "r"(S::TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -163,9 +163,9 @@ __global__ void __launch_bounds__(128, 6) dirichlet_tc_kernel(const __grid_const
             {
                 float C2[K + 1], S2[K + 1];
                 fourier_powers<float, K>(X2.val(), C2, S2);
-                float a[32];
+                float a[4 * S::KC];
 #pragma unroll
-                for (int q = 0; q < 32; ++q) a[q] = 0.f;
+                for (int q = 0; q < 4 * S::KC; ++q) a[q] = 0.f;
 #pragma unroll
                 for (int q = 1; q <= K; ++q) { a[q - 1] = S2[q]; a[K + q - 1] = C2[q]; }
                 a[2 * K] = 1.f;
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(128, 6) dirichlet_tc_kernel(const __grid_const
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64u) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::TMEM_COLS) : "memory");
     }
 }
 
@@ -259,7 +259,7 @@ int dirichlet_tc_blocks_per_sm()
 {
     using S = Shape<K>;
     cudaFuncSetAttribute(dirichlet_tc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
-    return resident_ctas((const void*)dirichlet_tc_kernel<K>, 128, S::SMEM, 64);
+    return resident_ctas((const void*)dirichlet_tc_kernel<K>, 128, S::SMEM, (int)S::TMEM_COLS);
 }
 
 }  // namespace tdtc

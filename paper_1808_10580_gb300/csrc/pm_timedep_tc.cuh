@@ -31,14 +31,18 @@ struct Shape {
     static constexpr int KD = 2 * K + 1;              // A columns used
     static constexpr int KS = (KD + 7) / 8;           // MMA k-steps (K = 8 per tf32 instruction)
     static constexpr int KC = 2 * KS;                 // 16-byte chunks (4 tf32) per tile row
+    static constexpr int WS = 4 * KC;                 // row stride of W (tf32 entries)
     static constexpr int NC = 4 * K + 1;              // accumulator columns used
     static constexpr int NP = (NC + 15) / 16 * 16;    // MMA N (multiple of 16)
     static constexpr int SBO = KC * 128;              // bytes between 8-row groups of a tile
     static constexpr int A_BYTES = 128 * KC * 16;     // 128 rows x 8 KS tf32
     static constexpr int B_BYTES = NP * KC * 16;      // NP rows x 8 KS tf32
     static constexpr int SMEM = 2 * A_BYTES + 2 * B_BYTES + 128 + 64;
-    static_assert(KD <= 4 * KC, "A columns fit the k-steps");
-    static_assert(NP <= 64, "64 TMEM columns");
+    static constexpr uint32_t TMEM_COLS = NP <= 64 ? 64u : 128u;  // allocation: a power of 2 >= 32
+    // CTAs per SM that fit the 228 KB of shared memory (1 KB reserved each), at most 6
+    static constexpr int MIN_CTAS = (233472 / (SMEM + 1024)) < 6 ? (233472 / (SMEM + 1024)) : 6;
+    static_assert(NP <= 128, "accumulator within 128 TMEM columns");
+    static_assert(MIN_CTAS >= 1, "tiles fit shared memory");
 };
 
 // Instruction descriptor, kind::tf32: FP32 accumulator, TF32 A and B, both K-major.
@@ -107,7 +111,7 @@ inline int resident_ctas(const void* fn, int threads, int dyn_smem, int tmem_col
 
 template <int K>
 struct Params {
-    float W[Shape<K>::NP * 32];   // W^T: row nc (accumulator column), entry k (A column)
+    float W[Shape<K>::NP * Shape<K>::WS];   // W^T: row nc (accumulator column), entry k (A column)
     Theta0Table<float> th;
     const ObsRec* obs;
     const int32_t* order;
@@ -240,7 +244,7 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, const float4& v)
 // This thread's row of the particle tiles (row = sb + tile_off(r, 0); chunk c
 // 128 c bytes further): harmonics a[0..KD) split into hi / lo.
 template <int K>
-__device__ __forceinline__ void write_row(uint32_t row, const float (&a)[32])
+__device__ __forceinline__ void write_row(uint32_t row, const float (&a)[4 * Shape<K>::KC])
 {
     using S = Shape<K>;
 #pragma unroll
@@ -274,7 +278,7 @@ __device__ __forceinline__ void issue_step_mma(uint32_t tmem, uint32_t sb, uint3
 }
 
 template <int K>
-__global__ void __launch_bounds__(128, 6) timedep_tc_kernel(const __grid_constant__ Params<K> p)
+__global__ void __launch_bounds__(128, Shape<K>::MIN_CTAS) timedep_tc_kernel(const __grid_constant__ Params<K> p)
 {
     using S = Shape<K>;
     extern __shared__ uint8_t smem_raw[];
@@ -296,7 +300,7 @@ __global__ void __launch_bounds__(128, 6) timedep_tc_kernel(const __grid_constan
         float* lv = &l.x;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const float w = p.W[r * 32 + 4 * c + e];
+            const float w = p.W[r * S::WS + 4 * c + e];
             hv[e] = to_tf32(w);
             lv[e] = to_tf32(w - hv[e]);
         }
@@ -314,7 +318,7 @@ __global__ void __launch_bounds__(128, 6) timedep_tc_kernel(const __grid_constan
     __syncwarp();
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(tmem_slot)),
-                     "r"(64u)
+                     "r"(S::TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -379,9 +383,9 @@ __global__ void __launch_bounds__(128, 6) timedep_tc_kernel(const __grid_constan
         {
             float C2[K + 1], S2[K + 1];
             fourier_powers<float, K>(X2.val(), C2, S2);
-            float a[32];
+            float a[4 * S::KC];
 #pragma unroll
-            for (int q = 0; q < 32; ++q) a[q] = 0.f;
+            for (int q = 0; q < 4 * S::KC; ++q) a[q] = 0.f;
 #pragma unroll
             for (int q = 1; q <= K; ++q) { a[q - 1] = S2[q]; a[K + q - 1] = C2[q]; }
             a[2 * K] = 1.f;
@@ -430,7 +434,7 @@ __global__ void __launch_bounds__(128, 6) timedep_tc_kernel(const __grid_constan
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64u) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::TMEM_COLS) : "memory");
     }
 }
 
@@ -439,9 +443,9 @@ template <int K>
 void build_W(const double* t, float* W)
 {
     using S = Shape<K>;
-    for (int q = 0; q < S::NP * 32; ++q) W[q] = 0.f;
+    for (int q = 0; q < S::NP * S::WS; ++q) W[q] = 0.f;
     auto T = [&](int m, int n, int q) { return t[(size_t)(m * (K + 1) + n) * 8 + q]; };
-    auto set = [&](int col, int row, double v) { W[col * 32 + row] = (float)v; };
+    auto set = [&](int col, int row, double v) { W[col * S::WS + row] = (float)v; };
     const int rS = 0, rC = K, rOne = 2 * K;  // A columns: S2_n at n-1, C2_n at K+n-1, constant at 2K
     for (int n = 1; n <= K; ++n) {  // m = 0: v1 only
         set(0, rS + n - 1, T(0, n, 0));

@@ -19,7 +19,7 @@ def c():
     pm.pm_destroy(h)
 
 
-@pytest.mark.parametrize("K", [4, 5, 6, 8, 10, 12])
+@pytest.mark.parametrize("K", [4, 5, 6, 8, 10, 12, 16])
 def test_one_step_positions_match_oracle(c, orc, K):
     # One Euler step of length dt from 300 points: X1 - x = -v(x) dt + noise, so the
     # end points expose the velocity the tensor-core path evaluated.
