@@ -92,7 +92,11 @@ __global__ void __launch_bounds__(128, Shape<K>::MIN_CTAS) batched_tc_kernel(con
     int b = (int)(((long long)blockIdx.x * p.B) / gridDim.x);  // spread CTAs over the instances
     bool have_inst = false;
     bool exhausted = true;  // warp-uniform: no unclaimed paths left in b for this warp
-    BatchInstDev I{};
+    // The CTA's current instance lives in shared memory; only the fields the
+    // step loop reads every step stay in registers.
+    __shared__ BatchInstDev sI;
+    int kind = 0;
+    uint32_t stream = 0, key0 = 0, key1 = 0;
     float s_dt = 0.f, drift_dt = 0.f, dt = 0.f;
     int64_t pid = -1, n = 0;
     int32_t N = 0;
@@ -115,25 +119,26 @@ __global__ void __launch_bounds__(128, Shape<K>::MIN_CTAS) batched_tc_kernel(con
                 const int leader = __ffs(mask) - 1;
                 if (lane == leader) base = atomicAdd(&p.next_path[b], (unsigned long long)__popc(mask));
                 base = __shfl_sync(full, base, leader);
-                if ((int64_t)(base + __popc(mask)) >= I.n_paths) exhausted = true;
+                if ((int64_t)(base + __popc(mask)) >= sI.n_paths) exhausted = true;
                 if (need) {
                     const int64_t cand = (int64_t)base + __popc(mask & ((1u << lane) - 1u));
-                    if (cand < I.n_paths) {
+                    if (cand < sI.n_paths) {
                         pid = cand;
-                        j = (uint32_t)(cand / I.M);
-                        i = (uint32_t)(cand - (int64_t)j * I.M);
-                        const RowRec rr = p.rows[I.row0 + j];
+                        const int64_t Mi = sI.M;
+                        j = (uint32_t)(cand / Mi);
+                        i = (uint32_t)(cand - (int64_t)j * Mi);
+                        const RowRec rr = p.rows[sI.row0 + j];
                         X1.set(rr.x1);
                         X2.set(rr.x2);
                         n = 0;
                         N = rr.nsteps;
                         h_last = (float)rr.h_last;
                         s_last = (float)rr.s_last;
-                        if (I.kind == 0 && N == 0) {
-                            p.g[I.path_base + pid] = theta0_eval(p.th, X1, X2);
+                        if (kind == 0 && N == 0) {
+                            p.g[sI.path_base + pid] = theta0_eval(p.th, X1, X2);
                             pid = -1;
-                        } else if (I.kind == 1 && radial_excess(X1, X2, p.R2hi, p.R2lo) >= 0.f) {
-                            p.g[I.path_base + pid] =
+                        } else if (kind == 1 && radial_excess(X1, X2, p.R2hi, p.R2lo) >= 0.f) {
+                            p.g[sI.path_base + pid] =
                                 boundary_value(p.ga, p.gb, p.n_ang, p.R, p.quad, X1.full(), X2.full());
                             pid = -1;
                         }
@@ -164,12 +169,17 @@ __global__ void __launch_bounds__(128, Shape<K>::MIN_CTAS) batched_tc_kernel(con
             const int found = *s_next;
             if (found < 0) break;
             b = found;
-            I = p.inst[b];
+            if (tid == 0) sI = p.inst[b];  // visible after the barrier below
+            const BatchInstDev& In = p.inst[b];
             have_inst = true;
             exhausted = false;
-            dt = (float)I.dt;
-            s_dt = (float)sqrt(2.0 * I.kappa * I.dt);
-            drift_dt = (float)(I.drift_scale * I.dt);
+            kind = In.kind;
+            stream = In.stream;
+            key0 = In.key0;
+            key1 = In.key1;
+            dt = (float)In.dt;
+            s_dt = (float)sqrt(2.0 * In.kappa * In.dt);
+            drift_dt = (float)(In.drift_scale * In.dt);
             // coefficient tiles of the new instance (the previous MMA has completed)
             const float* tab = p.tables + (size_t)b * TS;
             for (int q = tid; q < S::NP * 4 * S::KC; q += 128) {
@@ -186,7 +196,7 @@ __global__ void __launch_bounds__(128, Shape<K>::MIN_CTAS) batched_tc_kernel(con
 
         // ---- two Euler steps per Philox call, one MMA per step ----------------------
         u32x4 r{0, 0, 0, 0};
-        if (pid >= 0) r = philox4x32_10(u32x4{(uint32_t)(n >> 1), i, j, I.stream}, I.key0, I.key1);
+        if (pid >= 0) r = philox4x32_10(u32x4{(uint32_t)(n >> 1), i, j, stream}, key0, key1);
 #pragma unroll 1
         for (int half = 0; half < 2; ++half) {
             {
@@ -218,7 +228,7 @@ __global__ void __launch_bounds__(128, Shape<K>::MIN_CTAS) batched_tc_kernel(con
             velocity_from_tmem<K>(t_row, C1, S1, v1, v2);
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             if (pid < 0) continue;
-            if (I.kind == 0) {
+            if (kind == 0) {
                 const bool last = (n == N - 1);
                 const float h = last ? h_last : dt, s = last ? s_last : s_dt;
                 em_update<float>(X1, v1, h, s, xi1);
@@ -227,7 +237,7 @@ __global__ void __launch_bounds__(128, Shape<K>::MIN_CTAS) batched_tc_kernel(con
                 X2.wrap();
                 ++n;
                 if (n >= N) {
-                    p.g[I.path_base + pid] = theta0_eval(p.th, X1, X2);
+                    p.g[sI.path_base + pid] = theta0_eval(p.th, X1, X2);
                     lane_steps += (unsigned long long)n;
                     pid = -1;
                 }
@@ -236,12 +246,12 @@ __global__ void __launch_bounds__(128, Shape<K>::MIN_CTAS) batched_tc_kernel(con
                 em_update<float>(X2, v2, drift_dt, s_dt, xi2);
                 ++n;
                 const bool exited = radial_excess(X1, X2, p.R2hi, p.R2lo) >= 0.f;
-                if (exited || n >= I.max_steps) {
+                if (exited || n >= sI.max_steps) {
                     double gv = 0.0;
                     if (exited) gv = boundary_value(p.ga, p.gb, p.n_ang, p.R, p.quad, X1.full(), X2.full()) -
-                                     p.f_const * ((double)n * I.dt);
+                                     p.f_const * ((double)n * sI.dt);
                     else atomicAdd(p.n_unexited, 1ull);
-                    p.g[I.path_base + pid] = gv;
+                    p.g[sI.path_base + pid] = gv;
                     lane_steps += (unsigned long long)n;
                     pid = -1;
                 }
