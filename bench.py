@@ -651,6 +651,56 @@ def run_bvp(args):
     return 0
 
 
+def run_layout(args):
+    """Shared paths on the observation layout of the paper's turbulent-flow
+    example (auxiliary line): 2 points x 13 times in [0, 0.5], K = 16 field
+    on the tensor cores, M paths per observation; independent paths per
+    observation against paths shared by the 13 times of each point."""
+    import torch
+
+    import paper_1808_10580_gb300 as pm
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    ctx = pm.pm_create(0, stream.cuda_stream)
+    pm.pm_set_kernel_timing(ctx, 1)
+    w = inputs.two_point_time_series(M=args.M or 100_000)
+    n = len(w.t)
+    fld = pm.Field(w.K, w.u)
+    th = pm.Fourier(w.theta0.k, w.theta0.a, w.theta0.b)
+    x = torch.from_numpy(w.x).to(dev)
+    t = torch.from_numpy(w.t).to(dev)
+    out = {}
+    for name, extra in (("independent", 0), ("shared", pm.PM_SHARE_PATHS)):
+        mean = torch.empty(n, dtype=torch.float64, device=dev)
+        var = torch.empty_like(mean)
+        ms, steps = [], 0
+        for k in range(args.warmup + args.steps):
+            pm.pm_forward_timedep(ctx, fld, w.kappa, th, x, t, n, w.M, w.dt, w.seed,
+                                  pm.PM_FP32 | pm.PM_TENSOR | extra, mean, var)
+            if k >= args.warmup:
+                ms.append(pm.pm_last_kernel_ms(ctx))
+                steps = pm.pm_last_step_count(ctx)
+        out[name] = {"kernel_ms": statistics.median(ms), "particle_steps": steps,
+                     "evals_per_s": 1e3 / statistics.median(ms), "mean": mean.cpu().numpy(),
+                     "se": np.sqrt(var.cpu().numpy() / w.M)}
+    d = np.abs(out["shared"]["mean"] - out["independent"]["mean"])
+    se = np.sqrt(out["shared"]["se"] ** 2 + out["independent"]["se"] ** 2)
+    line = {"metric": METRIC, "auxiliary": True, "data": "synthetic", "unit": "forward-map evals/s",
+            "value": out["shared"]["evals_per_s"], "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "dtype": "f32", "config": {"workload": w.name, "K": w.K, "n_obs": n, "M": w.M, "dt": w.dt,
+                                       "kappa": w.kappa},
+            "independent": {k: v for k, v in out["independent"].items() if k in ("kernel_ms", "particle_steps",
+                                                                                  "evals_per_s")},
+            "shared": {k: v for k, v in out["shared"].items() if k in ("kernel_ms", "particle_steps", "evals_per_s")},
+            "speedup": out["independent"]["kernel_ms"] / out["shared"]["kernel_ms"],
+            "max_diff_in_se": float((d / np.maximum(se, 1e-300)).max())}
+    print(json.dumps(line), flush=True)
+    pm.pm_destroy(ctx)
+    return 0
+
+
 def run_mcmc(args):
     """Surrogate-screened pCN against plain pCN on the same GPU (auxiliary line):
     64 chains started at the data-generating field, the same beta for both
@@ -718,7 +768,7 @@ def main():
                     help="timedep: skip the one FP64-path evaluation reported beside the line")
     ap.add_argument("--M", type=int, default=0, help="particles per observation (default: the workload's own; "
                     "smaller values are for profiling captures only)")
-    ap.add_argument("--workload", default="timedep", choices=["timedep", "dirichlet", "batched", "mcmc", "sweep", "surrogate", "bvp"],
+    ap.add_argument("--workload", default="timedep", choices=["timedep", "dirichlet", "batched", "mcmc", "sweep", "surrogate", "bvp", "layout"],
                     help="timedep: the headline line; dirichlet / batched / mcmc: auxiliary measurements")
     ap.add_argument("--train-pairs", type=int, default=1 << 16, help="mcmc: surrogate training pairs")
     ap.add_argument("--betas", default="0.03", help="mcmc: comma-separated pCN steps (each the same for both samplers)")
@@ -758,6 +808,8 @@ def main():
         return run_surrogate(args)
     if args.workload == "bvp":
         return run_bvp(args)
+    if args.workload == "layout":
+        return run_layout(args)
     if args.workload != "timedep":
         return run_aux(args)
     return run_gpu(args)

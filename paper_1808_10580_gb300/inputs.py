@@ -181,6 +181,21 @@ def timedep_k10(M: int = 10_000) -> TimedepWorkload:
                            Fourier(k, a, b), x, t, M, 1e-3, 4001)
 
 
+def two_point_time_series(K: int = 16, M: int = 100_000) -> TimedepWorkload:
+    """The observation layout of the paper's turbulent-flow example (Section
+    4, Example 3): 2 locations x 13 times evenly spaced in [0, 0.5] (26
+    observations), kappa = 3e-5.  The example's field (|k|_2 <= 80) and data
+    are not available; a prior field with |k|_inf <= K (seed 1006) and the
+    16-mode theta0 of the 440-mode workload stand in.  dt = 1e-3, path seed 4006."""
+    k, a, b = random_theta0(16, 4, 2001)
+    pts = np.array([[0.3, 0.6], [0.7, 0.25]])
+    times = np.linspace(0.0, 0.5, 13)
+    x = np.repeat(pts, len(times), axis=0)
+    t = np.tile(times, len(pts))
+    return TimedepWorkload(f"two_points_13_times_k{K}_M{M}", K, prior_field(K, 1006), 3e-5, Fourier(k, a, b), x, t, M,
+                           1e-3, 4006)
+
+
 def dirichlet_disk_k10(M: int = 100_000) -> DirichletWorkload:
     """Unit disk, K=10 field x 0.5, kappa=0.05, g = y1^2 - y2^2 + 0.1 sin 3phi,
     50 uniform-area points r <= 0.9, M=1e5, dt=1e-4."""
