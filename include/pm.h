@@ -79,7 +79,7 @@ extern "C" {
  * cores (tcgen05 TF32 with a three-term hi/lo split, about float accuracy);
  * supported for K in {4, 5, 6, 8, 10, 12, 16}, other K fall back to the FP32 pipes. */
 #define PM_TENSOR 8u
-/* pm_forward_timedep with PM_TENSOR: observations at bit-identical points x
+/* pm_forward_timedep: observations at bit-identical points x
  * share their paths (Theorem 3.1: the value at t_j needs the path only up to
  * time t_j, so one path serves every t_j at the same x).  Such a group
  * draws its noise from the RNG stream of its
@@ -164,7 +164,6 @@ typedef struct pm_path_opts {
  *   dt      Euler-Maruyama step > 0
  *   seed    64-bit Philox key
  *   flags   PM_FP32 | PM_FP64, PM_DEVICE_PTRS, PM_ASYNC, PM_TENSOR, PM_SHARE_PATHS
- *           (PM_SHARE_PATHS needs PM_TENSOR, float paths and a tensor-core K)
  *   mean    [n_obs] output; var [n_obs] output or NULL
  * n_obs == 0 is a no-op.  Returns PM_OK or an error. */
 int pm_forward_timedep(pm_ctx* ctx, const pm_field* field, double kappa, const pm_fourier* theta0,

@@ -426,7 +426,6 @@ int pm_forward_timedep(pm_ctx* c, const pm_field* field, double kappa, const pm_
     const int K = field->K;
     const bool tc = !fp64 && (flags & PM_TENSOR) && (K == 4 || K == 5 || K == 6 || K == 8 || K == 10 || K == 12 || K == 16);
     const bool share = flags & PM_SHARE_PATHS;
-    if (share && !tc) return fail(PM_EINVAL, "PM_SHARE_PATHS needs PM_TENSOR, float paths and K in {4,5,6,8,10,12,16}");
     if ((rc = set_device(c))) return rc;
 
     // Shared paths: the groups, from host copies of x and t.

@@ -24,6 +24,8 @@ struct TimedepParams {
     int64_t M, path_offset;
     int32_t n_obs, chunks;
     uint32_t inst, key0, key1;
+    const int4* groups;       // shared paths: {m0, m1, stream, nmax} per grid row
+    const int32_t* members;   // [n_obs] observation indices of the groups
 };
 
 template <typename Real>
@@ -135,6 +137,79 @@ __global__ void __launch_bounds__(BLOCK) timedep_kernel(const __grid_constant__ 
     if (threadIdx.x == 0) p.part[(int64_t)j * p.chunks + c] = s;
 }
 
+// Shared paths (PM_SHARE_PATHS) on the FP32 / FP64 pipes: one CTA = one chunk
+// of BLOCK paths of a group of observations at one point; a path runs to the
+// group's largest step count and every member takes its own last step from
+// the path's position at its step N_j - 1 (same velocity and noise), so each
+// member's values equal those of a single-observation call on the group's
+// stream.  Members finish at steps every thread of the CTA shares, so the
+// per-member CTA sums run inside the step loop.
+template <typename Real, int K, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) timedep_shared_kernel(const __grid_constant__ TimedepParams<Real, K> p)
+{
+    const int slot = blockIdx.x / p.chunks;
+    const int c = blockIdx.x - slot * p.chunks;
+    const int4 G = p.groups[slot];
+    const int m1 = G.y;
+    const uint32_t stream = (uint32_t)G.z;
+    const int64_t i = (int64_t)c * BLOCK + threadIdx.x;
+    const bool active = i < p.M;
+    const uint32_t pid = (uint32_t)(p.path_offset + (active ? i : 0));
+    Coord<Real> X1, X2;
+    {
+        const ObsRec o = p.obs[p.members[G.x]];
+        X1.set(o.x1);
+        X2.set(o.x2);
+    }
+    const ParamTable<Real, K> tab{p.field};
+    auto finish = [&](int m, const Coord<Real>& Y1, const Coord<Real>& Y2) {
+        const int jm = p.members[m];
+        double g = 0.0;
+        if (active) {
+            g = theta0_eval(p.th, Y1, Y2);
+            const int64_t w = (int64_t)jm * p.M + i;
+            if (p.g_out) p.g_out[w] = g;
+            if (p.x_out) { p.x_out[2 * w] = Y1.full(); p.x_out[2 * w + 1] = Y2.full(); }
+        }
+        const double2 s = block_sum2<BLOCK>(g, g * g);
+        if (threadIdx.x == 0) p.part[(int64_t)jm * p.chunks + c] = s;
+        __syncthreads();  // block_sum2's scratch is reused by the next member
+    };
+    auto steps_of = [&](int m) { return m < m1 ? p.obs[p.members[m]].nsteps : -1; };
+    int m = G.x;
+    while (steps_of(m) == 0) finish(m++, X1, X2);
+    const int N = m < m1 ? steps_of(m1 - 1) : 0;
+    int stop = steps_of(m) - 1;
+    for (int n = 0; n < N; n += 2) {
+        const u32x4 r = philox4x32_10(u32x4{(uint32_t)(n >> 1), pid, stream, p.inst}, p.key0, p.key1);
+#pragma unroll 1
+        for (int half = 0; half < 2; ++half) {
+            const int nn = n + half;
+            if (nn >= N) break;
+            Real xi1, xi2;
+            box_muller<Real>(half ? r.z : r.x, half ? r.w : r.y, xi1, xi2);
+            Real x1[1] = {X1.val()}, x2[1] = {X2.val()}, v1[1], v2[1];
+            velocity<Real, K, 1>(tab, x1, x2, v1, v2);
+            while (nn == stop) {
+                const ObsRec o = p.obs[p.members[m]];
+                Coord<Real> Y1 = X1, Y2 = X2;
+                em_update<Real>(Y1, v1[0], (Real)o.h_last, (Real)o.s_last, xi1);
+                em_update<Real>(Y2, v2[0], (Real)o.h_last, (Real)o.s_last, xi2);
+                Y1.wrap();
+                Y2.wrap();
+                finish(m++, Y1, Y2);
+                stop = steps_of(m) - 1;
+            }
+            if (nn + 1 < N) {
+                em_update<Real>(X1, v1[0], p.dt, p.s_dt, xi1);
+                em_update<Real>(X2, v2[0], p.dt, p.s_dt, xi2);
+                X1.wrap();
+                X2.wrap();
+            }
+        }
+    }
+}
+
 template <typename Real, int K>
 cudaError_t launch_timedep(const TimedepLaunch& L, cudaStream_t stream)
 {
@@ -162,6 +237,13 @@ cudaError_t launch_timedep(const TimedepLaunch& L, cudaStream_t stream)
     p.inst = L.inst;
     p.key0 = L.key0;
     p.key1 = L.key1;
+    p.groups = L.groups;
+    p.members = L.members;
+    if (L.groups) {
+        const int64_t grid = (int64_t)L.n_groups * L.chunks;
+        timedep_shared_kernel<Real, K, kTimedepBlock><<<(unsigned)grid, kTimedepBlock, 0, stream>>>(p);
+        return cudaGetLastError();
+    }
     const int64_t grid = (int64_t)L.n_obs * L.chunks;
     timedep_kernel<Real, K, kTimedepBlock><<<(unsigned)grid, kTimedepBlock, 0, stream>>>(p);
     return cudaGetLastError();

@@ -1,4 +1,4 @@
-"""Shared paths (PM_SHARE_PATHS with the tensor-core path): observations at one
+"""Shared paths (PM_SHARE_PATHS, tensor-core and FP32/FP64-pipe kernels): observations at one
 point x share their paths, each member stopping at its own time.  Checked
 against single-observation calls on the same RNG stream (bit for bit: the same
 arithmetic), against the FP64 oracle with the same stream map on fields where
@@ -98,9 +98,33 @@ def test_headline_means_agree_with_unshared_in_distribution(c):
     assert np.mean(np.abs(ms - mu) <= 5 * se) >= 0.99
 
 
-def test_flag_needs_the_tensor_path(c):
-    w = mixed_workload()
-    with pytest.raises(pm.PMError):
-        _gpu.timedep(c, w, pm.PM_FP32 | pm.PM_SHARE_PATHS)
-    with pytest.raises(pm.PMError):
-        _gpu.timedep(c, w, pm.PM_FP64 | pm.PM_TENSOR | pm.PM_SHARE_PATHS)
+@pytest.mark.parametrize("flags", [pm.PM_FP32, pm.PM_FP64])
+def test_fp32_and_fp64_pipes_share_paths_too(c, flags):
+    # The FP32/FP64-pipe kernels: members equal single-observation calls on the
+    # group's stream, bit for bit.
+    w = mixed_workload(M=200)
+    w.u = inputs.prior_field(4, 77)
+    w.K = 4
+    mean, var, g = _gpu.timedep(c, w, flags | pm.PM_SHARE_PATHS, g_out=True)
+    _, stream_of, _, _ = pm.pm_path_groups(w.x, w.t, w.dt)
+    for j in range(len(w.t)):
+        s = int(stream_of[j])
+        v = copy.copy(w)
+        v.x = np.repeat(w.x[j:j + 1], s + 1, axis=0)
+        v.t = np.full(s + 1, 0.02)
+        v.t[s] = w.t[j]
+        m1, v1, g1 = _gpu.timedep(c, v, flags, g_out=True)
+        assert np.array_equal(g1[s], g[j]), j
+        assert m1[s] == mean[j] and v1[s] == var[j], j
+
+
+def test_fp64_shared_paths_match_the_oracle_path_by_path(c, orc):
+    # Double paths on the 2-mode field: the oracle on the stream map, per path.
+    w = mixed_workload(M=128)
+    w.K = 2
+    w.u = inputs.prior_field(2, 1000)
+    mean, var, g = _gpu.timedep(c, w, pm.PM_FP64 | pm.PM_SHARE_PATHS, g_out=True)
+    _, stream_of, _, _ = pm.pm_path_groups(w.x, w.t, w.dt)
+    go = orc.timedep_paths(2, w.u, w.kappa, w.theta0, w.x, w.t, w.dt, w.seed, npaths=w.M,
+                           obs_id=stream_of.astype(np.int64))
+    assert np.median(np.abs(g - go)) <= 1e-12 and np.abs(g - go).max() <= 1e-8
