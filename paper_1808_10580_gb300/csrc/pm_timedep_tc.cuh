@@ -11,13 +11,16 @@
 // coefficients: hi = x rounded to TF32, lo = (x - hi) rounded; the particle
 // harmonics, every step: hi = x with its low 13 bits cleared, lo = x - hi) and
 // three products hi.hi + lo.hi + hi.lo are accumulated (the lo.lo term and
-// the reduction of lo, ~2^-20 relative, are dropped): close to float accuracy.  The remaining 4K+1 FMAs per particle, the
-// harmonics, the noise and the Euler step stay on the FP32 pipes.
+// the reduction of lo, ~2^-20 relative, are dropped): close to float
+// accuracy.  The remaining 4K+1 FMAs per particle, the harmonics, the noise
+// and the Euler step stay on the FP32 pipes.
 //
 // Per step: every thread writes its particle's row of A (hi and lo) into a
-// K-major tile (layout at tile_off), a CTA barrier hands the tile to the tensor core
-// (one thread issues 3 x ceil((2K+1)/8) MMAs and commits to an mbarrier), and
-// every thread reads its 4K+1 accumulator columns back with tcgen05.ld.
+// K-major tile (layout at tile_off), a CTA barrier hands the tile to the
+// tensor core (one thread issues 3 x ceil((2K+1)/8) MMAs and commits to an
+// mbarrier), the threads compute the step's noise and x1 harmonics while it
+// runs, and every thread reads its 4K+1 accumulator columns back with
+// tcgen05.ld.
 #pragma once
 #include <algorithm>
 #include "pm_gemm_tc.cuh"
