@@ -2,11 +2,11 @@
 // the surrogate network:  C[M x N] = A[M x K] . B[N x K]^T, both operands
 // K-major BF16, FP32 accumulation in tensor memory, fused epilogue.
 //
-// One CTA computes a 128 x 64 tile with 4 warps:
-//   warp 0 / lane 0  TMA producer: 128B-swizzled 128x64 (A) and 64x64 (B) tiles
+// One CTA computes a 128 x BN tile (BN = 64 or 256) with 4 warps:
+//   warp 0 / lane 0  TMA producer: 128B-swizzled 128x64 (A) and BNx64 (B) tiles
 //                    into a 4-stage shared-memory ring (mbarrier expect-tx);
 //   warp 1 / lane 0  MMA issuer: four tcgen05.mma (K = 16 each) per stage into a
-//                    128 x 64 FP32 accumulator in TMEM; tcgen05.commit frees the
+//                    128 x BN FP32 accumulator in TMEM; tcgen05.commit frees the
 //                    stage, and a final commit signals the epilogue;
 //   warps 0-3        epilogue: tcgen05.ld of rows 32w..32w+31, bias / ReLU /
 //                    ReLU-mask, BF16 row-major, BF16 transposed and FP32 stores.
@@ -27,6 +27,23 @@ constexpr int B_BYTES = BN * BK * 2;            // 8 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;  // 24 KB (a multiple of 1024)
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr uint32_t TMEM_COLS = 64;
+
+// Tile width N of one CTA: 64 (many small tiles: the network's shapes) or 256
+// (large products: four times the reuse of each A tile, one CTA per SM).
+template <int BN_>
+struct GemmCfg {
+    static constexpr int BN = BN_;
+    static constexpr int B_BYTES = BN * BK * 2;
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+    static constexpr uint32_t TMEM_COLS = (uint32_t)BN;
+    // Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both
+    // K-major, N = BN, M = BM.
+    static constexpr uint32_t IDESC =
+        (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    static_assert(BN % 16 == 0 && BN <= 256, "MMA N");
+    static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
+};
 constexpr uint32_t kWaitLimit = 1u << 22;       // bounded spins (a few seconds at most)
 
 struct Epilogue {
@@ -45,7 +62,7 @@ struct Epilogue {
 
 struct alignas(64) GemmParams {
     CUtensorMap tmA;             // A: [M][K] BF16, box {64, 128}, 128B swizzle
-    CUtensorMap tmB;             // B: [N][K] BF16, box {64, 64}, 128B swizzle
+    CUtensorMap tmB;             // B: [N][K] BF16, box {64, BN}, 128B swizzle
     Epilogue ep;
     int M, N, K;
     unsigned* err;               // set to 1 when a bounded wait expires
@@ -99,16 +116,13 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr)
     return d;
 }
 
-// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both
-// K-major, N = BN, M = BM.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate)
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate)
 {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
             tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 
@@ -138,8 +152,12 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
 // The GEMM kernel itself is compiled in one translation unit only (pm_mlp.cu
 // defines PM_DEFINE_GEMM_KERNEL); other users of this header take the helpers.
 #ifdef PM_DEFINE_GEMM_KERNEL
+template <int BN_>
 __global__ void __launch_bounds__(128, 1) gemm_bf16_tc_kernel(const __grid_constant__ GemmParams p)
 {
+    using G = GemmCfg<BN_>;
+    constexpr int BN = G::BN, STAGE_BYTES = G::STAGE_BYTES;
+    constexpr uint32_t TMEM_COLS = G::TMEM_COLS;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* bars = (uint64_t*)(smem + STAGES * STAGE_BYTES);
@@ -196,7 +214,7 @@ __global__ void __launch_bounds__(128, 1) gemm_bf16_tc_kernel(const __grid_const
             const uint64_t da = smem_desc_sw128(sa), db = smem_desc_sw128(sb);
 #pragma unroll
             for (int k = 0; k < BK / 16; ++k)  // K = 16 per instruction: advance 32 bytes within the swizzled row
-                mma_bf16(tmem, da + 2 * k, db + 2 * k, (kt > 0 || k > 0) ? 1u : 0u);
+                mma_bf16(tmem, da + 2 * k, db + 2 * k, G::IDESC, (kt > 0 || k > 0) ? 1u : 0u);
             mma_commit(empty0 + 8 * s);
         }
         mma_commit(accum);  // fires when every MMA issued above has completed

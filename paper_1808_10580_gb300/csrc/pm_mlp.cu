@@ -94,14 +94,30 @@ int gemm(pm_ctx* c, const bf16* A, int lda, const bf16* B, int ldb, int M, int N
     p.N = N;
     p.K = K;
     p.err = err;
-    static bool attr_set[64] = {};
-    if (!attr_set[c->device & 63]) {
-        PM_CUDA(cudaFuncSetAttribute(tc::gemm_bf16_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES),
-                "gemm smem attribute");
-        attr_set[c->device & 63] = true;
+    // 256-wide tiles when the product has enough of them for two waves over the
+    // SMs; otherwise 64-wide tiles (more CTAs for the network's small shapes).
+    const bool wide = (N % 256 == 0) && (int64_t)(M / tc::BM) * (N / 256) >= 2 * (int64_t)c->sm_count;
+    if (wide && !make_map(&p.tmB, B, (uint64_t)N, (uint64_t)K, (uint64_t)ldb, 256))
+        return fail(PM_ECUDA, "tensor map encoding failed");
+    static bool attr_set[2][64] = {};
+    if (!attr_set[wide][c->device & 63]) {
+        if (wide)
+            PM_CUDA(cudaFuncSetAttribute(tc::gemm_bf16_tc_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         tc::GemmCfg<256>::SMEM_BYTES),
+                    "gemm smem attribute");
+        else
+            PM_CUDA(cudaFuncSetAttribute(tc::gemm_bf16_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         tc::GemmCfg<64>::SMEM_BYTES),
+                    "gemm smem attribute");
+        attr_set[wide][c->device & 63] = true;
     }
-    dim3 grid((unsigned)(M / tc::BM), (unsigned)(N / tc::BN));
-    tc::gemm_bf16_tc_kernel<<<grid, 128, tc::SMEM_BYTES, c->stream>>>(p);
+    if (wide) {
+        dim3 grid((unsigned)(M / tc::BM), (unsigned)(N / 256));
+        tc::gemm_bf16_tc_kernel<256><<<grid, 128, tc::GemmCfg<256>::SMEM_BYTES, c->stream>>>(p);
+    } else {
+        dim3 grid((unsigned)(M / tc::BM), (unsigned)(N / tc::BN));
+        tc::gemm_bf16_tc_kernel<64><<<grid, 128, tc::GemmCfg<64>::SMEM_BYTES, c->stream>>>(p);
+    }
     PM_CUDA(cudaGetLastError(), "gemm launch");
     count_launch(c);
     return PM_OK;

@@ -22,7 +22,8 @@ def bf16_round(a):
     return torch.from_numpy(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).to(torch.float32).numpy()
 
 
-@pytest.mark.parametrize("M,N,K", [(128, 64, 64), (256, 192, 320), (384, 512, 512), (128, 448, 1024)])
+@pytest.mark.parametrize("M,N,K", [(128, 64, 64), (256, 192, 320), (384, 512, 512), (128, 448, 1024),
+                                   (4096, 2560, 256)])  # the last takes the 256-wide tiles
 def test_gemm_matches_fp64_product_of_bf16_operands(c, M, N, K):
     rng = np.random.default_rng(M + N + K)
     A = rng.standard_normal((M, K)).astype(np.float32)
