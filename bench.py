@@ -487,7 +487,9 @@ def run_sweep(args):
     """Cost against the number of real coefficients N_u (the scaling the paper
     plots for its GPU code, Section 4): the time-dependent workload's 300
     observations x M paths with a prior field of each K, on the FP32 pipes and
-    on the tensor cores where the tensor path has the K (auxiliary line)."""
+    on the tensor cores where the tensor path has the K (auxiliary line).
+    K = 24, 32, 40 (N_u up to 6560, beyond the 3209 coefficients of the
+    paper's second example) run the wide-K kernels."""
     import torch
 
     import paper_1808_10580_gb300 as pm
@@ -504,11 +506,11 @@ def run_sweep(args):
     mean = torch.empty(len(w.t), dtype=torch.float64, device=dev)
     steps = particle_steps(w)
     rows = []
-    for K in (2, 3, 4, 5, 6, 8, 10, 12, 16):
+    for K in (2, 3, 4, 5, 6, 8, 10, 12, 16, 24, 32, 40):
         fld = pm.Field(K, inputs.prior_field(K, 1001))
         row = {"K": K, "n_u": (2 * K + 1) ** 2 - 1}
         for name, flags in (("fp32_ms", pm.PM_FP32), ("tensor_ms", pm.PM_FP32 | pm.PM_TENSOR)):
-            if name == "tensor_ms" and K not in (4, 5, 6, 8, 10, 12, 16):
+            if name == "tensor_ms" and K not in (4, 5, 6, 8, 10, 12, 16, 24, 32, 40):
                 continue
             ms = []
             for k in range(args.warmup + args.steps):
@@ -516,6 +518,8 @@ def run_sweep(args):
                 if k >= args.warmup:
                     ms.append(pm.pm_last_kernel_ms(ctx))
             row[name] = statistics.median(ms)
+        if "tensor_ms" in row:
+            row["tensor_speedup"] = row["fp32_ms"] / row["tensor_ms"]
         rows.append(row)
     fp32 = np.array([[r["n_u"], r["fp32_ms"]] for r in rows if r["K"] >= 4])
     slope, icpt = np.polyfit(fp32[:, 0], fp32[:, 1], 1)

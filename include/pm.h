@@ -20,7 +20,9 @@
  *   half-plane lattice H_K = {(m,n): m > 0, |n| <= K} U {(0,n): 0 < n <= K},
  *   ordered by m, then n ascending; u = (a_0, b_0, a_1, b_1, ...) has 2|H_K| =
  *   (2K+1)^2 - 1 doubles.  v = (-d psi/dx2, d psi/dx1), i.e. the paper's
- *   k_perp = (-k_y, k_x) direction.  Supported K: 0..6, 8, 10, 12, 16.
+ *   k_perp = (-k_y, k_x) direction.  Supported K: 0..6, 8, 10, 12, 16; the
+ *   time-dependent map with float paths also takes the wide bounds K = 24,
+ *   32, 40 (N_u = 2400, 4224, 6560; PM_EINVAL elsewhere).
  * Random numbers.  Step n of path i of observation j in instance b draws
  *   Philox4x32-10 (Salmon et al., SC'11) on counter {n/2, i, j, b} under key
  *   {seed & 0xffffffff, seed >> 32}; words (r0, r1) feed even n and (r2, r3)
@@ -75,9 +77,10 @@ extern "C" {
 #define PM_FP64 1u
 #define PM_DEVICE_PTRS 2u
 #define PM_ASYNC 4u
-/* Time-dependent float paths only: evaluate the velocity sum on the tensor
- * cores (tcgen05 TF32 with a three-term hi/lo split, about float accuracy);
- * supported for K in {4, 5, 6, 8, 10, 12, 16}, other K fall back to the FP32 pipes. */
+/* Float paths: evaluate the velocity sum on the tensor cores (tcgen05 TF32
+ * with a three-term hi/lo split, about float accuracy); supported for K in
+ * {4, 5, 6, 8, 10, 12, 16} (and K = 24, 32, 40 for the time-dependent map),
+ * other K run on the FP32 pipes. */
 #define PM_TENSOR 8u
 /* pm_forward_timedep: observations at bit-identical points x
  * share their paths (Theorem 3.1: the value at t_j needs the path only up to

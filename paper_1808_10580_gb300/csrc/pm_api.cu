@@ -202,10 +202,15 @@ int set_device(pm_ctx* c)
 }
 
 // Common checks of a field description.
-int check_field(const pm_field* f)
+int check_field(const pm_field* f, bool allow_wide)
 {
     if (!f) return fail(PM_EINVAL, "field is NULL");
-    if (!supported_K(f->K)) return fail(PM_EINVAL, "K=%d is not one of the compiled bounds 0..6, 8, 10, 12, 16", f->K);
+    if (allow_wide && wide_K(f->K)) {
+        // accepted: the time-dependent map with float paths (checked by the caller)
+    } else if (!supported_K(f->K)) {
+        return fail(PM_EINVAL, "K=%d is not one of the compiled bounds 0..6, 8, 10, 12, 16%s", f->K,
+                    allow_wide ? " (24, 32, 40: float paths)" : "");
+    }
     const int64_t nu = (int64_t)(2 * f->K + 1) * (2 * f->K + 1) - 1;
     if (nu > 0 && !f->u) return fail(PM_EINVAL, "field coefficients are NULL");
     if (nu > 0 && !finite_array(f->u, nu)) return fail(PM_EINVAL, "field coefficients contain NaN or Inf");
@@ -396,8 +401,9 @@ int pm_forward_timedep(pm_ctx* c, const pm_field* field, double kappa, const pm_
                        double* mean, double* var, const pm_path_opts* opts)
 {
     if (!c) return fail(PM_EINVAL, "ctx is NULL");
-    int rc = check_field(field);
+    int rc = check_field(field, true);
     if (rc) return rc;
+    if (wide_K(field->K) && (flags & PM_FP64)) return fail(PM_EINVAL, "K=%d runs with float paths only", field->K);
     if (!th) return fail(PM_EINVAL, "theta0 is NULL");
     if (th->n < 0 || th->n > PM_MAX_THETA0_MODES) return fail(PM_EINVAL, "theta0 has %d modes (max %d)", th->n, PM_MAX_THETA0_MODES);
     if (th->n > 0 && (!th->k || !th->a || !th->b)) return fail(PM_EINVAL, "theta0 arrays are NULL");
@@ -424,7 +430,9 @@ int pm_forward_timedep(pm_ctx* c, const pm_field* field, double kappa, const pm_
     if (n_obs * chunks64 > 0x7fffffffLL) return fail(PM_EINVAL, "n_obs * ceil(M/%d) exceeds the grid limit", kTimedepBlock);
     const int32_t chunks = (int32_t)chunks64;
     const int K = field->K;
-    const bool tc = !fp64 && (flags & PM_TENSOR) && (K == 4 || K == 5 || K == 6 || K == 8 || K == 10 || K == 12 || K == 16);
+    const bool tc = !fp64 && (flags & PM_TENSOR) && (K == 4 || K == 5 || K == 6 || K == 8 || K == 10 || K == 12 || K == 16 ||
+                                                     wide_K(K));
+    const bool wide = wide_K(K);
     const bool share = flags & PM_SHARE_PATHS;
     if ((rc = set_device(c))) return rc;
 
@@ -449,8 +457,9 @@ int pm_forward_timedep(pm_ctx* c, const pm_field* field, double kappa, const pm_
     // Workspace layout.
     const bool sort = n_obs <= 8192 && !share;
     auto layout = [&](Bump& b) {
-        struct P { unsigned* err; unsigned long long* steps; ObsRec* rec; int32_t* order; double2* part; int4* grp; int32_t* mem; double *x, *t, *mean, *var, *g, *xo; } p{};
+        struct P { unsigned* err; unsigned long long* steps; ObsRec* rec; int32_t* order; double2* part; int4* grp; int32_t* mem; float* tab; double *x, *t, *mean, *var, *g, *xo; } p{};
         p.err = b.take<unsigned>(64);     // error flag, then the step counter 128 bytes on
+        p.tab = wide ? b.take<float>((size_t)wide_table_floats(K)) : nullptr;
         p.steps = (unsigned long long*)(p.err ? p.err + 32 : nullptr);
         p.rec = b.take<ObsRec>((size_t)n_obs);
         p.order = sort ? b.take<int32_t>((size_t)n_obs) : nullptr;
@@ -527,6 +536,7 @@ int pm_forward_timedep(pm_ctx* c, const pm_field* field, double kappa, const pm_
     L.groups = share ? W.grp : nullptr;
     L.members = share ? W.mem : nullptr;
     L.n_groups = (int32_t)PG.groups.size();
+    L.table_dev = W.tab;
     c->last_grid = (share ? (int64_t)PG.groups.size() : n_obs) * (int64_t)chunks;
     L.inst = opts ? opts->instance : 0u;
     L.key0 = (uint32_t)(seed & 0xffffffffu);
@@ -541,7 +551,16 @@ int pm_forward_timedep(pm_ctx* c, const pm_field* field, double kappa, const pm_
         case 8: e = tdtc::launch_timedep_tc<8>(L, W.err + 1, c->stream); break;
         case 10: e = tdtc::launch_timedep_tc<10>(L, W.err + 1, c->stream); break;
         case 12: e = tdtc::launch_timedep_tc<12>(L, W.err + 1, c->stream); break;
+        case 24: e = tdtc::launch_timedep_tc<24>(L, W.err + 1, c->stream); break;
+        case 32: e = tdtc::launch_timedep_tc<32>(L, W.err + 1, c->stream); break;
+        case 40: e = tdtc::launch_timedep_tc<40>(L, W.err + 1, c->stream); break;
         default: e = tdtc::launch_timedep_tc<16>(L, W.err + 1, c->stream); break;
+        }
+    } else if (wide) {
+        switch (K) {
+        case 24: e = launch_timedep<float, 24>(L, c->stream); break;
+        case 32: e = launch_timedep<float, 32>(L, c->stream); break;
+        default: e = launch_timedep<float, 40>(L, c->stream); break;
         }
     } else {
         e = fp64 ? dispatch_timedep<double>(K, L, c->stream) : dispatch_timedep<float>(K, L, c->stream);

@@ -136,11 +136,18 @@ struct SharedTable {
     }
 };
 
+// Wave-number bounds above this are "wide": the table (8 (K+1)^2 floats, more
+// than the kernel-parameter bank holds from K = 32 on) is staged in shared
+// memory, and the loop over m stays rolled (the unrolled sum would be some
+// 10^4 instructions, far beyond the instruction cache).
+constexpr int kMaxUnrolledK = 16;
+
 // P particles at once (each coefficient quad is fetched once and serves all P).
 template <typename Real, int K, int P, typename Tab>
 __device__ __forceinline__ void velocity(const Tab& tab, const Real (&x1)[P], const Real (&x2)[P],
                                          Real (&v1)[P], Real (&v2)[P])
 {
+    constexpr bool kRolled = K > kMaxUnrolledK;
     Real C2[P][K + 1], S2[P][K + 1], c1[P], s1[P];
 #pragma unroll
     for (int q = 0; q < P; ++q) {
@@ -159,7 +166,7 @@ __device__ __forceinline__ void velocity(const Tab& tab, const Real (&x1)[P], co
     Real C1m[P], S1m[P];
 #pragma unroll
     for (int q = 0; q < P; ++q) { C1m[q] = (Real)1; S1m[q] = (Real)0; }
-#pragma unroll
+#pragma unroll(kRolled ? 1 : K)
     for (int m = 1; m <= K; ++m) {
         Real p1c[P], p1s[P], p2c[P], p2s[P];
         const Quad<Real> F0 = tab.quad((m * (K + 1)) * 2 + 1);  // n = 0 column: f0 and f2

@@ -61,7 +61,7 @@ bool is_device_pointer(const void* p);
 int ensure_workspace(pm_ctx* c, size_t bytes);
 int ensure_host(pm_ctx* c, size_t bytes);
 int set_device(pm_ctx* c);
-int check_field(const pm_field* f);
+int check_field(const pm_field* f, bool allow_wide = false);
 int check_ptrs(uint32_t flags, std::initializer_list<const void*> ptrs);
 void count_launch(pm_ctx* c, int n = 1);
 

@@ -2,6 +2,7 @@
 // the path precision Real and the wave-number bound K.  Included by the
 // per-precision translation units, which instantiate them for the supported K.
 #pragma once
+#include <vector>
 #include "pm_device.cuh"
 #include "pm_launch.h"
 
@@ -11,9 +12,19 @@ namespace pm {
 // velocity table is read as FMA operands at compile-time offsets, and every
 // launch carries its own copy (no shared constant symbol, so concurrent calls
 // on different streams cannot interfere).
-template <typename Real, int K>
-struct TimedepParams {
+// Velocity table of a launch: in the parameter bank, or (wide K, float paths)
+// a device copy that every CTA stages into its shared memory.
+template <typename Real, int K, bool Wide = (K > kMaxUnrolledK)>
+struct FieldSource {
     FieldTable<Real, K> field;
+};
+template <int K>
+struct FieldSource<float, K, true> {
+    const float4* table;  // device [coef_count<K>() / 4]
+};
+
+template <typename Real, int K>
+struct TimedepParams : FieldSource<Real, K> {
     Theta0Table<Real> th;
     const ObsRec* obs;
     const int32_t* order;
@@ -83,6 +94,26 @@ __device__ __forceinline__ double2 block_sum2(double a, double b)
     return r;
 }
 
+// The table a kernel reads: its parameter-bank copy, or for wide K the shared
+// memory copy staged here (all threads of the CTA must call this).
+template <typename Real, int K, typename Src>
+__device__ __forceinline__ auto field_table(const Src& src)
+{
+    if constexpr (K > kMaxUnrolledK) {
+        extern __shared__ float4 s_field[];
+        constexpr int nq = coef_count<K>() / 4;
+        for (int q = threadIdx.x; q < nq; q += blockDim.x) s_field[q] = __ldg(src.table + q);
+        __syncthreads();
+        return SharedTable{s_field};
+    } else {
+        return ParamTable<Real, K>{src.field};
+    }
+}
+
+// Dynamic shared memory of the kernels that read the table above.
+template <typename Real, int K>
+constexpr int field_smem() { return K > kMaxUnrolledK ? coef_count<K>() * (int)sizeof(float) : 0; }
+
 // ---------------------------------------------------------------------------
 // Algorithm 1.  One CTA = one chunk of BLOCK consecutive paths of one
 // observation; all its paths take the same N_j steps, so the step loop is
@@ -97,6 +128,7 @@ __global__ void __launch_bounds__(BLOCK) timedep_kernel(const __grid_constant__ 
     const int j = p.order ? p.order[slot] : slot;
     const int64_t i = (int64_t)c * BLOCK + threadIdx.x;
     const bool active = i < p.M;
+    const auto tab = field_table<Real, K>(p);
     double g = 0.0;
     if (active) {
         const ObsRec o = p.obs[j];
@@ -106,7 +138,6 @@ __global__ void __launch_bounds__(BLOCK) timedep_kernel(const __grid_constant__ 
         const uint32_t pid = (uint32_t)(p.path_offset + i);
         const int N = o.nsteps;
         const Real h_last = (Real)o.h_last, s_last = (Real)o.s_last;
-        const ParamTable<Real, K> tab{p.field};
         for (int n = 0; n < N; n += 2) {
             const u32x4 r = philox4x32_10(u32x4{(uint32_t)(n >> 1), pid, (uint32_t)j, p.inst}, p.key0, p.key1);
             // One copy of the step body (kept rolled): the unrolled velocity sum is
@@ -161,7 +192,7 @@ __global__ void __launch_bounds__(BLOCK) timedep_shared_kernel(const __grid_cons
         X1.set(o.x1);
         X2.set(o.x2);
     }
-    const ParamTable<Real, K> tab{p.field};
+    const auto tab = field_table<Real, K>(p);
     auto finish = [&](int m, const Coord<Real>& Y1, const Coord<Real>& Y2) {
         const int jm = p.members[m];
         double g = 0.0;
@@ -214,7 +245,23 @@ template <typename Real, int K>
 cudaError_t launch_timedep(const TimedepLaunch& L, cudaStream_t stream)
 {
     TimedepParams<Real, K> p;
-    for (int t = 0; t < table_size(K); ++t) p.field.c[t] = (Real)L.coef[t];
+    constexpr int smem = field_smem<Real, K>();
+    if constexpr (K > kMaxUnrolledK) {
+        static_assert(sizeof(Real) == 4, "wide K: float paths only");
+        // The float table into the caller's device buffer (the host vector is
+        // read before the copy call returns).
+        if (!L.table_dev) return cudaErrorInvalidValue;
+        std::vector<float> h((size_t)table_size(K));
+        for (int t = 0; t < table_size(K); ++t) h[(size_t)t] = (float)L.coef[t];
+        cudaError_t e = cudaMemcpyAsync(L.table_dev, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, stream);
+        if (e != cudaSuccess) return e;
+        p.table = reinterpret_cast<const float4*>(L.table_dev);
+        e = cudaFuncSetAttribute(L.groups ? timedep_shared_kernel<Real, K, kTimedepBlock> : timedep_kernel<Real, K, kTimedepBlock>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+    } else {
+        for (int t = 0; t < table_size(K); ++t) p.field.c[t] = (Real)L.coef[t];
+    }
     p.th.n = L.nq;
     for (int q = 0; q < kMaxTheta0; ++q) {
         const bool on = q < L.nq;
@@ -241,11 +288,11 @@ cudaError_t launch_timedep(const TimedepLaunch& L, cudaStream_t stream)
     p.members = L.members;
     if (L.groups) {
         const int64_t grid = (int64_t)L.n_groups * L.chunks;
-        timedep_shared_kernel<Real, K, kTimedepBlock><<<(unsigned)grid, kTimedepBlock, 0, stream>>>(p);
+        timedep_shared_kernel<Real, K, kTimedepBlock><<<(unsigned)grid, kTimedepBlock, smem, stream>>>(p);
         return cudaGetLastError();
     }
     const int64_t grid = (int64_t)L.n_obs * L.chunks;
-    timedep_kernel<Real, K, kTimedepBlock><<<(unsigned)grid, kTimedepBlock, 0, stream>>>(p);
+    timedep_kernel<Real, K, kTimedepBlock><<<(unsigned)grid, kTimedepBlock, smem, stream>>>(p);
     return cudaGetLastError();
 }
 
@@ -457,6 +504,10 @@ cudaError_t launch_velocity(const double* coef, const double* x, int64_t n, doub
 }
 
 }  // namespace pm
+
+// Wide K: the time-dependent map only (float paths).
+#define PM_INSTANTIATE_WIDE(K) \
+    template cudaError_t pm::launch_timedep<float, K>(const pm::TimedepLaunch&, cudaStream_t);
 
 // Explicit instantiation of the launchers for one precision and one K.
 #define PM_INSTANTIATE(Real, K)                                                                        \

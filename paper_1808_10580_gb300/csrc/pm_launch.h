@@ -43,7 +43,24 @@ struct TimedepLaunch {
     const int4* groups = nullptr;  // device [n_groups]
     const int32_t* members = nullptr;  // device [n_obs]
     int32_t n_groups = 0;
+    // Wide K (K > 16): device buffer of wide_table_floats(K) floats that the
+    // launcher fills with its coefficient table before the kernel reads it.
+    float* table_dev = nullptr;
 };
+
+// Wave-number bounds of the time-dependent map beyond the unrolled kernels.
+inline bool wide_K(int K) { return K == 24 || K == 32 || K == 40; }
+
+// Floats of the device table a wide-K launch needs: the product-basis table
+// (8 (K+1)^2) of the FP32-pipe kernel or the padded W^T of the tensor-core
+// kernel (NP x 4 KC, NP = 4K+1 rounded up to 16, KC = 2 ceil((2K+1)/8)).
+inline int64_t wide_table_floats(int K)
+{
+    const int64_t simt = 8 * (int64_t)(K + 1) * (K + 1);
+    const int64_t np = (4 * K + 1 + 15) / 16 * 16, kc = 2 * ((2 * K + 1 + 7) / 8);
+    const int64_t tc = np * 4 * kc;
+    return simt > tc ? simt : tc;
+}
 
 struct DirichletLaunch {
     const double* coef;      // host table

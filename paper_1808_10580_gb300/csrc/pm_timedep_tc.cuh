@@ -29,24 +29,41 @@
 namespace pm {
 namespace tdtc {
 
-template <int K>
+// F ("folded"): the constant column of A (the n = 0 terms of v2) and the
+// m = 0 column of P (the x1-independent part of v1) leave the product and are
+// summed on the FP32 pipes (4K FMAs per particle), so that A has 2K columns
+// and P 4K: for K a multiple of 4 that saves one MMA k-step and 16 columns of N.
+template <int K, bool F = false>
 struct Shape {
-    static constexpr int KD = 2 * K + 1;              // A columns used
+    static constexpr bool FOLD = F;
+    static constexpr int KD = F ? 2 * K : 2 * K + 1;  // A columns used
     static constexpr int KS = (KD + 7) / 8;           // MMA k-steps (K = 8 per tf32 instruction)
     static constexpr int KC = 2 * KS;                 // 16-byte chunks (4 tf32) per tile row
     static constexpr int WS = 4 * KC;                 // row stride of W (tf32 entries)
-    static constexpr int NC = 4 * K + 1;              // accumulator columns used
+    static constexpr int NC = F ? 4 * K : 4 * K + 1;  // accumulator columns used
     static constexpr int NP = (NC + 15) / 16 * 16;    // MMA N (multiple of 16)
     static constexpr int SBO = KC * 128;              // bytes between 8-row groups of a tile
     static constexpr int A_BYTES = 128 * KC * 16;     // 128 rows x 8 KS tf32
     static constexpr int B_BYTES = NP * KC * 16;      // NP rows x 8 KS tf32
     static constexpr int SMEM = 2 * A_BYTES + 2 * B_BYTES + 128 + 64;
-    static constexpr uint32_t TMEM_COLS = NP <= 64 ? 64u : 128u;  // allocation: a power of 2 >= 32
+    // allocation: a power of 2 >= 32
+    static constexpr uint32_t TMEM_COLS = NP <= 64 ? 64u : NP <= 128 ? 128u : 256u;
     // CTAs per SM that fit the 228 KB of shared memory (1 KB reserved each), at most 6
     static constexpr int MIN_CTAS = (233472 / (SMEM + 1024)) < 6 ? (233472 / (SMEM + 1024)) : 6;
-    static_assert(NP <= 128, "accumulator within 128 TMEM columns");
+    // W^T travels in the kernel-parameter bank up to 16 KB, else in global memory.
+    static constexpr bool W_PARAM = NP * WS * 4 <= 16384;
+    static_assert(NP <= 256, "accumulator within 256 TMEM columns (one MMA: N <= 256)");
     static_assert(MIN_CTAS >= 1, "tiles fit shared memory");
 };
+
+// The time-dependent kernel folds where that removes padding (K a multiple of
+// 4) and measured faster: not at K = 4 (the product is too small for the
+// saving to pay for the FMAs), nor at K = 24 (measured 91 ms against 81 ms
+// unfolded on the 300 x 1e4-path workload).
+template <int K>
+constexpr bool fold_of() { return K % 4 == 0 && K >= 8 && K != 24; }
+template <int K>
+using TdShape = Shape<K, fold_of<K>()>;
 
 // Instruction descriptor, kind::tf32: FP32 accumulator, TF32 A and B, both K-major.
 template <int NP>
@@ -114,7 +131,13 @@ inline int resident_ctas(const void* fn, int threads, int dyn_smem, int tmem_col
 
 template <int K>
 struct Params {
-    float W[Shape<K>::NP * Shape<K>::WS];   // W^T: row nc (accumulator column), entry k (A column)
+    // W^T: row nc (accumulator column), entry k (A column); in W, or at Wg.
+    float W[TdShape<K>::W_PARAM ? TdShape<K>::NP * TdShape<K>::WS : 1];
+    const float* Wg;
+    // Folded shape: the m = 0 coefficients of v1 (pairs for S2_n, C2_n, n = 1..K)
+    // and the n = 0 coefficients of v2 (C1m at m-1, S1m at K+m-1).
+    float T0[2 * K];
+    float N0[2 * K];
     Theta0Table<float> th;
     const ObsRec* obs;
     const int32_t* order;
@@ -173,7 +196,7 @@ template <int K>
 __device__ __forceinline__ void velocity_from_tmem(uint32_t t_row, const float (&C1)[K + 1], const float (&S1)[K + 1],
                                                    float& v1, float& v2)
 {
-    constexpr int NP = Shape<K>::NP;
+    constexpr int NP = Shape<K, false>::NP;
     float v1c = 0.f, v1s = 0.f, v2c = 0.f, v2s = 0.f, p0 = 0.f;
 #pragma unroll
     for (int q = 0; q < NP / 16; ++q) {
@@ -193,6 +216,35 @@ __device__ __forceinline__ void velocity_from_tmem(uint32_t t_row, const float (
     v2 = v2c + v2s;
 }
 
+// Folded shape: columns m-1, K+m-1, 2K+m-1, 3K+m-1 hold P1c(m), P1s(m), and
+// P2c(m), P2s(m) without their n = 0 terms N0, which are added here before the
+// multiplication by the x1 harmonic; p0 (the m = 0 part of v1) comes from the
+// FP32 pipes.  The sums run over m in the same order as in the unfolded form.
+template <int K>
+__device__ __forceinline__ void velocity_from_tmem_folded(uint32_t t_row, const float (&C1)[K + 1],
+                                                          const float (&S1)[K + 1], const float* N0, float p0,
+                                                          float& v1, float& v2)
+{
+    constexpr int NP = Shape<K, true>::NP;
+    float v1c = 0.f, v1s = 0.f, v2c = 0.f, v2s = 0.f;
+#pragma unroll
+    for (int q = 0; q < NP / 16; ++q) {
+        float a[16];
+        tmem_ld16(t_row + 16u * q, a);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            const int col = 16 * q + e;
+            const int blk = col / K, m = col - blk * K + 1;
+            if (blk == 0) v1c = fmaf(C1[m], a[e], v1c);
+            else if (blk == 1) v1s = fmaf(S1[m], a[e], v1s);
+            else if (blk == 2) v2c = fmaf(C1[m], a[e] + N0[m - 1], v2c);
+            else if (blk == 3) v2s = fmaf(S1[m], a[e] + N0[K + m - 1], v2s);
+        }
+    }
+    v1 = p0 + (v1c + v1s);
+    v2 = v2c + v2s;
+}
+
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, const float4& v)
 {
     asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w) : "memory");
@@ -201,10 +253,10 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, const float4& v)
 // Tiles at shared address sb: A_hi, A_lo (A_BYTES each), then B_hi, B_lo.
 // This thread's row of the particle tiles (row = sb + tile_off(r, 0); chunk c
 // 128 c bytes further): harmonics a[0..KD) split into hi / lo.
-template <int K>
-__device__ __forceinline__ void write_row(uint32_t row, const float (&a)[4 * Shape<K>::KC])
+template <int K, bool F = false>
+__device__ __forceinline__ void write_row(uint32_t row, const float (&a)[4 * Shape<K, F>::KC])
 {
-    using S = Shape<K>;
+    using S = Shape<K, F>;
 #pragma unroll
     for (int c = 0; c < (S::KD + 3) / 4; ++c) {
         float4 h, l;
@@ -219,10 +271,10 @@ __device__ __forceinline__ void write_row(uint32_t row, const float (&a)[4 * Sha
 
 // One Euler step's product, issued by one thread: P = A_hi W_hi + A_lo W_hi +
 // A_hi W_lo over the KS k-steps, then a commit to the step's mbarrier.
-template <int K>
+template <int K, bool F = false>
 __device__ __forceinline__ void issue_step_mma(uint32_t tmem, uint32_t sb, uint32_t bar)
 {
-    using S = Shape<K>;
+    using S = Shape<K, F>;
     const uint64_t ah = tile_desc<S::SBO>(sb), al = tile_desc<S::SBO>(sb + S::A_BYTES);
     const uint64_t bh = tile_desc<S::SBO>(sb + 2 * S::A_BYTES), bl = tile_desc<S::SBO>(sb + 2 * S::A_BYTES + S::B_BYTES);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -236,9 +288,10 @@ __device__ __forceinline__ void issue_step_mma(uint32_t tmem, uint32_t sb, uint3
 }
 
 template <int K>
-__global__ void __launch_bounds__(128, Shape<K>::MIN_CTAS) timedep_tc_kernel(const __grid_constant__ Params<K> p)
+__global__ void __launch_bounds__(128, TdShape<K>::MIN_CTAS) timedep_tc_kernel(const __grid_constant__ Params<K> p)
 {
-    using S = Shape<K>;
+    using S = TdShape<K>;
+    constexpr bool F = S::FOLD;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     uint8_t* A_hi = smem;
@@ -258,7 +311,7 @@ __global__ void __launch_bounds__(128, Shape<K>::MIN_CTAS) timedep_tc_kernel(con
         float* lv = &l.x;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const float w = p.W[r * S::WS + 4 * c + e];
+            const float w = S::W_PARAM ? p.W[r * S::WS + 4 * c + e] : __ldg(p.Wg + r * S::WS + 4 * c + e);
             hv[e] = to_tf32(w);
             lv[e] = to_tf32(w - hv[e]);
         }
@@ -337,7 +390,8 @@ __global__ void __launch_bounds__(128, Shape<K>::MIN_CTAS) timedep_tc_kernel(con
     u32x4 r{0, 0, 0, 0};
 
     for (int n = 0; n < N; ++n) {
-        // Row of A: x2 harmonics (hi and lo).
+        // Row of A: x2 harmonics (hi and lo); folded: the m = 0 part of v1 here.
+        float p0 = 0.f;
         {
             float C2[K + 1], S2[K + 1];
             fourier_powers<float, K>(X2.val(), C2, S2);
@@ -346,15 +400,26 @@ __global__ void __launch_bounds__(128, Shape<K>::MIN_CTAS) timedep_tc_kernel(con
             for (int q = 0; q < 4 * S::KC; ++q) a[q] = 0.f;
 #pragma unroll
             for (int q = 1; q <= K; ++q) { a[q - 1] = S2[q]; a[K + q - 1] = C2[q]; }
-            a[2 * K] = 1.f;
-            write_row<K>(sb + row, a);
+            if constexpr (F) {
+                // eight independent partial sums: this runs before the step's barrier
+                float ps[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int q = 1; q <= K; ++q) {
+                    ps[(q - 1) & 3] = fmaf(p.T0[2 * q - 2], S2[q], ps[(q - 1) & 3]);
+                    ps[4 + ((q - 1) & 3)] = fmaf(p.T0[2 * q - 1], C2[q], ps[4 + ((q - 1) & 3)]);
+                }
+                p0 = ((ps[0] + ps[1]) + (ps[2] + ps[3])) + ((ps[4] + ps[5]) + (ps[6] + ps[7]));
+            } else {
+                a[2 * K] = 1.f;
+            }
+            write_row<K, F>(sb + row, a);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         // One barrier per step: the rows are in place, and a wait that gave up
         // in the previous step (any thread) ends the loop for the whole CTA.
         if (__syncthreads_or(failed)) { failed = true; break; }
-        if (tid == 0) issue_step_mma<K>(tmem, sb, bar_a);
+        if (tid == 0) issue_step_mma<K, F>(tmem, sb, bar_a);
         // While the product runs: the Brownian increment and the x1 harmonics.
         if ((n & 1) == 0) r = philox4x32_10(u32x4{(uint32_t)(n >> 1), pid, (uint32_t)stream, p.inst}, p.key0, p.key1);
         float xi1, xi2;
@@ -364,7 +429,8 @@ __global__ void __launch_bounds__(128, Shape<K>::MIN_CTAS) timedep_tc_kernel(con
         failed = !tc::mbar_wait(bar_a, (uint32_t)(n & 1));
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         float v1, v2;
-        velocity_from_tmem<K>(t_row, C1, S1, v1, v2);
+        if constexpr (F) velocity_from_tmem_folded<K>(t_row, C1, S1, p.N0, p0, v1, v2);
+        else velocity_from_tmem<K>(t_row, C1, S1, v1, v2);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         // Members whose last step is this one take it with their own length.
         while (n == stop) {
@@ -397,13 +463,26 @@ __global__ void __launch_bounds__(128, Shape<K>::MIN_CTAS) timedep_tc_kernel(con
 }
 
 // W^T of the product-basis table t[(m (K+1) + n) 8 + q] (e0..e3, f0..f3).
-template <int K>
+template <int K, bool F = false>
 void build_W(const double* t, float* W)
 {
-    using S = Shape<K>;
+    using S = Shape<K, F>;
     for (int q = 0; q < S::NP * S::WS; ++q) W[q] = 0.f;
     auto T = [&](int m, int n, int q) { return t[(size_t)(m * (K + 1) + n) * 8 + q]; };
     auto set = [&](int col, int row, double v) { W[col * S::WS + row] = (float)v; };
+    if constexpr (F) {
+        // Columns m-1, K+m-1, 2K+m-1, 3K+m-1 (m = 1..K); A columns S2_n at n-1, C2_n at K+n-1.
+        for (int m = 1; m <= K; ++m) {
+            const int c1c = m - 1, c1s = K + m - 1, c2c = 2 * K + m - 1, c2s = 3 * K + m - 1;
+            for (int n = 1; n <= K; ++n) {
+                set(c1c, n - 1, T(m, n, 0)); set(c1c, K + n - 1, T(m, n, 1));
+                set(c1s, n - 1, T(m, n, 2)); set(c1s, K + n - 1, T(m, n, 3));
+                set(c2c, K + n - 1, T(m, n, 4)); set(c2c, n - 1, T(m, n, 5));
+                set(c2s, K + n - 1, T(m, n, 6)); set(c2s, n - 1, T(m, n, 7));
+            }
+        }
+        return;
+    }
     const int rS = 0, rC = K, rOne = 2 * K;  // A columns: S2_n at n-1, C2_n at K+n-1, constant at 2K
     for (int n = 1; n <= K; ++n) {  // m = 0: v1 only
         set(0, rS + n - 1, T(0, n, 0));
@@ -425,9 +504,30 @@ void build_W(const double* t, float* W)
 template <int K>
 cudaError_t launch_timedep_tc(const TimedepLaunch& L, unsigned* err, cudaStream_t stream)
 {
-    using S = Shape<K>;
+    using S = TdShape<K>;
     Params<K> p;
-    build_W<K>(L.coef, p.W);
+    p.Wg = nullptr;
+    {
+        auto T = [&](int m, int n, int q) { return L.coef[(size_t)(m * (K + 1) + n) * 8 + q]; };
+        for (int n = 1; n <= K; ++n) {
+            p.T0[2 * n - 2] = (float)T(0, n, 0);  // multiplies S2_n
+            p.T0[2 * n - 1] = (float)T(0, n, 1);  // multiplies C2_n
+            p.N0[n - 1] = (float)T(n, 0, 4);      // n = 0 term of P2c(m = n)
+            p.N0[K + n - 1] = (float)T(n, 0, 6);  // n = 0 term of P2s(m = n)
+        }
+    }
+    if constexpr (S::W_PARAM) {
+        build_W<K, S::FOLD>(L.coef, p.W);
+    } else {
+        // Into the caller's device buffer (the host vector is read before the
+        // copy call returns).
+        if (!L.table_dev) return cudaErrorInvalidValue;
+        std::vector<float> W((size_t)(S::NP * S::WS));
+        build_W<K, S::FOLD>(L.coef, W.data());
+        const cudaError_t e = cudaMemcpyAsync(L.table_dev, W.data(), W.size() * sizeof(float), cudaMemcpyHostToDevice, stream);
+        if (e != cudaSuccess) return e;
+        p.Wg = L.table_dev;
+    }
     p.th.n = L.nq;
     for (int q = 0; q < kMaxTheta0; ++q) {
         const bool on = q < L.nq;
