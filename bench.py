@@ -59,8 +59,23 @@ def measured_peaks():
 def tensor_flops_per_step(K: int) -> int:
     """FLOP per particle-step of the tensor-core path: the per-step contraction
     P = A W with A one row of (2K+1) basis values and W the (2K+1) x (4K+1)
-    coefficient matrix, done as three TF32 products (hi.hi, lo.hi, hi.lo)."""
+    coefficient matrix, done as three products (hi.hi, lo.hi, hi.lo)."""
     return 3 * 2 * (2 * K + 1) * (4 * K + 1)
+
+
+def tensor_operands(K: int) -> str:
+    """Operand type of the library's tensor-core particle kernels at this K:
+    FP16 (kind::f16) from K = 10 on, TF32 below."""
+    return "f16" if K >= 10 else "tf32"
+
+
+def tensor_peak(K: int, peaks: dict, peaks_kind: str):
+    """Dense peak for the operand type at K: FP16 runs at the BF16 rate (the
+    measured cuBLAS bf16 figure), TF32 at 1.1/2.25 of it (nominal ratio)."""
+    bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    if tensor_operands(K) == "f16":
+        return bf16, f"FP16 dense = bf16_tflops {bf16} ({peaks_kind}, burst; same dense rate)"
+    return bf16 * 1.1 / 2.25, f"TF32 dense = bf16_tflops {bf16} ({peaks_kind}, burst) x 1.1/2.25"
 
 
 def profile_traffic(name="timedep_k10_kernel.md"):
@@ -301,15 +316,13 @@ def run_gpu(args):
         kern_mean_ms = statistics.mean(kern_ms)
         simt_rate = steps_per_eval * flops_per_step(w.K) / (kern_mean_ms / 1e3) / 1e12
         if args.tensor:
-            # TF32 dense peak = measured bf16 dense peak x (1.1 / 2.25), the nominal ratio.
-            bf16 = float(peaks.get("bf16_tflops", 1900.0))
-            peak_tflops = bf16 * 1.1 / 2.25
+            peak_tflops, peak_basis = tensor_peak(w.K, peaks, peaks_kind)
             achieved = steps_per_eval * tensor_flops_per_step(w.K) / (kern_mean_ms / 1e3) / 1e12
             roof = {"bound": "tensor", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                     "frac": achieved / peak_tflops, "traffic": profile_traffic("timedep_k10_tc_kernel.md"),
                     "kernel": f"timedep_tc_kernel<{w.K}>", "kernel_ms": kern_mean_ms,
                     "flop_per_particle_step": tensor_flops_per_step(w.K),
-                    "peak_basis": f"TF32 dense = bf16_tflops {bf16} ({peaks_kind}, burst) x 1.1/2.25",
+                    "peak_basis": peak_basis, "operands": tensor_operands(w.K),
                     "single_product_frac": achieved / 3 / peak_tflops,
                     "fp32_equivalent": {"achieved": simt_rate, "peak": fp32_peak,
                                         "flop_per_particle_step": flops_per_step(w.K),
@@ -506,7 +519,8 @@ def run_sweep(args):
     mean = torch.empty(len(w.t), dtype=torch.float64, device=dev)
     steps = particle_steps(w)
     rows = []
-    for K in (2, 3, 4, 5, 6, 8, 10, 12, 16, 24, 32, 40):
+    ks = [int(k) for k in args.sweep_k.split(",")] if args.sweep_k else [2, 3, 4, 5, 6, 8, 10, 12, 16, 24, 32, 40]
+    for K in ks:
         fld = pm.Field(K, inputs.prior_field(K, 1001))
         row = {"K": K, "n_u": (2 * K + 1) ** 2 - 1}
         for name, flags in (("fp32_ms", pm.PM_FP32), ("tensor_ms", pm.PM_FP32 | pm.PM_TENSOR)):
@@ -522,7 +536,7 @@ def run_sweep(args):
             row["tensor_speedup"] = row["fp32_ms"] / row["tensor_ms"]
         rows.append(row)
     fp32 = np.array([[r["n_u"], r["fp32_ms"]] for r in rows if r["K"] >= 4])
-    slope, icpt = np.polyfit(fp32[:, 0], fp32[:, 1], 1)
+    slope, icpt = np.polyfit(fp32[:, 0], fp32[:, 1], 1) if len(fp32) >= 2 else (None, None)
     line = {"metric": "particle-map kernel time vs N_u", "auxiliary": True, "data": "synthetic",
             "unit": "ms per evaluation", "value": None, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "config": {"workload": f"{w.name} with a prior field of each K", "particle_steps_per_eval": steps},
@@ -772,6 +786,7 @@ def main():
                     help="timedep: skip the one FP64-path evaluation reported beside the line")
     ap.add_argument("--M", type=int, default=0, help="particles per observation (default: the workload's own; "
                     "smaller values are for profiling captures only)")
+    ap.add_argument("--sweep-k", default="", help="sweep: comma-separated K values (default 2..40)")
     ap.add_argument("--workload", default="timedep", choices=["timedep", "dirichlet", "batched", "mcmc", "sweep", "surrogate", "bvp", "layout"],
                     help="timedep: the headline line; dirichlet / batched / mcmc: auxiliary measurements")
     ap.add_argument("--train-pairs", type=int, default=1 << 16, help="mcmc: surrogate training pairs")

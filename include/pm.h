@@ -77,8 +77,10 @@ extern "C" {
 #define PM_FP64 1u
 #define PM_DEVICE_PTRS 2u
 #define PM_ASYNC 4u
-/* Float paths: evaluate the velocity sum on the tensor cores (tcgen05 TF32
- * with a three-term hi/lo split, about float accuracy); supported for K in
+/* Float paths: evaluate the velocity sum on the tensor cores (tcgen05 with a
+ * three-term hi/lo split of TF32 operands for K <= 8 and of FP16 operands,
+ * with W scaled by a power of two, from K = 10: about float accuracy, results
+ * differ from the FP32-pipe kernels by rounding); supported for K in
  * {4, 5, 6, 8, 10, 12, 16} (and K = 24, 32, 40 for the time-dependent map),
  * other K run on the FP32 pipes. */
 #define PM_TENSOR 8u

@@ -3,7 +3,8 @@
 //
 // A CTA works on one instance at a time: that instance's coefficient matrix
 // W_b is the B operand of the per-step MMA (see pm_timedep_tc.cuh), kept as
-// TF32 hi / lo tiles in shared memory.  Its lanes take paths of the instance
+// hi / lo tiles (TF32, or FP16 with a per-instance power-of-two scale) in
+// shared memory.  Its lanes take paths of the instance
 // from the instance's path counter (one atomic per warp per refill) and step
 // together; when the instance has no unclaimed paths left and every lane of
 // the CTA has finished, the CTA moves to the next instance with work and
@@ -49,9 +50,13 @@ __device__ __forceinline__ float w_entry(const float* tab, int nc, int k)
 }
 
 template <int K>
-__global__ void __launch_bounds__(128, Shape<K>::MIN_CTAS) batched_tc_kernel(const __grid_constant__ BatchKernelParams p)
+using BatShape = Shape<K, false, half_of<K>()>;
+
+template <int K>
+__global__ void __launch_bounds__(128, BatShape<K>::MIN_CTAS) batched_tc_kernel(const __grid_constant__ BatchKernelParams p)
 {
-    using S = Shape<K>;
+    using S = BatShape<K>;
+    constexpr bool H = S::HALF;
     constexpr int TS = table_size(K);
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
@@ -95,6 +100,8 @@ __global__ void __launch_bounds__(128, Shape<K>::MIN_CTAS) batched_tc_kernel(con
     // The CTA's current instance lives in shared memory; only the fields the
     // step loop reads every step stay in registers.
     __shared__ BatchInstDev sI;
+    __shared__ int s_wmax;  // FP16 operands: bits of max |table entry| of the instance
+    float inv_s = 1.f;      // FP16 operands: 1 / (power-of-two scale of W)
     int kind = 0;
     uint32_t stream = 0, key0 = 0, key1 = 0;
     float s_dt = 0.f, drift_dt = 0.f, dt = 0.f;
@@ -164,6 +171,7 @@ __global__ void __launch_bounds__(128, Shape<K>::MIN_CTAS) batched_tc_kernel(con
                     if (m2) found = __shfl_sync(full, cand_b, __ffs(m2) - 1);
                 }
                 if (lane == 0) *s_next = found;
+                if (lane == 0) s_wmax = 0;
             }
             __syncthreads();
             const int found = *s_next;
@@ -182,13 +190,32 @@ __global__ void __launch_bounds__(128, Shape<K>::MIN_CTAS) batched_tc_kernel(con
             drift_dt = (float)(In.drift_scale * In.dt);
             // coefficient tiles of the new instance (the previous MMA has completed)
             const float* tab = p.tables + (size_t)b * TS;
-            for (int q = tid; q < S::NP * 4 * S::KC; q += 128) {
-                const int nc = q / (4 * S::KC), k = q - nc * (4 * S::KC);
-                const float w = w_entry<K>(tab, nc, k);
-                const float hi = to_tf32(w);
-                const uint32_t off = tile_off<S::KC>(nc, k >> 2) + 4u * (uint32_t)(k & 3);
-                *reinterpret_cast<float*>(B_hi + off) = hi;
-                *reinterpret_cast<float*>(B_lo + off) = to_tf32(w - hi);
+            float sc = 1.f;
+            if constexpr (H) {
+                // the scale of W: every nonzero table entry is an entry of W
+                float wm = 0.f;
+                for (int q = tid; q < TS; q += 128) wm = fmaxf(wm, fabsf(tab[q]));
+                atomicMax(&s_wmax, __float_as_int(wm));
+                __syncthreads();
+                const int e = w_scale_exp(__int_as_float(s_wmax));
+                sc = ldexpf(1.f, e);
+                inv_s = ldexpf(1.f, -e);
+            }
+            for (int q = tid; q < S::NP * S::WS; q += 128) {
+                const int nc = q / S::WS, k = q - nc * S::WS;
+                const float w = w_entry<K>(tab, nc, k) * sc;
+                if constexpr (H) {
+                    const __half hi = __float2half_rn(w);
+                    const __half lo = __float2half_rn(w - __half2float(hi));
+                    const uint32_t off = tile_off<S::KC>(nc, k >> 3) + 2u * (uint32_t)(k & 7);
+                    *reinterpret_cast<__half*>(B_hi + off) = hi;
+                    *reinterpret_cast<__half*>(B_lo + off) = lo;
+                } else {
+                    const float hi = to_tf32(w);
+                    const uint32_t off = tile_off<S::KC>(nc, k >> 2) + 4u * (uint32_t)(k & 3);
+                    *reinterpret_cast<float*>(B_hi + off) = hi;
+                    *reinterpret_cast<float*>(B_lo + off) = to_tf32(w - hi);
+                }
             }
             __syncthreads();
             continue;
@@ -202,20 +229,20 @@ __global__ void __launch_bounds__(128, Shape<K>::MIN_CTAS) batched_tc_kernel(con
             {
                 float C2[K + 1], S2[K + 1];
                 fourier_powers<float, K>(X2.val(), C2, S2);
-                float a[4 * S::KC];
+                float a[S::WS];
 #pragma unroll
-                for (int q = 0; q < 4 * S::KC; ++q) a[q] = 0.f;
+                for (int q = 0; q < S::WS; ++q) a[q] = 0.f;
 #pragma unroll
                 for (int q = 1; q <= K; ++q) { a[q - 1] = S2[q]; a[K + q - 1] = C2[q]; }
                 a[2 * K] = 1.f;
-                write_row<K>(sb + row, a);
+                write_row<K, false, H>(sb + row, a);
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             // One barrier per step: the rows are in place, and a wait that gave
             // up in the previous step (any thread) stops the whole CTA.
             if (__syncthreads_or(failed)) { stop = true; break; }
-            if (tid == 0) issue_step_mma<K>(tmem, sb, bar_a);
+            if (tid == 0) issue_step_mma<K, false, H>(tmem, sb, bar_a);
             // While the product runs: the Brownian increment and the x1 harmonics.
             float xi1, xi2;
             box_muller<float>(half ? r.z : r.x, half ? r.w : r.y, xi1, xi2);
@@ -225,7 +252,7 @@ __global__ void __launch_bounds__(128, Shape<K>::MIN_CTAS) batched_tc_kernel(con
             phase ^= 1u;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             float v1, v2;
-            velocity_from_tmem<K>(t_row, C1, S1, v1, v2);
+            velocity_from_tmem<K, H>(t_row, C1, S1, v1, v2, inv_s);
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             if (pid < 0) continue;
             if (kind == 0) {
@@ -265,14 +292,14 @@ __global__ void __launch_bounds__(128, Shape<K>::MIN_CTAS) batched_tc_kernel(con
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Shape<K>::TMEM_COLS) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BatShape<K>::TMEM_COLS) : "memory");
     }
 }
 
 template <int K>
 cudaError_t launch_batched_tc(const BatchKernelParams& p, int grid, cudaStream_t s)
 {
-    batched_tc_kernel<K><<<grid, 128, Shape<K>::SMEM + 64, s>>>(p);
+    batched_tc_kernel<K><<<grid, 128, BatShape<K>::SMEM + 64, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -280,9 +307,9 @@ cudaError_t launch_batched_tc(const BatchKernelParams& p, int grid, cudaStream_t
 template <int K>
 int batched_tc_blocks_per_sm()
 {
-    const int smem = Shape<K>::SMEM + 64;
+    const int smem = BatShape<K>::SMEM + 64;
     cudaFuncSetAttribute(batched_tc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    return resident_ctas((const void*)batched_tc_kernel<K>, 128, smem, (int)Shape<K>::TMEM_COLS);
+    return resident_ctas((const void*)batched_tc_kernel<K>, 128, smem, (int)BatShape<K>::TMEM_COLS);
 }
 
 }  // namespace tdtc

@@ -15,8 +15,12 @@ namespace pm {
 namespace tdtc {
 
 template <int K>
+using DirShape = Shape<K, false, half_of<K>()>;
+
+template <int K>
 struct DirParams {
-    float W[Shape<K>::NP * Shape<K>::WS];
+    float W[DirShape<K>::NP * DirShape<K>::WS];
+    float inv_s;  // FP16 operands: 1 / (power-of-two scale of W)
     double ga[kMaxBoundary];
     double gb[kMaxBoundary];
     double R, quad, f_const, dt;
@@ -61,9 +65,10 @@ __device__ __forceinline__ void dir_finish(const DirParams<K>& p, int64_t pid, b
 }
 
 template <int K>
-__global__ void __launch_bounds__(128, Shape<K>::MIN_CTAS) dirichlet_tc_kernel(const __grid_constant__ DirParams<K> p)
+__global__ void __launch_bounds__(128, DirShape<K>::MIN_CTAS) dirichlet_tc_kernel(const __grid_constant__ DirParams<K> p)
 {
-    using S = Shape<K>;
+    using S = DirShape<K>;
+    constexpr bool H = S::HALF;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     uint8_t* A_hi = smem;
@@ -76,20 +81,7 @@ __global__ void __launch_bounds__(128, Shape<K>::MIN_CTAS) dirichlet_tc_kernel(c
     const unsigned full = 0xffffffffu;
     const uint32_t bar_a = tc::smem_u32(bar);
 
-    for (int q = tid; q < S::NP * S::KC; q += 128) {
-        const int r = q / S::KC, c = q - r * S::KC;
-        float4 h, l;
-        float* hv = &h.x;
-        float* lv = &l.x;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const float w = p.W[r * S::WS + 4 * c + e];
-            hv[e] = to_tf32(w);
-            lv[e] = to_tf32(w - hv[e]);
-        }
-        *reinterpret_cast<float4*>(B_hi + tile_off<S::KC>(r, c)) = h;
-        *reinterpret_cast<float4*>(B_lo + tile_off<S::KC>(r, c)) = l;
-    }
+    stage_B<S>(B_hi, B_lo, tid, [&](int q) { return p.W[q]; });
     for (int c = 0; c < S::KC; ++c) {
         *reinterpret_cast<float4*>(A_hi + tile_off<S::KC>(tid, c)) = make_float4(0.f, 0.f, 0.f, 0.f);
         *reinterpret_cast<float4*>(A_lo + tile_off<S::KC>(tid, c)) = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -163,20 +155,20 @@ __global__ void __launch_bounds__(128, Shape<K>::MIN_CTAS) dirichlet_tc_kernel(c
             {
                 float C2[K + 1], S2[K + 1];
                 fourier_powers<float, K>(X2.val(), C2, S2);
-                float a[4 * S::KC];
+                float a[S::WS];
 #pragma unroll
-                for (int q = 0; q < 4 * S::KC; ++q) a[q] = 0.f;
+                for (int q = 0; q < S::WS; ++q) a[q] = 0.f;
 #pragma unroll
                 for (int q = 1; q <= K; ++q) { a[q - 1] = S2[q]; a[K + q - 1] = C2[q]; }
                 a[2 * K] = 1.f;
-                write_row<K>(sb + row, a);
+                write_row<K, false, H>(sb + row, a);
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             // One barrier per step: the rows are in place, and a wait that gave
             // up in the previous step (any thread) stops the whole CTA.
             if (__syncthreads_or(failed)) { stop = true; break; }
-            if (tid == 0) issue_step_mma<K>(tmem, sb, bar_a);
+            if (tid == 0) issue_step_mma<K, false, H>(tmem, sb, bar_a);
             // While the product runs: the Brownian increment and the x1 harmonics.
             float xi1, xi2;
             box_muller<float>(half ? r.z : r.x, half ? r.w : r.y, xi1, xi2);
@@ -186,7 +178,7 @@ __global__ void __launch_bounds__(128, Shape<K>::MIN_CTAS) dirichlet_tc_kernel(c
             phase ^= 1u;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             float v1, v2;
-            velocity_from_tmem<K>(t_row, C1, S1, v1, v2);
+            velocity_from_tmem<K, H>(t_row, C1, S1, v1, v2, p.inv_s);
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             if (pid >= 0) {
                 em_update<float>(X1, v1, p.drift_dt, p.s_dt, xi1);
@@ -215,9 +207,10 @@ __global__ void __launch_bounds__(128, Shape<K>::MIN_CTAS) dirichlet_tc_kernel(c
 template <int K>
 cudaError_t launch_dirichlet_tc(const DirichletLaunch& L, unsigned* err, cudaStream_t stream)
 {
-    using S = Shape<K>;
+    using S = DirShape<K>;
     DirParams<K> p;
-    build_W<K>(L.coef, p.W);
+    build_W<K, false, S::HALF>(L.coef, p.W);
+    p.inv_s = scale_W_host<S>(p.W, nullptr, 0);
     for (int m = 0; m < kMaxBoundary; ++m) {
         p.ga[m] = m < L.n_ang ? L.ga[m] : 0.0;
         p.gb[m] = m < L.n_ang ? L.gb[m] : 0.0;
@@ -257,7 +250,7 @@ cudaError_t launch_dirichlet_tc(const DirichletLaunch& L, unsigned* err, cudaStr
 template <int K>
 int dirichlet_tc_blocks_per_sm()
 {
-    using S = Shape<K>;
+    using S = DirShape<K>;
     cudaFuncSetAttribute(dirichlet_tc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
     return resident_ctas((const void*)dirichlet_tc_kernel<K>, 128, S::SMEM, (int)S::TMEM_COLS);
 }

@@ -53,12 +53,16 @@ inline bool wide_K(int K) { return K == 24 || K == 32 || K == 40; }
 
 // Floats of the device table a wide-K launch needs: the product-basis table
 // (8 (K+1)^2) of the FP32-pipe kernel or the padded W^T of the tensor-core
-// kernel (NP x 4 KC, NP = 4K+1 rounded up to 16, KC = 2 ceil((2K+1)/8)).
+// kernel (NP rows of 2 ceil((2K+1)/8) chunks of 4 TF32, or of
+// 2 ceil((2K+1)/16) chunks of 8 FP16; NP = 4K+1 rounded up to 16), whichever
+// is largest.
 inline int64_t wide_table_floats(int K)
 {
     const int64_t simt = 8 * (int64_t)(K + 1) * (K + 1);
-    const int64_t np = (4 * K + 1 + 15) / 16 * 16, kc = 2 * ((2 * K + 1 + 7) / 8);
-    const int64_t tc = np * 4 * kc;
+    const int64_t np = (4 * K + 1 + 15) / 16 * 16;
+    const int64_t tf32 = np * 4 * (2 * ((2 * K + 1 + 7) / 8));
+    const int64_t f16 = np * 8 * (2 * ((2 * K + 1 + 15) / 16));
+    const int64_t tc = tf32 > f16 ? tf32 : f16;
     return simt > tc ? simt : tc;
 }
 

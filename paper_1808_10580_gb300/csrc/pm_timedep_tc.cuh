@@ -23,6 +23,9 @@
 // tcgen05.ld.
 #pragma once
 #include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <cuda_fp16.h>
 #include "pm_gemm_tc.cuh"
 #include "pm_kernels.cuh"
 
@@ -33,18 +36,26 @@ namespace tdtc {
 // m = 0 column of P (the x1-independent part of v1) leave the product and are
 // summed on the FP32 pipes (4K FMAs per particle), so that A has 2K columns
 // and P 4K: for K a multiple of 4 that saves one MMA k-step and 16 columns of N.
-template <int K, bool F = false>
+//
+// H ("half"): the operands are FP16 instead of TF32 (kind::f16).  FP16 keeps
+// the same 11 significant bits as TF32, so the same hi + lo split and three
+// products give the same accuracy, with half the tile bytes and twice the MMA
+// rate; W is scaled by a power of two so that its entries sit in FP16's
+// normal range, and the accumulator is scaled back exactly.
+template <int K, bool F = false, bool H = false>
 struct Shape {
     static constexpr bool FOLD = F;
+    static constexpr bool HALF = H;
+    static constexpr int EPC = H ? 8 : 4;             // operand elements per 16-byte chunk
     static constexpr int KD = F ? 2 * K : 2 * K + 1;  // A columns used
-    static constexpr int KS = (KD + 7) / 8;           // MMA k-steps (K = 8 per tf32 instruction)
-    static constexpr int KC = 2 * KS;                 // 16-byte chunks (4 tf32) per tile row
-    static constexpr int WS = 4 * KC;                 // row stride of W (tf32 entries)
+    static constexpr int KS = (KD + 2 * EPC - 1) / (2 * EPC);  // MMA k-steps (two chunks each)
+    static constexpr int KC = 2 * KS;                 // 16-byte chunks per tile row
+    static constexpr int WS = EPC * KC;               // row stride of W (elements)
     static constexpr int NC = F ? 4 * K : 4 * K + 1;  // accumulator columns used
     static constexpr int NP = (NC + 15) / 16 * 16;    // MMA N (multiple of 16)
     static constexpr int SBO = KC * 128;              // bytes between 8-row groups of a tile
-    static constexpr int A_BYTES = 128 * KC * 16;     // 128 rows x 8 KS tf32
-    static constexpr int B_BYTES = NP * KC * 16;      // NP rows x 8 KS tf32
+    static constexpr int A_BYTES = 128 * KC * 16;     // 128 rows x KC chunks
+    static constexpr int B_BYTES = NP * KC * 16;      // NP rows x KC chunks
     static constexpr int SMEM = 2 * A_BYTES + 2 * B_BYTES + 128 + 64;
     // allocation: a power of 2 >= 32
     static constexpr uint32_t TMEM_COLS = NP <= 64 ? 64u : NP <= 128 ? 128u : 256u;
@@ -62,12 +73,32 @@ struct Shape {
 // unfolded on the 300 x 1e4-path workload).
 template <int K>
 constexpr bool fold_of() { return K % 4 == 0 && K >= 8 && K != 24; }
+// FP16 operands where they measured faster: from K = 10 on (K <= 8: the
+// product is small and the wider split costs more than the MMA time it saves).
 template <int K>
-using TdShape = Shape<K, fold_of<K>()>;
+constexpr bool half_of() { return K >= 10; }
+template <int K>
+using TdShape = Shape<K, fold_of<K>(), half_of<K>()>;
 
 // Instruction descriptor, kind::tf32: FP32 accumulator, TF32 A and B, both K-major.
 template <int NP>
 __host__ __device__ constexpr uint32_t idesc_tf32() { return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NP >> 3) << 17) | ((uint32_t)(128 >> 4) << 24); }
+
+// Instruction descriptor, kind::f16: FP32 accumulator, FP16 A and B (both the
+// same type), both K-major.
+template <int NP>
+__host__ __device__ constexpr uint32_t idesc_f16() { return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(NP >> 3) << 17) | ((uint32_t)(128 >> 4) << 24); }
+
+// hi = a rounded to FP16, lo = (a - hi) rounded to FP16, two values packed per
+// word (a0 in the low half); the dropped remainder is ~2^-22 |a|.
+__device__ __forceinline__ void split_f16x2(float a0, float a1, uint32_t& hi, uint32_t& lo)
+{
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(a1), "f"(a0));
+    __half2 h2;
+    memcpy(&h2, &hi, 4);
+    const float2 f = __half22float2(h2);
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(a1 - f.y), "f"(a0 - f.x));
+}
 
 __device__ __forceinline__ float to_tf32(float x)
 {
@@ -138,6 +169,7 @@ struct Params {
     // and the n = 0 coefficients of v2 (C1m at m-1, S1m at K+m-1).
     float T0[2 * K];
     float N0[2 * K];
+    float inv_s;              // FP16 operands: 1 / (power-of-two scale of W)
     Theta0Table<float> th;
     const ObsRec* obs;
     const int32_t* order;
@@ -152,6 +184,16 @@ struct Params {
     const int4* groups;       // shared paths: {m0, m1, stream, nmax} per grid row, or nullptr
     const int32_t* members;   // [n_obs] observation indices of the groups
 };
+
+template <int NP>
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc_f16<NP>()), "r"(accumulate)
+        : "memory");
+}
 
 template <int NP>
 __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate)
@@ -192,9 +234,9 @@ __device__ __forceinline__ void split_tf32(float a, float& hi, float& lo)
 //   v1 = P(0) + sum_m C1m P1c(m) + S1m P1s(m)      (columns 0 .. 2K),
 //   v2 = sum_m C1m P2c(m)  +  sum_m S1m P2s(m)      (columns 2K+1 .. 4K).
 // Terms are added in the order of their columns within each sum.
-template <int K>
+template <int K, bool H = false>
 __device__ __forceinline__ void velocity_from_tmem(uint32_t t_row, const float (&C1)[K + 1], const float (&S1)[K + 1],
-                                                   float& v1, float& v2)
+                                                   float& v1, float& v2, float inv_s = 1.f)
 {
     constexpr int NP = Shape<K, false>::NP;
     float v1c = 0.f, v1s = 0.f, v2c = 0.f, v2s = 0.f, p0 = 0.f;
@@ -214,16 +256,20 @@ __device__ __forceinline__ void velocity_from_tmem(uint32_t t_row, const float (
     }
     v1 = p0 + (v1c + v1s);
     v2 = v2c + v2s;
+    if constexpr (H) {
+        v1 *= inv_s;
+        v2 *= inv_s;
+    }
 }
 
 // Folded shape: columns m-1, K+m-1, 2K+m-1, 3K+m-1 hold P1c(m), P1s(m), and
 // P2c(m), P2s(m) without their n = 0 terms N0, which are added here before the
 // multiplication by the x1 harmonic; p0 (the m = 0 part of v1) comes from the
 // FP32 pipes.  The sums run over m in the same order as in the unfolded form.
-template <int K>
+template <int K, bool H = false>
 __device__ __forceinline__ void velocity_from_tmem_folded(uint32_t t_row, const float (&C1)[K + 1],
                                                           const float (&S1)[K + 1], const float* N0, float p0,
-                                                          float& v1, float& v2)
+                                                          float& v1, float& v2, float inv_s = 1.f)
 {
     constexpr int NP = Shape<K, true>::NP;
     float v1c = 0.f, v1s = 0.f, v2c = 0.f, v2s = 0.f;
@@ -241,8 +287,74 @@ __device__ __forceinline__ void velocity_from_tmem_folded(uint32_t t_row, const 
             else if (blk == 3) v2s = fmaf(S1[m], a[e] + N0[K + m - 1], v2s);
         }
     }
-    v1 = p0 + (v1c + v1s);
-    v2 = v2c + v2s;
+    if constexpr (H) {
+        v1 = p0 + inv_s * (v1c + v1s);  // N0 carries the scale of W
+        v2 = inv_s * (v2c + v2s);
+    } else {
+        v1 = p0 + (v1c + v1s);
+        v2 = v2c + v2s;
+    }
+}
+
+// Exponent e of the power-of-two scale of W for FP16 operands: the largest
+// |entry| times 2^e lies in [2^13, 2^14) (e = 0 for a zero W).
+__host__ __device__ inline int w_scale_exp(float wmax)
+{
+    if (!(wmax > 0.f)) return 0;
+    int E = 0;
+    frexpf(wmax, &E);  // wmax = f 2^E, f in [1/2, 1)
+    const int e = 14 - E;
+    return e < -60 ? -60 : (e > 60 ? 60 : e);
+}
+
+// The coefficient tiles (hi / lo) of the B operand from W^T: entry k of row nc
+// is w(nc * WS + k), already scaled for FP16 operands.
+template <typename S, typename Load>
+__device__ __forceinline__ void stage_B(uint8_t* B_hi, uint8_t* B_lo, int tid, Load w)
+{
+    for (int q = tid; q < S::NP * S::KC; q += 128) {
+        const int r = q / S::KC, c = q - r * S::KC;
+        if constexpr (S::HALF) {
+            uint32_t hv[4], lv[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int i0 = r * S::WS + 8 * c + 2 * e;
+                split_f16x2(w(i0), w(i0 + 1), hv[e], lv[e]);
+            }
+            *reinterpret_cast<uint4*>(B_hi + tile_off<S::KC>(r, c)) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+            *reinterpret_cast<uint4*>(B_lo + tile_off<S::KC>(r, c)) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+        } else {
+            float4 h, l;
+            float* hv = &h.x;
+            float* lv = &l.x;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float x = w(r * S::WS + 4 * c + e);
+                hv[e] = to_tf32(x);
+                lv[e] = to_tf32(x - hv[e]);
+            }
+            *reinterpret_cast<float4*>(B_hi + tile_off<S::KC>(r, c)) = h;
+            *reinterpret_cast<float4*>(B_lo + tile_off<S::KC>(r, c)) = l;
+        }
+    }
+}
+
+// Host: scales W (and the n = 0 terms of a folded shape, N0[2K]) by 2^e for
+// FP16 operands; returns 2^-e, the factor that undoes it.
+template <typename S>
+float scale_W_host(float* W, float* N0, int nN0)
+{
+    if constexpr (!S::HALF) {
+        return 1.f;
+    } else {
+        float wmax = 0.f;
+        for (int q = 0; q < S::NP * S::WS; ++q) wmax = std::max(wmax, std::fabs(W[q]));
+        const int e = w_scale_exp(wmax);
+        const float sc = std::ldexp(1.f, e);
+        for (int q = 0; q < S::NP * S::WS; ++q) W[q] *= sc;
+        for (int q = 0; q < nN0; ++q) N0[q] *= sc;
+        return std::ldexp(1.f, -e);
+    }
 }
 
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, const float4& v)
@@ -253,37 +365,62 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, const float4& v)
 // Tiles at shared address sb: A_hi, A_lo (A_BYTES each), then B_hi, B_lo.
 // This thread's row of the particle tiles (row = sb + tile_off(r, 0); chunk c
 // 128 c bytes further): harmonics a[0..KD) split into hi / lo.
-template <int K, bool F = false>
-__device__ __forceinline__ void write_row(uint32_t row, const float (&a)[4 * Shape<K, F>::KC])
+__device__ __forceinline__ void st_shared_v4u(uint32_t addr, const uint32_t (&v)[4])
 {
-    using S = Shape<K, F>;
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]) : "memory");
+}
+
+template <int K, bool F = false, bool H = false>
+__device__ __forceinline__ void write_row(uint32_t row, const float (&a)[Shape<K, F, H>::WS])
+{
+    using S = Shape<K, F, H>;
+    if constexpr (H) {
 #pragma unroll
-    for (int c = 0; c < (S::KD + 3) / 4; ++c) {
-        float4 h, l;
-        split_tf32(a[4 * c], h.x, l.x);
-        split_tf32(a[4 * c + 1], h.y, l.y);
-        split_tf32(a[4 * c + 2], h.z, l.z);
-        split_tf32(a[4 * c + 3], h.w, l.w);
-        st_shared_v4(row + 128u * c, h);
-        st_shared_v4(row + (uint32_t)S::A_BYTES + 128u * c, l);
+        for (int c = 0; c < (S::KD + 7) / 8; ++c) {
+            uint32_t h[4], l[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) split_f16x2(a[8 * c + 2 * q], a[8 * c + 2 * q + 1], h[q], l[q]);
+            st_shared_v4u(row + 128u * c, h);
+            st_shared_v4u(row + (uint32_t)S::A_BYTES + 128u * c, l);
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < (S::KD + 3) / 4; ++c) {
+            float4 h, l;
+            split_tf32(a[4 * c], h.x, l.x);
+            split_tf32(a[4 * c + 1], h.y, l.y);
+            split_tf32(a[4 * c + 2], h.z, l.z);
+            split_tf32(a[4 * c + 3], h.w, l.w);
+            st_shared_v4(row + 128u * c, h);
+            st_shared_v4(row + (uint32_t)S::A_BYTES + 128u * c, l);
+        }
     }
 }
 
 // One Euler step's product, issued by one thread: P = A_hi W_hi + A_lo W_hi +
 // A_hi W_lo over the KS k-steps, then a commit to the step's mbarrier.
-template <int K, bool F = false>
+template <int K, bool F = false, bool H = false>
 __device__ __forceinline__ void issue_step_mma(uint32_t tmem, uint32_t sb, uint32_t bar)
 {
-    using S = Shape<K, F>;
+    using S = Shape<K, F, H>;
     const uint64_t ah = tile_desc<S::SBO>(sb), al = tile_desc<S::SBO>(sb + S::A_BYTES);
     const uint64_t bh = tile_desc<S::SBO>(sb + 2 * S::A_BYTES), bl = tile_desc<S::SBO>(sb + 2 * S::A_BYTES + S::B_BYTES);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if constexpr (H) {
 #pragma unroll
-    for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, ah + kKStep * k, bh + kKStep * k, k > 0 ? 1u : 0u);
+        for (int k = 0; k < S::KS; ++k) mma_f16<S::NP>(tmem, ah + kKStep * k, bh + kKStep * k, k > 0 ? 1u : 0u);
 #pragma unroll
-    for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, al + kKStep * k, bh + kKStep * k, 1u);
+        for (int k = 0; k < S::KS; ++k) mma_f16<S::NP>(tmem, al + kKStep * k, bh + kKStep * k, 1u);
 #pragma unroll
-    for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, ah + kKStep * k, bl + kKStep * k, 1u);
+        for (int k = 0; k < S::KS; ++k) mma_f16<S::NP>(tmem, ah + kKStep * k, bl + kKStep * k, 1u);
+    } else {
+#pragma unroll
+        for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, ah + kKStep * k, bh + kKStep * k, k > 0 ? 1u : 0u);
+#pragma unroll
+        for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, al + kKStep * k, bh + kKStep * k, 1u);
+#pragma unroll
+        for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, ah + kKStep * k, bl + kKStep * k, 1u);
+    }
     tc::mma_commit(bar);
 }
 
@@ -292,6 +429,7 @@ __global__ void __launch_bounds__(128, TdShape<K>::MIN_CTAS) timedep_tc_kernel(c
 {
     using S = TdShape<K>;
     constexpr bool F = S::FOLD;
+    constexpr bool H = S::HALF;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     uint8_t* A_hi = smem;
@@ -304,20 +442,8 @@ __global__ void __launch_bounds__(128, TdShape<K>::MIN_CTAS) timedep_tc_kernel(c
     const uint32_t bar_a = tc::smem_u32(bar);
 
     // Coefficient tiles (hi / lo) and zero padding of the particle tiles.
-    for (int q = tid; q < S::NP * S::KC; q += 128) {
-        const int r = q / S::KC, c = q - r * S::KC;
-        float4 h, l;
-        float* hv = &h.x;
-        float* lv = &l.x;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const float w = S::W_PARAM ? p.W[r * S::WS + 4 * c + e] : __ldg(p.Wg + r * S::WS + 4 * c + e);
-            hv[e] = to_tf32(w);
-            lv[e] = to_tf32(w - hv[e]);
-        }
-        *reinterpret_cast<float4*>(B_hi + tile_off<S::KC>(r, c)) = h;
-        *reinterpret_cast<float4*>(B_lo + tile_off<S::KC>(r, c)) = l;
-    }
+    if constexpr (S::W_PARAM) stage_B<S>(B_hi, B_lo, tid, [&](int q) { return p.W[q]; });
+    else stage_B<S>(B_hi, B_lo, tid, [&](int q) { return __ldg(p.Wg + q); });
     for (int c = 0; c < S::KC; ++c) {
         *reinterpret_cast<float4*>(A_hi + tile_off<S::KC>(tid, c)) = make_float4(0.f, 0.f, 0.f, 0.f);
         *reinterpret_cast<float4*>(A_lo + tile_off<S::KC>(tid, c)) = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -395,9 +521,9 @@ __global__ void __launch_bounds__(128, TdShape<K>::MIN_CTAS) timedep_tc_kernel(c
         {
             float C2[K + 1], S2[K + 1];
             fourier_powers<float, K>(X2.val(), C2, S2);
-            float a[4 * S::KC];
+            float a[S::WS];
 #pragma unroll
-            for (int q = 0; q < 4 * S::KC; ++q) a[q] = 0.f;
+            for (int q = 0; q < S::WS; ++q) a[q] = 0.f;
 #pragma unroll
             for (int q = 1; q <= K; ++q) { a[q - 1] = S2[q]; a[K + q - 1] = C2[q]; }
             if constexpr (F) {
@@ -412,14 +538,14 @@ __global__ void __launch_bounds__(128, TdShape<K>::MIN_CTAS) timedep_tc_kernel(c
             } else {
                 a[2 * K] = 1.f;
             }
-            write_row<K, F>(sb + row, a);
+            write_row<K, F, H>(sb + row, a);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         // One barrier per step: the rows are in place, and a wait that gave up
         // in the previous step (any thread) ends the loop for the whole CTA.
         if (__syncthreads_or(failed)) { failed = true; break; }
-        if (tid == 0) issue_step_mma<K, F>(tmem, sb, bar_a);
+        if (tid == 0) issue_step_mma<K, F, H>(tmem, sb, bar_a);
         // While the product runs: the Brownian increment and the x1 harmonics.
         if ((n & 1) == 0) r = philox4x32_10(u32x4{(uint32_t)(n >> 1), pid, (uint32_t)stream, p.inst}, p.key0, p.key1);
         float xi1, xi2;
@@ -429,8 +555,8 @@ __global__ void __launch_bounds__(128, TdShape<K>::MIN_CTAS) timedep_tc_kernel(c
         failed = !tc::mbar_wait(bar_a, (uint32_t)(n & 1));
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         float v1, v2;
-        if constexpr (F) velocity_from_tmem_folded<K>(t_row, C1, S1, p.N0, p0, v1, v2);
-        else velocity_from_tmem<K>(t_row, C1, S1, v1, v2);
+        if constexpr (F) velocity_from_tmem_folded<K, H>(t_row, C1, S1, p.N0, p0, v1, v2, p.inv_s);
+        else velocity_from_tmem<K, H>(t_row, C1, S1, v1, v2, p.inv_s);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         // Members whose last step is this one take it with their own length.
         while (n == stop) {
@@ -463,10 +589,10 @@ __global__ void __launch_bounds__(128, TdShape<K>::MIN_CTAS) timedep_tc_kernel(c
 }
 
 // W^T of the product-basis table t[(m (K+1) + n) 8 + q] (e0..e3, f0..f3).
-template <int K, bool F = false>
+template <int K, bool F = false, bool H = false>
 void build_W(const double* t, float* W)
 {
-    using S = Shape<K, F>;
+    using S = Shape<K, F, H>;
     for (int q = 0; q < S::NP * S::WS; ++q) W[q] = 0.f;
     auto T = [&](int m, int n, int q) { return t[(size_t)(m * (K + 1) + n) * 8 + q]; };
     auto set = [&](int col, int row, double v) { W[col * S::WS + row] = (float)v; };
@@ -516,14 +642,18 @@ cudaError_t launch_timedep_tc(const TimedepLaunch& L, unsigned* err, cudaStream_
             p.N0[K + n - 1] = (float)T(n, 0, 6);  // n = 0 term of P2s(m = n)
         }
     }
+    // FP16 operands: W (and the n = 0 terms that join its columns) times 2^e,
+    // with the largest entry in [2^13, 2^14), far inside FP16's range.
+    std::vector<float> Wv((size_t)(S::NP * S::WS));
+    build_W<K, S::FOLD, S::HALF>(L.coef, Wv.data());
+    p.inv_s = scale_W_host<S>(Wv.data(), p.N0, S::FOLD ? 2 * K : 0);
     if constexpr (S::W_PARAM) {
-        build_W<K, S::FOLD>(L.coef, p.W);
+        for (size_t q = 0; q < Wv.size(); ++q) p.W[q] = Wv[q];
     } else {
         // Into the caller's device buffer (the host vector is read before the
         // copy call returns).
         if (!L.table_dev) return cudaErrorInvalidValue;
-        std::vector<float> W((size_t)(S::NP * S::WS));
-        build_W<K, S::FOLD>(L.coef, W.data());
+        std::vector<float>& W = Wv;
         const cudaError_t e = cudaMemcpyAsync(L.table_dev, W.data(), W.size() * sizeof(float), cudaMemcpyHostToDevice, stream);
         if (e != cudaSuccess) return e;
         p.Wg = L.table_dev;
