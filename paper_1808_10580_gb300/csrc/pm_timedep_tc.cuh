@@ -90,14 +90,18 @@ template <int NP>
 __host__ __device__ constexpr uint32_t idesc_f16() { return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(NP >> 3) << 17) | ((uint32_t)(128 >> 4) << 24); }
 
 // hi = a rounded to FP16, lo = (a - hi) rounded to FP16, two values packed per
-// word (a0 in the low half); the dropped remainder is ~2^-22 |a|.
+// word (a0 in the low half); the dropped remainder is ~2^-22 |a|.  a - hi is
+// formed by the mixed-precision FMA (FP16 operands, FP32 addend) hi * (-1) + a,
+// which is exact, so no separate widening of hi is needed.
 __device__ __forceinline__ void split_f16x2(float a0, float a1, uint32_t& hi, uint32_t& lo)
 {
     asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(a1), "f"(a0));
-    __half2 h2;
-    memcpy(&h2, &hi, 4);
-    const float2 f = __half22float2(h2);
-    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(a1 - f.y), "f"(a0 - f.x));
+    float r0, r1;
+    asm("{\n .reg .b16 h0, h1, m1;\n mov.b32 {h0, h1}, %2;\n mov.b16 m1, 0xBC00;\n"
+        " fma.rn.f32.f16 %0, h0, m1, %3;\n fma.rn.f32.f16 %1, h1, m1, %4;\n}\n"
+        : "=f"(r0), "=f"(r1)
+        : "r"(hi), "f"(a0), "f"(a1));
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(r1), "f"(r0));
 }
 
 __device__ __forceinline__ float to_tf32(float x)
