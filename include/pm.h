@@ -22,7 +22,7 @@
  *   (2K+1)^2 - 1 doubles.  v = (-d psi/dx2, d psi/dx1), i.e. the paper's
  *   k_perp = (-k_y, k_x) direction.  Supported K: 0..6, 8, 10, 12, 16; the
  *   time-dependent map with float paths also takes the wide bounds K = 24,
- *   32, 40 (N_u = 2400, 4224, 6560; PM_EINVAL elsewhere).
+ *   32, 40, 48, 56, 64 (N_u = 2400 ... 16640; PM_EINVAL elsewhere).
  * Random numbers.  Step n of path i of observation j in instance b draws
  *   Philox4x32-10 (Salmon et al., SC'11) on counter {n/2, i, j, b} under key
  *   {seed & 0xffffffff, seed >> 32}; words (r0, r1) feed even n and (r2, r3)
@@ -81,7 +81,7 @@ extern "C" {
  * three-term hi/lo split of TF32 operands for K <= 8 and of FP16 operands,
  * with W scaled by a power of two, from K = 10: about float accuracy, results
  * differ from the FP32-pipe kernels by rounding); supported for K in
- * {4, 5, 6, 8, 10, 12, 16} (and K = 24, 32, 40 for the time-dependent map),
+ * {4, 5, 6, 8, 10, 12, 16} (and the wide K for the time-dependent map),
  * other K run on the FP32 pipes. */
 #define PM_TENSOR 8u
 /* pm_forward_timedep: observations at bit-identical points x

@@ -209,7 +209,7 @@ int check_field(const pm_field* f, bool allow_wide)
         // accepted: the time-dependent map with float paths (checked by the caller)
     } else if (!supported_K(f->K)) {
         return fail(PM_EINVAL, "K=%d is not one of the compiled bounds 0..6, 8, 10, 12, 16%s", f->K,
-                    allow_wide ? " (24, 32, 40: float paths)" : "");
+                    allow_wide ? " (24, 32, 40, 48, 56, 64: float paths)" : "");
     }
     const int64_t nu = (int64_t)(2 * f->K + 1) * (2 * f->K + 1) - 1;
     if (nu > 0 && !f->u) return fail(PM_EINVAL, "field coefficients are NULL");
@@ -554,13 +554,19 @@ int pm_forward_timedep(pm_ctx* c, const pm_field* field, double kappa, const pm_
         case 24: e = tdtc::launch_timedep_tc<24>(L, W.err + 1, c->stream); break;
         case 32: e = tdtc::launch_timedep_tc<32>(L, W.err + 1, c->stream); break;
         case 40: e = tdtc::launch_timedep_tc<40>(L, W.err + 1, c->stream); break;
+        case 48: e = tdtc::launch_timedep_tc<48>(L, W.err + 1, c->stream); break;
+        case 56: e = tdtc::launch_timedep_tc<56>(L, W.err + 1, c->stream); break;
+        case 64: e = tdtc::launch_timedep_tc<64>(L, W.err + 1, c->stream); break;
         default: e = tdtc::launch_timedep_tc<16>(L, W.err + 1, c->stream); break;
         }
     } else if (wide) {
         switch (K) {
         case 24: e = launch_timedep<float, 24>(L, c->stream); break;
         case 32: e = launch_timedep<float, 32>(L, c->stream); break;
-        default: e = launch_timedep<float, 40>(L, c->stream); break;
+        case 40: e = launch_timedep<float, 40>(L, c->stream); break;
+        case 48: e = launch_timedep<float, 48>(L, c->stream); break;
+        case 56: e = launch_timedep<float, 56>(L, c->stream); break;
+        default: e = launch_timedep<float, 64>(L, c->stream); break;
         }
     } else {
         e = fp64 ? dispatch_timedep<double>(K, L, c->stream) : dispatch_timedep<float>(K, L, c->stream);

@@ -49,7 +49,7 @@ struct TimedepLaunch {
 };
 
 // Wave-number bounds of the time-dependent map beyond the unrolled kernels.
-inline bool wide_K(int K) { return K == 24 || K == 32 || K == 40; }
+inline bool wide_K(int K) { return K == 24 || K == 32 || K == 40 || K == 48 || K == 56 || K == 64; }
 
 // Floats of the device table a wide-K launch needs: the product-basis table
 // (8 (K+1)^2) of the FP32-pipe kernel or the padded W^T of the tensor-core

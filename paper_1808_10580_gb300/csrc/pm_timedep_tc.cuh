@@ -242,7 +242,7 @@ template <int K, bool H = false>
 __device__ __forceinline__ void velocity_from_tmem(uint32_t t_row, const float (&C1)[K + 1], const float (&S1)[K + 1],
                                                    float& v1, float& v2, float inv_s = 1.f)
 {
-    constexpr int NP = Shape<K, false>::NP;
+    constexpr int NP = (4 * K + 1 + 15) / 16 * 16;  // as Shape<K, false, H>::NP
     float v1c = 0.f, v1s = 0.f, v2c = 0.f, v2s = 0.f, p0 = 0.f;
 #pragma unroll
     for (int q = 0; q < NP / 16; ++q) {
@@ -275,7 +275,7 @@ __device__ __forceinline__ void velocity_from_tmem_folded(uint32_t t_row, const 
                                                           const float (&S1)[K + 1], const float* N0, float p0,
                                                           float& v1, float& v2, float inv_s = 1.f)
 {
-    constexpr int NP = Shape<K, true>::NP;
+    constexpr int NP = (4 * K + 15) / 16 * 16;  // as Shape<K, true, H>::NP
     float v1c = 0.f, v1s = 0.f, v2c = 0.f, v2s = 0.f;
 #pragma unroll
     for (int q = 0; q < NP / 16; ++q) {

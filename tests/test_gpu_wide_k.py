@@ -1,5 +1,5 @@
-"""The time-dependent map at the wide wave-number bounds K = 24, 32, 40
-(N_u = 2400, 4224, 6560 real coefficients; Section 4's larger Fourier bases):
+"""The time-dependent map at the wide wave-number bounds K = 24 ... 64
+(N_u = 2400 ... 16640 real coefficients; Section 4's larger Fourier bases):
 the FP32-pipe kernel with its velocity table in shared memory and the
 tensor-core kernel with 256 accumulator columns, each against the FP64 oracle,
 against each other, and with shared paths against single-observation calls."""
@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 pm = _gpu.pm
 torch = _gpu.torch
 TC = pm.PM_FP32 | pm.PM_TENSOR
-WIDE = [24, 32, 40]
+WIDE = [24, 32, 40, 48, 56, 64]
 
 
 @pytest.fixture(scope="module")
@@ -69,21 +69,22 @@ def test_shear_at_the_highest_modes_matches_oracle(c, orc, K):
 
 @pytest.mark.parametrize("K", WIDE)
 def test_tensor_and_pipes_agree_on_a_prior_field(c, K):
-    # A prior draw, 8 points x 2000 paths (a ragged last tile).  Over 10 steps the
+    # A prior draw, 8 points x 2000 paths (a ragged last tile).  Over a few steps the
     # two float kernels' paths stay together; over 100 steps the flow's stretching
-    # (velocity gradients grow with the number of modes) separates paths that
-    # differ by rounding, so the estimates agree in distribution only.
+    # (the velocity gradient of a prior draw grows like the square root of the
+    # number of modes) separates paths that differ by rounding, so the estimates
+    # agree in distribution only.
     w = wide_workload(K, 2000, n_pts=8)
-    w.t = np.full(8, 0.01)
+    w.t = np.full(8, 0.003)
     _, _, g_tc = _gpu.timedep(c, w, TC, g_out=True)
     _, _, g_sm = _gpu.timedep(c, w, pm.PM_FP32, g_out=True)
-    assert np.median(np.abs(g_tc - g_sm)) <= 1e-4
+    assert np.median(np.abs(g_tc - g_sm)) <= 1e-4, np.median(np.abs(g_tc - g_sm))
     w.t = np.full(8, 0.1)
     m_tc, v_tc, g_tc = _gpu.timedep(c, w, TC, g_out=True)
     m_sm, v_sm, g_sm = _gpu.timedep(c, w, pm.PM_FP32, g_out=True)
     assert np.all(np.isfinite(g_tc)) and np.all(np.isfinite(g_sm))
     se = np.sqrt((v_tc + v_sm) / w.M)
-    assert np.all(np.abs(m_tc - m_sm) <= 5 * se + 1e-6)
+    assert np.all(np.abs(m_tc - m_sm) <= 5 * se + 1e-6), (m_tc - m_sm) / se
 
 
 @pytest.mark.parametrize("tensor", [False, True])
