@@ -6,21 +6,19 @@
 //   a = (S2_1..S2_K, C2_1..C2_K, 1).
 // For the 128 particles of a CTA this is one matrix product per Euler step,
 //   P[128 x (4K+1)] = A[128 x (2K+1)] . W[(2K+1) x (4K+1)],
-// issued as tcgen05.mma kind::tf32 with the FP32 accumulator in tensor memory.
-// TF32 keeps 10 mantissa bits, so every operand is split x = hi + lo (the
-// coefficients: hi = x rounded to TF32, lo = (x - hi) rounded; the particle
-// harmonics, every step: hi = x with its low 13 bits cleared, lo = x - hi) and
-// three products hi.hi + lo.hi + hi.lo are accumulated (the lo.lo term and
-// the reduction of lo, ~2^-20 relative, are dropped): close to float
-// accuracy.  The remaining 4K+1 FMAs per particle, the harmonics, the noise
-// and the Euler step stay on the FP32 pipes.
+// issued as tcgen05.mma with the FP32 accumulator in tensor memory: kind::tf32
+// for K <= 8, kind::f16 with FP16 operands from K = 10 (see Shape).  Both
+// operand types keep 11 significant bits, so every operand is split
+// x = hi + lo and three products hi.hi + lo.hi + hi.lo are accumulated (the
+// lo.lo term and the rounding of lo, ~2^-21 relative, are dropped): close to
+// float accuracy.  The remaining 4K+1 FMAs per particle, the harmonics, the
+// noise and the Euler step stay on the FP32 pipes.
 //
 // Per step: every thread writes its particle's row of A (hi and lo) into a
 // K-major tile (layout at tile_off), a CTA barrier hands the tile to the
-// tensor core (one thread issues 3 x ceil((2K+1)/8) MMAs and commits to an
-// mbarrier), the threads compute the step's noise and x1 harmonics while it
-// runs, and every thread reads its 4K+1 accumulator columns back with
-// tcgen05.ld.
+// tensor core (one thread issues 3 KS MMAs and commits to an mbarrier), the
+// threads compute the step's noise and x1 harmonics while it runs, and every
+// thread reads its accumulator columns back with tcgen05.ld.
 #pragma once
 #include <algorithm>
 #include <cmath>
@@ -112,9 +110,10 @@ __device__ __forceinline__ float to_tf32(float x)
 }
 
 // Tiles are K-major without swizzling: 8 x 16-byte core matrices (8 rows x 4
-// tf32, 128 contiguous bytes), the KC core matrices of an 8-row group side by
-// side (128 B apart along K), 8-row groups SBO = KC x 128 B apart.  One MMA
-// k-step (8 tf32) spans two core matrices along K.
+// tf32 or 8 fp16, 128 contiguous bytes), the KC core matrices of an 8-row
+// group side by side (128 B apart along K), 8-row groups SBO = KC x 128 B
+// apart.  One MMA k-step (8 tf32 or 16 fp16: 32 bytes) spans two core
+// matrices along K.
 // Byte offset of 16-byte chunk c of row r.
 template <int KC>
 __device__ __forceinline__ uint32_t tile_off(int r, int c) { return (uint32_t)((r >> 3) * (KC * 128) + (r & 7) * 16 + c * 128); }
