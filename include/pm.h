@@ -235,7 +235,10 @@ int pm_path_groups(const double* x, const double* t, int64_t n_obs, double dt, i
  *   exit_step    [n_obs][M] steps taken to exit (-1 = capped), or NULL
  *   n_unexited   total capped paths, or NULL (host or device per flags)
  * Paths of uneven length are load-balanced by a persistent kernel in which
- * every lane takes a new path as soon as its current one exits.
+ * every lane takes a new path as soon as its current one exits; observations
+ * are claimed in order of their driftless mean exit time, longest first (with
+ * PM_DEVICE_PTRS the call reads x back to the host for that, a stream
+ * synchronisation).  Results do not depend on the order.
  * Returns PM_OK, PM_WARN_UNEXITED (outputs written), or an error. */
 int pm_forward_dirichlet(pm_ctx* ctx, const pm_field* field, double drift_scale, double kappa,
                          const pm_dirichlet_data* g, const double* x, int64_t n_obs, int64_t M,

@@ -27,6 +27,7 @@ struct DirParams {
     int32_t n_ang;
     float drift_dt, s_dt, R2hi, R2lo;
     const double* x;
+    const int32_t* order;    // [n_obs] observation claimed in slot s, or nullptr
     int64_t n_obs, M, total, max_steps, path_offset;
     unsigned long long* counter;
     unsigned long long* n_unexited;
@@ -128,9 +129,11 @@ __global__ void __launch_bounds__(128, DirShape<K>::MIN_CTAS) dirichlet_tc_kerne
             if (need) {
                 const int64_t cand = (int64_t)base + __popc(mask & ((1u << lane) - 1u));
                 if (cand < p.total) {
-                    pid = cand;
-                    j = (uint32_t)(cand / p.M);
-                    i = (uint32_t)(cand - (int64_t)j * p.M + p.path_offset);
+                    // claim order: slots in p.order (longest expected walks first)
+                    const int64_t slot = cand / p.M, ii = cand - slot * p.M;
+                    j = (uint32_t)(p.order ? (int64_t)p.order[slot] : slot);
+                    i = (uint32_t)(ii + p.path_offset);
+                    pid = (int64_t)j * p.M + ii;
                     X1.set(p.x[2 * (int64_t)j]);
                     X2.set(p.x[2 * (int64_t)j + 1]);
                     n = 0;
@@ -226,6 +229,7 @@ cudaError_t launch_dirichlet_tc(const DirichletLaunch& L, unsigned* err, cudaStr
     p.R2hi = (float)R2;
     p.R2lo = (float)(R2 - (double)p.R2hi);
     p.x = L.x;
+    p.order = L.order;
     p.n_obs = L.n_obs;
     p.M = L.M;
     p.total = L.n_obs * L.M;

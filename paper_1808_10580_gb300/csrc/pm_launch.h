@@ -74,6 +74,7 @@ struct DirichletLaunch {
     const double* ga;        // host [n_ang]
     const double* gb;
     const double* x;         // device [n_obs][2]
+    const int32_t* order = nullptr;  // device [n_obs]: observation whose paths are claimed in slot s
     int64_t n_obs, M;
     double dt, s_dt;
     int64_t max_steps;
