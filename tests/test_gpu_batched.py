@@ -96,3 +96,44 @@ def test_rows_must_tile(c):
     mean = np.empty(n_rows)
     with pytest.raises(pm.PMError, match="tile"):
         pm.pm_forward_batched(c, b, pm.PM_FP32, mean)
+
+
+def test_full_size_batch_sampled(c, orc):
+    # The batched workload as the bench runs it (256 instances x 100 observations x
+    # M = 4096, tensor cores): sampled instances equal their single-instance calls bit
+    # for bit, and the first 16 paths of every observation of one instance of each kind
+    # agree with the FP64 oracle on the same streams in distribution (the 440-mode flow
+    # is chaotic, so float and double paths separate; early Dirichlet exits agree).
+    ws = inputs.batched_instances()
+    flags = pm.PM_FP32 | pm.PM_TENSOR
+    rc, mean, var, nu = _gpu.batched(c, ws, flags=flags)
+    assert rc == 0 and nu == 0 and np.all(np.isfinite(mean)) and np.all(var >= 0)
+    P = 16
+    for b in (0, 1, 128, 255):
+        w = ws[b]
+        n = len(w.x)
+        fld = pm.Field(w.K, w.u)
+        m = np.empty(n)
+        g = np.empty(n * w.M)
+        if isinstance(w, inputs.TimedepWorkload):
+            th = pm.Fourier(w.theta0.k, w.theta0.a, w.theta0.b)
+            pm.pm_forward_timedep(c, fld, w.kappa, th, w.x, w.t, n, w.M, w.dt, w.seed, flags, m, instance=b, g_out=g)
+        else:
+            es = np.empty(n * w.M, dtype=np.int32)
+            gd = pm.DirichletData(w.g.R, w.g.quad, w.g.f_const, w.g.a, w.g.b)
+            pm.pm_forward_dirichlet(c, fld, w.drift_scale, w.kappa, gd, w.x, n, w.M, w.dt, w.max_steps, w.seed,
+                                    flags, m, None, es, None, instance=b, g_out=g)
+        np.testing.assert_allclose(mean[100 * b:100 * (b + 1)], m, rtol=0, atol=1e-12)
+        if b > 1:
+            continue
+        g = g.reshape(n, w.M)[:, :P]
+        if isinstance(w, inputs.TimedepWorkload):
+            go = orc.timedep_paths(w.K, w.u, w.kappa, w.theta0, w.x, w.t, w.dt, w.seed, npaths=P, inst=b)
+        else:
+            go, so = orc.dirichlet_paths(w.K, w.u, w.drift_scale, w.kappa, w.g, w.x, w.dt, w.max_steps, w.seed,
+                                         npaths=P, inst=b)
+            st = es.reshape(n, w.M)[:, :P]
+            early = so < 100
+            assert early.sum() > 20 and np.mean(st[early] == so[early]) >= 0.99
+        d = (g - go).ravel()
+        assert abs(d.mean()) <= 5 * d.std(ddof=1) / np.sqrt(d.size)
