@@ -93,3 +93,35 @@ def test_velocity_is_perpendicular_to_single_wave_vector(orc):
         v = orc.velocity(K, u, x)
         assert np.abs(v @ modes[h].astype(float)).max() < 1e-12
         assert np.abs(v).max() > 0.1
+
+
+@pytest.mark.parametrize("K", [24, 40, 64])
+def test_wide_bounds_enumerate_the_box_once(orc, K):
+    # |H_K| = ((2K+1)^2 - 1) / 2 half-modes, and with their negatives every nonzero
+    # lattice point of the box exactly once.
+    hm = orc.half_modes(K)
+    assert len(hm) == ((2 * K + 1) ** 2 - 1) // 2
+    assert np.array_equal(hm, inputs.half_mode_list(K))
+    full = {tuple(v) for v in hm} | {(-m, -n) for m, n in hm}
+    assert len(full) == 2 * len(hm) == (2 * K + 1) ** 2 - 1
+
+
+@pytest.mark.parametrize("K", [24, 64])
+def test_single_high_mode_velocity_closed_form(orc, K):
+    # psi = a cos(2 pi k.x) + b sin(2 pi k.x)  =>  v = (-d2 psi, d1 psi)
+    #     = 2 pi (-k2, k1) (b cos(2 pi k.x) - a sin(2 pi k.x)), written out here
+    # for modes at the corners and edges of the box.
+    modes = orc.half_modes(K)
+    rng = np.random.default_rng(K)
+    x = rng.random((25, 2))
+    picks = [(K, K), (K, -K), (0, K), (1, -K), (K - 1, 3)]
+    index = {tuple(v): h for h, v in enumerate(modes)}
+    for k in picks:
+        h = index[k]
+        a, b = 0.3, -0.8
+        u = np.zeros(2 * len(modes))
+        u[2 * h], u[2 * h + 1] = a, b
+        th = 2 * np.pi * (x @ np.array(k, dtype=float))
+        amp = 2 * np.pi * (b * np.cos(th) - a * np.sin(th))
+        want = np.stack([-k[1] * amp, k[0] * amp], axis=1)
+        assert np.allclose(orc.velocity(K, u, x), want, rtol=0, atol=1e-9 * K), k
