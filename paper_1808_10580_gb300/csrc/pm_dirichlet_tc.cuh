@@ -17,6 +17,9 @@ namespace tdtc {
 template <int K>
 using DirShape = Shape<K, false, half_of<K>()>;
 
+// Pairs of Euler steps between two refills of the lanes.
+constexpr int kRefillPairs = 4;
+
 template <int K>
 struct DirParams {
     float W[DirShape<K>::NP * DirShape<K>::WS];
@@ -151,47 +154,52 @@ __global__ void __launch_bounds__(128, DirShape<K>::MIN_CTAS) dirichlet_tc_kerne
             if (__syncthreads_and(done)) break;
             continue;
         }
-        u32x4 r{0, 0, 0, 0};
-        if (pid >= 0) r = philox4x32_10(u32x4{(uint32_t)(n >> 1), i, j, p.inst}, p.key0, p.key1);
+        // kRefillPairs pairs of steps between refills (a lane whose path exits
+        // waits for the next refill; the RNG stays keyed by the step index).
 #pragma unroll 1
-        for (int half = 0; half < 2; ++half) {
-            {
-                float C2[K + 1], S2[K + 1];
-                fourier_powers<float, K>(X2.val(), C2, S2);
-                float a[S::WS];
+        for (int pair = 0; pair < kRefillPairs && !stop; ++pair) {
+            u32x4 r{0, 0, 0, 0};
+            if (pid >= 0) r = philox4x32_10(u32x4{(uint32_t)(n >> 1), i, j, p.inst}, p.key0, p.key1);
+#pragma unroll 1
+            for (int half = 0; half < 2; ++half) {
+                {
+                    float C2[K + 1], S2[K + 1];
+                    fourier_powers<float, K>(X2.val(), C2, S2);
+                    float a[S::WS];
 #pragma unroll
-                for (int q = 0; q < S::WS; ++q) a[q] = 0.f;
+                    for (int q = 0; q < S::WS; ++q) a[q] = 0.f;
 #pragma unroll
-                for (int q = 1; q <= K; ++q) { a[q - 1] = S2[q]; a[K + q - 1] = C2[q]; }
-                a[2 * K] = 1.f;
-                write_row<K, false, H>(sb + row, a);
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            // One barrier per step: the rows are in place, and a wait that gave
-            // up in the previous step (any thread) stops the whole CTA.
-            if (__syncthreads_or(failed)) { stop = true; break; }
-            if (tid == 0) issue_step_mma<K, false, H>(tmem, sb, bar_a);
-            // While the product runs: the Brownian increment and the x1 harmonics.
-            float xi1, xi2;
-            box_muller<float>(half ? r.z : r.x, half ? r.w : r.y, xi1, xi2);
-            float C1[K + 1], S1[K + 1];
-            fourier_powers<float, K>(X1.val(), C1, S1);
-            failed = !tc::mbar_wait(bar_a, phase);
-            phase ^= 1u;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            float v1, v2;
-            velocity_from_tmem<K, H>(t_row, C1, S1, v1, v2, p.inv_s);
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            if (pid >= 0) {
-                em_update<float>(X1, v1, p.drift_dt, p.s_dt, xi1);
-                em_update<float>(X2, v2, p.drift_dt, p.s_dt, xi2);
-                ++n;
-                const bool exited = radial_excess(X1, X2, p.R2hi, p.R2lo) >= 0.f;
-                if (exited || n >= p.max_steps) {
-                    dir_finish(p, pid, exited, n, X1, X2);
-                    lane_steps += (unsigned long long)n;
-                    pid = -1;
+                    for (int q = 1; q <= K; ++q) { a[q - 1] = S2[q]; a[K + q - 1] = C2[q]; }
+                    a[2 * K] = 1.f;
+                    write_row<K, false, H>(sb + row, a);
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                // One barrier per step: the rows are in place, and a wait that gave
+                // up in the previous step (any thread) stops the whole CTA.
+                if (__syncthreads_or(failed)) { stop = true; break; }
+                if (tid == 0) issue_step_mma<K, false, H>(tmem, sb, bar_a);
+                // While the product runs: the Brownian increment and the x1 harmonics.
+                float xi1, xi2;
+                box_muller<float>(half ? r.z : r.x, half ? r.w : r.y, xi1, xi2);
+                float C1[K + 1], S1[K + 1];
+                fourier_powers<float, K>(X1.val(), C1, S1);
+                failed = !tc::mbar_wait(bar_a, phase);
+                phase ^= 1u;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                float v1, v2;
+                velocity_from_tmem<K, H>(t_row, C1, S1, v1, v2, p.inv_s);
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                if (pid >= 0) {
+                    em_update<float>(X1, v1, p.drift_dt, p.s_dt, xi1);
+                    em_update<float>(X2, v2, p.drift_dt, p.s_dt, xi2);
+                    ++n;
+                    const bool exited = radial_excess(X1, X2, p.R2hi, p.R2lo) >= 0.f;
+                    if (exited || n >= p.max_steps) {
+                        dir_finish(p, pid, exited, n, X1, X2);
+                        lane_steps += (unsigned long long)n;
+                        pid = -1;
+                    }
                 }
             }
         }
