@@ -1,5 +1,6 @@
 """Parity of the time-dependent map with the velocity sum on the tensor cores
-(PM_TENSOR: tcgen05 TF32 with a three-term hi/lo split) against the FP64 oracle
+(PM_TENSOR: tcgen05 with a three-term hi/lo split of TF32 operands for K <= 8
+and of FP16 operands from K = 10) against the FP64 oracle
 and against the FP32-pipe kernel."""
 import numpy as np
 import pytest
@@ -39,7 +40,7 @@ def test_one_step_positions_match_oracle(c, orc, K):
     d_tc -= np.round(d_tc)
     d_sm = xs - xo
     d_sm -= np.round(d_sm)
-    # 3xTF32 keeps ~21 bits per product: velocity error <= ~1e-6 of the term scale
+    # three products of 11-bit operands keep ~21 bits: velocity error <= ~1e-6 of the term scale
     assert np.abs(d_tc).max() <= w.dt * 4e-6 * scale + 1e-7, (np.abs(d_tc).max(), np.abs(d_sm).max())
 
 
