@@ -426,13 +426,14 @@ int pm_forward_timedep(pm_ctx* c, const pm_field* field, double kappa, const pm_
     if ((rc = check_ptrs(flags, {x, t, mean, var, g_out, x_out}))) return rc;
     const bool dev = flags & PM_DEVICE_PTRS;
     const bool fp64 = flags & PM_FP64;
-    const int64_t chunks64 = (M + kTimedepBlock - 1) / kTimedepBlock;
-    if (n_obs * chunks64 > 0x7fffffffLL) return fail(PM_EINVAL, "n_obs * ceil(M/%d) exceeds the grid limit", kTimedepBlock);
-    const int32_t chunks = (int32_t)chunks64;
     const int K = field->K;
     const bool tc = !fp64 && (flags & PM_TENSOR) && (K == 4 || K == 5 || K == 6 || K == 8 || K == 10 || K == 12 || K == 16 ||
                                                      wide_K(K));
     const bool wide = wide_K(K);
+    const int rows = tc ? td_tc_rows(K) : kTimedepBlock;  // paths per CTA
+    const int64_t chunks64 = (M + rows - 1) / rows;
+    if (n_obs * chunks64 > 0x7fffffffLL) return fail(PM_EINVAL, "n_obs * ceil(M/%d) exceeds the grid limit", rows);
+    const int32_t chunks = (int32_t)chunks64;
     const bool share = flags & PM_SHARE_PATHS;
     if ((rc = set_device(c))) return rc;
 

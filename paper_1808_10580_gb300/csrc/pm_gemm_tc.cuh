@@ -60,7 +60,7 @@ struct Epilogue {
     int M_valid, N_valid;        // rows/columns beyond these are stored as 0
 };
 
-struct alignas(64) GemmParams {
+struct GemmParams {  // aligned as its tensor maps require
     CUtensorMap tmA;             // A: [M][K] BF16, box {64, 128}, 128B swizzle
     CUtensorMap tmB;             // B: [N][K] BF16, box {64, BN}, 128B swizzle
     Epilogue ep;

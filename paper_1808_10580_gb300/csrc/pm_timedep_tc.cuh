@@ -78,6 +78,16 @@ constexpr bool half_of() { return K >= 10; }
 template <int K>
 using TdShape = Shape<K, fold_of<K>(), half_of<K>()>;
 
+// Particle tiles of 128 rows per CTA of the time-dependent kernel: two where
+// one tile's CTA already fills the SM's shared memory with W and a second
+// tile still fits beside it, so that the SM has two sets of particles to
+// alternate; the two tiles share the coefficient tiles.  K = 48 (measured
+// 171.6 against 186.1 ms on the 300 x 1e4-path workload); at K = 56 the
+// 256-thread CTA spills registers and measured slower (257.0 against 240.1 ms).
+// (Mirrored by td_tc_rows in pm_launch.h.)
+template <int K>
+constexpr int td_sets() { return K == 48 ? 2 : 1; }
+
 // Instruction descriptor, kind::tf32: FP32 accumulator, TF32 A and B, both K-major.
 template <int NP>
 __host__ __device__ constexpr uint32_t idesc_tf32() { return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NP >> 3) << 17) | ((uint32_t)(128 >> 4) << 24); }
@@ -315,7 +325,7 @@ __host__ __device__ inline int w_scale_exp(float wmax)
 template <typename S, typename Load>
 __device__ __forceinline__ void stage_B(uint8_t* B_hi, uint8_t* B_lo, int tid, Load w)
 {
-    for (int q = tid; q < S::NP * S::KC; q += 128) {
+    for (int q = tid; q < S::NP * S::KC; q += (int)blockDim.x) {
         const int r = q / S::KC, c = q - r * S::KC;
         if constexpr (S::HALF) {
             uint32_t hv[4], lv[4];
@@ -367,14 +377,16 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, const float4& v)
 
 // Tiles at shared address sb: A_hi, A_lo (A_BYTES each), then B_hi, B_lo.
 // This thread's row of the particle tiles (row = sb + tile_off(r, 0); chunk c
-// 128 c bytes further): harmonics a[0..KD) split into hi / lo.
+// 128 c bytes further; the lo tile lo_off bytes after the hi tile): harmonics
+// a[0..KD) split into hi / lo.
 __device__ __forceinline__ void st_shared_v4u(uint32_t addr, const uint32_t (&v)[4])
 {
     asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]) : "memory");
 }
 
 template <int K, bool F = false, bool H = false>
-__device__ __forceinline__ void write_row(uint32_t row, const float (&a)[Shape<K, F, H>::WS])
+__device__ __forceinline__ void write_row(uint32_t row, const float (&a)[Shape<K, F, H>::WS],
+                                          uint32_t lo_off = Shape<K, F, H>::A_BYTES)
 {
     using S = Shape<K, F, H>;
     if constexpr (H) {
@@ -384,7 +396,7 @@ __device__ __forceinline__ void write_row(uint32_t row, const float (&a)[Shape<K
 #pragma unroll
             for (int q = 0; q < 4; ++q) split_f16x2(a[8 * c + 2 * q], a[8 * c + 2 * q + 1], h[q], l[q]);
             st_shared_v4u(row + 128u * c, h);
-            st_shared_v4u(row + (uint32_t)S::A_BYTES + 128u * c, l);
+            st_shared_v4u(row + lo_off + 128u * c, l);
         }
     } else {
 #pragma unroll
@@ -395,20 +407,19 @@ __device__ __forceinline__ void write_row(uint32_t row, const float (&a)[Shape<K
             split_tf32(a[4 * c + 2], h.z, l.z);
             split_tf32(a[4 * c + 3], h.w, l.w);
             st_shared_v4(row + 128u * c, h);
-            st_shared_v4(row + (uint32_t)S::A_BYTES + 128u * c, l);
+            st_shared_v4(row + lo_off + 128u * c, l);
         }
     }
 }
 
 // One Euler step's product, issued by one thread: P = A_hi W_hi + A_lo W_hi +
 // A_hi W_lo over the KS k-steps, then a commit to the step's mbarrier.
+// The three products of one 128-row particle tile (descriptors ah, al) with
+// the coefficient tiles (bh, bl) into the accumulator at tmem, no commit.
 template <int K, bool F = false, bool H = false>
-__device__ __forceinline__ void issue_step_mma(uint32_t tmem, uint32_t sb, uint32_t bar)
+__device__ __forceinline__ void issue_tile_mma(uint32_t tmem, uint64_t ah, uint64_t al, uint64_t bh, uint64_t bl)
 {
     using S = Shape<K, F, H>;
-    const uint64_t ah = tile_desc<S::SBO>(sb), al = tile_desc<S::SBO>(sb + S::A_BYTES);
-    const uint64_t bh = tile_desc<S::SBO>(sb + 2 * S::A_BYTES), bl = tile_desc<S::SBO>(sb + 2 * S::A_BYTES + S::B_BYTES);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if constexpr (H) {
 #pragma unroll
         for (int k = 0; k < S::KS; ++k) mma_f16<S::NP>(tmem, ah + kKStep * k, bh + kKStep * k, k > 0 ? 1u : 0u);
@@ -424,20 +435,48 @@ __device__ __forceinline__ void issue_step_mma(uint32_t tmem, uint32_t sb, uint3
 #pragma unroll
         for (int k = 0; k < S::KS; ++k) mma_tf32<S::NP>(tmem, ah + kKStep * k, bl + kKStep * k, 1u);
     }
+}
+
+// One Euler step's product for a CTA with one particle tile, issued by one
+// thread, then a commit to the step's mbarrier.
+template <int K, bool F = false, bool H = false>
+__device__ __forceinline__ void issue_step_mma(uint32_t tmem, uint32_t sb, uint32_t bar)
+{
+    using S = Shape<K, F, H>;
+    const uint64_t ah = tile_desc<S::SBO>(sb), al = tile_desc<S::SBO>(sb + S::A_BYTES);
+    const uint64_t bh = tile_desc<S::SBO>(sb + 2 * S::A_BYTES), bl = tile_desc<S::SBO>(sb + 2 * S::A_BYTES + S::B_BYTES);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    issue_tile_mma<K, F, H>(tmem, ah, al, bh, bl);
     tc::mma_commit(bar);
 }
 
+// Shared memory, threads and tensor-memory columns of the time-dependent kernel.
 template <int K>
-__global__ void __launch_bounds__(128, TdShape<K>::MIN_CTAS) timedep_tc_kernel(const __grid_constant__ Params<K> p)
+struct TdLaunch {
+    using S = TdShape<K>;
+    static constexpr int SETS = td_sets<K>();
+    static constexpr int THREADS = 128 * SETS;
+    static constexpr int SMEM = SETS == 1 ? S::SMEM : 2 * SETS * S::A_BYTES + 2 * S::B_BYTES + 128 + 64;
+    static constexpr uint32_t TMEM_COLS = SETS == 1 ? S::TMEM_COLS : 512u;  // set s at column 256 s
+    static constexpr int MIN_CTAS = SETS == 1 ? S::MIN_CTAS : 1;
+    static_assert(SETS == 1 || (S::NP <= 256 && SMEM + 1024 <= 233472), "two tiles fit");
+};
+
+template <int K>
+__global__ void __launch_bounds__(TdLaunch<K>::THREADS, TdLaunch<K>::MIN_CTAS)
+    timedep_tc_kernel(const __grid_constant__ Params<K> p)
 {
     using S = TdShape<K>;
+    using LC = TdLaunch<K>;
     constexpr bool F = S::FOLD;
     constexpr bool H = S::HALF;
+    constexpr int SETS = LC::SETS, ROWS = LC::THREADS;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+    // A tiles of ROWS rows (set s = rows 128 s .. 128 s + 127), then W's tiles.
     uint8_t* A_hi = smem;
-    uint8_t* A_lo = smem + S::A_BYTES;
-    uint8_t* B_hi = smem + 2 * S::A_BYTES;
+    uint8_t* A_lo = smem + SETS * S::A_BYTES;
+    uint8_t* B_hi = smem + 2 * SETS * S::A_BYTES;
     uint8_t* B_lo = B_hi + S::B_BYTES;
     uint64_t* bar = (uint64_t*)(B_lo + S::B_BYTES);
     uint32_t* tmem_slot = (uint32_t*)(bar + 1);
@@ -458,7 +497,7 @@ __global__ void __launch_bounds__(128, TdShape<K>::MIN_CTAS) timedep_tc_kernel(c
     __syncwarp();
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(tmem_slot)),
-                     "r"(S::TMEM_COLS)
+                     "r"(LC::TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -466,7 +505,8 @@ __global__ void __launch_bounds__(128, TdShape<K>::MIN_CTAS) timedep_tc_kernel(c
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
-    const uint32_t t_row = tmem + ((uint32_t)(warp * 32) << 16);
+    // warp w reads TMEM lanes 32 (w mod 4) of its set's accumulator (columns 256 s)
+    const uint32_t t_row = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * 256);
 
     const uint32_t row = tile_off<S::KC>(tid, 0);
     const uint32_t sb = tc::smem_u32(A_hi);  // A_hi, A_lo, B_hi, B_lo back to back
@@ -486,7 +526,7 @@ __global__ void __launch_bounds__(128, TdShape<K>::MIN_CTAS) timedep_tc_kernel(c
         m1 = stream + 1;
     }
     auto member = [&](int m) { return p.groups ? p.members[m] : m; };
-    const int64_t i = (int64_t)cidx * 128 + tid;
+    const int64_t i = (int64_t)cidx * ROWS + tid;
     const bool active = i < p.M;
     Coord<float> X1, X2;
     {
@@ -506,7 +546,7 @@ __global__ void __launch_bounds__(128, TdShape<K>::MIN_CTAS) timedep_tc_kernel(c
             if (p.g_out) p.g_out[w] = g;
             if (p.x_out) { p.x_out[2 * w] = Y1.full(); p.x_out[2 * w + 1] = Y2.full(); }
         }
-        const double2 sum = block_sum2<128>(g, g * g);
+        const double2 sum = block_sum2<ROWS>(g, g * g);
         if (tid == 0) p.part[(int64_t)jm * p.chunks + cidx] = sum;
         __syncthreads();  // block_sum2's scratch is reused by the next member
     };
@@ -541,14 +581,29 @@ __global__ void __launch_bounds__(128, TdShape<K>::MIN_CTAS) timedep_tc_kernel(c
             } else {
                 a[2 * K] = 1.f;
             }
-            write_row<K, F, H>(sb + row, a);
+            write_row<K, F, H>(sb + row, a, (uint32_t)(SETS * S::A_BYTES));
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         // One barrier per step: the rows are in place, and a wait that gave up
         // in the previous step (any thread) ends the loop for the whole CTA.
         if (__syncthreads_or(failed)) { failed = true; break; }
-        if (tid == 0) issue_step_mma<K, F, H>(tmem, sb, bar_a);
+        if (tid == 0) {
+            if constexpr (SETS == 1) {
+                issue_step_mma<K, F, H>(tmem, sb, bar_a);
+            } else {
+                const uint32_t b0 = sb + 2 * SETS * S::A_BYTES;
+                const uint64_t bh = tile_desc<S::SBO>(b0), bl = tile_desc<S::SBO>(b0 + S::B_BYTES);
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+                for (int st = 0; st < SETS; ++st) {
+                    const uint32_t a0 = sb + st * S::A_BYTES;
+                    issue_tile_mma<K, F, H>(tmem + 256u * st, tile_desc<S::SBO>(a0),
+                                            tile_desc<S::SBO>(a0 + SETS * S::A_BYTES), bh, bl);
+                }
+                tc::mma_commit(bar_a);
+            }
+        }
         // While the product runs: the Brownian increment and the x1 harmonics.
         if ((n & 1) == 0) r = philox4x32_10(u32x4{(uint32_t)(n >> 1), pid, (uint32_t)stream, p.inst}, p.key0, p.key1);
         float xi1, xi2;
@@ -587,7 +642,7 @@ __global__ void __launch_bounds__(128, TdShape<K>::MIN_CTAS) timedep_tc_kernel(c
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::TMEM_COLS) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(LC::TMEM_COLS) : "memory");
     }
 }
 
@@ -686,10 +741,11 @@ cudaError_t launch_timedep_tc(const TimedepLaunch& L, unsigned* err, cudaStream_
     p.err = err;
     p.groups = L.groups;
     p.members = L.members;
-    cudaError_t e = cudaFuncSetAttribute(timedep_tc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+    using LC = TdLaunch<K>;
+    cudaError_t e = cudaFuncSetAttribute(timedep_tc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, LC::SMEM);
     if (e != cudaSuccess) return e;
     const int64_t grid = (int64_t)(L.groups ? L.n_groups : L.n_obs) * L.chunks;
-    timedep_tc_kernel<K><<<(unsigned)grid, 128, S::SMEM, stream>>>(p);
+    timedep_tc_kernel<K><<<(unsigned)grid, LC::THREADS, LC::SMEM, stream>>>(p);
     return cudaGetLastError();
 }
 
