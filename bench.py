@@ -78,17 +78,23 @@ def tensor_peak(K: int, peaks: dict, peaks_kind: str):
     return bf16 * 1.1 / 2.25, f"TF32 dense = bf16_tflops {bf16} ({peaks_kind}, burst) x 1.1/2.25"
 
 
-def profile_traffic(name="timedep_k10_kernel.md"):
-    """DRAM bytes per launch of the particle kernel from the committed ncu summary
-    (line 'traffic_bytes_per_launch: <int>'), or None."""
+def profile_value(name, key):
+    """The number on the line '<key>: <number>' of a committed ncu summary, or None."""
     p = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(p):
         return None
     for line in open(p):
-        if line.startswith("traffic_bytes_per_launch:"):
+        if line.startswith(key + ":"):
             v = line.split(":", 1)[1].strip()
-            return None if v in ("", "null") else int(float(v))
+            return None if v in ("", "null") else float(v)
     return None
+
+
+def profile_traffic(name="timedep_k10_kernel.md"):
+    """DRAM bytes per launch of the particle kernel from the committed ncu summary
+    (line 'traffic_bytes_per_launch: <int>'), or None."""
+    v = profile_value(name, "traffic_bytes_per_launch")
+    return None if v is None else int(v)
 
 
 class ClockSampler:
@@ -319,11 +325,16 @@ def run_gpu(args):
             peak_tflops, peak_basis = tensor_peak(w.K, peaks, peaks_kind)
             achieved = steps_per_eval * tensor_flops_per_step(w.K) / (kern_mean_ms / 1e3) / 1e12
             roof = {"bound": "tensor", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                    "frac": achieved / peak_tflops, "traffic": profile_traffic("timedep_k10_tc_kernel.md"),
+                    "frac": achieved / peak_tflops,
+                    "traffic": profile_traffic("timedep_k10_tc_kernel.md") if w.K == 10 else None,
                     "kernel": f"timedep_tc_kernel<{w.K}>", "kernel_ms": kern_mean_ms,
                     "flop_per_particle_step": tensor_flops_per_step(w.K),
                     "peak_basis": peak_basis, "operands": tensor_operands(w.K),
                     "single_product_frac": achieved / 3 / peak_tflops,
+                    "issue_active_frac_ncu": (profile_value("timedep_k10_tc_kernel.md", "issue_active_frac")
+                                              if w.K == 10 else None),
+                    "binding_constraint": "SIMT instruction issue (harmonics, operand split, RNG, Euler "
+                                          "step), not the tensor pipe: see issue_active_frac_ncu",
                     "fp32_equivalent": {"achieved": simt_rate, "peak": fp32_peak,
                                         "flop_per_particle_step": flops_per_step(w.K),
                                         "note": "the same steps counted as FP32 direct-sum work, against "
