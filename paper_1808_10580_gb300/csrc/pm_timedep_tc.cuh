@@ -22,7 +22,6 @@
 #pragma once
 #include <algorithm>
 #include <cmath>
-#include <cstring>
 #include <cuda_fp16.h>
 #include "pm_gemm_tc.cuh"
 #include "pm_kernels.cuh"
