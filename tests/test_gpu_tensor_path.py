@@ -190,3 +190,26 @@ def test_tensor_path_host_and_device_pointers_agree(c, device):
     a = _gpu.timedep(c, w, pm.PM_FP32 | pm.PM_TENSOR, device=True)
     b = _gpu.timedep(c, w, pm.PM_FP32 | pm.PM_TENSOR, device=device)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+@pytest.mark.parametrize("K", [10, 16])
+@pytest.mark.parametrize("scale", [1e-6, 1e3])
+def test_fp16_scale_of_w_at_extreme_field_sizes(c, orc, K, scale):
+    # FP16 operands carry W times 2^e with its largest entry in [2^13, 2^14); fields
+    # of very small and very large size move e far from 0 (and, folded at K = 16,
+    # the n = 0 terms share the scale).  One step from 64 points, as above; the drift
+    # of the large field is kept to a fraction of the domain by a short step.
+    w = inputs.timedep_k10(M=128)
+    w.K = K
+    w.u = inputs.prior_field(K, 900 + K) * scale
+    rng = np.random.default_rng(K)
+    w.x = rng.random((64, 2))
+    w.dt = 0.01 / max(1.0, scale)
+    w.t = np.full(64, w.dt)
+    _, _, xe = _gpu.timedep(c, w, pm.PM_FP32 | pm.PM_TENSOR, x_out=True)
+    _, xo = orc.timedep_paths(K, w.u, w.kappa, w.theta0, w.x, w.t, w.dt, w.seed, npaths=128, want_x=True)
+    modes = orc.half_modes(K).astype(float)
+    term_scale = float((2 * np.pi * np.sqrt((modes ** 2).sum(1)) * np.abs(w.u.reshape(-1, 2)).sum(1)).sum())
+    d = xe - xo
+    d -= np.round(d)
+    assert np.abs(d).max() <= w.dt * 4e-6 * term_scale + 1e-7, np.abs(d).max()
