@@ -17,36 +17,26 @@
 namespace pm {
 namespace tdtc {
 
-// Entry W[k][nc] of the coefficient matrix from the product-basis table
-// tab[(m (K+1) + n) 8 + q] (e0..e3, f0..f3): A column k holds S2_{k+1}
-// (k < K), C2_{k-K+1} (K <= k < 2K) or the constant 1 (k = 2K); accumulator
-// column nc is P1c(nc) for nc <= K, P1s(nc-K), P2c(nc-2K), P2s(nc-3K) above.
+// Entry W[k][nc] of the coefficient matrix (unfolded shape) from the
+// product-basis table tab[(m (K+1) + n) 8 + q] (e0..e3, f0..f3): A column k
+// holds S2_n (k = 2(n-1)), C2_n (k = 2(n-1)+1) or the constant 1 (k = 2K);
+// accumulator column 0 is P(0), columns 1 + 4(m-1) + j are P1c, P1s, P2c, P2s
+// of m (the layout of build_W).
 template <int K>
 __device__ __forceinline__ float w_entry(const float* tab, int nc, int k)
 {
     int n = 0, type = 0;  // type 0: S2_n, 1: C2_n, 2: constant
-    if (k < K) { n = k + 1; type = 0; }
-    else if (k < 2 * K) { n = k - K + 1; type = 1; }
+    if (k < 2 * K) { n = k / 2 + 1; type = k & 1; }
     else if (k == 2 * K) { type = 2; }
     else return 0.f;
     auto T = [&](int m, int nn, int q) { return tab[(m * (K + 1) + nn) * 8 + q]; };
-    if (nc <= K) {  // P1c(m), m = nc (m = 0 included)
-        const int m = nc;
-        return type == 0 ? T(m, n, 0) : type == 1 ? T(m, n, 1) : 0.f;
-    }
-    if (nc <= 2 * K) {  // P1s(m)
-        const int m = nc - K;
-        return type == 0 ? T(m, n, 2) : type == 1 ? T(m, n, 3) : 0.f;
-    }
-    if (nc <= 3 * K) {  // P2c(m)
-        const int m = nc - 2 * K;
-        return type == 1 ? T(m, n, 4) : type == 0 ? T(m, n, 5) : T(m, 0, 4);
-    }
-    if (nc <= 4 * K) {  // P2s(m)
-        const int m = nc - 3 * K;
-        return type == 1 ? T(m, n, 6) : type == 0 ? T(m, n, 7) : T(m, 0, 6);
-    }
-    return 0.f;
+    if (nc == 0) return type == 0 ? T(0, n, 0) : type == 1 ? T(0, n, 1) : 0.f;  // P(0)
+    if (nc > 4 * K) return 0.f;
+    const int m = (nc - 1) / 4 + 1, j = (nc - 1) % 4;
+    if (j == 0) return type == 0 ? T(m, n, 0) : type == 1 ? T(m, n, 1) : 0.f;          // P1c
+    if (j == 1) return type == 0 ? T(m, n, 2) : type == 1 ? T(m, n, 3) : 0.f;          // P1s
+    if (j == 2) return type == 1 ? T(m, n, 4) : type == 0 ? T(m, n, 5) : T(m, 0, 4);   // P2c
+    return type == 1 ? T(m, n, 6) : type == 0 ? T(m, n, 7) : T(m, 0, 6);               // P2s
 }
 
 template <int K>
@@ -56,7 +46,7 @@ using BatShape = Shape<K, false, half_of<K>()>;
 constexpr int kBatchRefillPairs = 4;
 
 template <int K>
-__global__ void __launch_bounds__(128, BatShape<K>::MIN_CTAS) batched_tc_kernel(const __grid_constant__ BatchKernelParams p)
+__global__ void __launch_bounds__(128, BatShape<K>::MIN_CTAS6) batched_tc_kernel(const __grid_constant__ BatchKernelParams p)
 {
     using S = BatShape<K>;
     constexpr bool H = S::HALF;
@@ -232,17 +222,7 @@ __global__ void __launch_bounds__(128, BatShape<K>::MIN_CTAS) batched_tc_kernel(
             if (pid >= 0) r = philox4x32_10(u32x4{(uint32_t)(n >> 1), i, j, stream}, key0, key1);
 #pragma unroll 1
             for (int half = 0; half < 2; ++half) {
-                {
-                    float C2[K + 1], S2[K + 1];
-                    fourier_powers<float, K>(X2.val(), C2, S2);
-                    float a[S::WS];
-#pragma unroll
-                    for (int q = 0; q < S::WS; ++q) a[q] = 0.f;
-#pragma unroll
-                    for (int q = 1; q <= K; ++q) { a[q - 1] = S2[q]; a[K + q - 1] = C2[q]; }
-                    a[2 * K] = 1.f;
-                    write_row<K, false, H>(sb + row, a);
-                }
+                write_row_stream<K, false, H>(sb + row, (uint32_t)S::A_BYTES, X2.val(), nullptr);
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 // One barrier per step: the rows are in place, and a wait that gave
@@ -252,13 +232,13 @@ __global__ void __launch_bounds__(128, BatShape<K>::MIN_CTAS) batched_tc_kernel(
                 // While the product runs: the Brownian increment and the x1 harmonics.
                 float xi1, xi2;
                 box_muller<float>(half ? r.z : r.x, half ? r.w : r.y, xi1, xi2);
-                float C1[K + 1], S1[K + 1];
-                fourier_powers<float, K>(X1.val(), C1, S1);
+                HarmArray<K> h1;  // during the product
+                h1.init(X1.val());
                 failed = !tc::mbar_wait(bar_a, phase);
                 phase ^= 1u;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 float v1, v2;
-                velocity_from_tmem<K, H>(t_row, C1, S1, v1, v2, inv_s);
+                velocity_stream<K, false, H>(t_row, h1, nullptr, 0.f, inv_s, v1, v2);
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 if (pid < 0) continue;
                 if (kind == 0) {

@@ -69,7 +69,7 @@ __device__ __forceinline__ void dir_finish(const DirParams<K>& p, int64_t pid, b
 }
 
 template <int K>
-__global__ void __launch_bounds__(128, DirShape<K>::MIN_CTAS) dirichlet_tc_kernel(const __grid_constant__ DirParams<K> p)
+__global__ void __launch_bounds__(128, DirShape<K>::MIN_CTAS6) dirichlet_tc_kernel(const __grid_constant__ DirParams<K> p)
 {
     using S = DirShape<K>;
     constexpr bool H = S::HALF;
@@ -162,17 +162,7 @@ __global__ void __launch_bounds__(128, DirShape<K>::MIN_CTAS) dirichlet_tc_kerne
             if (pid >= 0) r = philox4x32_10(u32x4{(uint32_t)(n >> 1), i, j, p.inst}, p.key0, p.key1);
 #pragma unroll 1
             for (int half = 0; half < 2; ++half) {
-                {
-                    float C2[K + 1], S2[K + 1];
-                    fourier_powers<float, K>(X2.val(), C2, S2);
-                    float a[S::WS];
-#pragma unroll
-                    for (int q = 0; q < S::WS; ++q) a[q] = 0.f;
-#pragma unroll
-                    for (int q = 1; q <= K; ++q) { a[q - 1] = S2[q]; a[K + q - 1] = C2[q]; }
-                    a[2 * K] = 1.f;
-                    write_row<K, false, H>(sb + row, a);
-                }
+                write_row_stream<K, false, H>(sb + row, (uint32_t)S::A_BYTES, X2.val(), nullptr);
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 // One barrier per step: the rows are in place, and a wait that gave
@@ -182,13 +172,13 @@ __global__ void __launch_bounds__(128, DirShape<K>::MIN_CTAS) dirichlet_tc_kerne
                 // While the product runs: the Brownian increment and the x1 harmonics.
                 float xi1, xi2;
                 box_muller<float>(half ? r.z : r.x, half ? r.w : r.y, xi1, xi2);
-                float C1[K + 1], S1[K + 1];
-                fourier_powers<float, K>(X1.val(), C1, S1);
+                HarmArray<K> h1;  // during the product
+                h1.init(X1.val());
                 failed = !tc::mbar_wait(bar_a, phase);
                 phase ^= 1u;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 float v1, v2;
-                velocity_from_tmem<K, H>(t_row, C1, S1, v1, v2, p.inv_s);
+                velocity_stream<K, false, H>(t_row, h1, nullptr, 0.f, p.inv_s, v1, v2);
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 if (pid >= 0) {
                     em_update<float>(X1, v1, p.drift_dt, p.s_dt, xi1);

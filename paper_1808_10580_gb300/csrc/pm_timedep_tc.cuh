@@ -21,6 +21,7 @@
 // thread reads its accumulator columns back with tcgen05.ld.
 #pragma once
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <cuda_fp16.h>
 #include "pm_gemm_tc.cuh"
@@ -56,8 +57,13 @@ struct Shape {
     static constexpr int SMEM = 2 * A_BYTES + 2 * B_BYTES + 128 + 64;
     // allocation: a power of 2 >= 32
     static constexpr uint32_t TMEM_COLS = NP <= 64 ? 64u : NP <= 128 ? 128u : 256u;
-    // CTAs per SM that fit the 228 KB of shared memory (1 KB reserved each), at most 6
-    static constexpr int MIN_CTAS = (233472 / (SMEM + 1024)) < 6 ? (233472 / (SMEM + 1024)) : 6;
+    // CTAs per SM the kernels are compiled for: what the 228 KB of shared memory
+    // (1 KB reserved each) and the 512 TMEM columns hold, at most 8 (32 warps)
+    static constexpr int CTAS_SMEM = 233472 / (SMEM + 1024);
+    static constexpr int CTAS_TMEM = 512 / (int)TMEM_COLS;
+    static constexpr int MIN_CTAS = CTAS_SMEM < CTAS_TMEM ? (CTAS_SMEM < 8 ? CTAS_SMEM : 8) : (CTAS_TMEM < 8 ? CTAS_TMEM : 8);
+    // the same with at most 6 (kernels that hold the x1 harmonics across the MMA wait)
+    static constexpr int MIN_CTAS6 = MIN_CTAS < 6 ? MIN_CTAS : 6;
     // W^T travels in the kernel-parameter bank up to 16 KB, else in global memory.
     static constexpr bool W_PARAM = NP * WS * 4 <= 16384;
     static_assert(NP <= 256, "accumulator within 256 TMEM columns (one MMA: N <= 256)");
@@ -242,72 +248,6 @@ __device__ __forceinline__ void split_tf32(float a, float& hi, float& lo)
     lo = a - hi;
 }
 
-// The velocity from this lane's accumulator row, read 16 columns at a time:
-//   v1 = P(0) + sum_m C1m P1c(m) + S1m P1s(m)      (columns 0 .. 2K),
-//   v2 = sum_m C1m P2c(m)  +  sum_m S1m P2s(m)      (columns 2K+1 .. 4K).
-// Terms are added in the order of their columns within each sum.
-template <int K, bool H = false>
-__device__ __forceinline__ void velocity_from_tmem(uint32_t t_row, const float (&C1)[K + 1], const float (&S1)[K + 1],
-                                                   float& v1, float& v2, float inv_s = 1.f)
-{
-    constexpr int NP = (4 * K + 1 + 15) / 16 * 16;  // as Shape<K, false, H>::NP
-    float v1c = 0.f, v1s = 0.f, v2c = 0.f, v2s = 0.f, p0 = 0.f;
-#pragma unroll
-    for (int q = 0; q < NP / 16; ++q) {
-        float a[16];
-        tmem_ld16(t_row + 16u * q, a);
-#pragma unroll
-        for (int e = 0; e < 16; ++e) {
-            const int col = 16 * q + e;
-            if (col == 0) p0 = a[e];
-            else if (col <= K) v1c = fmaf(C1[col], a[e], v1c);
-            else if (col <= 2 * K) v1s = fmaf(S1[col - K], a[e], v1s);
-            else if (col <= 3 * K) v2c = fmaf(C1[col - 2 * K], a[e], v2c);
-            else if (col <= 4 * K) v2s = fmaf(S1[col - 3 * K], a[e], v2s);
-        }
-    }
-    v1 = p0 + (v1c + v1s);
-    v2 = v2c + v2s;
-    if constexpr (H) {
-        v1 *= inv_s;
-        v2 *= inv_s;
-    }
-}
-
-// Folded shape: columns m-1, K+m-1, 2K+m-1, 3K+m-1 hold P1c(m), P1s(m), and
-// P2c(m), P2s(m) without their n = 0 terms N0, which are added here before the
-// multiplication by the x1 harmonic; p0 (the m = 0 part of v1) comes from the
-// FP32 pipes.  The sums run over m in the same order as in the unfolded form.
-template <int K, bool H = false>
-__device__ __forceinline__ void velocity_from_tmem_folded(uint32_t t_row, const float (&C1)[K + 1],
-                                                          const float (&S1)[K + 1], const float* N0, float p0,
-                                                          float& v1, float& v2, float inv_s = 1.f)
-{
-    constexpr int NP = (4 * K + 15) / 16 * 16;  // as Shape<K, true, H>::NP
-    float v1c = 0.f, v1s = 0.f, v2c = 0.f, v2s = 0.f;
-#pragma unroll
-    for (int q = 0; q < NP / 16; ++q) {
-        float a[16];
-        tmem_ld16(t_row + 16u * q, a);
-#pragma unroll
-        for (int e = 0; e < 16; ++e) {
-            const int col = 16 * q + e;
-            const int blk = col / K, m = col - blk * K + 1;
-            if (blk == 0) v1c = fmaf(C1[m], a[e], v1c);
-            else if (blk == 1) v1s = fmaf(S1[m], a[e], v1s);
-            else if (blk == 2) v2c = fmaf(C1[m], a[e] + N0[m - 1], v2c);
-            else if (blk == 3) v2s = fmaf(S1[m], a[e] + N0[K + m - 1], v2s);
-        }
-    }
-    if constexpr (H) {
-        v1 = p0 + inv_s * (v1c + v1s);  // N0 carries the scale of W
-        v2 = inv_s * (v2c + v2s);
-    } else {
-        v1 = p0 + (v1c + v1s);
-        v2 = v2c + v2s;
-    }
-}
-
 // Exponent e of the power-of-two scale of W for FP16 operands: the largest
 // |entry| times 2^e lies in [2^13, 2^14) (e = 0 for a zero W).
 __host__ __device__ inline int w_scale_exp(float wmax)
@@ -374,40 +314,184 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, const float4& v)
     asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w) : "memory");
 }
 
-// Tiles at shared address sb: A_hi, A_lo (A_BYTES each), then B_hi, B_lo.
-// This thread's row of the particle tiles (row = sb + tile_off(r, 0); chunk c
-// 128 c bytes further; the lo tile lo_off bytes after the hi tile): harmonics
-// a[0..KD) split into hi / lo.
+// Tiles at shared address sb: A_hi, A_lo (A_BYTES each), then B_hi, B_lo; a
+// thread's row of the particle tiles starts at sb + tile_off(r, 0), chunk c
+// 128 c bytes further, the lo tile lo_off bytes after the hi tile.
 __device__ __forceinline__ void st_shared_v4u(uint32_t addr, const uint32_t (&v)[4])
 {
     asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]) : "memory");
 }
 
-template <int K, bool F = false, bool H = false>
-__device__ __forceinline__ void write_row(uint32_t row, const float (&a)[Shape<K, F, H>::WS],
-                                          uint32_t lo_off = Shape<K, F, H>::A_BYTES)
+// Layouts of A and P.  A columns interleave the x2 harmonics: S2_n at 2(n-1),
+// C2_n at 2(n-1)+1 (n = 1..K), the constant 1 at 2K (unfolded shape).  P has
+// four consecutive columns per m = 1..K: P1c, P1s, P2c, P2s, after P(0) at
+// column 0 in the unfolded shape.  Both orders let a thread produce and
+// consume the harmonics in groups of four instead of holding all K at once.
+__host__ __device__ constexpr int acol_s(int n) { return 2 * (n - 1); }
+__host__ __device__ constexpr int acol_c(int n) { return 2 * (n - 1) + 1; }
+template <bool F>
+__host__ __device__ constexpr int pcol(int m, int j) { return (F ? 0 : 1) + 4 * (m - 1) + j; }
+
+// e^{i n 2 pi x} for n = 4g + j (j = 1..4): e^{i j 2 pi x} (from one sin/cos
+// and products) times the group base e^{i 4g 2 pi x}, which advances by
+// e^{i 4 2 pi x} per group: a recurrence of depth g + 2.
+struct Harm4 {
+    float c[5], s[5];
+    float bc, bs;
+    __device__ __forceinline__ void init(float x)
+    {
+        float s1, c1;
+        sincos2pi(x, &s1, &c1);
+        c[0] = 1.f; s[0] = 0.f;
+        c[1] = c1; s[1] = s1;
+        c[2] = fmaf(c1, c1, -s1 * s1); s[2] = 2.f * (s1 * c1);
+        c[3] = fmaf(c[2], c1, -s[2] * s1); s[3] = fmaf(s[2], c1, c[2] * s1);
+        c[4] = fmaf(c[2], c[2], -s[2] * s[2]); s[4] = 2.f * (s[2] * c[2]);
+        bc = 1.f; bs = 0.f;
+    }
+    // e^{i (4g + j) 2 pi x} of the current group g, j = 1..4
+    __device__ __forceinline__ void get(int j, float& C, float& S) const
+    {
+        C = fmaf(bc, c[j], -bs * s[j]);
+        S = fmaf(bs, c[j], bc * s[j]);
+    }
+    __device__ __forceinline__ void next_group()
+    {
+        const float nc = fmaf(bc, c[4], -bs * s[4]);
+        bs = fmaf(bs, c[4], bc * s[4]);
+        bc = nc;
+    }
+};
+
+// This thread's row of A from its x2, written as hi / lo tiles at row and
+// row + lo_off, eight columns (four harmonics) at a time; folded shape: returns
+// the m = 0 part of v1, p0 = sum_n T0[2n-2] S2_n + T0[2n-1] C2_n (eight
+// independent partial sums: this runs before the step's barrier).
+template <int K, bool F, bool H>
+__device__ __forceinline__ float write_row_stream(uint32_t row, uint32_t lo_off, float x2, const float* T0)
 {
-    using S = Shape<K, F, H>;
+    constexpr int NCOL = 2 * K + (F ? 0 : 1);
+    Harm4 h;
+    h.init(x2);
+    float ps[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int g = 0; g < (NCOL + 7) / 8; ++g) {
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+            const int n = 4 * g + e / 2 + 1;
+            if (n <= K) {
+                float C, Sn;
+                h.get(e / 2 + 1, C, Sn);
+                v[e] = Sn;
+                v[e + 1] = C;
+                if constexpr (F) {
+                    ps[(n - 1) & 3] = fmaf(T0[2 * n - 2], Sn, ps[(n - 1) & 3]);
+                    ps[4 + ((n - 1) & 3)] = fmaf(T0[2 * n - 1], C, ps[4 + ((n - 1) & 3)]);
+                }
+            } else {
+                v[e] = (!F && 8 * g + e == 2 * K) ? 1.f : 0.f;
+                v[e + 1] = 0.f;
+            }
+        }
+        if constexpr (H) {
+            uint32_t hv[4], lv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) split_f16x2(v[2 * q], v[2 * q + 1], hv[q], lv[q]);
+            st_shared_v4u(row + 128u * g, hv);
+            st_shared_v4u(row + lo_off + 128u * g, lv);
+        } else {
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                float4 hi, lo;
+                split_tf32(v[4 * half], hi.x, lo.x);
+                split_tf32(v[4 * half + 1], hi.y, lo.y);
+                split_tf32(v[4 * half + 2], hi.z, lo.z);
+                split_tf32(v[4 * half + 3], hi.w, lo.w);
+                st_shared_v4(row + 128u * (2 * g + half), hi);
+                st_shared_v4(row + lo_off + 128u * (2 * g + half), lo);
+            }
+        }
+        h.next_group();
+    }
+    if constexpr (F) return ((ps[0] + ps[1]) + (ps[2] + ps[3])) + ((ps[4] + ps[5]) + (ps[6] + ps[7]));
+    return 0.f;
+}
+
+// Sources of the x1 harmonics (C1m, S1m), m = 1..K in order, both from the
+// same Harm4 sequence (so results do not depend on the choice): computed as
+// the velocity sum needs them (few registers, after the MMA wait), or all
+// before the wait into arrays (overlapping the MMA, K + 1 pairs of registers).
+struct HarmStream {
+    Harm4 h;
+    __device__ __forceinline__ void init(float x) { h.init(x); }
+    __device__ __forceinline__ void at(int m, float& C, float& S)
+    {
+        const int jj = (m - 1) % 4 + 1;
+        if (jj == 1 && m > 1) h.next_group();
+        h.get(jj, C, S);
+    }
+};
+
+template <int K>
+struct HarmArray {
+    float c[K + 1], s[K + 1];
+    __device__ __forceinline__ void init(float x)
+    {
+        HarmStream st;
+        st.init(x);
+#pragma unroll
+        for (int m = 1; m <= K; ++m) st.at(m, c[m], s[m]);
+    }
+    __device__ __forceinline__ void at(int m, float& C, float& S) const
+    {
+        C = c[m];
+        S = s[m];
+    }
+};
+
+// The velocity from this lane's accumulator row and the x1 harmonics (source
+// src, initialised from x1), read 16 columns at a time:
+//   v1 = P(0) + sum_m C1m P1c(m) + S1m P1s(m),
+//   v2 = sum_m C1m (P2c(m) + N0c(m)) + S1m (P2s(m) + N0s(m)),
+// with P(0) and N0 from the FP32 pipes in the folded shape; each sum runs
+// over m in order.  FP16 operands: the sums over the accumulator carry the
+// scale of W, removed by inv_s.
+template <int K, bool F, bool H, typename Src>
+__device__ __forceinline__ void velocity_stream(uint32_t t_row, Src& src, const float* N0, float p0_in, float inv_s,
+                                                float& v1, float& v2)
+{
+    constexpr int NP = ((F ? 4 * K : 4 * K + 1) + 15) / 16 * 16;
+    float v1c = 0.f, v1s = 0.f, v2c = 0.f, v2s = 0.f, p0 = p0_in;
+    float Cm = 0.f, Sm = 0.f;
+#pragma unroll
+    for (int q = 0; q < NP / 16; ++q) {
+        float a[16];
+        tmem_ld16(t_row + 16u * q, a);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            const int col = 16 * q + e;
+            if (!F && col == 0) {
+                p0 = a[e];
+                continue;
+            }
+            const int cc = col - (F ? 0 : 1);
+            if (cc >= 4 * K) continue;
+            const int m = cc / 4 + 1, j = cc % 4;
+            if (j == 0) src.at(m, Cm, Sm);
+            if (j == 0) v1c = fmaf(Cm, a[e], v1c);
+            else if (j == 1) v1s = fmaf(Sm, a[e], v1s);
+            else if (j == 2) v2c = fmaf(Cm, F ? a[e] + N0[m - 1] : a[e], v2c);
+            else v2s = fmaf(Sm, F ? a[e] + N0[K + m - 1] : a[e], v2s);
+        }
+    }
     if constexpr (H) {
-#pragma unroll
-        for (int c = 0; c < (S::KD + 7) / 8; ++c) {
-            uint32_t h[4], l[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) split_f16x2(a[8 * c + 2 * q], a[8 * c + 2 * q + 1], h[q], l[q]);
-            st_shared_v4u(row + 128u * c, h);
-            st_shared_v4u(row + lo_off + 128u * c, l);
-        }
+        if constexpr (F) v1 = p0 + inv_s * (v1c + v1s);  // N0 carries the scale of W
+        else v1 = inv_s * (p0 + (v1c + v1s));
+        v2 = inv_s * (v2c + v2s);
     } else {
-#pragma unroll
-        for (int c = 0; c < (S::KD + 3) / 4; ++c) {
-            float4 h, l;
-            split_tf32(a[4 * c], h.x, l.x);
-            split_tf32(a[4 * c + 1], h.y, l.y);
-            split_tf32(a[4 * c + 2], h.z, l.z);
-            split_tf32(a[4 * c + 3], h.w, l.w);
-            st_shared_v4(row + 128u * c, h);
-            st_shared_v4(row + lo_off + 128u * c, l);
-        }
+        v1 = p0 + (v1c + v1s);
+        v2 = v2c + v2s;
     }
 }
 
@@ -449,6 +533,15 @@ __device__ __forceinline__ void issue_step_mma(uint32_t tmem, uint32_t sb, uint3
     tc::mma_commit(bar);
 }
 
+// The time-dependent kernel streams the x1 harmonics from K = 10 on, which
+// keeps it within 64 registers and 8 CTAs per SM (measured faster: 26.7
+// against 27.3 ms at K = 10); below, the product is short and computing them
+// during it (6 CTAs per SM) measured faster.
+template <int K>
+constexpr bool td_stream() { return K >= 10; }
+template <int K>
+using td_harm_t = std::conditional_t<td_stream<K>(), HarmStream, HarmArray<K>>;
+
 // Shared memory, threads and tensor-memory columns of the time-dependent kernel.
 template <int K>
 struct TdLaunch {
@@ -457,7 +550,7 @@ struct TdLaunch {
     static constexpr int THREADS = 128 * SETS;
     static constexpr int SMEM = SETS == 1 ? S::SMEM : 2 * SETS * S::A_BYTES + 2 * S::B_BYTES + 128 + 64;
     static constexpr uint32_t TMEM_COLS = SETS == 1 ? S::TMEM_COLS : 512u;  // set s at column 256 s
-    static constexpr int MIN_CTAS = SETS == 1 ? S::MIN_CTAS : 1;
+    static constexpr int MIN_CTAS = SETS == 1 ? (td_stream<K>() ? S::MIN_CTAS : S::MIN_CTAS6) : 1;
     static_assert(SETS == 1 || (S::NP <= 256 && SMEM + 1024 <= 233472), "two tiles fit");
 };
 
@@ -559,29 +652,7 @@ __global__ void __launch_bounds__(TdLaunch<K>::THREADS, TdLaunch<K>::MIN_CTAS)
 
     for (int n = 0; n < N; ++n) {
         // Row of A: x2 harmonics (hi and lo); folded: the m = 0 part of v1 here.
-        float p0 = 0.f;
-        {
-            float C2[K + 1], S2[K + 1];
-            fourier_powers<float, K>(X2.val(), C2, S2);
-            float a[S::WS];
-#pragma unroll
-            for (int q = 0; q < S::WS; ++q) a[q] = 0.f;
-#pragma unroll
-            for (int q = 1; q <= K; ++q) { a[q - 1] = S2[q]; a[K + q - 1] = C2[q]; }
-            if constexpr (F) {
-                // eight independent partial sums: this runs before the step's barrier
-                float ps[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                for (int q = 1; q <= K; ++q) {
-                    ps[(q - 1) & 3] = fmaf(p.T0[2 * q - 2], S2[q], ps[(q - 1) & 3]);
-                    ps[4 + ((q - 1) & 3)] = fmaf(p.T0[2 * q - 1], C2[q], ps[4 + ((q - 1) & 3)]);
-                }
-                p0 = ((ps[0] + ps[1]) + (ps[2] + ps[3])) + ((ps[4] + ps[5]) + (ps[6] + ps[7]));
-            } else {
-                a[2 * K] = 1.f;
-            }
-            write_row<K, F, H>(sb + row, a, (uint32_t)(SETS * S::A_BYTES));
-        }
+        const float p0 = write_row_stream<K, F, H>(sb + row, (uint32_t)(SETS * S::A_BYTES), X2.val(), p.T0);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         // One barrier per step: the rows are in place, and a wait that gave up
@@ -607,13 +678,12 @@ __global__ void __launch_bounds__(TdLaunch<K>::THREADS, TdLaunch<K>::MIN_CTAS)
         if ((n & 1) == 0) r = philox4x32_10(u32x4{(uint32_t)(n >> 1), pid, (uint32_t)stream, p.inst}, p.key0, p.key1);
         float xi1, xi2;
         box_muller<float>((n & 1) ? r.z : r.x, (n & 1) ? r.w : r.y, xi1, xi2);
-        float C1[K + 1], S1[K + 1];
-        fourier_powers<float, K>(X1.val(), C1, S1);
+        td_harm_t<K> h1;
+        h1.init(X1.val());
         failed = !tc::mbar_wait(bar_a, (uint32_t)(n & 1));
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         float v1, v2;
-        if constexpr (F) velocity_from_tmem_folded<K, H>(t_row, C1, S1, p.N0, p0, v1, v2, p.inv_s);
-        else velocity_from_tmem<K, H>(t_row, C1, S1, v1, v2, p.inv_s);
+        velocity_stream<K, F, H>(t_row, h1, p.N0, p0, p.inv_s, v1, v2);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         // Members whose last step is this one take it with their own length.
         while (n == stop) {
@@ -653,34 +723,25 @@ void build_W(const double* t, float* W)
     for (int q = 0; q < S::NP * S::WS; ++q) W[q] = 0.f;
     auto T = [&](int m, int n, int q) { return t[(size_t)(m * (K + 1) + n) * 8 + q]; };
     auto set = [&](int col, int row, double v) { W[col * S::WS + row] = (float)v; };
-    if constexpr (F) {
-        // Columns m-1, K+m-1, 2K+m-1, 3K+m-1 (m = 1..K); A columns S2_n at n-1, C2_n at K+n-1.
-        for (int m = 1; m <= K; ++m) {
-            const int c1c = m - 1, c1s = K + m - 1, c2c = 2 * K + m - 1, c2s = 3 * K + m - 1;
-            for (int n = 1; n <= K; ++n) {
-                set(c1c, n - 1, T(m, n, 0)); set(c1c, K + n - 1, T(m, n, 1));
-                set(c1s, n - 1, T(m, n, 2)); set(c1s, K + n - 1, T(m, n, 3));
-                set(c2c, K + n - 1, T(m, n, 4)); set(c2c, n - 1, T(m, n, 5));
-                set(c2s, K + n - 1, T(m, n, 6)); set(c2s, n - 1, T(m, n, 7));
-            }
-        }
-        return;
-    }
-    const int rS = 0, rC = K, rOne = 2 * K;  // A columns: S2_n at n-1, C2_n at K+n-1, constant at 2K
-    for (int n = 1; n <= K; ++n) {  // m = 0: v1 only
-        set(0, rS + n - 1, T(0, n, 0));
-        set(0, rC + n - 1, T(0, n, 1));
-    }
+    // A columns: S2_n at acol_s(n), C2_n at acol_c(n), the constant at 2K (unfolded).
     for (int m = 1; m <= K; ++m) {
-        const int c1c = m, c1s = K + m, c2c = 2 * K + m, c2s = 3 * K + m;
+        const int c1c = pcol<F>(m, 0), c1s = pcol<F>(m, 1), c2c = pcol<F>(m, 2), c2s = pcol<F>(m, 3);
         for (int n = 1; n <= K; ++n) {
-            set(c1c, rS + n - 1, T(m, n, 0)); set(c1c, rC + n - 1, T(m, n, 1));
-            set(c1s, rS + n - 1, T(m, n, 2)); set(c1s, rC + n - 1, T(m, n, 3));
-            set(c2c, rC + n - 1, T(m, n, 4)); set(c2c, rS + n - 1, T(m, n, 5));
-            set(c2s, rC + n - 1, T(m, n, 6)); set(c2s, rS + n - 1, T(m, n, 7));
+            set(c1c, acol_s(n), T(m, n, 0)); set(c1c, acol_c(n), T(m, n, 1));
+            set(c1s, acol_s(n), T(m, n, 2)); set(c1s, acol_c(n), T(m, n, 3));
+            set(c2c, acol_c(n), T(m, n, 4)); set(c2c, acol_s(n), T(m, n, 5));
+            set(c2s, acol_c(n), T(m, n, 6)); set(c2s, acol_s(n), T(m, n, 7));
         }
-        set(c2c, rOne, T(m, 0, 4));
-        set(c2s, rOne, T(m, 0, 6));
+        if constexpr (!F) {
+            set(c2c, 2 * K, T(m, 0, 4));
+            set(c2s, 2 * K, T(m, 0, 6));
+        }
+    }
+    if constexpr (!F) {
+        for (int n = 1; n <= K; ++n) {  // m = 0: v1 only, accumulator column 0
+            set(0, acol_s(n), T(0, n, 0));
+            set(0, acol_c(n), T(0, n, 1));
+        }
     }
 }
 
