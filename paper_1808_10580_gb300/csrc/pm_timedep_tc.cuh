@@ -3,7 +3,7 @@
 // The velocity of the stream function (Eq. v_expand) in the product basis is
 //   v1 = P(0) + sum_{m>=1} C1m P1c(m) + S1m P1s(m),   v2 = sum_{m>=1} C1m P2c(m) + S1m P2s(m),
 // where every partial sum P(.)(m) is linear in the x2 harmonics
-//   a = (S2_1..S2_K, C2_1..C2_K, 1).
+//   a = (S2_1, C2_1, S2_2, C2_2, ..., S2_K, C2_K, 1)   (interleaved; see acol_s).
 // For the 128 particles of a CTA this is one matrix product per Euler step,
 //   P[128 x (4K+1)] = A[128 x (2K+1)] . W[(2K+1) x (4K+1)],
 // issued as tcgen05.mma with the FP32 accumulator in tensor memory: kind::tf32
@@ -15,14 +15,15 @@
 // noise and the Euler step stay on the FP32 pipes.
 //
 // Per step: every thread writes its particle's row of A (hi and lo) into a
-// K-major tile (layout at tile_off), a CTA barrier hands the tile to the
-// tensor core (one thread issues 3 KS MMAs and commits to an mbarrier), the
-// threads compute the step's noise and x1 harmonics while it runs, and every
-// thread reads its accumulator columns back with tcgen05.ld.
+// K-major tile (layout at tile_off), four harmonics at a time; a CTA barrier
+// hands the tile to the tensor core (one thread issues 3 KS MMAs and commits
+// to an mbarrier); the threads compute the step's noise (and, in some
+// kernels, the x1 harmonics) while it runs, and every thread reads its
+// accumulator columns back with tcgen05.ld, four per m.
 #pragma once
 #include <algorithm>
-#include <type_traits>
 #include <cmath>
+#include <type_traits>
 #include <cuda_fp16.h>
 #include "pm_gemm_tc.cuh"
 #include "pm_kernels.cuh"
