@@ -49,8 +49,8 @@ struct TimedepLaunch {
 };
 
 // Paths per CTA of the time-dependent tensor-core kernel at K: two 128-row
-// particle tiles at K = 48, one otherwise (see td_sets in pm_timedep_tc.cuh).
-inline int td_tc_rows(int K) { return K == 48 ? 256 : 128; }
+// particle tiles at K = 56, one otherwise (see td_sets in pm_timedep_tc.cuh).
+inline int td_tc_rows(int K) { return K == 56 ? 256 : 128; }
 
 // Wave-number bounds of the time-dependent map beyond the unrolled kernels.
 inline bool wide_K(int K) { return K == 24 || K == 32 || K == 40 || K == 48 || K == 56 || K == 64; }

@@ -87,12 +87,12 @@ using TdShape = Shape<K, fold_of<K>(), half_of<K>()>;
 // Particle tiles of 128 rows per CTA of the time-dependent kernel: two where
 // one tile's CTA already fills the SM's shared memory with W and a second
 // tile still fits beside it, so that the SM has two sets of particles to
-// alternate; the two tiles share the coefficient tiles.  K = 48 (measured
-// 171.6 against 186.1 ms on the 300 x 1e4-path workload); at K = 56 the
-// 256-thread CTA spills registers and measured slower (257.0 against 240.1 ms).
-// (Mirrored by td_tc_rows in pm_launch.h.)
+// alternate; the two tiles share the coefficient tiles.  K = 56 (measured
+// 227.8 against 235.6 ms on the 300 x 1e4-path workload); at K = 48 one and
+// two tiles measured the same (181.0 and 180.7 ms).  (Mirrored by td_tc_rows
+// in pm_launch.h.)
 template <int K>
-constexpr int td_sets() { return K == 48 ? 2 : 1; }
+constexpr int td_sets() { return K == 56 ? 2 : 1; }
 
 // Instruction descriptor, kind::tf32: FP32 accumulator, TF32 A and B, both K-major.
 template <int NP>
