@@ -23,7 +23,6 @@
 #pragma once
 #include <algorithm>
 #include <cmath>
-#include <type_traits>
 #include <cuda_fp16.h>
 #include "pm_gemm_tc.cuh"
 #include "pm_kernels.cuh"
@@ -534,14 +533,10 @@ __device__ __forceinline__ void issue_step_mma(uint32_t tmem, uint32_t sb, uint3
     tc::mma_commit(bar);
 }
 
-// The time-dependent kernel streams the x1 harmonics from K = 10 on, which
-// keeps it within 64 registers and 8 CTAs per SM (measured faster: 26.7
-// against 27.3 ms at K = 10); below, the product is short and computing them
-// during it (6 CTAs per SM) measured faster.
-template <int K>
-constexpr bool td_stream() { return K >= 10; }
-template <int K>
-using td_harm_t = std::conditional_t<td_stream<K>(), HarmStream, HarmArray<K>>;
+// The time-dependent kernel streams the x1 harmonics (HarmStream), which keeps
+// it within 64 registers and 8 CTAs per SM where shared memory allows (K = 10:
+// 26.7 ms; computing them during the product at 6 CTAs per SM measured slower
+// at every K, e.g. 20.1 against 19.9 ms at K = 4 and 27.1 against 25.9 at K = 8).
 
 // Shared memory, threads and tensor-memory columns of the time-dependent kernel.
 template <int K>
@@ -551,7 +546,7 @@ struct TdLaunch {
     static constexpr int THREADS = 128 * SETS;
     static constexpr int SMEM = SETS == 1 ? S::SMEM : 2 * SETS * S::A_BYTES + 2 * S::B_BYTES + 128 + 64;
     static constexpr uint32_t TMEM_COLS = SETS == 1 ? S::TMEM_COLS : 512u;  // set s at column 256 s
-    static constexpr int MIN_CTAS = SETS == 1 ? (td_stream<K>() ? S::MIN_CTAS : S::MIN_CTAS6) : 1;
+    static constexpr int MIN_CTAS = SETS == 1 ? S::MIN_CTAS : 1;
     static_assert(SETS == 1 || (S::NP <= 256 && SMEM + 1024 <= 233472), "two tiles fit");
 };
 
@@ -679,7 +674,7 @@ __global__ void __launch_bounds__(TdLaunch<K>::THREADS, TdLaunch<K>::MIN_CTAS)
         if ((n & 1) == 0) r = philox4x32_10(u32x4{(uint32_t)(n >> 1), pid, (uint32_t)stream, p.inst}, p.key0, p.key1);
         float xi1, xi2;
         box_muller<float>((n & 1) ? r.z : r.x, (n & 1) ? r.w : r.y, xi1, xi2);
-        td_harm_t<K> h1;
+        HarmStream h1;
         h1.init(X1.val());
         failed = !tc::mbar_wait(bar_a, (uint32_t)(n & 1));
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
