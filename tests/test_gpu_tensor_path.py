@@ -213,3 +213,49 @@ def test_fp16_scale_of_w_at_extreme_field_sizes(c, orc, K, scale):
     d = xe - xo
     d -= np.round(d)
     assert np.abs(d).max() <= w.dt * 4e-6 * term_scale + 1e-7, np.abs(d).max()
+
+
+@pytest.mark.parametrize("K", [4, 8, 16])
+def test_batched_tensor_at_other_bounds(K):
+    # The batched kernel at other wave-number bounds against single-instance calls:
+    # Dirichlet instances share the unfolded shape, so bit for bit; time-dependent
+    # instances equal too where the single-problem kernel is unfolded (K = 4), and
+    # agree within Monte Carlo error where it folds the constant column (K = 8, 16).
+    from tests.test_gpu_batched import small_instances
+    h, s = _gpu.side_stream_ctx()
+    try:
+        with torch.cuda.stream(s):
+            ws = small_instances(B=4, M=256)
+            for b, w in enumerate(ws):
+                w.K = K
+                w.u = inputs.prior_field(K, 1100 + K, counter=b)
+            b_, n_rows = _gpu.batch_from_workloads(ws, device=True)
+            mean = torch.empty(n_rows, dtype=torch.float64, device="cuda")
+            var = torch.empty_like(mean)
+            rc = pm.pm_forward_batched(h, b_, pm.PM_FP32 | pm.PM_TENSOR, mean, var)
+            torch.cuda.synchronize()
+            got, gv = mean.cpu().numpy(), var.cpu().numpy()
+            row = 0
+            for k, w in enumerate(ws):
+                n = len(w.x)
+                m = np.empty(n)
+                v = np.empty(n)
+                if isinstance(w, inputs.TimedepWorkload):
+                    pm.pm_forward_timedep(h, pm.Field(w.K, w.u), w.kappa,
+                                          pm.Fourier(w.theta0.k, w.theta0.a, w.theta0.b), w.x, w.t, n, w.M, w.dt,
+                                          w.seed, pm.PM_FP32 | pm.PM_TENSOR, m, v, instance=k)
+                    if K % 4:  # unfolded shape in both kernels
+                        np.testing.assert_allclose(got[row:row + n], m, rtol=0, atol=1e-12)
+                    else:
+                        se = np.sqrt((gv[row:row + n] + v) / w.M)
+                        assert np.all(np.abs(got[row:row + n] - m) <= 5 * se + 1e-6)
+                else:
+                    pm.pm_forward_dirichlet(h, pm.Field(w.K, w.u), w.drift_scale, w.kappa,
+                                            pm.DirichletData(w.g.R, w.g.quad, w.g.f_const, w.g.a, w.g.b), w.x, n,
+                                            w.M, w.dt, w.max_steps, w.seed, pm.PM_FP32 | pm.PM_TENSOR, m, v,
+                                            instance=k)
+                    np.testing.assert_allclose(got[row:row + n], m, rtol=0, atol=1e-12)
+                row += n
+        assert rc == 0
+    finally:
+        pm.pm_destroy(h)
