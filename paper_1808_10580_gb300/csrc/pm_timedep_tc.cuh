@@ -33,7 +33,8 @@ namespace tdtc {
 // F ("folded"): the constant column of A (the n = 0 terms of v2) and the
 // m = 0 column of P (the x1-independent part of v1) leave the product and are
 // summed on the FP32 pipes (4K FMAs per particle), so that A has 2K columns
-// and P 4K: for K a multiple of 4 that saves one MMA k-step and 16 columns of N.
+// and P 4K: for K a multiple of 4 that saves 16 columns of N and, where 2K + 1
+// would start a new k-step, a k-step.
 //
 // H ("half"): the operands are FP16 instead of TF32 (kind::f16).  FP16 keeps
 // the same 11 significant bits as TF32, so the same hi + lo split and three
