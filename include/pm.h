@@ -478,16 +478,24 @@ void pm_pcn_destroy(pm_pcn* chains);
  * and that every GPU which loads the library holds until the process exits.
  * The call allocates nothing: no cudaMalloc, cudaFree or allocating library
  * routine.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *   - Every call looks up the array's device address (cudaGetSymbolAddress)
+ *     in the current device's context, so a call after cudaDeviceReset finds
+ *     the array where the new context loaded it.  Under CUDA's lazy module
+ *     loading the first call on a device also loads the library's kernels
+ *     (the driver may allocate for that, once): make one call on each device
+ *     before the code that must not allocate, and before any stream capture.
  *   - Problems whose scratch (about n_obs * (48 + 16 * ceil(M/128)) bytes)
  *     exceeds PM_NOALLOC_SCRATCH_BYTES are rejected with PM_EINVAL.
+ *   - x, t, mean and var must be device memory of the current device (or
+ *     managed memory); anything else is rejected with PM_EINVAL before any
+ *     work is queued.
  *   - All calls share the one array: calls whose work overlaps on the GPU
  *     (other streams, other host threads) race and give wrong results;
  *     serialise them.
- *   - flags: PM_FP32 or PM_FP64, plus PM_ASYNC to return without waiting
- *     (then invalid x/t values are not reported).
+ *   - flags: PM_FP32 or PM_FP64, plus PM_ASYNC to return without waiting.
+ *     With PM_ASYNC the call cannot report invalid observation inputs (NaN
+ *     or negative times, non-finite points): they are detected on the GPU,
+ *     and the flag that records them is only read by a synchronous call.
  * ------------------------------------------------------------------------- */
 #define PM_NOALLOC_SCRATCH_BYTES (4u << 20)
 

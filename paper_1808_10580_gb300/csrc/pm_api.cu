@@ -104,15 +104,19 @@ constexpr double kTwoPi = 6.283185307179586476925286766559;
 // Half-mode index of (m, n) in the coefficient layout of pm_field.
 inline int64_t half_index(int K, int m, int n) { return m == 0 ? (n - 1) : K + (int64_t)(m - 1) * (2 * K + 1) + (n + K); }
 
+}  // namespace
+
+namespace pm {
+
 // Section 4.1, Eq. v_expand: stream-function coefficients (a_h, b_h) of the
 // half-plane modes -> the product-basis velocity table the kernels read.
 // For m, n >= 1 the pair (m, n), (m, -n) folds into
 //   A = a(m,n) + a(m,-n), B = b(m,n) - b(m,-n), G = b(m,n) + b(m,-n), D = a(m,-n) - a(m,n)
 // (psi = A C1 C2 + B C1 S2 + G S1 C2 + D S1 S2); then e = 2 pi n (A, -B, G, -D)
 // feed v1 = -d2 psi and f = 2 pi m (G, D, -A, -B) feed v2 = d1 psi.
-std::vector<double> stage_coefficients(int K, const double* u)
+void stage_coefficients_into(int K, const double* u, double* tab)
 {
-    std::vector<double> tab((size_t)table_size(K), 0.0);
+    for (int q = 0; q < table_size(K); ++q) tab[q] = 0.0;
     auto a = [&](int m, int n) { return u[2 * half_index(K, m, n)]; };
     auto b = [&](int m, int n) { return u[2 * half_index(K, m, n) + 1]; };
     for (int m = 0; m <= K; ++m) {
@@ -133,6 +137,16 @@ std::vector<double> stage_coefficients(int K, const double* u)
             e[4] = sm * G; e[5] = sm * D; e[6] = -sm * A; e[7] = -sm * B;
         }
     }
+}
+
+}  // namespace pm
+
+namespace {
+
+std::vector<double> stage_coefficients(int K, const double* u)
+{
+    std::vector<double> tab((size_t)table_size(K), 0.0);
+    pm::stage_coefficients_into(K, u, tab.data());
     return tab;
 }
 
@@ -146,14 +160,18 @@ bool finite_array(const double* p, int64_t n)
     return true;
 }
 
-bool is_device_pointer(const void* p)
+// Device (or managed) memory that belongs to `device`: a pointer into another
+// GPU's memory is rejected, since the kernels would read it over the peer
+// link or fault.
+bool is_device_pointer(const void* p, int device)
 {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == device;
 }
 }  // namespace pm
 
@@ -217,12 +235,28 @@ int check_field(const pm_field* f, bool allow_wide)
     return PM_OK;
 }
 
-int check_ptrs(uint32_t flags, std::initializer_list<const void*> ptrs)
+int check_ptrs(const pm_ctx* c, uint32_t flags, std::initializer_list<const void*> ptrs)
 {
     if (!(flags & PM_DEVICE_PTRS)) return PM_OK;
     for (const void* p : ptrs)
-        if (p && !is_device_pointer(p))
-            return fail(PM_EINVAL, "PM_DEVICE_PTRS is set but a pointer is not device memory");
+        if (p && !is_device_pointer(p, c->device))
+            return fail(PM_EINVAL, "PM_DEVICE_PTRS is set but a pointer is not device memory of the context's device %d",
+                        c->device);
+    return PM_OK;
+}
+
+int check_theta0(const pm_fourier* th)
+{
+    if (!th) return fail(PM_EINVAL, "theta0 is NULL");
+    if (th->n < 0 || th->n > PM_MAX_THETA0_MODES) return fail(PM_EINVAL, "theta0 has %d modes (max %d)", th->n, PM_MAX_THETA0_MODES);
+    if (th->n > 0 && (!th->k || !th->a || !th->b)) return fail(PM_EINVAL, "theta0 arrays are NULL");
+    if (th->n > 0 && (!finite_array(th->a, th->n) || !finite_array(th->b, th->n)))
+        return fail(PM_EINVAL, "theta0 amplitudes contain NaN or Inf");
+    // The float kernels reduce the phase k.x modulo 1 in float: exact only
+    // while |k| x stays far below 2^23.
+    for (int q = 0; q < th->n; ++q)
+        if (std::abs(th->k[2 * q]) > 4096 || std::abs(th->k[2 * q + 1]) > 4096)
+            return fail(PM_EINVAL, "theta0 wave number out of range (|k| <= 4096)");
     return PM_OK;
 }
 
@@ -404,14 +438,7 @@ int pm_forward_timedep(pm_ctx* c, const pm_field* field, double kappa, const pm_
     int rc = check_field(field, true);
     if (rc) return rc;
     if (wide_K(field->K) && (flags & PM_FP64)) return fail(PM_EINVAL, "K=%d runs with float paths only", field->K);
-    if (!th) return fail(PM_EINVAL, "theta0 is NULL");
-    if (th->n < 0 || th->n > PM_MAX_THETA0_MODES) return fail(PM_EINVAL, "theta0 has %d modes (max %d)", th->n, PM_MAX_THETA0_MODES);
-    if (th->n > 0 && (!th->k || !th->a || !th->b)) return fail(PM_EINVAL, "theta0 arrays are NULL");
-    if (th->n > 0 && (!finite_array(th->a, th->n) || !finite_array(th->b, th->n)))
-        return fail(PM_EINVAL, "theta0 amplitudes contain NaN or Inf");
-    for (int q = 0; q < th->n; ++q)
-        if (std::abs(th->k[2 * q]) > 4096 || std::abs(th->k[2 * q + 1]) > 4096)
-            return fail(PM_EINVAL, "theta0 wave number out of range");
+    if ((rc = check_theta0(th))) return rc;
     if (!(std::isfinite(kappa) && kappa >= 0)) return fail(PM_EINVAL, "kappa must be finite and >= 0");
     if (!(std::isfinite(dt) && dt > 0)) return fail(PM_EINVAL, "dt must be finite and > 0");
     if (n_obs < 0) return fail(PM_EINVAL, "n_obs < 0");
@@ -423,7 +450,7 @@ int pm_forward_timedep(pm_ctx* c, const pm_field* field, double kappa, const pm_
     if (!x || !t || !mean) return fail(PM_EINVAL, "x, t and mean must not be NULL");
     double* g_out = opts ? opts->g_out : nullptr;
     double* x_out = opts ? opts->x_out : nullptr;
-    if ((rc = check_ptrs(flags, {x, t, mean, var, g_out, x_out}))) return rc;
+    if ((rc = check_ptrs(c, flags, {x, t, mean, var, g_out, x_out}))) return rc;
     const bool dev = flags & PM_DEVICE_PTRS;
     const bool fp64 = flags & PM_FP64;
     const int K = field->K;
@@ -673,7 +700,7 @@ int pm_forward_dirichlet(pm_ctx* c, const pm_field* field, double drift_scale, d
     if (!x || !mean) return fail(PM_EINVAL, "x and mean must not be NULL");
     double* g_out = opts ? opts->g_out : nullptr;
     double* x_out = opts ? opts->x_out : nullptr;
-    if ((rc = check_ptrs(flags, {x, mean, var, exit_step, n_unexited, g_out, x_out}))) return rc;
+    if ((rc = check_ptrs(c, flags, {x, mean, var, exit_step, n_unexited, g_out, x_out}))) return rc;
     const bool dev = flags & PM_DEVICE_PTRS;
     const bool fp64 = flags & PM_FP64;
     if (!dev && !finite_array(x, 2 * n_obs)) return fail(PM_EINVAL, "observation points contain NaN or Inf");
@@ -849,7 +876,7 @@ int pm_philox(pm_ctx* c, const uint32_t* ctr, uint32_t key0, uint32_t key1, int6
     if (n < 0) return fail(PM_EINVAL, "n < 0");
     if (n == 0) return PM_OK;
     if (!ctr || !out) return fail(PM_EINVAL, "NULL array");
-    int rc = check_ptrs(flags, {ctr, out});
+    int rc = check_ptrs(c, flags, {ctr, out});
     if (rc) return rc;
     if ((rc = set_device(c))) return rc;
     const bool dev = flags & PM_DEVICE_PTRS;
@@ -881,7 +908,7 @@ int pm_normals(pm_ctx* c, uint64_t seed, uint32_t b, uint32_t j, uint32_t i, int
     if (count < 0 || n0 < 0) return fail(PM_EINVAL, "negative step range");
     if (count == 0) return PM_OK;
     if (!out) return fail(PM_EINVAL, "out is NULL");
-    int rc = check_ptrs(flags, {out});
+    int rc = check_ptrs(c, flags, {out});
     if (rc) return rc;
     if ((rc = set_device(c))) return rc;
     const bool dev = flags & PM_DEVICE_PTRS;
@@ -906,7 +933,7 @@ int pm_velocity(pm_ctx* c, const pm_field* field, const double* x, int64_t npts,
     if (npts < 0) return fail(PM_EINVAL, "npts < 0");
     if (npts == 0) return PM_OK;
     if (!x || !v) return fail(PM_EINVAL, "NULL array");
-    if ((rc = check_ptrs(flags, {x, v}))) return rc;
+    if ((rc = check_ptrs(c, flags, {x, v}))) return rc;
     if ((rc = set_device(c))) return rc;
     const bool dev = flags & PM_DEVICE_PTRS;
     const double* dx = x;

@@ -117,7 +117,7 @@ extern "C" int pm_forward_batched(pm_ctx* c, const pm_batch* bt, uint32_t flags,
         } else {
             any_td = true;
         }
-        if (NU > 0 && dev && !is_device_pointer(I.u)) return fail(PM_EINVAL, "instance %d: u is not device memory", b);
+        if (NU > 0 && dev && !is_device_pointer(I.u, c->device)) return fail(PM_EINVAL, "instance %d: u is not device memory", b);
         if (NU > 0 && !dev && !finite_array(I.u, NU)) return fail(PM_EINVAL, "instance %d: coefficients not finite", b);
         if (I.n_obs > ((int64_t)1 << 62) / I.M) return fail(PM_EINVAL, "instance %d: too many paths", b);
         ranges.push_back({I.row0, I.n_obs});
@@ -147,7 +147,7 @@ extern "C" int pm_forward_batched(pm_ctx* c, const pm_batch* bt, uint32_t flags,
         if (gd->n_ang > 0 && (!gd->a || !gd->b || !finite_array(gd->a, gd->n_ang) || !finite_array(gd->b, gd->n_ang)))
             return fail(PM_EINVAL, "boundary arrays NULL or not finite");
     }
-    int rc = check_ptrs(flags, {bt->x, bt->t, mean, var, n_unexited});
+    int rc = check_ptrs(c, flags, {bt->x, bt->t, mean, var, n_unexited});
     if (rc) return rc;
     if (!dev && !finite_array(bt->x, 2 * bt->n_rows)) return fail(PM_EINVAL, "x contains NaN or Inf");
     if ((rc = set_device(c))) return rc;

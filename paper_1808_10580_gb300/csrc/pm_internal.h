@@ -57,12 +57,18 @@ int fail(int code, const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
 bool supported_K(int K);
 bool finite_array(const double* p, int64_t n);
-bool is_device_pointer(const void* p);
+bool is_device_pointer(const void* p, int device);
 int ensure_workspace(pm_ctx* c, size_t bytes);
 int ensure_host(pm_ctx* c, size_t bytes);
 int set_device(pm_ctx* c);
 int check_field(const pm_field* f, bool allow_wide = false);
-int check_ptrs(uint32_t flags, std::initializer_list<const void*> ptrs);
+int check_ptrs(const pm_ctx* c, uint32_t flags, std::initializer_list<const void*> ptrs);
+// theta0 description: modes within PM_MAX_THETA0_MODES, arrays present and
+// finite, wave numbers |k| <= 4096 (the float phase reduction's range).
+int check_theta0(const pm_fourier* th);
+// Section 4.1, Eq. v_expand: the product-basis table of the stream-function
+// coefficients u (2|H_K| doubles) into tab (table_size(K) doubles, caller's storage).
+void stage_coefficients_into(int K, const double* u, double* tab);
 void count_launch(pm_ctx* c, int n = 1);
 
 // Autotuner (pm_autotune.cu).  kind: PM_TUNE_DIRICHLET or PM_TUNE_BATCHED.

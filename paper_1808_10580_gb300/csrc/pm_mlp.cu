@@ -557,7 +557,7 @@ int pm_surrogate_train(pm_ctx* c, pm_mlp* n, const float* U, const float* Y, int
     int rc = set_device(c);
     if (rc) return rc;
     const bool dev = flags & PM_DEVICE_PTRS;
-    if ((rc = check_ptrs(flags, {U, Y}))) return rc;
+    if ((rc = check_ptrs(c, flags, {U, Y}))) return rc;
     const int64_t nb = (N + o->batch - 1) / o->batch;
     const int B = (int)std::min<int64_t>(o->batch, N);
     const int Bp = (B + 127) / 128 * 128;
@@ -624,7 +624,7 @@ int pm_surrogate_infer(pm_ctx* c, const pm_mlp* nc, const float* U, int64_t B, f
     int rc = set_device(c);
     if (rc) return rc;
     const bool dev = flags & PM_DEVICE_PTRS;
-    if ((rc = check_ptrs(flags, {U, Yout}))) return rc;
+    if ((rc = check_ptrs(c, flags, {U, Yout}))) return rc;
     const int Bp = (int)((B + 127) / 128 * 128);
     if ((rc = mlp_reserve(c, n, Bp))) return rc;
     const float* dU = U;
@@ -652,7 +652,7 @@ int pm_gemm_bf16(pm_ctx* c, const void* A, int32_t lda, const void* B, int32_t l
     if (!c || !A || !B || !C) return fail(PM_EINVAL, "NULL argument");
     int rc = set_device(c);
     if (rc) return rc;
-    if ((rc = check_ptrs(PM_DEVICE_PTRS, {A, B, C}))) return rc;
+    if ((rc = check_ptrs(c, PM_DEVICE_PTRS, {A, B, C}))) return rc;
     if (ldc % 4 || ((uintptr_t)C % 16)) return fail(PM_EINVAL, "C must be 16-byte aligned with ldc a multiple of 4");
     if ((rc = ensure_workspace(c, 256))) return rc;
     unsigned* err = (unsigned*)c->ws;

@@ -14,9 +14,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 
 #include "../../include/pm.h"
+#include "pm_internal.h"
 #include "pm_launch.h"
 
 using namespace pm;
@@ -24,15 +24,11 @@ using namespace pm;
 namespace {
 
 constexpr size_t kScratchBytes = PM_NOALLOC_SCRATCH_BYTES;
-constexpr int kMaxDevices = 64;
 
 // The shared scratch.  In host code `g_noalloc_scratch` names a host-side
 // stand-in, not the device array: kernels receive the device address that
 // cudaGetSymbolAddress returns for the current device.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
-
-std::mutex g_setup_mutex;
-void* g_scratch_dev[kMaxDevices] = {};
 
 // Messages go to the same per-thread slot pm_last_error() reads.
 int nfail(int code, const char* msg) { return pm::set_error(code, msg); }
@@ -44,65 +40,33 @@ int nfail_cuda(cudaError_t e, const char* what)
     return pm::set_error(e == cudaErrorMemoryAllocation ? PM_ENOMEM : PM_ECUDA, buf);
 }
 
-// Device address of the scratch on the current device, looked up once per device.
-int scratch_address(int device, void** out)
+// Device address of the scratch in the current device's context, looked up on
+// every call: after a cudaDeviceReset the module is loaded again in a new
+// context and the array may sit elsewhere, so no address is kept between
+// calls.  Once the module is loaded the lookup allocates nothing.
+int scratch_address(void** out)
 {
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_dev[device]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return nfail_cuda(e, "cudaGetSymbolAddress(scratch)");
-        g_scratch_dev[device] = p;
-    }
-    *out = g_scratch_dev[device];
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return nfail_cuda(e, "cudaGetSymbolAddress(scratch)");
+    *out = p;
     return PM_OK;
 }
 
-bool finite_all(const double* p, int64_t n)
-{
-    for (int64_t i = 0; i < n; ++i)
-        if (!std::isfinite(p[i])) return false;
-    return true;
-}
-
-bool on_device(const void* p)
+// Device (or managed) memory of `device`; a pointer into another GPU's memory
+// is rejected (the kernels would read it over the peer link, or fault).
+bool on_device(const void* p, int device)
 {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == device;
 }
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
-
-constexpr double kTwoPi = 6.283185307179586476925286766559;
-
-// Same product-basis table as the main entry point builds (see pm_api.cu),
-// written into caller-provided storage so that nothing is allocated.
-void fill_table(int K, const double* u, double* tab)
-{
-    const int n = table_size(K);
-    for (int q = 0; q < n; ++q) tab[q] = 0.0;
-    auto idx = [&](int m, int nn) -> int64_t { return m == 0 ? (nn - 1) : K + (int64_t)(m - 1) * (2 * K + 1) + (nn + K); };
-    for (int m = 0; m <= K; ++m)
-        for (int nn = 0; nn <= K; ++nn) {
-            if (m == 0 && nn == 0) continue;
-            double A = 0, B = 0, G = 0, D = 0;
-            if (m == 0) { A = u[2 * idx(0, nn)]; B = u[2 * idx(0, nn) + 1]; }
-            else if (nn == 0) { A = u[2 * idx(m, 0)]; G = u[2 * idx(m, 0) + 1]; }
-            else {
-                const double ap = u[2 * idx(m, nn)], bp = u[2 * idx(m, nn) + 1];
-                const double am = u[2 * idx(m, -nn)], bm = u[2 * idx(m, -nn) + 1];
-                A = ap + am; B = bp - bm; G = bp + bm; D = am - ap;
-            }
-            double* e = tab + (size_t)(m * (K + 1) + nn) * 8;
-            const double sn = kTwoPi * nn, sm = kTwoPi * m;
-            e[0] = sn * A; e[1] = -sn * B; e[2] = sn * G; e[3] = -sn * D;
-            e[4] = sm * G; e[5] = sm * D; e[6] = -sm * A; e[7] = -sm * B;
-        }
-}
 
 template <typename Real>
 cudaError_t dispatch(int K, const TimedepLaunch& L, cudaStream_t s)
@@ -134,16 +98,18 @@ extern "C" int pm_forward_timedep_noalloc(const pm_field* field, double kappa, c
     if (!(K >= 0 && K <= 6) && K != 8 && K != 10 && K != 12 && K != 16)
         return nfail(PM_EINVAL, "K is not one of the compiled bounds 0..6, 8, 10, 12, 16");
     const int64_t nu = (int64_t)(2 * K + 1) * (2 * K + 1) - 1;
-    if (nu > 0 && (!field->u || !finite_all(field->u, nu))) return nfail(PM_EINVAL, "field coefficients NULL or not finite");
-    if (!th || th->n < 0 || th->n > PM_MAX_THETA0_MODES) return nfail(PM_EINVAL, "theta0 missing or too many modes");
-    if (th->n > 0 && (!th->k || !th->a || !th->b || !finite_all(th->a, th->n) || !finite_all(th->b, th->n)))
-        return nfail(PM_EINVAL, "theta0 arrays NULL or not finite");
+    if (nu > 0 && (!field->u || !pm::finite_array(field->u, nu))) return nfail(PM_EINVAL, "field coefficients NULL or not finite");
+    int rc = pm::check_theta0(th);
+    if (rc) return rc;
     if (!(std::isfinite(kappa) && kappa >= 0)) return nfail(PM_EINVAL, "kappa must be finite and >= 0");
     if (!(std::isfinite(dt) && dt > 0)) return nfail(PM_EINVAL, "dt must be finite and > 0");
     if (n_obs < 0 || M < 1 || M > ((int64_t)1 << 32)) return nfail(PM_EINVAL, "need n_obs >= 0 and 1 <= M <= 2^32");
     if (n_obs == 0) return PM_OK;
     if (!x || !t || !mean) return nfail(PM_EINVAL, "x, t and mean must not be NULL");
-    if (!on_device(x) || !on_device(t) || !on_device(mean) || (var && !on_device(var)))
+    int device = 0;
+    cudaError_t e = cudaGetDevice(&device);
+    if (e != cudaSuccess) return nfail_cuda(e, "cudaGetDevice");
+    if (!on_device(x, device) || !on_device(t, device) || !on_device(mean, device) || (var && !on_device(var, device)))
         return nfail(PM_EINVAL, "x, t, mean and var must be device pointers on the current device");
 
     // Scratch layout: flag | records | order | per-CTA partials.
@@ -162,13 +128,8 @@ extern "C" int pm_forward_timedep_noalloc(const pm_field* field, double kappa, c
         return nfail(PM_EINVAL, buf);
     }
 
-    int device = 0;
-    cudaError_t e = cudaGetDevice(&device);
-    if (e != cudaSuccess) return nfail_cuda(e, "cudaGetDevice");
-    if (device < 0 || device >= kMaxDevices) return nfail(PM_EINVAL, "device index out of range");
     void* base = nullptr;
-    int rc = scratch_address(device, &base);
-    if (rc) return rc;
+    if ((rc = scratch_address(&base))) return rc;
     char* s = (char*)base;
     unsigned* err = (unsigned*)s;
     ObsRec* rec = (ObsRec*)(s + off_rec);
@@ -184,7 +145,7 @@ extern "C" int pm_forward_timedep_noalloc(const pm_field* field, double kappa, c
     if (e != cudaSuccess) return nfail_cuda(e, "prep kernel");
 
     double tab[table_size(16)];
-    fill_table(K, field->u, tab);
+    pm::stage_coefficients_into(K, field->u, tab);
     TimedepLaunch L{};
     L.coef = tab;
     L.nq = th->n;

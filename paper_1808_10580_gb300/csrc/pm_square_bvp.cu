@@ -204,7 +204,7 @@ extern "C" int pm_forward_square_bvp(pm_ctx* c, const pm_square_bvp* prob, const
     if (off < 0 || off + M > ((int64_t)1 << 32)) return fail(PM_EINVAL, "path_offset + M exceeds 2^32");
     if (!x || !mean) return fail(PM_EINVAL, "x and mean must not be NULL");
     double* g_out = opts ? opts->g_out : nullptr;
-    int rc = check_ptrs(flags, {x, mean, var, exit_step, n_unexited, g_out});
+    int rc = check_ptrs(c, flags, {x, mean, var, exit_step, n_unexited, g_out});
     if (rc) return rc;
     if (!(flags & PM_DEVICE_PTRS) && !finite_array(x, 2 * n_obs)) return fail(PM_EINVAL, "x contains NaN or Inf");
     if ((rc = set_device(c))) return rc;

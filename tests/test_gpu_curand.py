@@ -25,12 +25,12 @@ ROOT = os.path.dirname(HERE)
 
 
 @pytest.fixture(scope="module")
-def curand():
+def curand(tmp_path_factory):
+    # The probe is test-only: built under pytest's temporary directory, never
+    # beside the library's own build products.
     nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
     src = os.path.join(HERE, "gpu_probes", "curand_philox_probe.cu")
-    out_dir = os.path.join(ROOT, "paper_1808_10580_gb300", "_build")
-    os.makedirs(out_dir, exist_ok=True)
-    out = os.path.join(out_dir, "curand_philox_probe.so")
+    out = str(tmp_path_factory.mktemp("curand_probe") / "curand_philox_probe.so")
     subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O2", "-shared", "-Xcompiler", "-fPIC",
                     src, "-o", out], check=True, capture_output=True)
     lib = ctypes.CDLL(out)
