@@ -46,6 +46,17 @@ def flops_per_step(K: int) -> int:
     return 2 * (2 * n_u + 4 * K)
 
 
+def method_flops_per_step(K: int) -> int:
+    """The method's own work per particle-step, independent of how a kernel
+    organises it: the velocity of Eq. v_expand summed directly takes 8 FMAs per
+    half-mode (the complex product of the x1 and x2 harmonics, then p cos + q
+    sin for both velocity components), about 8H instructions, plus about 90
+    for the noise, the Euler step and the wrap; an FMA counts as 2 FLOP.
+    K = 10: 2 (8 * 220 + 90) = 3700 FLOP."""
+    H = ((2 * K + 1) ** 2 - 1) // 2
+    return 2 * (8 * H + 90)
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -76,6 +87,45 @@ def tensor_peak(K: int, peaks: dict, peaks_kind: str):
     if tensor_operands(K) == "f16":
         return bf16, f"FP16 dense = bf16_tflops {bf16} ({peaks_kind}, burst; same dense rate)"
     return bf16 * 1.1 / 2.25, f"TF32 dense = bf16_tflops {bf16} ({peaks_kind}, burst) x 1.1/2.25"
+
+
+def tensor_roofline(K, steps, kernel_ms, peaks, peaks_kind):
+    """Roofline of the tensor-core particle kernel: the method's work
+    (method_flops_per_step) per second against the dense peak of its operand
+    type; beside it the fraction the issued MMAs reach (three hi/lo products of
+    the padded contraction)."""
+    peak, basis = tensor_peak(K, peaks, peaks_kind)
+    sec = kernel_ms / 1e3
+    achieved = steps * method_flops_per_step(K) / sec / 1e12
+    issued = steps * tensor_flops_per_step(K) / sec / 1e12
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "flop_per_particle_step": method_flops_per_step(K),
+            "work_basis": "the method's work: direct-sum velocity, 8 FMAs per half-mode + ~90 per step",
+            "peak_basis": basis, "operands": tensor_operands(K), "tensor_issued_frac": issued / peak,
+            "tensor_issued_flop_per_particle_step": tensor_flops_per_step(K),
+            "tensor_issued_note": "the MMAs the kernel issues: three hi/lo products of the padded "
+                                  "(2K+1) x (4K+1) contraction"}
+
+
+def fp32_peak_tflops(peaks, sm_count):
+    """FP32 FMA pipe: SMs x 128 lanes x 2 FLOP x the maximum SM clock."""
+    return sm_count * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+
+
+def fp32_roofline(K, steps, kernel_ms, peaks, peaks_kind, sm_count):
+    """Roofline of the FP32-pipe particle kernel: the FMAs it executes
+    (flops_per_step) per second against the FP32 pipe peak; beside it the
+    method's work (method_flops_per_step) on the same peak."""
+    peak = fp32_peak_tflops(peaks, sm_count)
+    sec = kernel_ms / 1e3
+    achieved = steps * flops_per_step(K) / sec / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "flop_per_particle_step": flops_per_step(K),
+            "flop_note": "the FMAs it executes: 2 per real coefficient + 4 per x1 harmonic",
+            "method_work_frac": steps * method_flops_per_step(K) / sec / 1e12 / peak,
+            "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 FLOP x sm_max_mhz "
+                          f"{peaks.get('sm_max_mhz', 2070.0)} ({peaks_kind})",
+            "particle_steps_per_s": steps / sec}
 
 
 def profile_value(name, key):
@@ -298,6 +348,22 @@ def run_gpu(args):
         e2e_times.append(time.perf_counter() - t0)
     e2e_value = steps_per_eval * world / statistics.median(e2e_times)
 
+    # The same map on the FP32 pipes (timedep_kernel<float, K, 128>: the
+    # product-basis sum, no tensor cores), kernel time by events.
+    simt = None
+    if args.tensor and not args.no_fp32_compare:
+        flags32 = pm.PM_FP32 | pm.PM_ASYNC | (pm.PM_SHARE_PATHS if args.share_paths else 0)
+        ms32 = []
+        for k in range(4):
+            flush.zero_()
+            pm.pm_forward_timedep(ctx, fld, w.kappa, th, x, t, n_obs, w.M, w.dt, w.seed, flags32, mean, var,
+                                  instance=inst)
+            if k >= 1:
+                ms32.append(pm.pm_last_kernel_ms(ctx))
+        simt = {"kernel": f"timedep_kernel<float,{w.K},128>", "kernel_ms": statistics.mean(ms32)}
+        step()                                     # leave the tensor-core estimate in mean / var
+        torch.cuda.synchronize(dev)
+
     # Monte Carlo standard error of the timed estimate.
     se = np.sqrt(var.cpu().numpy() / w.M)
 
@@ -318,28 +384,18 @@ def run_gpu(args):
     if rank == 0:
         peaks, peaks_kind = measured_peaks()
         sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-        fp32_peak = sm_count * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        fp32_peak = fp32_peak_tflops(peaks, sm_count)
         kern_mean_ms = statistics.mean(kern_ms)
         simt_rate = steps_per_eval * flops_per_step(w.K) / (kern_mean_ms / 1e3) / 1e12
         if args.tensor:
-            peak_tflops, peak_basis = tensor_peak(w.K, peaks, peaks_kind)
-            achieved = steps_per_eval * tensor_flops_per_step(w.K) / (kern_mean_ms / 1e3) / 1e12
-            roof = {"bound": "tensor", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                    "frac": achieved / peak_tflops,
+            roof = tensor_roofline(w.K, steps_per_eval, kern_mean_ms, peaks, peaks_kind)
+            roof.update({
                     "traffic": profile_traffic("timedep_k10_tc_kernel.md") if w.K == 10 else None,
                     "kernel": f"timedep_tc_kernel<{w.K}>", "kernel_ms": kern_mean_ms,
-                    "flop_per_particle_step": tensor_flops_per_step(w.K),
-                    "peak_basis": peak_basis, "operands": tensor_operands(w.K),
-                    "single_product_frac": achieved / 3 / peak_tflops,
                     "issue_active_frac_ncu": (profile_value("timedep_k10_tc_kernel.md", "issue_active_frac")
                                               if w.K == 10 else None),
                     "binding_constraint": "SIMT instruction issue (harmonics, operand split, RNG, Euler "
-                                          "step), not the tensor pipe: see issue_active_frac_ncu",
-                    "fp32_equivalent": {"achieved": simt_rate, "peak": fp32_peak,
-                                        "flop_per_particle_step": flops_per_step(w.K),
-                                        "note": "the same steps counted as FP32 direct-sum work, against "
-                                                "the FP32 pipe peak; above 1 because the sum runs on "
-                                                "the tensor cores"}}
+                                          "step), not the tensor pipe: see issue_active_frac_ncu"})
         else:
             peak_tflops = fp32_peak
             achieved = simt_rate
@@ -349,10 +405,18 @@ def run_gpu(args):
                     "flop_per_particle_step": flops_per_step(w.K),
                     "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 FLOP x sm_max_mhz "
                                   f"{peaks.get('sm_max_mhz', 2070.0)} ({peaks_kind})"}
+        if simt is not None:
+            simt.update(fp32_roofline(w.K, steps_per_eval, simt["kernel_ms"], peaks, peaks_kind, sm_count))
+            simt["tensor_speedup"] = simt["kernel_ms"] / kern_mean_ms
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": ("f32 paths; velocity contraction f16 hi/lo x3 on tensor cores; f64 reductions"
+                      if args.tensor and tensor_operands(w.K) == "f16" else
+                      "f32 paths; velocity contraction tf32 hi/lo x3 on tensor cores; f64 reductions"
+                      if args.tensor else "f32 paths; f64 reductions"),
+            "data": "synthetic",
             "config": {"workload": w.name, "K": w.K, "n_u": (2 * w.K + 1) ** 2 - 1, "n_obs": n_obs, "M": w.M,
                        "dt": w.dt, "kappa": w.kappa, "particle_steps_per_eval": steps_per_eval,
                        "shared_paths": bool(args.share_paths),
@@ -366,6 +430,7 @@ def run_gpu(args):
             "gpu_launches": int(launches),
             "clocks": clock,
             "plain_fp64_gpu": fp64,
+            "fp32_pipe_kernel": simt,
         }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, threads, P, g_or, secs = oracle_sample(w, obs_id=stream_of)
@@ -794,6 +859,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32-compare", action="store_true",
+                    help="skip timing the FP32-pipe kernel beside the tensor-core one")
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="timedep: skip the one FP64-path evaluation reported beside the line")
     ap.add_argument("--M", type=int, default=0, help="particles per observation (default: the workload's own; "

@@ -17,6 +17,31 @@ def test_tensor_flops_count_three_products_of_the_contraction():
     assert bench.tensor_flops_per_step(4) == 3 * 2 * 9 * 17
 
 
+def test_method_work_is_the_direct_sum_count():
+    # 8 FMAs per half-mode (H = 220 at K = 10) + ~90 per step, 2 FLOP per FMA
+    assert bench.method_flops_per_step(10) == 2 * (8 * 220 + 90) == 3700
+    assert bench.method_flops_per_step(2) == 2 * (8 * 12 + 90)
+
+
+def test_tensor_roofline_counts_the_method_work_against_the_operand_peak():
+    # the headline workload: 1.75e9 particle-steps in 26.717 ms on FP16 operands
+    r = bench.tensor_roofline(10, 1_750_000_000, 26.717, {"bf16_tflops": 1936.3}, "measured")
+    assert r["bound"] == "tensor" and r["peak"] == 1936.3
+    assert abs(r["achieved"] - 1.75e9 * 3700 / 26.717e-3 / 1e12) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / 1936.3) < 1e-12
+    assert abs(r["frac"] - 0.1252) < 1e-3
+    assert abs(r["tensor_issued_frac"] - 1.75e9 * 5166 / 26.717e-3 / 1e12 / 1936.3) < 1e-12
+
+
+def test_fp32_roofline_counts_the_executed_fmas_against_the_fp32_pipe():
+    r = bench.fp32_roofline(10, 1_750_000_000, 64.4, {"sm_max_mhz": 2070.0}, "measured", 152)
+    peak = 152 * 128 * 2 * 2070e6 / 1e12
+    assert abs(r["peak"] - peak) < 1e-9
+    assert abs(r["frac"] - 1.75e9 * 1840 / 64.4e-3 / 1e12 / peak) < 1e-12
+    assert abs(r["frac"] - 0.621) < 2e-3
+    assert r["method_work_frac"] > 1.0  # the product basis does half the direct sum's work
+
+
 def test_peak_follows_the_operand_type():
     peaks = {"bf16_tflops": 1898.6}
     assert bench.tensor_operands(10) == "f16" and bench.tensor_operands(8) == "tf32"

@@ -1,0 +1,185 @@
+"""Parity of the two headline maps with the FP64 oracle on samples the oracle
+can afford, with the GPU in the benchmark's launch configuration.
+
+Time-dependent map (Algorithm 1, Theorem 3.1) on the 440-mode field,
+kappa = 0.01, dt = 1e-3: the GPU runs the full 300 observations x M = 1e4 on
+the tensor cores; the oracle runs 60 of the observations (every fifth, 20 at
+each of t = 0.25, 0.5, 1) x M_o = 1000 paths.  The flow is chaotic: a change of
+one unit in the last place of a start point moves a path's end by O(1) before
+t = 0.25 (oracle alone: median |change of theta0(X_t)| 0.04 at t = 0.25 for a
+1e-6 change), so float and double paths on the same streams separate and the
+comparison at the workload's own times is in distribution:
+  * two-sample means (GPU on independent streams at M = 1e4, oracle at M_o)
+    and paired means (the GPU's first M_o paths on the oracle's streams),
+    per observation, at 3 sqrt(SE_1^2 + SE_2^2) with a binomial allowance for
+    the number of observations beyond 3 and a chi-square bound on the sum of
+    squared scores (family-wise false-alarm rate 1e-4 each; tests/_stats.py);
+  * the law of the end points X_t at t = 0.25: two-sample Kolmogorov-Smirnov
+    tests on both coordinates and both diagonals, Bonferroni over 80 tests;
+  * the per-path spread at t = 0.25 against the oracle's own sensitivity to a
+    one-ulp change of the start point;
+  * pathwise parity on the same field over a short horizon (t = 0.02, 20 Euler
+    steps, all 100 grid points), before the flow separates the paths: the
+    median observation within 1e-5 of the oracle and every one within 2e-4
+    (the oracle's own change under a one-ulp change of the start points:
+    median 1.1e-6, largest 2.1e-5), where a 1 % change of the largest
+    stream-function coefficient moves the median observation by 7.6e-3 and
+    every one by more than 1e-4 (checked on the GPU below and on the oracle
+    alone in tests/test_parity_power.py).
+Dirichlet map (Algorithm 2, Theorem 3.2) on the disk workload (50 observations,
+M = 1e5, dt = 1e-4): the oracle runs all 50 observations x M_o = 1000 paths;
+the GPU reruns M = M_o on the same streams (whose paths equal the first M_o of
+the full launch bit for bit), and runs the full size on independent streams.
+Means are compared as above; exit steps are compared path by path and their
+agreement is reported per exit-time bin."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from paper_1808_10580_gb300 import inputs
+from tests import _gpu
+from tests import _stats as S
+
+pytestmark = pytest.mark.gpu
+pm = _gpu.pm
+torch = _gpu.torch
+
+FLAGS = pm.PM_FP32 | pm.PM_TENSOR      # the benchmark's launch
+OBS = np.arange(0, 300, 5)             # 60 observations, 20 at each time
+MO = 1000                              # oracle paths per observation
+OTHER_SEED = 7919                      # offset of the independent GPU streams
+
+
+@pytest.fixture(scope="module")
+def c():
+    h, s = _gpu.side_stream_ctx()
+    with torch.cuda.stream(s):
+        yield h
+    pm.pm_destroy(h)
+
+
+@pytest.fixture(scope="module")
+def td(c, orc):
+    w = inputs.timedep_k10()
+    mean, var, g, xe = _gpu.timedep(c, w, FLAGS, g_out=True, x_out=True)
+    wi = dataclasses.replace(w, seed=w.seed + OTHER_SEED)
+    mi, vi, xi = _gpu.timedep(c, wi, FLAGS, x_out=True)
+    go, xo = orc.timedep_paths(w.K, w.u, w.kappa, w.theta0, w.x[OBS], w.t[OBS], w.dt, w.seed, npaths=MO,
+                               obs_id=OBS, want_x=True)
+    return dict(w=w, mean=mean, var=var, g=g, xe=xe, mi=mi, vi=vi, xi=xi, go=go, xo=xo)
+
+
+def test_timedep_two_sample_means(td, orc):
+    w = td["w"]
+    mo, vo, seo = orc.estimate(td["go"])
+    z = S.two_sample_z(td["mi"][OBS], np.sqrt(td["vi"][OBS] / w.M), mo, seo)
+    r = S.zcheck(z)
+    print("timedep two-sample", r)
+    assert r["ok"], r
+
+
+def test_timedep_paired_means_same_streams(td):
+    z = S.paired_z(td["g"][OBS, :MO], td["go"])
+    r = S.zcheck(z)
+    print("timedep paired", r)
+    assert r["ok"], r
+
+
+def test_timedep_end_point_law_at_quarter(td):
+    sel = OBS[td["w"].t[OBS] == 0.25]
+    rows = np.searchsorted(OBS, sel)
+    r = S.ks_positions(td["xi"][sel], td["xo"][rows])
+    print("timedep X_t KS at t = 0.25", r)
+    assert r["ok"], r
+
+
+def test_timedep_per_path_spread_within_rounding_sensitivity(td, orc):
+    # The GPU's paths leave the oracle's no faster than the oracle's own paths
+    # leave themselves after a one-ulp (float) change of the start point.
+    # Float positions are compensated (hi, lo) pairs and the velocity sum keeps
+    # ~2^-21 of its term scale, so the GPU injects below one float ulp of
+    # position per step; per-step injections of size e add up, through the
+    # growth e^{lambda t} with lambda ~ 35 per unit time, to about
+    # e / (lambda dt) ~ 30 e at the start: the bound allows 30 ulps.
+    w = td["w"]
+    sel = OBS[w.t[OBS] == 0.25]
+    rows = np.searchsorted(OBS, sel)
+    d_gpu = np.abs(td["g"][sel, :MO] - td["go"][rows])
+    gp = orc.timedep_paths(w.K, w.u, w.kappa, w.theta0, w.x[sel] * (1 + 2.0 ** -23), w.t[sel], w.dt, w.seed,
+                           npaths=MO, obs_id=sel)
+    sens = np.abs(gp - td["go"][rows])
+    print("t = 0.25 median |GPU - oracle| per path", np.median(d_gpu), "oracle 1-ulp sensitivity", np.median(sens))
+    assert np.median(d_gpu) <= 30 * np.median(sens)
+
+
+def short_horizon(w):
+    g = inputs.grid_points(10)
+    return dataclasses.replace(w, x=g, t=np.full(len(g), 0.02), M=MO)
+
+
+def test_timedep_short_horizon_pathwise(c, orc):
+    w = short_horizon(inputs.timedep_k10())
+    mean, var, g = _gpu.timedep(c, w, FLAGS, g_out=True)
+    go = orc.timedep_paths(w.K, w.u, w.kappa, w.theta0, w.x, w.t, w.dt, w.seed, npaths=MO)
+    mo, _, _ = orc.estimate(go)
+    d = np.abs(mean - mo)
+    print("t = 0.02 |GPU - oracle| per observation: max", d.max(), "median", np.median(d),
+          "per path median", np.median(np.abs(g - go)))
+    assert d.max() <= 2e-4 and np.median(d) <= 1e-5
+    # a 1 % change of the largest coefficient is far outside that bound
+    wp = dataclasses.replace(w, u=w.u.copy())
+    wp.u[int(np.argmax(np.abs(wp.u)))] *= 1.01
+    mp, _ = _gpu.timedep(c, wp, FLAGS)
+    dp = np.abs(mp - mo)
+    print("1 % coefficient change: |GPU - oracle| median", np.median(dp), "min", dp.min())
+    assert np.median(dp) > 1e-3
+
+
+@pytest.fixture(scope="module")
+def dr(c, orc):
+    w = inputs.dirichlet_disk_k10()
+    full = _gpu.dirichlet(c, w, FLAGS, want_paths=True)
+    small = _gpu.dirichlet(c, w, FLAGS, M=MO, want_paths=True)
+    ind = _gpu.dirichlet(c, dataclasses.replace(w, seed=w.seed + OTHER_SEED), FLAGS)
+    go, so = orc.dirichlet_paths(w.K, w.u, w.drift_scale, w.kappa, w.g, w.x, w.dt, w.max_steps, w.seed, npaths=MO)
+    return dict(w=w, full=full, small=small, ind=ind, go=go, so=so)
+
+
+def test_dirichlet_rerun_at_oracle_size_equals_full_launch(dr):
+    assert dr["full"]["rc"] == 0 and dr["full"]["unexited"] == 0
+    assert np.array_equal(dr["small"]["g"], dr["full"]["g"][:, :MO])
+    assert np.array_equal(dr["small"]["steps"], dr["full"]["steps"][:, :MO])
+
+
+def test_dirichlet_two_sample_means(dr, orc):
+    w = dr["w"]
+    mo, vo, seo = orc.estimate(dr["go"])
+    z = S.two_sample_z(dr["ind"]["mean"], np.sqrt(dr["ind"]["var"] / w.M), mo, seo)
+    r = S.zcheck(z)
+    print("dirichlet two-sample", r)
+    assert r["ok"], r
+
+
+def test_dirichlet_paired_means_same_streams(dr):
+    r = S.zcheck(S.paired_z(dr["small"]["g"], dr["go"]))
+    print("dirichlet paired", r)
+    assert r["ok"], r
+
+
+EXIT_BINS = [0, 250, 500, 1000, 2000, 4000, 8000, 16000, 1 << 40]
+
+
+def test_dirichlet_exit_steps_by_exit_time(dr):
+    so = dr["so"]
+    sg = dr["small"]["steps"].astype(np.int64)
+    rows = []
+    for lo, hi in zip(EXIT_BINS[:-1], EXIT_BINS[1:]):
+        m = (so >= lo) & (so < hi)
+        if m.any():
+            rows.append((lo, hi, int(m.sum()), float(np.mean(sg[m] == so[m]))))
+    for lo, hi, n, a in rows:
+        print(f"exit steps [{lo}, {hi}): {n} paths, {100 * a:.2f} % identical")
+    print("all:", float(np.mean(sg == so)))
+    early = so < 500
+    assert np.mean(sg[early] == so[early]) >= 0.999
