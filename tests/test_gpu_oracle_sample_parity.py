@@ -17,21 +17,23 @@ comparison at the workload's own times is in distribution:
   * the law of the end points X_t at t = 0.25: two-sample Kolmogorov-Smirnov
     tests on both coordinates and both diagonals, Bonferroni over 80 tests;
   * the per-path spread at t = 0.25 against the oracle's own sensitivity to a
-    one-ulp change of the start point;
+    one-ulp change of the start point (measured: GPU 1.3e-3 against 2.4e-3);
   * pathwise parity on the same field over a short horizon (t = 0.02, 20 Euler
-    steps, all 100 grid points), before the flow separates the paths: the
-    median observation within 1e-5 of the oracle and every one within 2e-4
-    (the oracle's own change under a one-ulp change of the start points:
-    median 1.1e-6, largest 2.1e-5), where a 1 % change of the largest
-    stream-function coefficient moves the median observation by 7.6e-3 and
-    every one by more than 1e-4 (checked on the GPU below and on the oracle
-    alone in tests/test_parity_power.py).
+    steps, all 100 grid points), before the flow separates the paths: every
+    observation within 1e-5 of the oracle, the median within 1e-6 (measured:
+    largest 2.1e-6, median 2.8e-7; the oracle's own change under a one-ulp
+    change of the start points: largest 2.1e-5, median 1.1e-6), where a 1 %
+    change of the largest stream-function coefficient moves every observation
+    by more than 1e-4 and the median by 7.6e-3 (checked on the GPU below and on
+    the oracle alone in tests/test_parity_power.py).
 Dirichlet map (Algorithm 2, Theorem 3.2) on the disk workload (50 observations,
 M = 1e5, dt = 1e-4): the oracle runs all 50 observations x M_o = 1000 paths;
 the GPU reruns M = M_o on the same streams (whose paths equal the first M_o of
 the full launch bit for bit), and runs the full size on independent streams.
 Means are compared as above; exit steps are compared path by path and their
-agreement is reported per exit-time bin."""
+agreement is reported per exit-time bin (measured: all exits before step 500
+identical, 99.98 % of those in [500, 1000), 98.9 % in [1000, 2000); later
+exits separate with the flow)."""
 import dataclasses
 
 import numpy as np
@@ -101,7 +103,8 @@ def test_timedep_per_path_spread_within_rounding_sensitivity(td, orc):
     # ~2^-21 of its term scale, so the GPU injects below one float ulp of
     # position per step; per-step injections of size e add up, through the
     # growth e^{lambda t} with lambda ~ 35 per unit time, to about
-    # e / (lambda dt) ~ 30 e at the start: the bound allows 30 ulps.
+    # e / (lambda dt) ~ 30 e at the start, which stays near one ulp: the bound
+    # allows three times the oracle's one-ulp spread.
     w = td["w"]
     sel = OBS[w.t[OBS] == 0.25]
     rows = np.searchsorted(OBS, sel)
@@ -110,7 +113,7 @@ def test_timedep_per_path_spread_within_rounding_sensitivity(td, orc):
                            npaths=MO, obs_id=sel)
     sens = np.abs(gp - td["go"][rows])
     print("t = 0.25 median |GPU - oracle| per path", np.median(d_gpu), "oracle 1-ulp sensitivity", np.median(sens))
-    assert np.median(d_gpu) <= 30 * np.median(sens)
+    assert np.median(d_gpu) <= 3 * np.median(sens)
 
 
 def short_horizon(w):
@@ -126,14 +129,14 @@ def test_timedep_short_horizon_pathwise(c, orc):
     d = np.abs(mean - mo)
     print("t = 0.02 |GPU - oracle| per observation: max", d.max(), "median", np.median(d),
           "per path median", np.median(np.abs(g - go)))
-    assert d.max() <= 2e-4 and np.median(d) <= 1e-5
+    assert d.max() <= 1e-5 and np.median(d) <= 1e-6
     # a 1 % change of the largest coefficient is far outside that bound
     wp = dataclasses.replace(w, u=w.u.copy())
     wp.u[int(np.argmax(np.abs(wp.u)))] *= 1.01
     mp, _ = _gpu.timedep(c, wp, FLAGS)
     dp = np.abs(mp - mo)
     print("1 % coefficient change: |GPU - oracle| median", np.median(dp), "min", dp.min())
-    assert np.median(dp) > 1e-3
+    assert dp.min() > 1e-5 and np.median(dp) > 1e-3
 
 
 @pytest.fixture(scope="module")
@@ -181,5 +184,7 @@ def test_dirichlet_exit_steps_by_exit_time(dr):
     for lo, hi, n, a in rows:
         print(f"exit steps [{lo}, {hi}): {n} paths, {100 * a:.2f} % identical")
     print("all:", float(np.mean(sg == so)))
-    early = so < 500
+    early = so < 1000
     assert np.mean(sg[early] == so[early]) >= 0.999
+    mid = (so >= 1000) & (so < 2000)
+    assert np.mean(sg[mid] == so[mid]) >= 0.98
