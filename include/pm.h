@@ -392,6 +392,18 @@ int pm_surrogate_train(pm_ctx* ctx, pm_mlp* net, const float* U, const float* Y,
 /* Y [B][n_out] = net(U [B][n_in]); pointers follow PM_DEVICE_PTRS. */
 int pm_surrogate_infer(pm_ctx* ctx, const pm_mlp* net, const float* U, int64_t B, float* Y, uint32_t flags);
 
+/* The gradient of the network with respect to its input, row by row: for
+ * each row b, dU[b] = J(U[b])^T dY[b] with J the Jacobian dY/dU of the
+ * network at U[b] (a vector-Jacobian product: the ReLU masks of the forward
+ * pass at U[b], then the three weight matrices transposed, on the tensor
+ * cores with BF16 operands and FP32 accumulation).  U [B][n_in], dY
+ * [B][n_out], dU [B][n_in]; pointers follow PM_DEVICE_PTRS.  This makes the
+ * surrogate differentiable in the parameter u, which the particle map is not
+ * (the paper notes that its estimator has no Frechet derivative): gradient-
+ * based MAP estimation runs on the surrogate. */
+int pm_surrogate_input_gradient(pm_ctx* ctx, const pm_mlp* net, const float* U, const float* dY, int64_t B, float* dU,
+                                uint32_t flags);
+
 /* Parameters and Adam state to / from a binary file. */
 int pm_surrogate_save(pm_ctx* ctx, const pm_mlp* net, const char* path);
 int pm_surrogate_load(pm_ctx* ctx, pm_mlp** out, const char* path);
@@ -535,6 +547,19 @@ int pm_velocity(pm_ctx* ctx, const pm_field* field, const double* x, int64_t npt
  * kernel's duration (synchronising on the end event). */
 int pm_set_kernel_timing(pm_ctx* ctx, int on);
 float pm_last_kernel_ms(pm_ctx* ctx);
+
+/* Test setting for the failure path of the tensor-core kernels.  Their waits
+ * for the tensor core (the per-step product of the PM_TENSOR particle kernels,
+ * the pipeline stages of the GEMM) are bounded; a wait that runs out sets an
+ * error flag, the kernel waits (with the full bound) for its own copies and
+ * products still in flight, frees its tensor memory and returns, and the call
+ * returns PM_ETIMEOUT.  pm_set_wait_limit makes the next call of
+ * pm_forward_timedep, pm_forward_dirichlet or pm_gemm_bf16 on this context
+ * give those waits at most `polls` polls (0: they give up without polling,
+ * so the failure path runs deterministically); the setting then returns to
+ * the full bound.  polls < 0 restores the full bound at once.  Calls that
+ * give up return no valid results. */
+int pm_set_wait_limit(pm_ctx* ctx, int64_t polls);
 
 /* Number of kernels the context has launched since it was created. */
 int64_t pm_launch_count(const pm_ctx* ctx);

@@ -6,7 +6,9 @@ MCMC proposals) follows textbook definitions, restated here in plain numpy:
     weights stored [out, in];
   * loss L = sum over the batch and the outputs of (y - target)^2 / (2 B n_out);
   * gradients by the chain rule (reverse mode), written out layer by layer;
-  * Adam (Kingma & Ba, ICLR 2015, Algorithm 1) with bias correction.
+  * Adam (Kingma & Ba, ICLR 2015, Algorithm 1) with bias correction, and the
+    decoupled weight decay of AdamW (Loshchilov & Hutter, ICLR 2019) on the
+    weight matrices; the step size may shrink by a fixed factor per epoch.
 """
 import numpy as np
 
@@ -58,13 +60,26 @@ def backward(P, cache, dY):
     return g
 
 
+def input_gradient(P, U, dY):
+    """Vector-Jacobian product at the input: dU[b] = J(U[b])^T dY[b], J = dY/dU
+    of the network at row b (the chain rule through the two ReLU layers)."""
+    _, (U, z1, h1, z2, h2) = forward(P, U)
+    dz2 = (np.asarray(dY, dtype=np.float64) @ P["W3"]) * (z2 > 0)
+    dz1 = (dz2 @ P["W2"]) * (z1 > 0)
+    return dz1 @ P["W1"]
+
+
 def adam_init(P):
     return dict(t=0, m={k: np.zeros_like(v) for k, v in P.items()}, v={k: np.zeros_like(v) for k, v in P.items()})
 
 
-def adam_step(P, g, S, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
-    """One Adam update of P in place: m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
-    theta -= lr * m_hat / (sqrt(v_hat) + eps) with m_hat = m/(1-b1^t), v_hat = v/(1-b2^t)."""
+def adam_step(P, g, S, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0):
+    """One AdamW update of P in place: Adam (Kingma & Ba, Algorithm 1) with the
+    decoupled weight decay of Loshchilov & Hutter (ICLR 2019) on the weight
+    matrices W1, W2, W3 (biases are not decayed):
+      m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;
+      m_hat = m / (1 - b1^t);  v_hat = v / (1 - b2^t);
+      theta -= lr * (m_hat / (sqrt(v_hat) + eps) + weight_decay * theta)."""
     S["t"] += 1
     t = S["t"]
     for k in P:
@@ -72,5 +87,12 @@ def adam_step(P, g, S, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
         S["v"][k] = beta2 * S["v"][k] + (1 - beta2) * g[k] ** 2
         mh = S["m"][k] / (1 - beta1 ** t)
         vh = S["v"][k] / (1 - beta2 ** t)
-        P[k] = P[k] - lr * mh / (np.sqrt(vh) + eps)
+        wd = weight_decay if k.startswith("W") else 0.0
+        P[k] = P[k] - lr * (mh / (np.sqrt(vh) + eps) + wd * P[k])
     return P
+
+
+def epoch_lr(lr0, lr_decay, epoch):
+    """Step size of epoch `epoch` (from 0) when training multiplies it by
+    lr_decay after every epoch."""
+    return lr0 * lr_decay ** epoch

@@ -115,6 +115,7 @@ def load(build_if_missing: bool = True):
                                         i64, dbl, i64, C.c_uint64, u32, vp]
     L.pm_set_graph_mode.argtypes = [vp, C.c_int]
     L.pm_set_kernel_timing.argtypes = [vp, C.c_int]
+    L.pm_set_wait_limit.argtypes = [vp, i64]
     L.pm_last_kernel_ms.argtypes = [vp]
     L.pm_last_kernel_ms.restype = C.c_float
     L.pm_launch_count.argtypes = [vp]
@@ -214,6 +215,12 @@ def pm_stream(ctx):
 
 def pm_set_kernel_timing(ctx, on):
     return _check(load().pm_set_kernel_timing(ctx, int(bool(on))))
+
+
+def pm_set_wait_limit(ctx, polls):
+    """Test setting: the next forward / GEMM call's tensor-core waits give up
+    after ``polls`` polls (0: at once); negative restores the full bound."""
+    return _check(load().pm_set_wait_limit(ctx, int(polls)))
 
 
 def pm_last_kernel_ms(ctx):
@@ -405,6 +412,7 @@ def _declare_surrogate(L):
     L.pm_surrogate_gradients.argtypes = [vp, vp, vp, vp, i64, vp] + [vp] * 6
     L.pm_surrogate_train.argtypes = [vp, vp, vp, vp, i64, C.POINTER(pm_train_opts), u32, vp]
     L.pm_surrogate_infer.argtypes = [vp, vp, vp, i64, vp, u32]
+    L.pm_surrogate_input_gradient.argtypes = [vp, vp, vp, vp, i64, vp, u32]
     L.pm_surrogate_save.argtypes = [vp, vp, C.c_char_p]
     L.pm_surrogate_load.argtypes = [vp, C.POINTER(vp), C.c_char_p]
     L.pm_gemm_bf16.argtypes = [vp, vp, i32, vp, i32, i32, i32, i32, vp, i32]
@@ -474,6 +482,18 @@ def pm_surrogate_infer(ctx, net, U, Y, flags=0):
     if _device(U, Y):
         flags |= PM_DEVICE_PTRS
     return _check(_slib().pm_surrogate_infer(ctx, net, _ptr(U), int(U.shape[0]), _ptr(Y), int(flags)))
+
+
+def pm_surrogate_input_gradient(ctx, net, U, dY, dU, flags=0):
+    """dU[b] = J(U[b])^T dY[b] for every row b (vector-Jacobian product of the
+    network at its input)."""
+    if _device(U, dY, dU):
+        flags |= PM_DEVICE_PTRS
+    else:
+        U, dY = _f32(U), _f32(dY)
+        assert dU.dtype == np.float32 and dU.flags["C_CONTIGUOUS"]
+    return _check(_slib().pm_surrogate_input_gradient(ctx, net, _ptr(U), _ptr(dY), int(U.shape[0]), _ptr(dU),
+                                                      int(flags)))
 
 
 def pm_surrogate_save(ctx, net, path):

@@ -262,6 +262,13 @@ int check_theta0(const pm_fourier* th)
 
 void count_launch(pm_ctx* c, int n) { c->launches += n; }
 
+uint32_t take_wait_limit(pm_ctx* c)
+{
+    const int64_t v = c->wait_limit_next;
+    c->wait_limit_next = -1;
+    return v < 0 ? kWaitPolls : (uint32_t)v;
+}
+
 }  // namespace pm
 
 extern "C" {
@@ -338,6 +345,13 @@ float pm_last_kernel_ms(pm_ctx* c)
 }
 
 int64_t pm_launch_count(const pm_ctx* c) { return c ? c->launches : 0; }
+
+int pm_set_wait_limit(pm_ctx* c, int64_t polls)
+{
+    if (!c) return fail(PM_EINVAL, "ctx is NULL");
+    c->wait_limit_next = polls < 0 ? -1 : (polls > (int64_t)kWaitPolls ? (int64_t)kWaitPolls : polls);
+    return PM_OK;
+}
 
 int64_t pm_last_step_count(const pm_ctx* c) { return c ? c->last_steps : -1; }
 
@@ -565,6 +579,7 @@ int pm_forward_timedep(pm_ctx* c, const pm_field* field, double kappa, const pm_
     L.members = share ? W.mem : nullptr;
     L.n_groups = (int32_t)PG.groups.size();
     L.table_dev = W.tab;
+    L.wait_limit = take_wait_limit(c);
     c->last_grid = (share ? (int64_t)PG.groups.size() : n_obs) * (int64_t)chunks;
     L.inst = opts ? opts->instance : 0u;
     L.key0 = (uint32_t)(seed & 0xffffffffu);
@@ -805,6 +820,7 @@ int pm_forward_dirichlet(pm_ctx* c, const pm_field* field, double drift_scale, d
     const int64_t need = (total + kDirichletBlock - 1) / kDirichletBlock;
     if (grid > need) grid = need;
     L.grid = (int)(grid > 0 ? grid : 1);
+    L.wait_limit = take_wait_limit(c);
     c->last_grid = L.grid;
     if (c->timing) PM_CUDA(cudaEventRecord(c->ev0, c->stream), "event");
     cudaError_t e;

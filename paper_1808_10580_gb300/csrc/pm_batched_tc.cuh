@@ -20,8 +20,8 @@ namespace tdtc {
 // Entry W[k][nc] of the coefficient matrix (unfolded shape) from the
 // product-basis table tab[(m (K+1) + n) 8 + q] (e0..e3, f0..f3): A column k
 // holds S2_n (k = 2(n-1)), C2_n (k = 2(n-1)+1) or the constant 1 (k = 2K);
-// accumulator column 0 is P(0), columns 1 + 4(m-1) + j are P1c, P1s, P2c, P2s
-// of m (the layout of build_W).
+// accumulator column pcol(m, j) holds P1c, P1s, P2c, P2s (j = 0..3) of m and
+// column p0col(K) P(0) (the layout of build_W).
 template <int K>
 __device__ __forceinline__ float w_entry(const float* tab, int nc, int k)
 {
@@ -30,9 +30,10 @@ __device__ __forceinline__ float w_entry(const float* tab, int nc, int k)
     else if (k == 2 * K) { type = 2; }
     else return 0.f;
     auto T = [&](int m, int nn, int q) { return tab[(m * (K + 1) + nn) * 8 + q]; };
-    if (nc == 0) return type == 0 ? T(0, n, 0) : type == 1 ? T(0, n, 1) : 0.f;  // P(0)
-    if (nc > 4 * K) return 0.f;
-    const int m = (nc - 1) / 4 + 1, j = (nc - 1) % 4;
+    if (nc == p0col(K)) return type == 0 ? T(0, n, 0) : type == 1 ? T(0, n, 1) : 0.f;  // P(0)
+    if (nc > p0col(K)) return 0.f;
+    const int r = nc % 8, j = r / 2, m = 2 * (nc / 8) + 1 + (r & 1);  // inverse of pcol
+    if (m > K) return 0.f;
     if (j == 0) return type == 0 ? T(m, n, 0) : type == 1 ? T(m, n, 1) : 0.f;          // P1c
     if (j == 1) return type == 0 ? T(m, n, 2) : type == 1 ? T(m, n, 3) : 0.f;          // P1s
     if (j == 2) return type == 1 ? T(m, n, 4) : type == 0 ? T(m, n, 5) : T(m, 0, 4);   // P2c
@@ -104,6 +105,7 @@ __global__ void __launch_bounds__(128, BatShape<K>::MIN_CTAS6) batched_tc_kernel
     uint32_t j = 0, i = 0;
     unsigned long long lane_steps = 0;
     uint32_t phase = 0;
+    bool issued_any = false;  // a product has been issued (its parity is phase ^ 1 after the flip)
     bool failed = false, stop = false;
     Coord<float> X1, X2;
     X1.set(0.0);
@@ -219,7 +221,7 @@ __global__ void __launch_bounds__(128, BatShape<K>::MIN_CTAS6) batched_tc_kernel
 #pragma unroll 1
         for (int pair = 0; pair < kBatchRefillPairs && !stop; ++pair) {
             u32x4 r{0, 0, 0, 0};
-            if (pid >= 0) r = philox4x32_10(u32x4{(uint32_t)(n >> 1), i, j, stream}, key0, key1);
+            if (pid >= 0) r = philox4x32_10_wide(u32x4{(uint32_t)(n >> 1), i, j, stream}, key0, key1);
 #pragma unroll 1
             for (int half = 0; half < 2; ++half) {
                 write_row_stream<K, false, H>(sb + row, (uint32_t)S::A_BYTES, X2.val(), nullptr);
@@ -234,7 +236,8 @@ __global__ void __launch_bounds__(128, BatShape<K>::MIN_CTAS6) batched_tc_kernel
                 box_muller<float>(half ? r.z : r.x, half ? r.w : r.y, xi1, xi2);
                 HarmArray<K> h1;  // during the product
                 h1.init(X1.val());
-                failed = !tc::mbar_wait(bar_a, phase);
+                issued_any = true;
+                failed = !tc::mbar_wait(bar_a, phase, tc::kWaitLimit);
                 phase ^= 1u;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 float v1, v2;
@@ -244,8 +247,7 @@ __global__ void __launch_bounds__(128, BatShape<K>::MIN_CTAS6) batched_tc_kernel
                 if (kind == 0) {
                     const bool last = (n == N - 1);
                     const float h = last ? h_last : dt, s = last ? s_last : s_dt;
-                    em_update<float>(X1, v1, h, s, xi1);
-                    em_update<float>(X2, v2, h, s, xi2);
+                    em_update2(X1, X2, v1, v2, h, s, xi1, xi2);
                     X1.wrap();
                     X2.wrap();
                     ++n;
@@ -255,8 +257,7 @@ __global__ void __launch_bounds__(128, BatShape<K>::MIN_CTAS6) batched_tc_kernel
                         pid = -1;
                     }
                 } else {
-                    em_update<float>(X1, v1, drift_dt, s_dt, xi1);
-                    em_update<float>(X2, v2, drift_dt, s_dt, xi2);
+                    em_update2(X1, X2, v1, v2, drift_dt, s_dt, xi1, xi2);
                     ++n;
                     const bool exited = radial_excess(X1, X2, p.R2hi, p.R2lo) >= 0.f;
                     if (exited || n >= sI.max_steps) {
@@ -275,6 +276,9 @@ __global__ void __launch_bounds__(128, BatShape<K>::MIN_CTAS6) batched_tc_kernel
     }
     if (failed && p.tc_err) atomicExch(p.tc_err, 1u);
     if (lane_steps) atomicAdd(p.steps, lane_steps);
+    // No product may still write tensor memory when it is freed: after a wait
+    // that gave up (stop), wait (full bound) for the last one issued.
+    if (stop && issued_any) tc::mbar_wait(bar_a, phase ^ 1u);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {

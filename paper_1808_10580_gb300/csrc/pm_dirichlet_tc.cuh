@@ -40,6 +40,7 @@ struct DirParams {
     double* x_out;
     uint32_t inst, key0, key1;
     unsigned* err;
+    uint32_t wait_limit;  // polls of the per-step MMA wait (tc::kWaitLimit unless a test lowers it)
 };
 
 template <int K>
@@ -115,6 +116,7 @@ __global__ void __launch_bounds__(128, DirShape<K>::MIN_CTAS6) dirichlet_tc_kern
     uint32_t j = 0, i = 0;
     unsigned long long lane_steps = 0;
     uint32_t phase = 0;
+    bool issued_any = false;  // a product has been issued (its parity is phase ^ 1 after the flip)
     bool failed = false, stop = false;
     Coord<float> X1, X2;
     X1.set(0.0);
@@ -159,7 +161,7 @@ __global__ void __launch_bounds__(128, DirShape<K>::MIN_CTAS6) dirichlet_tc_kern
 #pragma unroll 1
         for (int pair = 0; pair < kRefillPairs && !stop; ++pair) {
             u32x4 r{0, 0, 0, 0};
-            if (pid >= 0) r = philox4x32_10(u32x4{(uint32_t)(n >> 1), i, j, p.inst}, p.key0, p.key1);
+            if (pid >= 0) r = philox4x32_10_wide(u32x4{(uint32_t)(n >> 1), i, j, p.inst}, p.key0, p.key1);
 #pragma unroll 1
             for (int half = 0; half < 2; ++half) {
                 write_row_stream<K, false, H>(sb + row, (uint32_t)S::A_BYTES, X2.val(), nullptr);
@@ -174,15 +176,15 @@ __global__ void __launch_bounds__(128, DirShape<K>::MIN_CTAS6) dirichlet_tc_kern
                 box_muller<float>(half ? r.z : r.x, half ? r.w : r.y, xi1, xi2);
                 HarmArray<K> h1;  // during the product
                 h1.init(X1.val());
-                failed = !tc::mbar_wait(bar_a, phase);
+                issued_any = true;
+                failed = !tc::mbar_wait(bar_a, phase, p.wait_limit);
                 phase ^= 1u;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 float v1, v2;
                 velocity_stream<K, false, H>(t_row, h1, nullptr, 0.f, p.inv_s, v1, v2);
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 if (pid >= 0) {
-                    em_update<float>(X1, v1, p.drift_dt, p.s_dt, xi1);
-                    em_update<float>(X2, v2, p.drift_dt, p.s_dt, xi2);
+                    em_update2(X1, X2, v1, v2, p.drift_dt, p.s_dt, xi1, xi2);
                     ++n;
                     const bool exited = radial_excess(X1, X2, p.R2hi, p.R2lo) >= 0.f;
                     if (exited || n >= p.max_steps) {
@@ -197,6 +199,9 @@ __global__ void __launch_bounds__(128, DirShape<K>::MIN_CTAS6) dirichlet_tc_kern
     }
     if (failed) atomicExch(p.err, 1u);
     if (lane_steps) atomicAdd(p.steps, lane_steps);
+    // No product may still write tensor memory when it is freed: after a wait
+    // that gave up (stop), wait (full bound) for the last one issued.
+    if (stop && issued_any) tc::mbar_wait(bar_a, phase ^ 1u);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
@@ -243,6 +248,7 @@ cudaError_t launch_dirichlet_tc(const DirichletLaunch& L, unsigned* err, cudaStr
     p.key0 = L.key0;
     p.key1 = L.key1;
     p.err = err;
+    p.wait_limit = L.wait_limit;
     cudaError_t e = cudaFuncSetAttribute(dirichlet_tc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
     if (e != cudaSuccess) return e;
     dirichlet_tc_kernel<K><<<L.grid, 128, S::SMEM, stream>>>(p);

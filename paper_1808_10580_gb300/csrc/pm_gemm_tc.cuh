@@ -18,6 +18,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include "pm_launch.h"
+
 namespace pm {
 namespace tc {
 
@@ -44,7 +46,7 @@ struct GemmCfg {
     static_assert(BN % 16 == 0 && BN <= 256, "MMA N");
     static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
 };
-constexpr uint32_t kWaitLimit = 1u << 22;       // bounded spins (a few seconds at most)
+constexpr uint32_t kWaitLimit = kWaitPolls;     // bounded spins (a few seconds at most)
 
 struct Epilogue {
     const float* bias;           // [N] or nullptr
@@ -66,6 +68,7 @@ struct GemmParams {  // aligned as its tensor maps require
     Epilogue ep;
     int M, N, K;
     unsigned* err;               // set to 1 when a bounded wait expires
+    uint32_t wait_limit;         // polls of a progress wait (kWaitLimit unless a test lowers it)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -80,10 +83,14 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
-// Bounded wait for the completion of the phase with the given parity.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+// Bounded wait for the completion of the phase with the given parity: at
+// most `limit` polls (0: give up without polling).  Waits that drain a
+// CTA's own copies and products before it frees tensor memory and exits
+// always take the full bound kWaitLimit; the waits that make progress take
+// the launch's limit, which a test may lower (pm_set_wait_limit).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t limit = kWaitLimit)
 {
-    for (uint32_t it = 0; it < kWaitLimit; ++it) {
+    for (uint32_t it = 0; it < limit; ++it) {
         uint32_t ok;
         asm volatile(
             "{\n .reg .pred P1;\n mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n selp.b32 %0, 1, 0, P1;\n}\n"
@@ -193,7 +200,7 @@ __global__ void __launch_bounds__(128, 1) gemm_bf16_tc_kernel(const __grid_const
         for (int kt = 0; kt < num_k; ++kt) {
             const int s = kt % STAGES;
             const uint32_t use = (uint32_t)(kt / STAGES);
-            if (kt >= STAGES && !mbar_wait(empty0 + 8 * s, (use & 1u) ^ 1u)) { atomicExch(p.err, 1u); break; }
+            if (kt >= STAGES && !mbar_wait(empty0 + 8 * s, (use & 1u) ^ 1u, p.wait_limit)) { atomicExch(p.err, 1u); break; }
             const uint32_t sa = smem_u32(smem + s * STAGE_BYTES), sb = sa + A_BYTES;
             mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
             tma_load_2d(sa, &p.tmA, kt * BK, m0, full0 + 8 * s);
@@ -208,7 +215,7 @@ __global__ void __launch_bounds__(128, 1) gemm_bf16_tc_kernel(const __grid_const
         // MMA issuer.
         for (int kt = 0; kt < num_k; ++kt) {
             const int s = kt % STAGES;
-            if (!mbar_wait(full0 + 8 * s, (uint32_t)(kt / STAGES) & 1u)) { atomicExch(p.err, 1u); break; }
+            if (!mbar_wait(full0 + 8 * s, (uint32_t)(kt / STAGES) & 1u, p.wait_limit)) { atomicExch(p.err, 1u); break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t sa = smem_u32(smem + s * STAGE_BYTES), sb = sa + A_BYTES;
             const uint64_t da = smem_desc_sw128(sa), db = smem_desc_sw128(sb);
@@ -222,8 +229,14 @@ __global__ void __launch_bounds__(128, 1) gemm_bf16_tc_kernel(const __grid_const
     __syncwarp();
 
     // Epilogue: warp w reads accumulator lanes (rows) 32w .. 32w+31.
-    const bool ok = mbar_wait(accum, 0);
-    if (!ok && lane == 0) atomicExch(p.err, 1u);
+    const bool ok = mbar_wait(accum, 0, p.wait_limit);
+    if (!ok) {
+        if (lane == 0) atomicExch(p.err, 1u);
+        // The issuer commits `accum` on every path, after its last product:
+        // wait for it (full bound) so that no product still writes tensor
+        // memory when it is freed below.
+        mbar_wait(accum, 0);
+    }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok && *(volatile unsigned*)p.err == 0u) {
         const Epilogue& e = p.ep;

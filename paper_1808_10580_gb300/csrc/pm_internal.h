@@ -35,6 +35,9 @@ struct pm_ctx {
     // Autotuned resident CTAs per SM of the persistent kernels, by tune_key().
     std::map<uint64_t, int> ctas_per_sm;
     std::string device_name;
+    // Test setting: polls of the tensor-core progress waits of the next forward
+    // or GEMM call (pm_set_wait_limit); -1 = the full bound.
+    int64_t wait_limit_next = -1;
 };
 
 namespace pm {
@@ -70,6 +73,8 @@ int check_theta0(const pm_fourier* th);
 // coefficients u (2|H_K| doubles) into tab (table_size(K) doubles, caller's storage).
 void stage_coefficients_into(int K, const double* u, double* tab);
 void count_launch(pm_ctx* c, int n = 1);
+// The progress-wait bound of this call (pm_set_wait_limit), then back to the full bound.
+uint32_t take_wait_limit(pm_ctx* c);
 
 // Autotuner (pm_autotune.cu).  kind: PM_TUNE_DIRICHLET or PM_TUNE_BATCHED.
 uint64_t tune_key(int kind, int K, uint32_t flags);

@@ -8,6 +8,8 @@ namespace pm {
 
 constexpr int kMaxTheta0 = 64;    // PM_MAX_THETA0_MODES
 constexpr int kMaxBoundary = 32;  // PM_MAX_BOUNDARY_MODES
+// Full bound of a tensor-core wait (mbarrier polls, a few seconds at most).
+constexpr uint32_t kWaitPolls = 1u << 22;
 
 // Per-observation record built on the device from (x_j, t_j): start point,
 // step count N_j, length and noise scale of the last step.
@@ -46,6 +48,9 @@ struct TimedepLaunch {
     // Wide K (K > 16): device buffer of wide_table_floats(K) floats that the
     // launcher fills with its coefficient table before the kernel reads it.
     float* table_dev = nullptr;
+    // Tensor-core kernels: polls of the per-step MMA wait before it gives up
+    // (the full bound unless a test lowers it, see pm_set_wait_limit).
+    uint32_t wait_limit = kWaitPolls;
 };
 
 // Paths per CTA of the time-dependent tensor-core kernel at K: two 128-row
@@ -91,6 +96,7 @@ struct DirichletLaunch {
     int64_t path_offset;
     uint32_t inst, key0, key1;
     int grid;                        // persistent CTAs
+    uint32_t wait_limit = kWaitPolls;  // tensor-core kernel: polls of the per-step MMA wait
 };
 
 // Kernel block size of the time-dependent kernel (one path per thread).

@@ -76,7 +76,7 @@ tc::Epilogue no_epilogue(int M, int N)
 
 // C = A B^T with A [M][K] (ld lda), B [N][K] (ld ldb): M % 128, N % 64, K % 64 == 0.
 int gemm(pm_ctx* c, const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K, const tc::Epilogue& ep,
-         unsigned* err)
+         unsigned* err, uint32_t wait_limit = kWaitPolls)
 {
     if (M % tc::BM || N % tc::BN || K % tc::BK || M <= 0 || N <= 0 || K <= 0)
         return fail(PM_EINVAL, "gemm shape %d x %d x %d is not a multiple of 128 x 64 x 64", M, N, K);
@@ -94,6 +94,7 @@ int gemm(pm_ctx* c, const bf16* A, int lda, const bf16* B, int ldb, int M, int N
     p.N = N;
     p.K = K;
     p.err = err;
+    p.wait_limit = wait_limit;
     // 256-wide tiles when the product has enough of them for two waves over the
     // SMs; otherwise 64-wide tiles (more CTAs for the network's small shapes).
     const bool wide = (N % 256 == 0) && (int64_t)(M / tc::BM) * (N / 256) >= 2 * (int64_t)c->sm_count;
@@ -178,6 +179,14 @@ __global__ void loss_kernel(const float* __restrict__ Y, const float* __restrict
         for (int k = 0; k < (int)blockDim.x; ++k) s += red[k];
         row_loss[b] = s * 0.5 * scale;
     }
+}
+
+// A given output cotangent dY [B][n_out] (FP32) -> BF16 dYb [Bp][Nout], zero padding.
+__global__ void set_cotangent_kernel(const float* __restrict__ dY, int B, int n_out, int Nout, bf16* __restrict__ dYb)
+{
+    const int b = blockIdx.x;
+    for (int o = threadIdx.x; o < Nout; o += blockDim.x)
+        dYb[(size_t)b * Nout + o] = __float2bfloat16_rn((b < B && o < n_out) ? dY[(size_t)b * n_out + o] : 0.0f);
 }
 
 __global__ void sum_rows_kernel(const double* __restrict__ v, int n, float* __restrict__ out)
@@ -616,6 +625,60 @@ int pm_surrogate_train(pm_ctx* c, pm_mlp* n, const float* U, const float* Y, int
     return check_err(c, n);
 }
 
+int pm_surrogate_input_gradient(pm_ctx* c, const pm_mlp* nc, const float* U, const float* dY, int64_t B, float* dU,
+                                uint32_t flags)
+{
+    pm_mlp* n = const_cast<pm_mlp*>(nc);  // the activation workspace is scratch
+    if (!c || !n || !U || !dY || !dU) return fail(PM_EINVAL, "NULL argument");
+    if (B < 1 || B > (1 << 20)) return fail(PM_EINVAL, "batch size out of range");
+    int rc = set_device(c);
+    if (rc) return rc;
+    const bool dev = flags & PM_DEVICE_PTRS;
+    if ((rc = check_ptrs(c, flags, {U, dY, dU}))) return rc;
+    const int Bp = (int)((B + 127) / 128 * 128);
+    if ((rc = mlp_reserve(c, n, Bp))) return rc;
+    // workspace: the input and cotangent rows (host pointers only), then the FP32 product [Bp][Kin]
+    const size_t ub = (size_t)B * n->n_in * 4, yb = (size_t)B * n->n_out * 4;
+    Bump probe(nullptr);
+    probe.take<char>(dev ? 0 : ub);
+    probe.take<char>(dev ? 0 : yb);
+    probe.take<float>((size_t)Bp * n->Kin);
+    if ((rc = ensure_workspace(c, probe.off))) return rc;
+    Bump bw(c->ws);
+    const float* sU = dev ? U : (const float*)bw.take<char>(ub);
+    const float* sY = dev ? dY : (const float*)bw.take<char>(yb);
+    float* G = bw.take<float>((size_t)Bp * n->Kin);
+    if (!dev) {
+        PM_CUDA(cudaMemcpyAsync((void*)sU, U, ub, cudaMemcpyHostToDevice, c->stream), "copy U");
+        PM_CUDA(cudaMemcpyAsync((void*)sY, dY, yb, cudaMemcpyHostToDevice, c->stream), "copy dY");
+    }
+    PM_CUDA(cudaMemsetAsync(n->err, 0, 4, c->stream), "clear flag");
+    gather_batch_kernel<<<Bp, 128, 0, c->stream>>>(sU, nullptr, nullptr, 0, (int)B, Bp, n->n_in, n->Kin, n->n_out,
+                                                   n->Nout, n->Ub, n->Ut, nullptr);
+    set_cotangent_kernel<<<Bp, 128, 0, c->stream>>>(sY, (int)B, n->n_out, n->Nout, n->dYb);
+    PM_CUDA(cudaGetLastError(), "stage rows");
+    count_launch(c, 2);
+    // the activations (their ReLU masks) at U
+    if ((rc = mlp_forward(c, n, (int)B, Bp))) return rc;
+    // dH2 = (dY W3) * [H2 > 0];  dH1 = (dH2 W2) * [H1 > 0];  dU = dH1 W1
+    tc::Epilogue e = no_epilogue((int)B, n->H);
+    e.mask = n->H2; e.ld_mask = n->H;
+    e.out_bf16 = n->dH2b; e.ld_out = n->H;
+    if ((rc = gemm(c, n->dYb, n->Nout, n->W3t, n->Nout, Bp, n->H, n->Nout, e, n->err))) return rc;
+    e = no_epilogue((int)B, n->H);
+    e.mask = n->H1; e.ld_mask = n->H;
+    e.out_bf16 = n->dH1b; e.ld_out = n->H;
+    if ((rc = gemm(c, n->dH2b, n->H, n->W2t, n->H, Bp, n->H, n->H, e, n->err))) return rc;
+    e = no_epilogue((int)B, n->Kin);
+    e.out_f32 = G; e.ld_f32 = n->Kin;
+    if ((rc = gemm(c, n->dH1b, n->H, n->W1t, n->H, Bp, n->Kin, n->H, e, n->err))) return rc;
+    PM_CUDA(cudaMemcpy2DAsync(dU, (size_t)n->n_in * 4, G, (size_t)n->Kin * 4, (size_t)n->n_in * 4, (size_t)B,
+                              dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream),
+            "copy dU");
+    if (dev && (flags & PM_ASYNC)) return PM_OK;
+    return check_err(c, n);
+}
+
 int pm_surrogate_infer(pm_ctx* c, const pm_mlp* nc, const float* U, int64_t B, float* Yout, uint32_t flags)
 {
     pm_mlp* n = const_cast<pm_mlp*>(nc);  // the activation workspace is scratch
@@ -660,7 +723,7 @@ int pm_gemm_bf16(pm_ctx* c, const void* A, int32_t lda, const void* B, int32_t l
     tc::Epilogue e = no_epilogue(M, N);
     e.out_f32 = C;
     e.ld_f32 = ldc;
-    if ((rc = gemm(c, (const bf16*)A, lda, (const bf16*)B, ldb, M, N, K, e, err))) return rc;
+    if ((rc = gemm(c, (const bf16*)A, lda, (const bf16*)B, ldb, M, N, K, e, err, take_wait_limit(c)))) return rc;
     unsigned flag = 0;
     PM_CUDA(cudaMemcpyAsync(&flag, err, 4, cudaMemcpyDeviceToHost, c->stream), "copy flag");
     PM_CUDA(cudaStreamSynchronize(c->stream), "gemm");

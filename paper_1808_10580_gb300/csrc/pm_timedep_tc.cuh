@@ -50,7 +50,8 @@ struct Shape {
     static constexpr int KS = (KD + 2 * EPC - 1) / (2 * EPC);  // MMA k-steps (two chunks each)
     static constexpr int KC = 2 * KS;                 // 16-byte chunks per tile row
     static constexpr int WS = EPC * KC;               // row stride of W (elements)
-    static constexpr int NC = F ? 4 * K : 4 * K + 1;  // accumulator columns used
+    static constexpr int MC = 8 * ((K + 1) / 2);      // columns of the m >= 1 sums (pairs of m, see pcol)
+    static constexpr int NC = F ? MC : MC + 1;        // accumulator columns used
     static constexpr int NP = (NC + 15) / 16 * 16;    // MMA N (multiple of 16)
     static constexpr int SBO = KC * 128;              // bytes between 8-row groups of a tile
     static constexpr int A_BYTES = 128 * KC * 16;     // 128 rows x KC chunks
@@ -184,10 +185,11 @@ struct Params {
     // W^T: row nc (accumulator column), entry k (A column); in W, or at Wg.
     float W[TdShape<K>::W_PARAM ? TdShape<K>::NP * TdShape<K>::WS : 1];
     const float* Wg;
-    // Folded shape: the m = 0 coefficients of v1 (pairs for S2_n, C2_n, n = 1..K)
-    // and the n = 0 coefficients of v2 (C1m at m-1, S1m at K+m-1).
-    float T0[2 * K];
-    float N0[2 * K];
+    // Folded shape: the m = 0 coefficients of v1 (S2_n at n-1, C2_n at K+n-1)
+    // and the n = 0 coefficients of v2 (C1m at m-1, S1m at K+m-1); read in
+    // pairs over consecutive n (m), so 8-byte aligned.
+    alignas(8) float T0[2 * K];
+    alignas(8) float N0[2 * K];
     float inv_s;              // FP16 operands: 1 / (power-of-two scale of W)
     Theta0Table<float> th;
     const ObsRec* obs;
@@ -200,6 +202,7 @@ struct Params {
     int32_t n_obs, chunks;
     uint32_t inst, key0, key1;
     unsigned* err;
+    uint32_t wait_limit;      // polls of the per-step MMA wait (tc::kWaitLimit unless a test lowers it)
     const int4* groups;       // shared paths: {m0, m1, stream, nmax} per grid row, or nullptr
     const int32_t* members;   // [n_obs] observation indices of the groups
 };
@@ -324,168 +327,264 @@ __device__ __forceinline__ void st_shared_v4u(uint32_t addr, const uint32_t (&v)
 }
 
 // Layouts of A and P.  A columns interleave the x2 harmonics: S2_n at 2(n-1),
-// C2_n at 2(n-1)+1 (n = 1..K), the constant 1 at 2K (unfolded shape).  P has
-// four consecutive columns per m = 1..K: P1c, P1s, P2c, P2s, after P(0) at
-// column 0 in the unfolded shape.  Both orders let a thread produce and
-// consume the harmonics in groups of four instead of holding all K at once.
+// C2_n at 2(n-1)+1 (n = 1..K), the constant 1 at 2K (unfolded shape).  P
+// takes the m >= 1 sums in blocks of eight columns per pair of wave numbers
+// (m, m+1), m odd: P1c(m), P1c(m+1), P1s(m), P1s(m+1), P2c(m), P2c(m+1),
+// P2s(m), P2s(m+1) (for odd K the last block's m+1 = K+1 columns are zero);
+// P(0) follows them at column MC = 8 ceil(K/2) in the unfolded shape.  The
+// pairs of a block start at even columns, so each lands in an aligned
+// register pair of tcgen05.ld and meets the x1 harmonics of the same pair of
+// wave numbers in one packed FMA (see velocity_stream); and a thread
+// produces and consumes the harmonics four wave numbers at a time (one
+// 16-column load per group of four) instead of holding all K at once.
 __host__ __device__ constexpr int acol_s(int n) { return 2 * (n - 1); }
 __host__ __device__ constexpr int acol_c(int n) { return 2 * (n - 1) + 1; }
 template <bool F>
-__host__ __device__ constexpr int pcol(int m, int j) { return (F ? 0 : 1) + 4 * (m - 1) + j; }
+__host__ __device__ constexpr int pcol(int m, int j) { return 8 * ((m - 1) / 2) + 2 * j + ((m - 1) & 1); }
+__host__ __device__ constexpr int p0col(int K) { return 8 * ((K + 1) / 2); }
 
-// e^{i n 2 pi x} for n = 4g + j (j = 1..4): e^{i j 2 pi x} (from one sin/cos
-// and products) times the group base e^{i 4g 2 pi x}, which advances by
-// e^{i 4 2 pi x} per group: a recurrence of depth g + 2.
+// Packed FP32 pairs (sm_100 and later: one instruction for two independent
+// float operations, each rounded exactly as its scalar form).
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+// Euler step of both coordinates (Eq. euler), two at a time: per coordinate
+// the operations of em_update<float> and Coord<float>::add (increment
+// s xi - v h by one FMA, then added to (hi, lo) with the compensated two-sum),
+// so the results are those of the scalar form bit for bit.
+__device__ __forceinline__ void em_update2(Coord<float>& X1, Coord<float>& X2, float v1, float v2, float h, float s,
+                                           float xi1, float xi2)
+{
+    const float2 d = __ffma2_rn(make_float2(s, s), make_float2(xi1, xi2),
+                                __fmul2_rn(make_float2(-v1, -v2), make_float2(h, h)));
+    const float2 a = make_float2(X1.hi, X2.hi);
+    const float2 b = __fadd2_rn(d, make_float2(X1.lo, X2.lo));
+    const float2 sm = __fadd2_rn(a, b);
+    const float2 bp = __fadd2_rn(sm, neg2(a));
+    const float2 e = __fadd2_rn(__fadd2_rn(a, neg2(__fadd2_rn(sm, neg2(bp)))), __fadd2_rn(b, neg2(bp)));
+    X1.hi = sm.x;
+    X2.hi = sm.y;
+    X1.lo = e.x;
+    X2.lo = e.y;
+}
+
+// e^{i n 2 pi x} for n = 4g + j (j = 1..4), group by group: e^{i j 2 pi x}
+// from one sin/cos and products, times the group base e^{i 4g 2 pi x}, which
+// is the j = 4 harmonic of the group before (a recurrence of depth g + 2).
+// The values of a group come as pairs over j, C12 = (C_{4g+1}, C_{4g+2}),
+// C34 = (C_{4g+3}, C_{4g+4}) and likewise S12, S34, each pair from one packed
+// multiply and one packed FMA per component:
+//   C_n = bc c_j - bs s_j,   S_n = bs c_j + bc s_j   (FMA of the first product),
+// with the base (bc, bs) held in both halves of a pair.  Group 0 is e^{i j 2 pi x}
+// itself (the base is 1).
 struct Harm4 {
-    float c[5], s[5];
-    float bc, bs;
+    float2 c12, c34, s12, s34;  // cos / sin of j 2 pi x, j = 1..4, paired over j
+    float2 bc, bs;              // the current group base, in both halves
     __device__ __forceinline__ void init(float x)
     {
         float s1, c1;
         sincos2pi(x, &s1, &c1);
-        c[0] = 1.f; s[0] = 0.f;
-        c[1] = c1; s[1] = s1;
-        c[2] = fmaf(c1, c1, -s1 * s1); s[2] = 2.f * (s1 * c1);
-        c[3] = fmaf(c[2], c1, -s[2] * s1); s[3] = fmaf(s[2], c1, c[2] * s1);
-        c[4] = fmaf(c[2], c[2], -s[2] * s[2]); s[4] = 2.f * (s[2] * c[2]);
-        bc = 1.f; bs = 0.f;
+        const float c2 = fmaf(c1, c1, -s1 * s1), s2 = 2.f * (s1 * c1);
+        const float c3 = fmaf(c2, c1, -s2 * s1), s3 = fmaf(s2, c1, c2 * s1);
+        const float c4 = fmaf(c2, c2, -s2 * s2), s4 = 2.f * (s2 * c2);
+        c12 = make_float2(c1, c2);
+        c34 = make_float2(c3, c4);
+        s12 = make_float2(s1, s2);
+        s34 = make_float2(s3, s4);
+        bc = make_float2(c4, c4);  // base of group 1
+        bs = make_float2(s4, s4);
     }
-    // e^{i (4g + j) 2 pi x} of the current group g, j = 1..4
-    __device__ __forceinline__ void get(int j, float& C, float& S) const
+    // Group G's harmonics (G in order: 0, 1, 2, ...); from G = 1 on the base
+    // must be that of group G (advance() after each group).  With HALF, only
+    // C12 / S12 (the last group of K = 4g + 2).
+    template <int G, bool HALF = false>
+    __device__ __forceinline__ void group(float2& C12, float2& S12, float2& C34, float2& S34) const
     {
-        C = fmaf(bc, c[j], -bs * s[j]);
-        S = fmaf(bs, c[j], bc * s[j]);
+        if constexpr (G == 0) {
+            C12 = c12; S12 = s12; C34 = c34; S34 = s34;
+        } else {
+            const float2 nbs = neg2(bs);
+            C12 = __ffma2_rn(bc, c12, __fmul2_rn(nbs, s12));
+            S12 = __ffma2_rn(bs, c12, __fmul2_rn(bc, s12));
+            if constexpr (!HALF) {
+                C34 = __ffma2_rn(bc, c34, __fmul2_rn(nbs, s34));
+                S34 = __ffma2_rn(bs, c34, __fmul2_rn(bc, s34));
+            }
+        }
     }
-    __device__ __forceinline__ void next_group()
+    // The base of the next group: the j = 4 harmonic of group G >= 1 just formed.
+    __device__ __forceinline__ void advance(const float2& C34, const float2& S34)
     {
-        const float nc = fmaf(bc, c[4], -bs * s[4]);
-        bs = fmaf(bs, c[4], bc * s[4]);
-        bc = nc;
+        bc = make_float2(C34.y, C34.y);
+        bs = make_float2(S34.y, S34.y);
     }
 };
 
+// Harmonic groups of a coordinate, as the velocity sum consumes them: G = the
+// group index, Q = groups of four wave numbers, with K <= 4Q.
+template <int K>
+constexpr int harm_groups() { return (K + 3) / 4; }
+
 // This thread's row of A from its x2, written as hi / lo tiles at row and
 // row + lo_off, eight columns (four harmonics) at a time; folded shape: returns
-// the m = 0 part of v1, p0 = sum_n T0[2n-2] S2_n + T0[2n-1] C2_n (eight
-// independent partial sums: this runs before the step's barrier).
-template <int K, bool F, bool H>
-__device__ __forceinline__ float write_row_stream(uint32_t row, uint32_t lo_off, float x2, const float* T0)
+// the m = 0 part of v1, p0 = sum_n T0[n-1] S2_n + T0[K+n-1] C2_n (eight
+// independent partial sums, paired: this runs before the step's barrier).
+template <int K, bool F, bool H, int G = 0>
+__device__ __forceinline__ void write_row_groups(uint32_t row, uint32_t lo_off, Harm4& h, const float* T0, float2 (&ps)[4])
 {
     constexpr int NCOL = 2 * K + (F ? 0 : 1);
-    Harm4 h;
-    h.init(x2);
-    float ps[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int g = 0; g < (NCOL + 7) / 8; ++g) {
-        float v[8];
-#pragma unroll
-        for (int e = 0; e < 8; e += 2) {
-            const int n = 4 * g + e / 2 + 1;
-            if (n <= K) {
-                float C, Sn;
-                h.get(e / 2 + 1, C, Sn);
-                v[e] = Sn;
-                v[e + 1] = C;
-                if constexpr (F) {
-                    ps[(n - 1) & 3] = fmaf(T0[2 * n - 2], Sn, ps[(n - 1) & 3]);
-                    ps[4 + ((n - 1) & 3)] = fmaf(T0[2 * n - 1], C, ps[4 + ((n - 1) & 3)]);
-                }
-            } else {
-                v[e] = (!F && 8 * g + e == 2 * K) ? 1.f : 0.f;
-                v[e + 1] = 0.f;
-            }
+    if constexpr (8 * G < NCOL) {
+        float2 C12, S12, C34 = make_float2(0.f, 0.f), S34 = make_float2(0.f, 0.f);
+        constexpr bool half = 4 * G + 2 >= K;  // only n = 4G+1, 4G+2 exist
+        h.template group<G, half>(C12, S12, C34, S34);
+        if constexpr (G >= 1 && 4 * G + 4 < K) h.advance(C34, S34);  // (group 1's base comes from init)
+        // columns (S_n, C_n) for n = 4G+1 .. 4G+4, zero / the unit column beyond K
+        float v[8] = {S12.x, C12.x, S12.y, C12.y, S34.x, C34.x, S34.y, C34.y};
+        if constexpr (F) {
+            // 4G+j <= K for all j: folded shapes have K a multiple of 4
+            const float2* t0 = reinterpret_cast<const float2*>(T0);
+            ps[0] = __ffma2_rn(t0[2 * G], S12, ps[0]);
+            ps[1] = __ffma2_rn(t0[2 * G + 1], S34, ps[1]);
+            ps[2] = __ffma2_rn(t0[K / 2 + 2 * G], C12, ps[2]);
+            ps[3] = __ffma2_rn(t0[K / 2 + 2 * G + 1], C34, ps[3]);
         }
         if constexpr (H) {
             uint32_t hv[4], lv[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) split_f16x2(v[2 * q], v[2 * q + 1], hv[q], lv[q]);
-            st_shared_v4u(row + 128u * g, hv);
-            st_shared_v4u(row + lo_off + 128u * g, lv);
+            for (int q = 0; q < 4; ++q) {
+                if (4 * G + q + 1 <= K) {
+                    split_f16x2(v[2 * q], v[2 * q + 1], hv[q], lv[q]);
+                } else {  // the unit column (FP16 1.0 = 0x3C00 in the low half) or zero padding: exact
+                    hv[q] = (!F && 8 * G + 2 * q == 2 * K) ? 0x3C00u : 0u;
+                    lv[q] = 0u;
+                }
+            }
+            st_shared_v4u(row + 128u * G, hv);
+            st_shared_v4u(row + lo_off + 128u * G, lv);
         } else {
 #pragma unroll
-            for (int half = 0; half < 2; ++half) {
+            for (int e = 0; e < 8; ++e)
+                if (4 * G + e / 2 + 1 > K) v[e] = (!F && 8 * G + e == 2 * K) ? 1.f : 0.f;
+#pragma unroll
+            for (int half_ = 0; half_ < 2; ++half_) {
                 float4 hi, lo;
-                split_tf32(v[4 * half], hi.x, lo.x);
-                split_tf32(v[4 * half + 1], hi.y, lo.y);
-                split_tf32(v[4 * half + 2], hi.z, lo.z);
-                split_tf32(v[4 * half + 3], hi.w, lo.w);
-                st_shared_v4(row + 128u * (2 * g + half), hi);
-                st_shared_v4(row + lo_off + 128u * (2 * g + half), lo);
+                split_tf32(v[4 * half_], hi.x, lo.x);
+                split_tf32(v[4 * half_ + 1], hi.y, lo.y);
+                split_tf32(v[4 * half_ + 2], hi.z, lo.z);
+                split_tf32(v[4 * half_ + 3], hi.w, lo.w);
+                st_shared_v4(row + 128u * (2 * G + half_), hi);
+                st_shared_v4(row + lo_off + 128u * (2 * G + half_), lo);
             }
         }
-        h.next_group();
+        write_row_groups<K, F, H, G + 1>(row, lo_off, h, T0, ps);
     }
-    if constexpr (F) return ((ps[0] + ps[1]) + (ps[2] + ps[3])) + ((ps[4] + ps[5]) + (ps[6] + ps[7]));
+}
+
+template <int K, bool F, bool H>
+__device__ __forceinline__ float write_row_stream(uint32_t row, uint32_t lo_off, float x2, const float* T0)
+{
+    Harm4 h;
+    h.init(x2);
+    float2 ps[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    write_row_groups<K, F, H>(row, lo_off, h, T0, ps);
+    if constexpr (F) return ((ps[0].x + ps[0].y) + (ps[1].x + ps[1].y)) + ((ps[2].x + ps[2].y) + (ps[3].x + ps[3].y));
     return 0.f;
 }
 
-// Sources of the x1 harmonics (C1m, S1m), m = 1..K in order, both from the
-// same Harm4 sequence (so results do not depend on the choice): computed as
-// the velocity sum needs them (few registers, after the MMA wait), or all
-// before the wait into arrays (overlapping the MMA, K + 1 pairs of registers).
+// Sources of the x1 harmonics, group by group, both from the same Harm4
+// sequence (so results do not depend on the choice): computed as the
+// velocity sum needs them (few registers, after the MMA wait), or all before
+// the wait into arrays (overlapping the MMA, K + 1 pairs of registers).
 struct HarmStream {
     Harm4 h;
     __device__ __forceinline__ void init(float x) { h.init(x); }
-    __device__ __forceinline__ void at(int m, float& C, float& S)
+    template <int G, bool HALF>
+    __device__ __forceinline__ void group(float2& C12, float2& S12, float2& C34, float2& S34)
     {
-        const int jj = (m - 1) % 4 + 1;
-        if (jj == 1 && m > 1) h.next_group();
-        h.get(jj, C, S);
+        h.template group<G, HALF>(C12, S12, C34, S34);
+        if constexpr (G >= 1 && !HALF) h.advance(C34, S34);
     }
 };
 
 template <int K>
 struct HarmArray {
-    float c[K + 1], s[K + 1];
+    static constexpr int Q = harm_groups<K>();
+    float2 c12[Q], s12[Q], c34[Q], s34[Q];
+    template <int G>
+    __device__ __forceinline__ void fill(Harm4& h)
+    {
+        if constexpr (G < Q) {
+            constexpr bool half = 4 * G + 2 >= K;
+            c34[G] = s34[G] = make_float2(0.f, 0.f);
+            h.template group<G, half>(c12[G], s12[G], c34[G], s34[G]);
+            if constexpr (G >= 1 && !half) h.advance(c34[G], s34[G]);
+            fill<G + 1>(h);
+        }
+    }
     __device__ __forceinline__ void init(float x)
     {
-        HarmStream st;
-        st.init(x);
-#pragma unroll
-        for (int m = 1; m <= K; ++m) st.at(m, c[m], s[m]);
+        Harm4 h;
+        h.init(x);
+        fill<0>(h);
     }
-    __device__ __forceinline__ void at(int m, float& C, float& S) const
+    template <int G, bool HALF>
+    __device__ __forceinline__ void group(float2& C12, float2& S12, float2& C34, float2& S34) const
     {
-        C = c[m];
-        S = s[m];
+        C12 = c12[G]; S12 = s12[G]; C34 = c34[G]; S34 = s34[G];
     }
 };
 
 // The velocity from this lane's accumulator row and the x1 harmonics (source
-// src, initialised from x1), read 16 columns at a time:
+// src, initialised from x1), one 16-column load per group of four wave
+// numbers:
 //   v1 = P(0) + sum_m C1m P1c(m) + S1m P1s(m),
 //   v2 = sum_m C1m (P2c(m) + N0c(m)) + S1m (P2s(m) + N0s(m)),
-// with P(0) and N0 from the FP32 pipes in the folded shape; each sum runs
-// over m in order.  FP16 operands: the sums over the accumulator carry the
+// with P(0) and N0 from the FP32 pipes in the folded shape.  Each of the four
+// sums advances as a packed pair over (m, m+1), m odd (the column blocks of
+// pcol), so every packed FMA takes an aligned pair of accumulator columns and
+// a harmonic pair of the group as they come; the halves (odd and even m) are
+// added at the end.  FP16 operands: the sums over the accumulator carry the
 // scale of W, removed by inv_s.
+template <int K, bool F, bool H, int G, typename Src>
+__device__ __forceinline__ void velocity_groups(uint32_t t_row, Src& src, const float* N0, float& p0, float2 (&acc)[4])
+{
+    constexpr int NP = ((F ? p0col(K) : p0col(K) + 1) + 15) / 16 * 16;
+    if constexpr (16 * G < NP) {
+        float a[16];
+        tmem_ld16(t_row + 16u * G, a);
+        if constexpr (4 * G < K) {
+            constexpr bool half = 4 * G + 2 >= K;
+            float2 C12, S12, C34, S34;
+            src.template group<G, half>(C12, S12, C34, S34);
+#pragma unroll
+            for (int b = 0; b < (half ? 1 : 2); ++b) {  // the blocks (m, m+1), m = 4G+1 and 4G+3
+                const float2 C = b ? C34 : C12, S = b ? S34 : S12;
+                const float* e = a + 8 * b;
+                float2 p2c = make_float2(e[4], e[5]), p2s = make_float2(e[6], e[7]);
+                if constexpr (F) {
+                    const float2* n0 = reinterpret_cast<const float2*>(N0);
+                    p2c = __fadd2_rn(p2c, n0[2 * G + b]);          // N0c(m), N0c(m+1)
+                    p2s = __fadd2_rn(p2s, n0[K / 2 + 2 * G + b]);  // N0s(m), N0s(m+1)
+                }
+                acc[0] = __ffma2_rn(C, make_float2(e[0], e[1]), acc[0]);
+                acc[1] = __ffma2_rn(S, make_float2(e[2], e[3]), acc[1]);
+                acc[2] = __ffma2_rn(C, p2c, acc[2]);
+                acc[3] = __ffma2_rn(S, p2s, acc[3]);
+            }
+        }
+        if constexpr (!F && p0col(K) >= 16 * G && p0col(K) < 16 * G + 16) p0 = a[p0col(K) - 16 * G];
+        velocity_groups<K, F, H, G + 1>(t_row, src, N0, p0, acc);
+    }
+}
+
 template <int K, bool F, bool H, typename Src>
 __device__ __forceinline__ void velocity_stream(uint32_t t_row, Src& src, const float* N0, float p0_in, float inv_s,
                                                 float& v1, float& v2)
 {
-    constexpr int NP = ((F ? 4 * K : 4 * K + 1) + 15) / 16 * 16;
-    float v1c = 0.f, v1s = 0.f, v2c = 0.f, v2s = 0.f, p0 = p0_in;
-    float Cm = 0.f, Sm = 0.f;
-#pragma unroll
-    for (int q = 0; q < NP / 16; ++q) {
-        float a[16];
-        tmem_ld16(t_row + 16u * q, a);
-#pragma unroll
-        for (int e = 0; e < 16; ++e) {
-            const int col = 16 * q + e;
-            if (!F && col == 0) {
-                p0 = a[e];
-                continue;
-            }
-            const int cc = col - (F ? 0 : 1);
-            if (cc >= 4 * K) continue;
-            const int m = cc / 4 + 1, j = cc % 4;
-            if (j == 0) src.at(m, Cm, Sm);
-            if (j == 0) v1c = fmaf(Cm, a[e], v1c);
-            else if (j == 1) v1s = fmaf(Sm, a[e], v1s);
-            else if (j == 2) v2c = fmaf(Cm, F ? a[e] + N0[m - 1] : a[e], v2c);
-            else v2s = fmaf(Sm, F ? a[e] + N0[K + m - 1] : a[e], v2s);
-        }
-    }
+    float2 acc[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    float p0 = p0_in;
+    velocity_groups<K, F, H, 0>(t_row, src, N0, p0, acc);
+    const float v1c = acc[0].x + acc[0].y, v1s = acc[1].x + acc[1].y;
+    const float v2c = acc[2].x + acc[2].y, v2s = acc[3].x + acc[3].y;
     if constexpr (H) {
         if constexpr (F) v1 = p0 + inv_s * (v1c + v1s);  // N0 carries the scale of W
         else v1 = inv_s * (p0 + (v1c + v1s));
@@ -645,6 +744,7 @@ __global__ void __launch_bounds__(TdLaunch<K>::THREADS, TdLaunch<K>::MIN_CTAS)
     const int N = m < m1 ? steps_of(m1 - 1) : 0;
     int stop = steps_of(m) - 1;  // the step at which member m takes its last step
     bool failed = false;
+    int issued = -1;  // the last step whose product was issued
     u32x4 r{0, 0, 0, 0};
 
     for (int n = 0; n < N; ++n) {
@@ -655,6 +755,7 @@ __global__ void __launch_bounds__(TdLaunch<K>::THREADS, TdLaunch<K>::MIN_CTAS)
         // One barrier per step: the rows are in place, and a wait that gave up
         // in the previous step (any thread) ends the loop for the whole CTA.
         if (__syncthreads_or(failed)) { failed = true; break; }
+        issued = n;
         if (tid == 0) {
             if constexpr (SETS == 1) {
                 issue_step_mma<K, F, H>(tmem, sb, bar_a);
@@ -672,12 +773,12 @@ __global__ void __launch_bounds__(TdLaunch<K>::THREADS, TdLaunch<K>::MIN_CTAS)
             }
         }
         // While the product runs: the Brownian increment and the x1 harmonics.
-        if ((n & 1) == 0) r = philox4x32_10(u32x4{(uint32_t)(n >> 1), pid, (uint32_t)stream, p.inst}, p.key0, p.key1);
+        if ((n & 1) == 0) r = philox4x32_10_wide(u32x4{(uint32_t)(n >> 1), pid, (uint32_t)stream, p.inst}, p.key0, p.key1);
         float xi1, xi2;
         box_muller<float>((n & 1) ? r.z : r.x, (n & 1) ? r.w : r.y, xi1, xi2);
         HarmStream h1;
         h1.init(X1.val());
-        failed = !tc::mbar_wait(bar_a, (uint32_t)(n & 1));
+        failed = !tc::mbar_wait(bar_a, (uint32_t)(n & 1), p.wait_limit);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         float v1, v2;
         velocity_stream<K, F, H>(t_row, h1, p.N0, p0, p.inv_s, v1, v2);
@@ -687,16 +788,14 @@ __global__ void __launch_bounds__(TdLaunch<K>::THREADS, TdLaunch<K>::MIN_CTAS)
             const ObsRec o = p.obs[member(m)];
             const float hh = (float)o.h_last, ss = (float)o.s_last;
             Coord<float> Y1 = X1, Y2 = X2;
-            em_update<float>(Y1, v1, hh, ss, xi1);
-            em_update<float>(Y2, v2, hh, ss, xi2);
+            em_update2(Y1, Y2, v1, v2, hh, ss, xi1, xi2);
             Y1.wrap();
             Y2.wrap();
             finish(m++, Y1, Y2, true);
             stop = steps_of(m) - 1;
         }
         if (n + 1 < N) {
-            em_update<float>(X1, v1, p.dt, p.s_dt, xi1);
-            em_update<float>(X2, v2, p.dt, p.s_dt, xi2);
+            em_update2(X1, X2, v1, v2, p.dt, p.s_dt, xi1, xi2);
             X1.wrap();
             X2.wrap();
         }
@@ -704,6 +803,9 @@ __global__ void __launch_bounds__(TdLaunch<K>::THREADS, TdLaunch<K>::MIN_CTAS)
     failed = __syncthreads_or(failed);
     if (failed && tid == 0) atomicExch(p.err, 1u);
     while (m < m1) finish(m++, X1, X2, false);  // only after a failed wait
+    // No product may still write tensor memory when it is freed: after a wait
+    // that gave up, wait (full bound) for the last one issued.
+    if (failed && issued >= 0) tc::mbar_wait(bar_a, (uint32_t)(issued & 1));
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
@@ -735,9 +837,9 @@ void build_W(const double* t, float* W)
         }
     }
     if constexpr (!F) {
-        for (int n = 1; n <= K; ++n) {  // m = 0: v1 only, accumulator column 0
-            set(0, acol_s(n), T(0, n, 0));
-            set(0, acol_c(n), T(0, n, 1));
+        for (int n = 1; n <= K; ++n) {  // m = 0: v1 only, accumulator column 4K
+            set(p0col(K), acol_s(n), T(0, n, 0));
+            set(p0col(K), acol_c(n), T(0, n, 1));
         }
     }
 }
@@ -751,8 +853,8 @@ cudaError_t launch_timedep_tc(const TimedepLaunch& L, unsigned* err, cudaStream_
     {
         auto T = [&](int m, int n, int q) { return L.coef[(size_t)(m * (K + 1) + n) * 8 + q]; };
         for (int n = 1; n <= K; ++n) {
-            p.T0[2 * n - 2] = (float)T(0, n, 0);  // multiplies S2_n
-            p.T0[2 * n - 1] = (float)T(0, n, 1);  // multiplies C2_n
+            p.T0[n - 1] = (float)T(0, n, 0);      // multiplies S2_n
+            p.T0[K + n - 1] = (float)T(0, n, 1);  // multiplies C2_n
             p.N0[n - 1] = (float)T(n, 0, 4);      // n = 0 term of P2c(m = n)
             p.N0[K + n - 1] = (float)T(n, 0, 6);  // n = 0 term of P2s(m = n)
         }
@@ -796,6 +898,7 @@ cudaError_t launch_timedep_tc(const TimedepLaunch& L, unsigned* err, cudaStream_
     p.key0 = L.key0;
     p.key1 = L.key1;
     p.err = err;
+    p.wait_limit = L.wait_limit;
     p.groups = L.groups;
     p.members = L.members;
     using LC = TdLaunch<K>;
