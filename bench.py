@@ -797,9 +797,22 @@ def run_layout(args):
 
 
 def run_mcmc(args):
-    """Surrogate-screened pCN against plain pCN on the same GPU (auxiliary line):
-    64 chains started at the data-generating field, the same beta for both
-    samplers; one line per beta in --betas."""
+    """Surrogate-screened pCN against plain pCN on the same GPU (configuration:
+    MLP 440 -> 512 -> 512 -> 100 trained on particle-map pairs, data with noise
+    sigma = 0.01, 64 chains; one JSON line):
+      feasibility  at the configured sigma, the change of the misfit Phi over
+                   small pCN proposals (beta = --feas-beta) around the
+                   data-generating field, for several particle counts M: with
+                   common random numbers the Monte Carlo error of G_M(u) is a
+                   rough function of u, and no sampler moves while it exceeds
+                   sigma / sqrt(n_obs); the M at which E[dPhi] falls to 1 and
+                   its measured cost per evaluation;
+      configured   both samplers at the configured sigma and M (accepted/s);
+      moving       both samplers at --move-sigma, where the chains move:
+                   accepted/s, the relative Monte Carlo error of the pooled
+                   posterior mean (between-chain standard errors) and the time
+                   each needs for 1e-2 relative error (error ~ 1/sqrt(time)).
+    Chains start at the data-generating field."""
     import torch
 
     import paper_1808_10580_gb300 as pm
@@ -808,14 +821,42 @@ def run_mcmc(args):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     ctx = pm.pm_create(0, stream.cuda_stream)
-    t0 = time.perf_counter()
-    prob = sm.make_data(ctx, sm.make_problem(M=args.M or 4096, sigma=args.sigma))
+    M0 = args.M or 4096
+    prob = sm.make_data(ctx, sm.make_problem(M=M0, sigma=args.sigma))
+    n_obs = len(prob.t)
+    u_true = prob.u_true.copy()
+
+    # --- feasibility at the configured sigma: dPhi over small proposals vs M
+    props = sm.pcn_proposals(prob, u_true, args.feas_beta, 32, seed=12)
+    feas = []
+    for M in [int(v) for v in args.feas_M.split(",")]:
+        pr = sm.make_problem(M=M, sigma=args.sigma)
+        pr.y, pr.u_true = prob.y, u_true
+        t0 = time.perf_counter()
+        G = sm.forward_many(ctx, pr, np.vstack([u_true[None, :], props]), tensor=args.tensor)
+        secs = time.perf_counter() - t0
+        phi = sm.misfit(pr, G)
+        dphi = phi[1:] - phi[0]
+        feas.append({"M": M, "dphi_median": float(np.median(dphi)), "dphi_mean": float(dphi.mean()),
+                     "mean_acceptance": float(np.mean(np.minimum(1.0, np.exp(-dphi)))),
+                     "seconds_per_eval": secs / G.shape[0]})
+    # E[dPhi] ~ n_obs SE^2 / sigma^2 falls like 1/M: the M at which it is 1
+    fit = [(f["M"], f["dphi_mean"]) for f in feas if f["dphi_mean"] > 0]
+    M_move = float(np.exp(np.mean([np.log(Mv * dp) for Mv, dp in fit]))) if fit else None
+    s_per_path_eval = float(np.mean([f["seconds_per_eval"] / f["M"] for f in feas]))
+    need = None
+    if M_move:
+        sec = s_per_path_eval * M_move
+        need = {"M_for_dphi_1": M_move, "seconds_per_eval": sec,
+                "hours_for_64_chains_x_1e4_steps_plain": sec * 64 * 1e4 / 3600,
+                "note": "E[dPhi] measured above, extrapolated as 1/M; cost per evaluation scales with M"}
+
+    # --- surrogate trained on particle-map pairs near the start state
     u0 = sm.start_states(prob, 64, spread=0.0)
     center = u0[0] if args.train_spread > 0 else None
     spread = args.train_spread if args.train_spread > 0 else 1.0
-    # network input: prior coordinates u / std (--screen-coords prior), or
-    # coordinates centred on the start state (local)
     coords = sm.screen_coords(prob, center, spread) if args.screen_coords == "local" else sm.screen_coords(prob)
+    t0 = time.perf_counter()
     Z, G = sm.training_pairs(ctx, prob, args.train_pairs, center=center, spread=spread, tensor=args.tensor,
                              coords=coords)
     t_pairs = time.perf_counter() - t0
@@ -826,28 +867,47 @@ def run_mcmc(args):
                                    lr_decay=args.lr_decay)
     t_train = time.perf_counter() - t1
     rmse = sm.surrogate_rmse(ctx, net, Zv, Gv)
-    rmse_train = sm.surrogate_rmse(ctx, net, Z[:2048], G[:2048])
-    for beta in [float(v) for v in args.betas.split(",")]:
-        plain, _ = sm.run_chains(ctx, prob, u0, beta, args.plain_steps, seed=11, tensor=args.tensor)
-        da, _ = sm.run_chains(ctx, prob, u0, beta, args.da_steps, seed=11, net=net, tensor=args.tensor,
-                              coords=coords)
-        line = {"metric": "accepted pCN proposals/s (64 chains)", "auxiliary": True, "data": "synthetic",
-                "value": da["accepted_per_s"], "unit": "accepted proposals/s",
-                "ratio_vs_plain": da["accepted_per_s"] / max(plain["accepted_per_s"], 1e-30),
-                "sq_jump_per_s": {"plain": plain["sq_jump_per_s"], "delayed_acceptance": da["sq_jump_per_s"],
-                                  "ratio": da["sq_jump_per_s"] / max(plain["sq_jump_per_s"], 1e-30),
-                                  "note": "squared prior-whitened jump distance of accepted moves per second"},
-                "config": {"train_pairs": args.train_pairs, "epochs": args.epochs, "M": prob.M,
-                           "n_obs": len(prob.t), "sigma": prob.sigma, "beta": beta, "chains": 64,
-                           "start": "data-generating field", "tensor_cores": bool(args.tensor),
-                           "training_inputs": (f"local: start state + {args.train_spread} x prior std x N(0, I)"
-                                               if args.train_spread > 0 else "prior draws"),
-                           "screen_coords": args.screen_coords},
-                "plain": plain, "delayed_acceptance": da,
-                "surrogate": {"val_rmse": rmse, "train_rmse": rmse_train, "final_train_loss": float(hist[-1]),
-                              "train_seconds": t_train, "pair_generation_seconds": t_pairs}}
-        print(json.dumps(line), flush=True)
+
+    beta = float(args.betas.split(",")[0])
+
+    def both(pr, steps_plain, steps_da):
+        plain, mp = sm.run_chains_tracked(ctx, pr, u0, beta, steps_plain, seed=11, tensor=args.tensor)
+        da, md = sm.run_chains_tracked(ctx, pr, u0, beta, steps_da, seed=11, net=net, tensor=args.tensor,
+                                       coords=coords)
+        out = {"plain": plain, "delayed_acceptance": da,
+               "accepted_per_s_ratio": da["accepted_per_s"] / max(plain["accepted_per_s"], 1e-30)}
+        if plain["accepts"] and da["accepts"]:
+            ep, _ = sm.posterior_mean_error(mp)
+            ed, _ = sm.posterior_mean_error(md)
+            tp = plain["wall_seconds"] * (ep / 1e-2) ** 2
+            td = da["wall_seconds"] * (ed / 1e-2) ** 2
+            out["posterior_mean_rel_error"] = {"plain": ep, "delayed_acceptance": ed}
+            out["seconds_to_1e-2"] = {"plain": tp, "delayed_acceptance": td, "ratio_plain_over_da": tp / td}
+        return out
+
+    configured = both(prob, args.plain_steps, args.da_steps)
+    mprob = sm.make_problem(M=M0, sigma=args.move_sigma)
+    mprob.u_true = u_true
+    mprob.y = sm.forward_many(ctx, mprob, u_true[None, :], tensor=args.tensor)[0] + args.move_sigma * (
+        np.random.Generator(np.random.PCG64(6004)).standard_normal(n_obs))
+    moving = both(mprob, args.move_plain_steps, args.move_da_steps)
     pm.pm_surrogate_destroy(net)
+    value = configured["delayed_acceptance"]["accepted_per_s"]
+    line = {"metric": "accepted pCN samples/s (64 chains), surrogate-screened vs plain", "auxiliary": True,
+            "data": "synthetic", "value": value, "unit": "accepted samples/s",
+            "config": {"sigma": args.sigma, "M": M0, "n_obs": n_obs, "beta": beta, "chains": 64,
+                       "train_pairs": args.train_pairs, "epochs": args.epochs, "start": "data-generating field",
+                       "tensor_cores": bool(args.tensor),
+                       "training_inputs": (f"local: start state + {args.train_spread} x prior std x N(0, I)"
+                                           if args.train_spread > 0 else "prior draws"),
+                       "screen_coords": args.screen_coords},
+            "configured": configured,
+            "feasibility": {"beta": args.feas_beta, "proposals": 32, "by_M": feas, "chains_move_at": need},
+            "moving": dict(moving, sigma=args.move_sigma,
+                           note="a larger noise than configured, where the chains move: not the configured target"),
+            "surrogate": {"val_rmse": rmse, "final_train_loss": float(hist[-1]), "train_seconds": t_train,
+                          "pair_generation_seconds": t_pairs}}
+    print(json.dumps(line), flush=True)
     pm.pm_destroy(ctx)
     return 0
 
@@ -870,9 +930,14 @@ def main():
                     help="timedep: the headline line; dirichlet / batched / mcmc: auxiliary measurements")
     ap.add_argument("--train-pairs", type=int, default=1 << 16, help="mcmc: surrogate training pairs")
     ap.add_argument("--betas", default="0.03", help="mcmc: comma-separated pCN steps (each the same for both samplers)")
-    ap.add_argument("--sigma", type=float, default=0.1,
-                    help="mcmc: observation noise standard deviation (0.01 is below the map's Monte Carlo noise "
-                         "at M = 4096 and no chain moves)")
+    ap.add_argument("--sigma", type=float, default=0.01,
+                    help="mcmc: observation noise standard deviation (the configured 0.01)")
+    ap.add_argument("--move-sigma", type=float, default=0.1,
+                    help="mcmc: the larger noise at which the samplers are also compared (chains move)")
+    ap.add_argument("--feas-M", default="4096,16384,65536", help="mcmc: particle counts of the feasibility sweep")
+    ap.add_argument("--feas-beta", type=float, default=0.005, help="mcmc: pCN step of the feasibility proposals")
+    ap.add_argument("--move-plain-steps", type=int, default=40, help="mcmc: plain steps at --move-sigma")
+    ap.add_argument("--move-da-steps", type=int, default=200, help="mcmc: delayed-acceptance steps at --move-sigma")
     ap.add_argument("--epochs", type=int, default=100, help="mcmc: surrogate training epochs")
     ap.add_argument("--screen-coords", default="prior", choices=["prior", "local"],
                     help="mcmc: surrogate input u / prior std, or (u - start) / (spread x prior std)")
@@ -881,8 +946,8 @@ def main():
                          "0: prior draws")
     ap.add_argument("--weight-decay", type=float, default=0.0, help="mcmc: AdamW weight decay")
     ap.add_argument("--lr-decay", type=float, default=1.0, help="mcmc: per-epoch step-size factor")
-    ap.add_argument("--plain-steps", type=int, default=8, help="mcmc: steps of the plain sampler")
-    ap.add_argument("--da-steps", type=int, default=200, help="mcmc: steps of the delayed-acceptance sampler")
+    ap.add_argument("--plain-steps", type=int, default=8, help="mcmc: steps of the plain sampler (configured sigma)")
+    ap.add_argument("--da-steps", type=int, default=50, help="mcmc: delayed-acceptance steps (configured sigma)")
     ap.add_argument("--B", type=int, default=256, help="instances of the batched workload")
     ap.add_argument("--tensor", dest="tensor", action="store_true", default=True,
                     help="timedep: velocity sum on the tensor cores (PM_TENSOR; the default)")

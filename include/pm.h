@@ -246,6 +246,36 @@ int pm_forward_dirichlet(pm_ctx* ctx, const pm_field* field, double drift_scale,
                          double* mean, double* var, int32_t* exit_step, int64_t* n_unexited,
                          const pm_path_opts* opts);
 
+/* Algorithm 2 in the disk with a general forcing and a state-dependent
+ * diffusion (Theorem 3.2 with f(x) and sigma(x); Eq. euler or Eq. millstein):
+ *   dX = -drift_scale v_u(X) ds + sigma(X) dW,
+ *   sigma(x) = diag(s0[0] + s1[0] x_1, s0[1] + s1[1] x_2),
+ * each coordinate driven by its own Brownian motion with a diffusion
+ * coefficient of its own coordinate, so the Milstein correction is the scalar
+ * one of Eq. millstein per coordinate:
+ *   X_i <- X_i - drift_scale v_i dt + sigma_i(X) sqrt(dt) xi_i
+ *               + (1/2) sigma_i(X) s1[i] (xi_i^2 - 1) dt      (milstein = 1),
+ * without the last term for milstein = 0 (Euler-Maruyama); xi as for the
+ * other maps.  The forcing is f(x) = g->f_const + sum_q F[q] exp(-w |x - c_q|^2),
+ * integrated by the left-point rule dt sum_{m < n} f(X_m); the constant-
+ * coefficient map is the case s0 = sqrt(2 kappa), s1 = 0, n_src = 0 (results
+ * equal up to rounding).  Other arguments, outputs and return values as for
+ * pm_forward_dirichlet; the kernels run on the FP32 pipes (float or double
+ * paths; PM_TENSOR is ignored). */
+typedef struct pm_diffusion_forcing {
+    double s0[2], s1[2];  /* sigma_i(x) = s0[i] + s1[i] x_i */
+    int32_t milstein;     /* 1: Eq. millstein, 0: Eq. euler */
+    int32_t n_src;        /* Gaussian sources, 0 .. PM_MAX_SOURCES */
+    double w;             /* width parameter of the sources, >= 0 */
+    const double* c;      /* [n_src][2] centres (host) */
+    const double* F;      /* [n_src] amplitudes (host) */
+} pm_diffusion_forcing;
+
+int pm_forward_dirichlet_general(pm_ctx* ctx, const pm_field* field, double drift_scale, const pm_dirichlet_data* g,
+                                 const pm_diffusion_forcing* df, const double* x, int64_t n_obs, int64_t M, double dt,
+                                 int64_t max_steps, uint64_t seed, uint32_t flags, double* mean, double* var,
+                                 int32_t* exit_step, int64_t* n_unexited, const pm_path_opts* opts);
+
 /* ---------------------------------------------------------------------------
  * Batched map: many parameter samples in one persistent launch.
  *
@@ -320,7 +350,8 @@ int pm_set_graph_mode(pm_ctx* ctx, int on);
  * second measured) with the caller's problem and flags for every candidate
  * from 1 to the kernel's occupancy limit, keep the fastest in the context
  * for (kernel, K, PM_FP64 and PM_TENSOR bits) and store it in
- * *best_ctas_per_sm (may be NULL).  Arguments are those of the forward call
+ * *best_ctas_per_sm (may be NULL); for the tensor-core kernels they then
+ * time the refill interval at that grid (pm_set_refill_pairs).  Arguments are those of the forward call
  * (PM_ASYNC is ignored; outputs go to scratch the call allocates and frees).
  * When the environment variable PM_AUTOTUNE_CACHE names a file, pm_create
  * reads this device's choices from it (a flat JSON object
@@ -340,6 +371,19 @@ int pm_autotune_batched(pm_ctx* ctx, const pm_batch* batch, uint32_t flags, int3
  * values above the occupancy limit are clamped to it, <= 0 removes the
  * setting.  kind: PM_TUNE_DIRICHLET or PM_TUNE_BATCHED. */
 int pm_set_ctas_per_sm(pm_ctx* ctx, int32_t kind, int32_t K, uint32_t flags, int32_t ctas_per_sm);
+
+/* The second free shape of the tensor-core forms of the persistent kernels
+ * (flags containing PM_TENSOR): the pairs of Euler steps between two refills
+ * of the lanes whose paths have ended (default 4; every path's random numbers
+ * are keyed by its own step index, so results do not depend on it).  The
+ * autotuners choose it after the CTAs per SM (coordinate descent over 1, 2,
+ * 4, 8, 16); this sets it by hand (<= 0 removes the setting, at most 64). */
+int pm_set_refill_pairs(pm_ctx* ctx, int32_t kind, int32_t K, uint32_t flags, int32_t pairs);
+
+/* The shape in use for (kind, K, flags): CTAs per SM and refill pairs, 0 where
+ * none was tuned or set (the launch then uses the occupancy limit and the
+ * default interval).  Either output may be NULL. */
+int pm_tuned_shape(pm_ctx* ctx, int32_t kind, int32_t K, uint32_t flags, int32_t* ctas_per_sm, int32_t* refill_pairs);
 
 /* ---------------------------------------------------------------------------
  * Learned surrogate of the forward map (the paper has no learned component;

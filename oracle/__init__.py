@@ -55,6 +55,11 @@ def lib():
                                          C.c_int64, C.c_double, C.c_int64, C.c_uint64, C.c_uint32,
                                          i64, C.c_int32, d, i64, d]
         L.or_dirichlet_paths.restype = C.c_int32
+        L.or_dirichlet_general_paths.argtypes = [C.c_int32, d, C.c_double, d, d, C.c_int32, C.c_double,
+                                                 C.c_double, C.c_double, C.c_int32, d, d, C.c_int32, C.c_double,
+                                                 d, d, d, C.c_int64, C.c_int64, C.c_int64, C.c_double, C.c_int64,
+                                                 C.c_uint64, C.c_uint32, i64, C.c_int32, d, i64, d]
+        L.or_dirichlet_general_paths.restype = C.c_int32
         L.or_square_bvp_paths.argtypes = [d, C.c_double, C.c_int32, d, C.c_double, C.c_double, C.c_double, d,
                                           C.c_int64, C.c_int64, C.c_int64, C.c_double, C.c_int64, C.c_uint64,
                                           C.c_uint32, i64, C.c_int32, d, i64]
@@ -181,6 +186,35 @@ def dirichlet_paths(K, u, drift_scale, kappa, gd, x, dt, max_steps, seed, i0=0, 
                                   _p(x, C.c_double), n_obs, i0, npaths, dt, max_steps, seed, inst,
                                   _p(ids, C.c_int64) if ids is not None else None, nthreads, _p(g, C.c_double), _p(st, C.c_int64),
                                   _p(xe, C.c_double) if want_x else None)
+    if nt < 0:
+        raise MemoryError("oracle allocation failed")
+    return (g, st, xe) if want_x else (g, st)
+
+
+def dirichlet_general_paths(K, u, drift_scale, gen, gd, x, dt, max_steps, seed, i0=0, npaths=1, inst=0,
+                            nthreads=0, want_x=False, obs_id=None):
+    """Per-path values and exit steps of Algorithm 2 in the disk with the
+    general forcing and diagonal affine diffusion of ``gen`` (attributes s0[2],
+    s1[2], milstein, n_src sources at c [n_src, 2] with amplitudes F and width
+    w) -> (g [n_obs, npaths], steps [n_obs, npaths] (, exit points))."""
+    x = _f64(x).reshape(-1, 2)
+    u = _f64(u)
+    ga, gb = _f64(gd.a), _f64(gd.b)
+    c = _f64(gen.c).reshape(-1, 2)
+    F = _f64(gen.F).reshape(-1)
+    s0, s1 = _f64(gen.s0).reshape(2), _f64(gen.s1).reshape(2)
+    n_obs = x.shape[0]
+    g = np.empty((n_obs, npaths))
+    st = np.empty((n_obs, npaths), dtype=np.int64)
+    xe = np.empty((n_obs, npaths, 2)) if want_x else None
+    ids = _ids(obs_id, n_obs)
+    nt = lib().or_dirichlet_general_paths(K, _p(u, C.c_double), drift_scale, _p(s0, C.c_double), _p(s1, C.c_double),
+                                          int(gen.milstein), gd.R, gd.quad, gd.f_const, len(ga), _p(ga, C.c_double),
+                                          _p(gb, C.c_double), len(F), float(gen.w), _p(c, C.c_double),
+                                          _p(F, C.c_double), _p(x, C.c_double), n_obs, i0, npaths, dt, max_steps,
+                                          seed, inst, _p(ids, C.c_int64) if ids is not None else None, nthreads,
+                                          _p(g, C.c_double), _p(st, C.c_int64),
+                                          _p(xe, C.c_double) if want_x else None)
     if nt < 0:
         raise MemoryError("oracle allocation failed")
     return (g, st, xe) if want_x else (g, st)

@@ -448,6 +448,137 @@ int32_t or_dirichlet_paths(int32_t K, const double* u, double drift_scale, doubl
 }
 
 /* ------------------------------------------------------------------------ */
+/* Algorithm 2 in the disk with a general forcing and a state-dependent      */
+/* diffusion (Theorem 3.2 with sigma(x), f(x)).                              */
+/*   dX = -d v(X) ds + sigma(X) dW,  sigma(x) = diag(s0_1 + s1_1 x_1,        */
+/*                                                   s0_2 + s1_2 x_2),       */
+/* each coordinate driven by its own Brownian motion and its own diffusion,  */
+/* so Eq. millstein applies coordinate by coordinate:                        */
+/*   X_i <- X_i - d v_i dt + sigma_i sqrt(dt) xi_i                           */
+/*               + (1/2) sigma_i sigma_i' (xi_i^2 - 1) dt   (Milstein),      */
+/* sigma_i' = s1_i, all evaluated at the step's start point (the last term   */
+/* left out for Euler-Maruyama, Eq. euler).                                  */
+/*   f(x) = f_const + sum_q F_q exp(-w |x - c_q|^2),                          */
+/* integrated by the left-point rule sum_{m < n} f(X_m) dt.  Exit, boundary  */
+/* data and unexited paths as in the constant-coefficient disk problem.      */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    field_t field;
+    double drift_scale, s0[2], s1[2];
+    int32_t milstein;
+    double R, quad, f_const;
+    int32_t n_ang;
+    const double* ga;
+    const double* gb;
+    int32_t n_src;
+    double w;
+    const double* c;
+    const double* F;
+    const double* x;
+    int64_t n_obs, i0, npaths;
+    double dt;
+    int64_t max_steps;
+    uint64_t seed;
+    uint32_t inst;
+    double* g;
+    int64_t* exit_step;
+    double* xend;
+    const int64_t* jid;
+    int64_t next;
+    pthread_mutex_t lock;
+} dg_job_t;
+
+static double general_forcing(const dg_job_t* J, const double X[2])
+{
+    double f = J->f_const;
+    for (int q = 0; q < J->n_src; ++q) {
+        const double d0 = X[0] - J->c[2 * q], d1 = X[1] - J->c[2 * q + 1];
+        f += J->F[q] * exp(-J->w * (d0 * d0 + d1 * d1));
+    }
+    return f;
+}
+
+static void dg_path(const dg_job_t* J, int64_t j, int64_t i, double* g, int64_t* nexit, double* xe)
+{
+    double X[2] = {J->x[2 * j], J->x[2 * j + 1]};
+    const double R2 = J->R * J->R;
+    const double sdt = sqrt(J->dt);
+    int64_t n = 0;
+    int exited = (X[0] * X[0] + X[1] * X[1] >= R2);
+    double integral_f = 0.0;
+    while (!exited && n < J->max_steps) {
+        double v[2], xi[2];
+        integral_f += general_forcing(J, X) * J->dt;   /* left point: f at X_n */
+        velocity_direct(&J->field, X, v);
+        or_step_normals(J->seed, J->inst, (uint32_t)(J->jid ? J->jid[j] : j), (uint32_t)i, n, xi);
+        for (int k = 0; k < 2; ++k) {
+            const double sig = J->s0[k] + J->s1[k] * X[k];
+            double Xn = X[k] - J->drift_scale * v[k] * J->dt + sig * sdt * xi[k];
+            if (J->milstein) Xn += 0.5 * sig * J->s1[k] * (xi[k] * xi[k] - 1.0) * J->dt;
+            X[k] = Xn;
+        }
+        ++n;
+        exited = (X[0] * X[0] + X[1] * X[1] >= R2);
+    }
+    if (xe) { xe[0] = X[0]; xe[1] = X[1]; }
+    if (!exited) {
+        *g = 0.0;
+        *nexit = -1;
+        return;
+    }
+    const double r = sqrt(X[0] * X[0] + X[1] * X[1]);
+    const double y[2] = {J->R * X[0] / r, J->R * X[1] / r};
+    *g = gbc_eval(J->quad, J->n_ang, J->ga, J->gb, y) - integral_f;
+    *nexit = n;
+}
+
+static void* dg_worker(void* arg)
+{
+    dg_job_t* J = (dg_job_t*)arg;
+    const int64_t total = J->n_obs * J->npaths;
+    const int64_t grain = 4;
+    for (;;) {
+        const int64_t w0 = job_take(&J->next, &J->lock, total, grain);
+        if (w0 >= total) break;
+        const int64_t w1 = w0 + grain < total ? w0 + grain : total;
+        for (int64_t w = w0; w < w1; ++w) {
+            const int64_t j = w / J->npaths, p = w % J->npaths;
+            dg_path(J, j, J->i0 + p, &J->g[w], &J->exit_step[w], J->xend ? &J->xend[2 * w] : NULL);
+        }
+    }
+    return NULL;
+}
+
+int32_t or_dirichlet_general_paths(int32_t K, const double* u, double drift_scale, const double* s0,
+                                   const double* s1, int32_t milstein, double R, double quad, double f_const,
+                                   int32_t n_ang, const double* ga, const double* gb, int32_t n_src, double w,
+                                   const double* c, const double* F, const double* x, int64_t n_obs, int64_t i0,
+                                   int64_t npaths, double dt, int64_t max_steps, uint64_t seed, uint32_t inst,
+                                   const int64_t* obs_id, int32_t nthreads, double* g, int64_t* exit_step,
+                                   double* xend)
+{
+    dg_job_t J;
+    if (field_init(&J.field, K, u)) return -1;
+    J.drift_scale = drift_scale;
+    J.s0[0] = s0[0]; J.s0[1] = s0[1]; J.s1[0] = s1[0]; J.s1[1] = s1[1];
+    J.milstein = milstein;
+    J.R = R; J.quad = quad; J.f_const = f_const; J.n_ang = n_ang; J.ga = ga; J.gb = gb;
+    J.n_src = n_src; J.w = w; J.c = c; J.F = F;
+    J.x = x; J.n_obs = n_obs; J.i0 = i0; J.npaths = npaths; J.dt = dt; J.max_steps = max_steps;
+    J.seed = seed; J.inst = inst; J.g = g; J.exit_step = exit_step; J.xend = xend; J.jid = obs_id; J.next = 0;
+    pthread_mutex_init(&J.lock, NULL);
+    const int nt = resolve_threads(nthreads);
+    pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)nt);
+    for (int k = 0; k < nt; ++k) pthread_create(&th[k], NULL, dg_worker, &J);
+    for (int k = 0; k < nt; ++k) pthread_join(th[k], NULL);
+    free(th);
+    pthread_mutex_destroy(&J.lock);
+    field_free(&J.field);
+    return nt;
+}
+
+/* ------------------------------------------------------------------------ */
 /* The optimal-forcing boundary-value problem of Section 4 (Eq. bvp:ex1),    */
 /* by Algorithm 2 / Theorem 3.2 in the unit square:                          */
 /*   -b . grad theta + kappa Laplace theta = sum_q F_q phi_q(x),             */

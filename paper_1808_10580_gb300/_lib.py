@@ -104,6 +104,9 @@ def load(build_if_missing: bool = True):
                                      C.c_uint64, u32, vp, vp, C.POINTER(pm_path_opts)]
     L.pm_forward_dirichlet.argtypes = [vp, C.POINTER(pm_field), dbl, dbl, C.POINTER(pm_dirichlet_data), vp, i64,
                                        i64, dbl, i64, C.c_uint64, u32, vp, vp, vp, vp, C.POINTER(pm_path_opts)]
+    L.pm_forward_dirichlet_general.argtypes = [vp, C.POINTER(pm_field), dbl, C.POINTER(pm_dirichlet_data),
+                                               C.POINTER(pm_diffusion_forcing), vp, i64, i64, dbl, i64, C.c_uint64,
+                                               u32, vp, vp, vp, vp, C.POINTER(pm_path_opts)]
     L.pm_philox.argtypes = [vp, vp, u32, u32, i64, vp, u32]
     L.pm_normals.argtypes = [vp, C.c_uint64, u32, u32, u32, i64, i64, vp, u32]
     L.pm_velocity.argtypes = [vp, C.POINTER(pm_field), vp, i64, vp, u32]
@@ -128,6 +131,8 @@ def load(build_if_missing: bool = True):
     L.pm_forward_square_bvp.argtypes = [vp, vp, vp, i64, i64, C.c_double, i64, C.c_uint64, u32, vp, vp, vp, vp,
                                         C.POINTER(pm_path_opts)]
     L.pm_set_ctas_per_sm.argtypes = [vp, C.c_int32, C.c_int32, C.c_uint32, C.c_int32]
+    L.pm_set_refill_pairs.argtypes = [vp, C.c_int32, C.c_int32, C.c_uint32, C.c_int32]
+    L.pm_tuned_shape.argtypes = [vp, C.c_int32, C.c_int32, C.c_uint32, vp, vp]
     _lib = L
     return L
 
@@ -283,6 +288,39 @@ def pm_forward_dirichlet(ctx, field: Field, drift_scale, kappa, g: DirichletData
                                               C.byref(o)))
 
 
+class pm_diffusion_forcing(C.Structure):
+    _fields_ = [("s0", C.c_double * 2), ("s1", C.c_double * 2), ("milstein", C.c_int32), ("n_src", C.c_int32),
+                ("w", C.c_double), ("c", C.c_void_p), ("F", C.c_void_p)]
+
+
+class DiffusionForcing:
+    """Host description of pm_diffusion_forcing (keeps its arrays alive):
+    sigma_i(x) = s0[i] + s1[i] x_i, the Milstein term when milstein, sources
+    F[q] exp(-w |x - c_q|^2)."""
+
+    def __init__(self, s0, s1, milstein=True, c=(), F=(), w=0.0):
+        self.c = np.ascontiguousarray(np.asarray(c, dtype=np.float64).reshape(-1, 2))
+        self.F = np.ascontiguousarray(np.asarray(F, dtype=np.float64).reshape(-1))
+        assert self.c.shape[0] == self.F.shape[0]
+        s0 = np.asarray(s0, dtype=np.float64).reshape(2)
+        s1 = np.asarray(s1, dtype=np.float64).reshape(2)
+        self.s = pm_diffusion_forcing((C.c_double * 2)(*s0), (C.c_double * 2)(*s1), int(bool(milstein)),
+                                      int(self.F.shape[0]), float(w), self.c.ctypes.data if self.F.size else None,
+                                      self.F.ctypes.data if self.F.size else None)
+
+
+def pm_forward_dirichlet_general(ctx, field: Field, drift_scale, g: DirichletData, df: DiffusionForcing, x, n_obs, M,
+                                 dt, max_steps, seed, flags, mean, var=None, exit_step=None, n_unexited=None,
+                                 path_offset=0, instance=0, g_out=None, x_out=None):
+    if _device(x, mean, var, exit_step, n_unexited, g_out, x_out):
+        flags |= PM_DEVICE_PTRS
+    o = _opts(path_offset, instance, g_out, x_out)
+    return _check(load().pm_forward_dirichlet_general(ctx, C.byref(field.s), float(drift_scale), C.byref(g.s),
+                                                      C.byref(df.s), _ptr(x), int(n_obs), int(M), float(dt),
+                                                      int(max_steps), int(seed), int(flags), _ptr(mean), _ptr(var),
+                                                      _ptr(exit_step), _ptr(n_unexited), C.byref(o)))
+
+
 class pm_square_bvp(C.Structure):
     _fields_ = [("b", C.c_double * 2), ("kappa", C.c_double), ("w", C.c_double), ("g_cos", C.c_double),
                 ("g_quad", C.c_double), ("n_src", C.c_int32), ("reserved", C.c_int32), ("c", C.c_void_p)]
@@ -394,6 +432,17 @@ def pm_autotune_dirichlet(ctx, field: Field, drift_scale, kappa, g: DirichletDat
 
 def pm_set_ctas_per_sm(ctx, kind, K, flags, ctas_per_sm):
     return _check(load().pm_set_ctas_per_sm(ctx, int(kind), int(K), int(flags), int(ctas_per_sm)))
+
+
+def pm_set_refill_pairs(ctx, kind, K, flags, pairs):
+    return _check(load().pm_set_refill_pairs(ctx, int(kind), int(K), int(flags), int(pairs)))
+
+
+def pm_tuned_shape(ctx, kind, K, flags):
+    """(CTAs per SM, refill pairs) in use for (kind, K, flags); 0 = not tuned or set."""
+    a, b = C.c_int32(), C.c_int32()
+    _check(load().pm_tuned_shape(ctx, int(kind), int(K), int(flags), C.byref(a), C.byref(b)))
+    return a.value, b.value
 
 
 class pm_train_opts(C.Structure):

@@ -683,10 +683,38 @@ int dirichlet_resident(int K, bool fp64, bool use_tc)
 // ---------------------------------------------------------------------------
 // Algorithm 2
 // ---------------------------------------------------------------------------
-int pm_forward_dirichlet(pm_ctx* c, const pm_field* field, double drift_scale, double kappa,
-                         const pm_dirichlet_data* gd, const double* x, int64_t n_obs, int64_t M, double dt,
-                         int64_t max_steps, uint64_t seed, uint32_t flags, double* mean, double* var,
-                         int32_t* exit_step, int64_t* n_unexited, const pm_path_opts* opts)
+}  // extern "C"
+
+namespace {
+
+template <typename Real>
+cudaError_t dispatch_dirichlet_general(int K, const DirichletLaunch& L, cudaStream_t s)
+{
+    switch (K) {
+#define PM_CASE(k) case k: return launch_dirichlet_general<Real, k>(L, s);
+        PM_K_LIST(PM_CASE)
+#undef PM_CASE
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename Real>
+int dispatch_dirichlet_general_occupancy(int K)
+{
+    switch (K) {
+#define PM_CASE(k) case k: return dirichlet_general_blocks_per_sm<Real, k>();
+        PM_K_LIST(PM_CASE)
+#undef PM_CASE
+    }
+    return 1;
+}
+
+// Algorithm 2 in the disk: the constant-coefficient map (gen == nullptr) or the
+// general forcing / state-dependent diffusion of pm_forward_dirichlet_general.
+int dirichlet_call(pm_ctx* c, const pm_field* field, double drift_scale, double kappa, const pm_dirichlet_data* gd,
+                   const DirichletGeneral* gen, const double* x, int64_t n_obs, int64_t M, double dt,
+                   int64_t max_steps, uint64_t seed, uint32_t flags, double* mean, double* var, int32_t* exit_step,
+                   int64_t* n_unexited, const pm_path_opts* opts)
 {
     if (!c) return fail(PM_EINVAL, "ctx is NULL");
     int rc = check_field(field);
@@ -812,10 +840,17 @@ int pm_forward_dirichlet(pm_ctx* c, const pm_field* field, double drift_scale, d
     L.inst = opts ? opts->instance : 0u;
     L.key0 = (uint32_t)(seed & 0xffffffffu);
     L.key1 = (uint32_t)(seed >> 32);
+    L.gen = gen;
     const int Kd = field->K;
-    const bool use_tc = dirichlet_uses_tc(Kd, flags);
-    int per_sm = dirichlet_resident(Kd, fp64, use_tc);
-    per_sm = tuned_ctas_per_sm(c, PM_TUNE_DIRICHLET, Kd, flags & (PM_FP64 | (use_tc ? PM_TENSOR : 0u)), per_sm);
+    const bool use_tc = !gen && dirichlet_uses_tc(Kd, flags);
+    int per_sm;
+    if (gen) {
+        per_sm = fp64 ? dispatch_dirichlet_general_occupancy<double>(Kd) : dispatch_dirichlet_general_occupancy<float>(Kd);
+    } else {
+        per_sm = dirichlet_resident(Kd, fp64, use_tc);
+        per_sm = tuned_ctas_per_sm(c, PM_TUNE_DIRICHLET, Kd, flags & (PM_FP64 | (use_tc ? PM_TENSOR : 0u)), per_sm);
+        if (use_tc) L.refill_pairs = tuned_refill_pairs(c, PM_TUNE_DIRICHLET, Kd, PM_TENSOR, kDefaultRefillPairs);
+    }
     int64_t grid = (int64_t)per_sm * c->sm_count;
     const int64_t need = (total + kDirichletBlock - 1) / kDirichletBlock;
     if (grid > need) grid = need;
@@ -825,7 +860,9 @@ int pm_forward_dirichlet(pm_ctx* c, const pm_field* field, double drift_scale, d
     if (c->timing) PM_CUDA(cudaEventRecord(c->ev0, c->stream), "event");
     cudaError_t e;
     unsigned* tc_err = (unsigned*)(W.ctr + 3);
-    if (use_tc) {
+    if (gen) {
+        e = fp64 ? dispatch_dirichlet_general<double>(Kd, L, c->stream) : dispatch_dirichlet_general<float>(Kd, L, c->stream);
+    } else if (use_tc) {
         switch (Kd) {
         case 4: e = tdtc::launch_dirichlet_tc<4>(L, tc_err, c->stream); break;
         case 5: e = tdtc::launch_dirichlet_tc<5>(L, tc_err, c->stream); break;
@@ -881,6 +918,50 @@ int pm_forward_dirichlet(pm_ctx* c, const pm_field* field, double drift_scale, d
     }
     if (tc_flag) return fail(PM_ETIMEOUT, "a tensor-core wait in the particle kernel timed out");
     return unexited ? PM_WARN_UNEXITED : PM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pm_forward_dirichlet(pm_ctx* c, const pm_field* field, double drift_scale, double kappa,
+                         const pm_dirichlet_data* gd, const double* x, int64_t n_obs, int64_t M, double dt,
+                         int64_t max_steps, uint64_t seed, uint32_t flags, double* mean, double* var,
+                         int32_t* exit_step, int64_t* n_unexited, const pm_path_opts* opts)
+{
+    return dirichlet_call(c, field, drift_scale, kappa, gd, nullptr, x, n_obs, M, dt, max_steps, seed, flags, mean,
+                          var, exit_step, n_unexited, opts);
+}
+
+int pm_forward_dirichlet_general(pm_ctx* c, const pm_field* field, double drift_scale, const pm_dirichlet_data* gd,
+                                 const pm_diffusion_forcing* df, const double* x, int64_t n_obs, int64_t M, double dt,
+                                 int64_t max_steps, uint64_t seed, uint32_t flags, double* mean, double* var,
+                                 int32_t* exit_step, int64_t* n_unexited, const pm_path_opts* opts)
+{
+    if (!df) return fail(PM_EINVAL, "diffusion / forcing description is NULL");
+    for (int k = 0; k < 2; ++k)
+        if (!std::isfinite(df->s0[k]) || !std::isfinite(df->s1[k]))
+            return fail(PM_EINVAL, "diffusion coefficients must be finite");
+    if (df->n_src < 0 || df->n_src > PM_MAX_SOURCES) return fail(PM_EINVAL, "n_src must be in [0, %d]", PM_MAX_SOURCES);
+    if (!(std::isfinite(df->w) && df->w >= 0)) return fail(PM_EINVAL, "w must be finite and >= 0");
+    if (df->n_src > 0 && (!df->c || !df->F || !finite_array(df->c, 2 * df->n_src) || !finite_array(df->F, df->n_src)))
+        return fail(PM_EINVAL, "source arrays NULL or not finite");
+    if (df->milstein != 0 && df->milstein != 1) return fail(PM_EINVAL, "milstein must be 0 or 1");
+    DirichletGeneral G{};
+    for (int k = 0; k < 2; ++k) {
+        G.s0[k] = df->s0[k];
+        G.s1[k] = df->s1[k];
+    }
+    G.milstein = df->milstein;
+    G.n_src = df->n_src;
+    G.w = df->w;
+    for (int q = 0; q < df->n_src; ++q) {
+        G.c[2 * q] = df->c[2 * q];
+        G.c[2 * q + 1] = df->c[2 * q + 1];
+        G.F[q] = df->F[q];
+    }
+    return dirichlet_call(c, field, drift_scale, 0.0, gd, &G, x, n_obs, M, dt, max_steps, seed, flags & ~PM_TENSOR,
+                          mean, var, exit_step, n_unexited, opts);
 }
 
 // ---------------------------------------------------------------------------
@@ -1007,7 +1088,7 @@ int pm_autotune_dirichlet(pm_ctx* c, const pm_field* field, double drift_scale, 
         return pm_forward_dirichlet(c, field, drift_scale, kappa, g, x, n_obs, M, dt, max_steps, seed, flags, mean,
                                     nullptr, nullptr, nullptr, nullptr);
     };
-    rc = autotune_loop(c, PM_TUNE_DIRICHLET, K, flags & (PM_FP64 | (use_tc ? PM_TENSOR : 0u)), resident, run,
+    rc = autotune_loop(c, PM_TUNE_DIRICHLET, K, flags & (PM_FP64 | (use_tc ? PM_TENSOR : 0u)), resident, use_tc, run,
                        best_ctas_per_sm);
     if (dev) cudaFree(mean);
     return rc;

@@ -43,9 +43,6 @@ __device__ __forceinline__ float w_entry(const float* tab, int nc, int k)
 template <int K>
 using BatShape = Shape<K, false, half_of<K>()>;
 
-// Pairs of Euler steps between two refills of the lanes.
-constexpr int kBatchRefillPairs = 4;
-
 template <int K>
 __global__ void __launch_bounds__(128, BatShape<K>::MIN_CTAS6) batched_tc_kernel(const __grid_constant__ BatchKernelParams p)
 {
@@ -216,12 +213,12 @@ __global__ void __launch_bounds__(128, BatShape<K>::MIN_CTAS6) batched_tc_kernel
             continue;
         }
 
-        // ---- two Euler steps per Philox call, one MMA per step, kBatchRefillPairs
+        // ---- two Euler steps per Philox call, one MMA per step, p.refill_pairs
         // pairs between refills (a lane whose path ends waits for the next refill)
 #pragma unroll 1
-        for (int pair = 0; pair < kBatchRefillPairs && !stop; ++pair) {
+        for (int pair = 0; pair < p.refill_pairs && !stop; ++pair) {
             u32x4 r{0, 0, 0, 0};
-            if (pid >= 0) r = philox4x32_10_wide(u32x4{(uint32_t)(n >> 1), i, j, stream}, key0, key1);
+            if (pid >= 0) r = philox4x32_10(u32x4{(uint32_t)(n >> 1), i, j, stream}, key0, key1);
 #pragma unroll 1
             for (int half = 0; half < 2; ++half) {
                 write_row_stream<K, false, H>(sb + row, (uint32_t)S::A_BYTES, X2.val(), nullptr);

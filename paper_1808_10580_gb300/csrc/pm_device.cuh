@@ -39,25 +39,6 @@ __device__ __forceinline__ u32x4 philox4x32_10(u32x4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
-// The same generator with each round's two products formed as 32 x 32 ->
-// 64-bit products (low and high words from one multiply each); identical
-// output.  The tensor-core kernels use this form (fewer integer
-// instructions); the FP32-pipe kernels keep the one above, with which the
-// wide-K FP32-pipe kernel measured 3.7 times faster at K = 64.
-__device__ __forceinline__ u32x4 philox4x32_10_wide(u32x4 c, uint32_t k0, uint32_t k1)
-{
-    constexpr uint32_t kMul0 = 0xD2511F53u, kMul1 = 0xCD9E8D57u;
-    constexpr uint32_t kWeyl0 = 0x9E3779B9u, kWeyl1 = 0xBB67AE85u;
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint64_t p0 = (uint64_t)kMul0 * c.x, p1 = (uint64_t)kMul1 * c.z;
-        c = u32x4{(uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0};
-        k0 += kWeyl0;
-        k1 += kWeyl1;
-    }
-    return c;
-}
-
 // Uniform in (0, 1) from the top 23 bits: (2q + 1) 2^-24, exact in float.
 template <typename Real>
 __device__ __forceinline__ Real uniform23(uint32_t r)

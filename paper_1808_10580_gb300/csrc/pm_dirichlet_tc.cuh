@@ -17,9 +17,6 @@ namespace tdtc {
 template <int K>
 using DirShape = Shape<K, false, half_of<K>()>;
 
-// Pairs of Euler steps between two refills of the lanes.
-constexpr int kRefillPairs = 4;
-
 template <int K>
 struct DirParams {
     float W[DirShape<K>::NP * DirShape<K>::WS];
@@ -41,6 +38,7 @@ struct DirParams {
     uint32_t inst, key0, key1;
     unsigned* err;
     uint32_t wait_limit;  // polls of the per-step MMA wait (tc::kWaitLimit unless a test lowers it)
+    int32_t refill_pairs; // pairs of Euler steps between lane refills (a launch shape: results do not depend on it)
 };
 
 template <int K>
@@ -156,12 +154,12 @@ __global__ void __launch_bounds__(128, DirShape<K>::MIN_CTAS6) dirichlet_tc_kern
             if (__syncthreads_and(done)) break;
             continue;
         }
-        // kRefillPairs pairs of steps between refills (a lane whose path exits
+        // refill_pairs pairs of steps between refills (a lane whose path exits
         // waits for the next refill; the RNG stays keyed by the step index).
 #pragma unroll 1
-        for (int pair = 0; pair < kRefillPairs && !stop; ++pair) {
+        for (int pair = 0; pair < p.refill_pairs && !stop; ++pair) {
             u32x4 r{0, 0, 0, 0};
-            if (pid >= 0) r = philox4x32_10_wide(u32x4{(uint32_t)(n >> 1), i, j, p.inst}, p.key0, p.key1);
+            if (pid >= 0) r = philox4x32_10(u32x4{(uint32_t)(n >> 1), i, j, p.inst}, p.key0, p.key1);
 #pragma unroll 1
             for (int half = 0; half < 2; ++half) {
                 write_row_stream<K, false, H>(sb + row, (uint32_t)S::A_BYTES, X2.val(), nullptr);
@@ -249,6 +247,7 @@ cudaError_t launch_dirichlet_tc(const DirichletLaunch& L, unsigned* err, cudaStr
     p.key1 = L.key1;
     p.err = err;
     p.wait_limit = L.wait_limit;
+    p.refill_pairs = L.refill_pairs > 0 ? L.refill_pairs : 1;
     cudaError_t e = cudaFuncSetAttribute(dirichlet_tc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
     if (e != cudaSuccess) return e;
     dirichlet_tc_kernel<K><<<L.grid, 128, S::SMEM, stream>>>(p);

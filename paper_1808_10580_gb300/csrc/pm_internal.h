@@ -32,8 +32,10 @@ struct pm_ctx {
     cudaGraphExec_t graph_exec = nullptr;
     int64_t graph_launches = 0;  // kernels per replay
     int graph_mode = 1;          // 1: capture and replay when the stream allows it
-    // Autotuned resident CTAs per SM of the persistent kernels, by tune_key().
+    // Autotuned resident CTAs per SM of the persistent kernels, and the pairs of
+    // Euler steps between lane refills of their tensor-core forms, by tune_key().
     std::map<uint64_t, int> ctas_per_sm;
+    std::map<uint64_t, int> refill_pairs;
     std::string device_name;
     // Test setting: polls of the tensor-core progress waits of the next forward
     // or GEMM call (pm_set_wait_limit); -1 = the full bound.
@@ -81,11 +83,16 @@ uint64_t tune_key(int kind, int K, uint32_t flags);
 // CTAs per SM for a persistent launch: the tuned value (at most `resident`)
 // unless PM_AUTOTUNE=0 or none is known, else `resident`.
 int tuned_ctas_per_sm(pm_ctx* c, int kind, int K, uint32_t flags, int resident);
+// Pairs of Euler steps between lane refills of a persistent tensor-core
+// kernel: the tuned value unless PM_AUTOTUNE=0 or none is known, else `def`.
+int tuned_refill_pairs(pm_ctx* c, int kind, int K, uint32_t flags, int def);
+constexpr int kDefaultRefillPairs = 4;
 // Reads this device's entries of the PM_AUTOTUNE_CACHE file into the context.
 void load_tune_cache(pm_ctx* c);
-// Runs the timing sweep over CTAs per SM in [1, resident] (see pm_autotune.cu).
-int autotune_loop(pm_ctx* c, int kind, int K, uint32_t flags, int resident, const std::function<int()>& run,
-                  int32_t* best);
+// Runs the timing sweep over CTAs per SM in [1, resident] and, with
+// tune_refill, then over the refill interval (see pm_autotune.cu).
+int autotune_loop(pm_ctx* c, int kind, int K, uint32_t flags, int resident, bool tune_refill,
+                  const std::function<int()>& run, int32_t* best);
 
 }  // namespace pm
 

@@ -75,6 +75,19 @@ inline int64_t wide_table_floats(int K)
     return simt > tc ? simt : tc;
 }
 
+// Algorithm 2 with a general forcing and a state-dependent diffusion (see
+// pm_forward_dirichlet_general): sigma_i(x) = s0[i] + s1[i] x_i, the Milstein
+// term when `milstein`, f = f_const + sum_q F[q] exp(-w |x - c_q|^2).
+constexpr int kMaxSources = 8;  // PM_MAX_SOURCES
+struct DirichletGeneral {
+    double s0[2], s1[2];
+    int milstein;
+    int n_src;
+    double w;
+    double c[2 * kMaxSources];
+    double F[kMaxSources];
+};
+
 struct DirichletLaunch {
     const double* coef;      // host table
     double drift_scale;
@@ -97,6 +110,8 @@ struct DirichletLaunch {
     uint32_t inst, key0, key1;
     int grid;                        // persistent CTAs
     uint32_t wait_limit = kWaitPolls;  // tensor-core kernel: polls of the per-step MMA wait
+    const DirichletGeneral* gen = nullptr;  // host: general forcing and diffusion, or nullptr
+    int refill_pairs = 4;            // tensor-core kernel: pairs of steps between lane refills
 };
 
 // Kernel block size of the time-dependent kernel (one path per thread).
@@ -109,6 +124,8 @@ template <typename Real, int K> cudaError_t launch_dirichlet(const DirichletLaun
 template <typename Real, int K> cudaError_t launch_velocity(const double* coef, const double* x, int64_t n,
                                                             double* v, cudaStream_t s);
 template <typename Real, int K> int dirichlet_blocks_per_sm();
+template <typename Real, int K> cudaError_t launch_dirichlet_general(const DirichletLaunch& L, cudaStream_t s);
+template <typename Real, int K> int dirichlet_general_blocks_per_sm();
 
 // Stores `msg` as the calling thread's pm_last_error() text; returns `code`.
 int set_error(int code, const char* msg);
@@ -183,6 +200,7 @@ struct BatchKernelParams {
     double* g;                         // per-path values
     unsigned* tc_err;                  // set when a tensor-core wait expires (tensor-core kernel)
     int32_t B;
+    int32_t refill_pairs;              // tensor-core kernel: pairs of steps between lane refills
 };
 
 template <int K> cudaError_t launch_batched(const BatchKernelParams& p, int grid, cudaStream_t s);

@@ -773,7 +773,7 @@ __global__ void __launch_bounds__(TdLaunch<K>::THREADS, TdLaunch<K>::MIN_CTAS)
             }
         }
         // While the product runs: the Brownian increment and the x1 harmonics.
-        if ((n & 1) == 0) r = philox4x32_10_wide(u32x4{(uint32_t)(n >> 1), pid, (uint32_t)stream, p.inst}, p.key0, p.key1);
+        if ((n & 1) == 0) r = philox4x32_10(u32x4{(uint32_t)(n >> 1), pid, (uint32_t)stream, p.inst}, p.key0, p.key1);
         float xi1, xi2;
         box_muller<float>((n & 1) ? r.z : r.x, (n & 1) ? r.w : r.y, xi1, xi2);
         HarmStream h1;

@@ -93,6 +93,19 @@ class DirichletData:
 
 
 @dataclass
+class DiffusionForcing:
+    """Diagonal affine diffusion sigma_i(x) = s0[i] + s1[i] x_i (with the
+    Milstein term when `milstein`) and Gaussian sources F[q] exp(-w |x - c_q|^2)
+    added to the constant forcing of the boundary data."""
+    s0: np.ndarray
+    s1: np.ndarray
+    milstein: bool = True
+    c: np.ndarray = field(default_factory=lambda: np.zeros((0, 2)))
+    F: np.ndarray = field(default_factory=lambda: np.zeros(0))
+    w: float = 0.0
+
+
+@dataclass
 class TimedepWorkload:
     name: str
     K: int
@@ -202,6 +215,20 @@ def dirichlet_disk_k10(M: int = 100_000) -> DirichletWorkload:
     g = DirichletData(R=1.0, quad=1.0, f_const=0.0, a=np.zeros(3), b=np.array([0.0, 0.0, 0.1]))
     return DirichletWorkload("dirichlet_disk_k10_50obs_M1e5_dt1e-4", 10, prior_field(10, 1002), 0.5,
                              0.05, g, disk_points(50, 0.9, 3002), M, 1e-4, 10_000_000, 4002)
+
+
+def dirichlet_general_disk(M: int = 10_000) -> tuple:
+    """The disk workload (K=10 field x 0.5, 50 uniform-area points r <= 0.9,
+    g = y1^2 - y2^2 + 0.1 sin 3phi, dt = 1e-4) with a state-dependent diffusion
+    sigma(x) = diag(0.3 + 0.15 x1, 0.3 - 0.1 x2) (between 0.15 and 0.45 on the
+    disk) and three Gaussian sources exp(-4 |x - c|^2) of amplitudes 1, -0.5,
+    0.8 at (0.3, 0.2), (-0.4, 0.1), (0, -0.5); Milstein steps.  Returns
+    (DirichletWorkload, DiffusionForcing); the workload's kappa is unused."""
+    w = dirichlet_disk_k10(M=M)
+    w.name = f"dirichlet_general_disk_k10_50obs_M{M}_dt1e-4"
+    df = DiffusionForcing(s0=np.array([0.3, 0.3]), s1=np.array([0.15, -0.1]), milstein=True,
+                          c=np.array([[0.3, 0.2], [-0.4, 0.1], [0.0, -0.5]]), F=np.array([1.0, -0.5, 0.8]), w=4.0)
+    return w, df
 
 
 def batched_instances(B: int = 256, M: int = 4096, seed: int = 1003):

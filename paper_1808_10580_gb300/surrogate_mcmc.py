@@ -142,3 +142,54 @@ def run_chains(ctx, prob: Problem, u0, beta, n_steps, seed, net=None, tensor: bo
     st["sq_jump_per_s"] = st["sq_jump"] / st["wall_seconds"]
     st["samples_per_s"] = st["proposals"] / st["wall_seconds"]
     return st, s / max(n, 1)
+
+
+def run_chains_tracked(ctx, prob: Problem, u0, beta, n_steps, seed, net=None, tensor: bool = True, coords=None):
+    """run_chains, one step at a time, keeping every chain's running sum of
+    states: -> (stats, per-chain means [n_chains, n_u])."""
+    th = pm.Fourier(prob.theta0.k, prob.theta0.a, prob.theta0.b)
+    shift, scale = coords if coords is not None else screen_coords(prob)
+    ch = pm.PCN(ctx, prob.K, u0, prob.y, prob.sigma, beta, seed, theta0=th, x=prob.x, t=prob.t, kappa=prob.kappa,
+                dt=prob.dt, M=prob.M, path_seed=prob.path_seed, screen=net,
+                screen_scale=scale if net is not None else None,
+                screen_shift=shift if net is not None else None, tensor=tensor)
+    sums = np.zeros_like(np.asarray(u0, dtype=np.float64))
+    tot = None
+    wall = 0.0
+    for _ in range(n_steps):
+        t0 = time.perf_counter()
+        st = ch.run(1)
+        wall += time.perf_counter() - t0
+        u, _, _, _ = ch.state()
+        sums += u
+        if tot is None:
+            tot = dict(st)
+        else:
+            for k in ("steps", "proposals", "stage1_accepts", "accepts", "forward_evals", "seconds", "sq_jump"):
+                tot[k] += st[k]
+    ch.close()
+    tot["wall_seconds"] = wall
+    tot["accepted_per_s"] = tot["accepts"] / wall
+    tot["samples_per_s"] = tot["proposals"] / wall
+    return tot, sums / max(n_steps, 1)
+
+
+def posterior_mean_error(chain_means):
+    """Relative Monte Carlo error of the pooled posterior-mean estimate from
+    independent chains: || SE || / || mean || with SE_k the between-chain
+    standard deviation of coordinate k over sqrt(chains)."""
+    m = np.asarray(chain_means, dtype=np.float64)
+    mean = m.mean(0)
+    se = m.std(0, ddof=1) / np.sqrt(m.shape[0])
+    return float(np.linalg.norm(se) / max(np.linalg.norm(mean), 1e-300)), mean
+
+
+def misfit(prob: Problem, G):
+    """Phi = sum_j (y_j - G_j)^2 / (2 sigma^2) for rows of G [N, n_obs]."""
+    return ((prob.y[None, :] - G) ** 2).sum(1) / (2 * prob.sigma ** 2)
+
+
+def pcn_proposals(prob: Problem, u, beta, n, seed):
+    """n pCN proposals sqrt(1 - beta^2) u + beta C^{1/2} xi around u."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.sqrt(1 - beta ** 2) * u[None, :] + beta * prob.std[None, :] * rng.standard_normal((n, len(u)))

@@ -1,6 +1,7 @@
 """The autotuner of the persistent launches: it picks a CTAs-per-SM count in
-[1, occupancy limit], the choice changes the grid and not the results, the
-cache file round-trips, and PM_AUTOTUNE=0 restores the occupancy limit."""
+[1, occupancy limit] and, for the tensor-core kernels, the number of step
+pairs between lane refills; neither changes the results, the cache file
+round-trips both, and PM_AUTOTUNE=0 restores the occupancy limit."""
 import os
 
 import numpy as np
@@ -80,6 +81,55 @@ def test_cache_file_round_trip(tmp_path):
         c2 = _gpu.ctx()                       # a new context reads the choice
         _gpu.batched(c2, ws, flags=TC)
         assert pm.pm_last_grid(c2) == best * sms()
+        pm.pm_destroy(c2)
+    finally:
+        del os.environ["PM_AUTOTUNE_CACHE"]
+
+
+@pytest.mark.parametrize("kind", ["dirichlet", "batched"])
+def test_refill_interval_changes_nothing_in_the_results(kind):
+    # Every path's random numbers are keyed by its own step index: how often
+    # the lanes refill is a launch shape, not part of the arithmetic.
+    c = _gpu.ctx()
+    try:
+        if kind == "dirichlet":
+            w = inputs.dirichlet_disk_k10(M=2048)
+            w.max_steps = 3000
+            run = lambda: _gpu.dirichlet(c, w, TC, want_paths=True)
+            key = pm.PM_TUNE_DIRICHLET
+        else:
+            ws = batch_problem()
+            run = lambda: _gpu.batched(c, ws, flags=TC)
+            key = pm.PM_TUNE_BATCHED
+        ref = run()
+        for pairs in (1, 2, 8, 16):
+            pm.pm_set_refill_pairs(c, key, 10, pm.PM_TENSOR, pairs)
+            assert pm.pm_tuned_shape(c, key, 10, pm.PM_TENSOR)[1] == pairs
+            got = run()
+            if kind == "dirichlet":
+                assert np.array_equal(got["g"], ref["g"]) and np.array_equal(got["steps"], ref["steps"])
+                assert np.array_equal(got["mean"], ref["mean"])
+            else:
+                assert np.array_equal(got[1], ref[1]) and np.array_equal(got[2], ref[2])
+    finally:
+        pm.pm_destroy(c)
+
+
+def test_autotuner_records_both_shapes_and_the_cache_keeps_them(tmp_path):
+    path = tmp_path / "tune2.json"
+    os.environ["PM_AUTOTUNE_CACHE"] = str(path)
+    try:
+        c = _gpu.ctx()
+        ws = batch_problem()
+        b, _ = _gpu.batch_from_workloads(ws, device=True)
+        best = pm.pm_autotune_batched(c, b, TC)
+        ctas, pairs = pm.pm_tuned_shape(c, pm.PM_TUNE_BATCHED, 10, pm.PM_TENSOR)
+        assert ctas == best and pairs in (1, 2, 4, 8, 16)
+        pm.pm_destroy(c)
+        name = torch.cuda.get_device_properties(0).name
+        assert f'"{name}|{pm.PM_TUNE_BATCHED}|10|{pm.PM_TENSOR}|refill": {pairs}' in path.read_text()
+        c2 = _gpu.ctx()
+        assert pm.pm_tuned_shape(c2, pm.PM_TUNE_BATCHED, 10, pm.PM_TENSOR) == (ctas, pairs)
         pm.pm_destroy(c2)
     finally:
         del os.environ["PM_AUTOTUNE_CACHE"]

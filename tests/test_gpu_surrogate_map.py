@@ -31,8 +31,18 @@ def test_input_gradient_matches_the_oracle(c):
         got = np.empty((200, 40), np.float32)
         pm.pm_surrogate_input_gradient(c, net, U, dY, got)
         want = mlp.input_gradient(P, U.astype(np.float64), dY.astype(np.float64))
-        # BF16 operands and BF16 intermediate cotangents, FP32 accumulation
-        assert rel(got, want) <= 2e-2 and cosine(got.ravel(), want.ravel()) >= 0.999, (rel(got, want),)
+        # (1) Against the FP64 oracle: the GPU stores activations and cotangents
+        # in BF16, and the few pre-activations near 0 whose ReLU mask flips move
+        # the result by a few percent (as for the weight gradients).
+        assert rel(got, want) <= 6e-2 and cosine(got.ravel(), want.ravel()) >= 0.998, (rel(got, want),)
+        # (2) Against the oracle's formulas with the GPU's storage roundings
+        # (BF16 activations, cotangent and backward signals): FP32 accumulation order.
+        Ud, dYd = U.astype(np.float64), dY.astype(np.float64)
+        H1 = bf16_round(np.maximum(Ud @ P["W1"].T + P["b1"], 0)).astype(np.float64)
+        H2 = bf16_round(np.maximum(H1 @ P["W2"].T + P["b2"], 0)).astype(np.float64)
+        dH2 = bf16_round((dYd @ P["W3"]) * (H2 > 0)).astype(np.float64)
+        dH1 = bf16_round((dH2 @ P["W2"]) * (H1 > 0)).astype(np.float64)
+        assert rel(got, dH1 @ P["W1"]) <= 2e-3, rel(got, dH1 @ P["W1"])
         # device pointers: the same bits
         dU = torch.empty((200, 40), dtype=torch.float32, device="cuda")
         pm.pm_surrogate_input_gradient(c, net, torch.from_numpy(U).cuda(), torch.from_numpy(dY).cuda(), dU)
