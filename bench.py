@@ -483,6 +483,21 @@ def run_aux(args):
                                     w.seed, pm.PM_FP32 | (pm.PM_TENSOR if args.tensor else 0), mean, var)
         name, cfg = w.name, {"n_obs": len(w.x), "M": w.M, "dt": w.dt, "kappa": w.kappa, "drift_scale": w.drift_scale,
                              "tensor_cores": bool(args.tensor)}
+    elif args.workload == "dirichlet_general":
+        w, dfw = inputs.dirichlet_general_disk(M=args.M or 100_000)
+        fld = pm.Field(w.K, w.u)
+        gd = pm.DirichletData(w.g.R, w.g.quad, w.g.f_const, w.g.a, w.g.b)
+        dfp = pm.DiffusionForcing(dfw.s0, dfw.s1, dfw.milstein, dfw.c, dfw.F, dfw.w)
+        x = torch.from_numpy(w.x).to(dev)
+        mean = torch.empty(len(w.x), dtype=torch.float64, device=dev)
+        var = torch.empty_like(mean)
+
+        def step():
+            pm.pm_forward_dirichlet_general(ctx, fld, w.drift_scale, gd, dfp, x, len(w.x), w.M, w.dt, w.max_steps,
+                                            w.seed, pm.PM_FP32, mean, var)
+        name, cfg = w.name, {"n_obs": len(w.x), "M": w.M, "dt": w.dt, "drift_scale": w.drift_scale,
+                             "sigma": "diag(0.3 + 0.15 x1, 0.3 - 0.1 x2), Milstein", "sources": 3,
+                             "kernel": "dirichlet_general_kernel<float,10> (FP32 pipes)"}
     else:
         ws = inputs.batched_instances(B=args.B, M=args.M or 4096)
         xs, ts, inst = [], [], []
@@ -510,13 +525,17 @@ def run_aux(args):
         name, cfg = f"batched_{args.B}x100obs_M{args.M or 4096}", {"B": args.B, "rows": row,
                                                                     "tensor_cores": bool(args.tensor)}
     tuned = None
-    if args.autotune:
+    if args.autotune and args.workload in ("dirichlet", "batched"):
         flags = pm.PM_FP32 | (pm.PM_TENSOR if args.tensor else 0)
         if args.workload == "dirichlet":
-            tuned = pm.pm_autotune_dirichlet(ctx, fld, w.drift_scale, w.kappa, gd, x, len(w.x), w.M, w.dt,
-                                             w.max_steps, w.seed, flags)
+            pm.pm_autotune_dirichlet(ctx, fld, w.drift_scale, w.kappa, gd, x, len(w.x), w.M, w.dt, w.max_steps,
+                                     w.seed, flags)
+            kind = pm.PM_TUNE_DIRICHLET
         else:
-            tuned = pm.pm_autotune_batched(ctx, batch, flags)
+            pm.pm_autotune_batched(ctx, batch, flags)
+            kind = pm.PM_TUNE_BATCHED
+        ctas, pairs = pm.pm_tuned_shape(ctx, kind, 10, pm.PM_TENSOR if args.tensor else 0)
+        tuned = {"ctas_per_sm": ctas, "refill_step_pairs": pairs if args.tensor else None}
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize(dev)
@@ -535,7 +554,7 @@ def run_aux(args):
             "dtype": "f32", "data": "synthetic", "auxiliary": True,
             "config": dict(workload=name, particle_steps_per_call=steps[-1], **cfg)}
     line["config"]["grid"] = pm.pm_last_grid(ctx)
-    line["config"]["autotuned_ctas_per_sm"] = tuned
+    line["config"]["autotuned_shape"] = tuned
     if args.workload == "batched":
         # CUDA-graph replay against direct launches of the same call (the
         # difference is the launch overhead the graph removes)
@@ -552,8 +571,9 @@ def run_aux(args):
         direct = timed()
         pm.pm_set_graph_mode(ctx, 1)
         line["graph"] = {"replay_ms": replay, "direct_ms": direct, "launches_per_call": 4}
-    if args.workload == "dirichlet":
+    if args.workload in ("dirichlet", "dirichlet_general"):
         line["kernel_ms"] = pm.pm_last_kernel_ms(ctx)
+    if args.workload == "dirichlet":
         # Exit-step distribution of the same call (outside the timed region): the
         # longest path bounds the call from below at one path's step latency.
         es = torch.empty(len(w.x) * w.M, dtype=torch.int32, device=dev)
@@ -926,7 +946,8 @@ def main():
     ap.add_argument("--M", type=int, default=0, help="particles per observation (default: the workload's own; "
                     "smaller values are for profiling captures only)")
     ap.add_argument("--sweep-k", default="", help="sweep: comma-separated K values (default 2..64)")
-    ap.add_argument("--workload", default="timedep", choices=["timedep", "dirichlet", "batched", "mcmc", "sweep", "surrogate", "bvp", "layout"],
+    ap.add_argument("--workload", default="timedep", choices=["timedep", "dirichlet", "dirichlet_general", "batched", "mcmc", "sweep", "surrogate",
+                             "bvp", "layout"],
                     help="timedep: the headline line; dirichlet / batched / mcmc: auxiliary measurements")
     ap.add_argument("--train-pairs", type=int, default=1 << 16, help="mcmc: surrogate training pairs")
     ap.add_argument("--betas", default="0.03", help="mcmc: comma-separated pCN steps (each the same for both samplers)")
