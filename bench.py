@@ -860,16 +860,24 @@ def run_mcmc(args):
         feas.append({"M": M, "dphi_median": float(np.median(dphi)), "dphi_mean": float(dphi.mean()),
                      "mean_acceptance": float(np.mean(np.minimum(1.0, np.exp(-dphi)))),
                      "seconds_per_eval": secs / G.shape[0]})
-    # E[dPhi] ~ n_obs SE^2 / sigma^2 falls like 1/M: the M at which it is 1
-    fit = [(f["M"], f["dphi_mean"]) for f in feas if f["dphi_mean"] > 0]
-    M_move = float(np.exp(np.mean([np.log(Mv * dp) for Mv, dp in fit]))) if fit else None
-    s_per_path_eval = float(np.mean([f["seconds_per_eval"] / f["M"] for f in feas]))
+    # E[dPhi] = a / M + b: a the Monte Carlo roughness of G_M (n_obs SE^2 / sigma^2
+    # times M), b the change of the smooth misfit over proposals of this beta
+    # (the posterior's own curvature, ~ beta^2).  Chains move when both are ~ 1:
+    # M ~ a and beta ~ feas_beta / sqrt(b).
     need = None
-    if M_move:
-        sec = s_per_path_eval * M_move
-        need = {"M_for_dphi_1": M_move, "seconds_per_eval": sec,
+    if len(feas) >= 2:
+        Ms = np.array([f["M"] for f in feas], dtype=float)
+        dp = np.array([f["dphi_mean"] for f in feas])
+        (a_fit, b_fit), *_ = np.linalg.lstsq(np.stack([1.0 / Ms, np.ones_like(Ms)], 1), dp, rcond=None)
+        s_per_path_eval = float(np.mean([f["seconds_per_eval"] / f["M"] for f in feas]))
+        M_need = max(float(a_fit), 1.0)
+        sec = s_per_path_eval * M_need
+        need = {"fit": {"a": float(a_fit), "b": float(b_fit), "model": "E[dPhi] = a / M + b"},
+                "M_for_noise_term_1": M_need,
+                "beta_for_smooth_term_1": args.feas_beta / np.sqrt(b_fit) if b_fit > 0 else None,
+                "seconds_per_eval_at_that_M": sec,
                 "hours_for_64_chains_x_1e4_steps_plain": sec * 64 * 1e4 / 3600,
-                "note": "E[dPhi] measured above, extrapolated as 1/M; cost per evaluation scales with M"}
+                "note": "cost per evaluation from the measured time, proportional to M"}
 
     # --- surrogate trained on particle-map pairs near the start state
     u0 = sm.start_states(prob, 64, spread=0.0)
