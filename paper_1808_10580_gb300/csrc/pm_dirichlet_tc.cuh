@@ -162,7 +162,9 @@ __global__ void __launch_bounds__(128, DirShape<K>::MIN_CTAS6) dirichlet_tc_kern
             if (pid >= 0) r = philox4x32_10(u32x4{(uint32_t)(n >> 1), i, j, p.inst}, p.key0, p.key1);
 #pragma unroll 1
             for (int half = 0; half < 2; ++half) {
-                write_row_stream<K, false, H>(sb + row, (uint32_t)S::A_BYTES, X2.val(), nullptr);
+                float2 sx, cx;
+                sincos_turns2(make_float2(X1.val(), X2.val()), sx, cx);
+                write_row_stream<K, false, H>(sb + row, (uint32_t)S::A_BYTES, sx.y, cx.y, nullptr);
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 // One barrier per step: the rows are in place, and a wait that gave
@@ -173,9 +175,10 @@ __global__ void __launch_bounds__(128, DirShape<K>::MIN_CTAS6) dirichlet_tc_kern
                 float xi1, xi2;
                 box_muller<float>(half ? r.z : r.x, half ? r.w : r.y, xi1, xi2);
                 HarmArray<K> h1;  // during the product
-                h1.init(X1.val());
+                h1.init(sx.x, cx.x);
                 issued_any = true;
-                failed = !tc::mbar_wait(bar_a, phase, p.wait_limit);
+                failed = p.wait_limit >= tc::kWaitLimit ? !tc::mbar_wait(bar_a, phase)
+                                                        : !tc::mbar_wait(bar_a, phase, p.wait_limit);
                 phase ^= 1u;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 float v1, v2;
