@@ -576,6 +576,12 @@ int pm_philox(pm_ctx* ctx, const uint32_t* ctr, uint32_t key0, uint32_t key1, in
 int pm_normals(pm_ctx* ctx, uint64_t seed, uint32_t b, uint32_t j, uint32_t i, int64_t n0,
                int64_t count, double* out, uint32_t flags);
 
+/* sin(2 pi x) and cos(2 pi x) of n float points x (device pointers), as the
+ * tensor-core kernels form them for their harmonic recurrences: a quarter-turn
+ * reduction and the Taylor series of sin and cos in turns (the library's own,
+ * not the CUDA math library's).  Outputs s[n], c[n] (device). */
+int pm_sincos_turns(pm_ctx* ctx, const float* x, int64_t n, float* s, float* c);
+
 /* Velocity v_u at npts points x[npts][2] -> v[npts][2], evaluated by the same
  * device code as the particle step (product basis, trigonometric
  * recurrences) in the precision the flags select. */

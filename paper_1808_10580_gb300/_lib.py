@@ -118,6 +118,7 @@ def load(build_if_missing: bool = True):
                                         i64, dbl, i64, C.c_uint64, u32, vp]
     L.pm_set_graph_mode.argtypes = [vp, C.c_int]
     L.pm_set_kernel_timing.argtypes = [vp, C.c_int]
+    L.pm_sincos_turns.argtypes = [vp, vp, i64, vp, vp]
     L.pm_set_wait_limit.argtypes = [vp, i64]
     L.pm_last_kernel_ms.argtypes = [vp]
     L.pm_last_kernel_ms.restype = C.c_float
@@ -216,6 +217,11 @@ def pm_destroy(ctx):
 
 def pm_stream(ctx):
     return load().pm_stream(ctx)
+
+
+def pm_sincos_turns(ctx, x, s, c):
+    """sin and cos of 2 pi x (float32 CUDA tensors) as the tensor-core kernels form them."""
+    return _check(load().pm_sincos_turns(ctx, _ptr(x), int(x.numel()), _ptr(s), _ptr(c)))
 
 
 def pm_set_kernel_timing(ctx, on):

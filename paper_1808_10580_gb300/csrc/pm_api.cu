@@ -998,6 +998,21 @@ int pm_philox(pm_ctx* c, const uint32_t* ctr, uint32_t key0, uint32_t key1, int6
     return PM_OK;
 }
 
+int pm_sincos_turns(pm_ctx* c, const float* x, int64_t n, float* s, float* co)
+{
+    if (!c) return fail(PM_EINVAL, "ctx is NULL");
+    if (n < 0) return fail(PM_EINVAL, "n < 0");
+    if (n == 0) return PM_OK;
+    if (!x || !s || !co) return fail(PM_EINVAL, "NULL array");
+    int rc = check_ptrs(c, PM_DEVICE_PTRS, {x, s, co});
+    if (rc) return rc;
+    if ((rc = set_device(c))) return rc;
+    PM_CUDA(launch_sincos_turns(x, n, s, co, c->stream), "sincos kernel");
+    count_launch(c);
+    PM_CUDA(cudaStreamSynchronize(c->stream), "sincos");
+    return PM_OK;
+}
+
 int pm_normals(pm_ctx* c, uint64_t seed, uint32_t b, uint32_t j, uint32_t i, int64_t n0, int64_t count, double* out,
                uint32_t flags)
 {

@@ -219,6 +219,7 @@ __global__ void __launch_bounds__(128, BatShape<K>::MIN_CTAS6) batched_tc_kernel
         for (int pair = 0; pair < p.refill_pairs && !stop; ++pair) {
             u32x4 r{0, 0, 0, 0};
             if (pid >= 0) r = philox4x32_10(u32x4{(uint32_t)(n >> 1), i, j, stream}, key0, key1);
+            float2 z1, z2;  // the two steps' normals, formed during the first product
 #pragma unroll 1
             for (int half = 0; half < 2; ++half) {
                 float2 sx, cx;
@@ -231,8 +232,8 @@ __global__ void __launch_bounds__(128, BatShape<K>::MIN_CTAS6) batched_tc_kernel
                 if (__syncthreads_or(failed)) { stop = true; break; }
                 if (tid == 0) issue_step_mma<K, false, H>(tmem, sb, bar_a);
                 // While the product runs: the Brownian increment and the x1 harmonics.
-                float xi1, xi2;
-                box_muller<float>(half ? r.z : r.x, half ? r.w : r.y, xi1, xi2);
+                if (half == 0) box_muller2(r.x, r.y, r.z, r.w, z1, z2);
+                const float xi1 = half ? z1.y : z1.x, xi2 = half ? z2.y : z2.x;
                 HarmArray<K> h1;  // during the product
                 h1.init(sx.x, cx.x);
                 issued_any = true;

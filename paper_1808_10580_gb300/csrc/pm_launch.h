@@ -145,6 +145,7 @@ cudaError_t launch_reduce_paths(const double* g, int64_t n_obs, int64_t M, doubl
                                 cudaStream_t s, double2* part = nullptr);
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, int64_t n, uint32_t* out,
                           cudaStream_t s);
+cudaError_t launch_sincos_turns(const float* x, int64_t n, float* s, float* c, cudaStream_t st);
 cudaError_t launch_normals(uint64_t seed, uint32_t b, uint32_t j, uint32_t i, int64_t n0, int64_t count,
                            double* out, bool fp64, cudaStream_t s);
 

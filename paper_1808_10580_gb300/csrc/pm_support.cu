@@ -233,6 +233,31 @@ cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, int64_t
     return cudaGetLastError();
 }
 
+// sin and cos of 2 pi x as the tensor-core kernels' harmonic recurrences form
+// them (sincos_turns2), for points x[n] (float), two points per thread.
+__global__ void sincos_turns_kernel(const float* __restrict__ x, int64_t n, float* __restrict__ s, float* __restrict__ c)
+{
+    const int64_t q = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    if (q >= n) return;
+    const bool two = q + 1 < n;
+    float2 sv, cv;
+    sincos_turns2(make_float2(x[q], two ? x[q + 1] : 0.f), sv, cv);
+    s[q] = sv.x;
+    c[q] = cv.x;
+    if (two) {
+        s[q + 1] = sv.y;
+        c[q + 1] = cv.y;
+    }
+}
+
+cudaError_t launch_sincos_turns(const float* x, int64_t n, float* s, float* c, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const int64_t pairs = (n + 1) / 2;
+    sincos_turns_kernel<<<(unsigned)((pairs + 255) / 256), 256, 0, st>>>(x, n, s, c);
+    return cudaGetLastError();
+}
+
 template <typename Real>
 __global__ void normals_kernel(uint32_t k0, uint32_t k1, uint32_t b, uint32_t j, uint32_t i, int64_t n0,
                                int64_t count, double* __restrict__ out)

@@ -367,45 +367,6 @@ __device__ __forceinline__ void em_update2(Coord<float>& X1, Coord<float>& X2, f
     X2.lo = e.y;
 }
 
-// sin and cos of 2 pi x for both halves of x (the particle's two coordinates,
-// each in [0, 1) or at most a few units from it), for the harmonic
-// recurrences.  Reduction to a quarter turn: q = rint(4x) by the rounding of
-// 4x + 1.5 2^23 (exact for |4x| < 2^22; the low bits of that sum are q), and
-// r = x - q/4 in [-1/8, 1/8], formed exactly by one FMA; with t = 2 pi r in
-// [-pi/4, pi/4] the Taylor series of sin t to t^9 and of cos t to t^10 (the
-// next terms are below 1.8e-9 and 1.2e-10), written in r with the
-// coefficients (-1)^k (2 pi)^n / n!, evaluated by Horner's rule on packed
-// pairs; then the rotation by q quarter turns, (sin, cos) -> (cos, -sin) per
-// quarter.  Measured in an FP32 emulation against float64 sin/cos: absolute
-// error below 8.4e-8, relative below 1.7 ulp away from the exact zeros.
-__device__ __forceinline__ float2 pair(float v) { return make_float2(v, v); }
-
-__device__ __forceinline__ void sincos_turns2(float2 x, float2& s, float2& c)
-{
-    constexpr float kRound = 12582912.0f;  // 1.5 * 2^23
-    const float2 t = __ffma2_rn(x, pair(4.0f), pair(kRound));
-    const float2 q = __fadd2_rn(t, pair(-kRound));
-    const float2 r = __ffma2_rn(q, pair(-0.25f), x);
-    const float2 r2 = __fmul2_rn(r, r);
-    float2 ps = __ffma2_rn(r2, pair(42.058692932128906f), pair(-76.70585632324219f));
-    ps = __ffma2_rn(r2, ps, pair(81.6052474975586f));
-    ps = __ffma2_rn(r2, ps, pair(-41.34170150756836f));
-    ps = __ffma2_rn(r2, ps, pair(6.2831854820251465f));
-    const float2 S = __fmul2_rn(r, ps);
-    float2 pc = __ffma2_rn(r2, pair(-26.42625617980957f), pair(60.2446403503418f));
-    pc = __ffma2_rn(r2, pc, pair(-85.45681762695312f));
-    pc = __ffma2_rn(r2, pc, pair(64.93939208984375f));
-    pc = __ffma2_rn(r2, pc, pair(-19.739208221435547f));
-    const float2 C = __ffma2_rn(r2, pc, pair(1.0f));
-    const uint32_t q0 = __float_as_uint(t.x), q1 = __float_as_uint(t.y);
-    const float s0 = (q0 & 1u) ? C.x : S.x, c0 = (q0 & 1u) ? S.x : C.x;
-    const float s1 = (q1 & 1u) ? C.y : S.y, c1 = (q1 & 1u) ? S.y : C.y;
-    s = make_float2(__uint_as_float(__float_as_uint(s0) ^ ((q0 & 2u) << 30)),
-                    __uint_as_float(__float_as_uint(s1) ^ ((q1 & 2u) << 30)));
-    c = make_float2(__uint_as_float(__float_as_uint(c0) ^ (((q0 + 1u) & 2u) << 30)),
-                    __uint_as_float(__float_as_uint(c1) ^ (((q1 + 1u) & 2u) << 30)));
-}
-
 // e^{i n 2 pi x} for n = 4g + j (j = 1..4), group by group: e^{i j 2 pi x}
 // from one sin/cos and products, times the group base e^{i 4g 2 pi x}, which
 // is the j = 4 harmonic of the group before (a recurrence of depth g + 2).
@@ -783,7 +744,7 @@ __global__ void __launch_bounds__(TdLaunch<K>::THREADS, TdLaunch<K>::MIN_CTAS)
     int stop = steps_of(m) - 1;  // the step at which member m takes its last step
     bool failed = false;
     int issued = -1;  // the last step whose product was issued
-    u32x4 r{0, 0, 0, 0};
+    float2 z1 = make_float2(0.f, 0.f), z2 = z1;  // the normals of the even step (.x) and the next (.y)
 
     for (int n = 0; n < N; ++n) {
         // sin and cos of 2 pi x of both coordinates, then the row of A: x2
@@ -814,9 +775,11 @@ __global__ void __launch_bounds__(TdLaunch<K>::THREADS, TdLaunch<K>::MIN_CTAS)
             }
         }
         // While the product runs: the Brownian increment and the x1 harmonics.
-        if ((n & 1) == 0) r = philox4x32_10(u32x4{(uint32_t)(n >> 1), pid, (uint32_t)stream, p.inst}, p.key0, p.key1);
-        float xi1, xi2;
-        box_muller<float>((n & 1) ? r.z : r.x, (n & 1) ? r.w : r.y, xi1, xi2);
+        if ((n & 1) == 0) {
+            const u32x4 r = philox4x32_10(u32x4{(uint32_t)(n >> 1), pid, (uint32_t)stream, p.inst}, p.key0, p.key1);
+            box_muller2(r.x, r.y, r.z, r.w, z1, z2);
+        }
+        const float xi1 = (n & 1) ? z1.y : z1.x, xi2 = (n & 1) ? z2.y : z2.x;
         HarmStream h1;
         h1.init(sx.x, cx.x);
         // (the full bound unless a test lowered it: the common path keeps the

@@ -8,6 +8,7 @@ from tests import _gpu
 
 pytestmark = pytest.mark.gpu
 pm = _gpu.pm
+torch = _gpu.torch
 
 
 @pytest.fixture(scope="module")
@@ -33,7 +34,10 @@ def test_normals_match_oracle(c, orc, fp64):
     out = np.empty((4096, 2))
     pm.pm_normals(c, seed, 3, 7, 11, 5, 4096, out, pm.PM_FP64 if fp64 else pm.PM_FP32)
     ref = orc.normals(seed, 3, 7, 11, 5, 4096)
-    tol = 1e-13 if fp64 else 4e-6  # float: log, sqrt and sincospi each within a few ulp
+    # float: log and sqrt within a few ulp, the angle's sin and cos from the
+    # quarter-turn series (absolute error below 1e-7)
+    tol = 1e-13 if fp64 else 4e-6
+    print("normals, fp64" if fp64 else "normals, float", "largest |GPU - oracle|", np.abs(out - ref).max())
     assert np.abs(out - ref).max() < tol
 
 
@@ -51,3 +55,32 @@ def test_velocity_matches_direct_sum(c, orc, K, fp64):
     scale = float((2 * np.pi * np.sqrt((modes ** 2).sum(1)) * np.abs(u.reshape(-1, 2)).sum(1)).sum()) if K else 1.0
     tol = (1e-13 if fp64 else 2e-6 * max(K, 1)) * scale
     assert np.abs(v - ref).max() <= tol, (np.abs(v - ref).max(), tol)
+
+
+def test_own_sincos_of_two_pi_x_meets_its_error_bound():
+    # The tensor-core kernels' sin/cos of 2 pi x (quarter-turn reduction, Taylor
+    # series in turns) against float64 on 2e6 random points of [0, 1), a dense
+    # grid, the quarter turns and points around them, and positions a little
+    # outside [0, 1): absolute error below 1e-7, relative below 2 ulp where
+    # |value| > 1e-6 (near the exact zeros the float64 reference itself is
+    # rounded at 1e-16 while the float result is exact or tiny).
+    c = _gpu.ctx()
+    try:
+        rng = np.random.default_rng(42)
+        q = np.float32([0.0, 0.125, 0.25, 0.375, 0.5, 0.625, 0.75, 0.875, 1.0])
+        x = np.concatenate([rng.random(2_000_000).astype(np.float32), np.linspace(0, 1, 100_001, dtype=np.float32),
+                            q, np.nextafter(q, np.float32(2)), np.nextafter(q, np.float32(-2)),
+                            np.float32([-0.3, -1e-3, 1.2, 2.7])])
+        xt = torch.from_numpy(x).cuda()
+        s = torch.empty_like(xt)
+        co = torch.empty_like(xt)
+        pm.pm_sincos_turns(c, xt, s, co)
+        s, co = s.cpu().numpy().astype(np.float64), co.cpu().numpy().astype(np.float64)
+        ts, tc = np.sin(2 * np.pi * x.astype(np.float64)), np.cos(2 * np.pi * x.astype(np.float64))
+        assert np.abs(s - ts).max() < 1e-7 and np.abs(co - tc).max() < 1e-7
+        for got, ref in ((s, ts), (co, tc)):
+            big = np.abs(ref) > 1e-6
+            ulp = np.spacing(np.abs(ref[big]).astype(np.float32)).astype(np.float64)
+            assert (np.abs(got[big] - ref[big]) / ulp).max() < 2.0
+    finally:
+        pm.pm_destroy(c)

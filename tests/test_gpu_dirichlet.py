@@ -49,10 +49,15 @@ def test_drift_field_paired_paths(c, orc):
     g, st = orc.dirichlet_paths(w.K, w.u, w.drift_scale, w.kappa, w.g, w.x, w.dt, w.max_steps, w.seed, npaths=w.M)
     d = (r["g"] - g).reshape(-1)
     assert abs(d.mean()) <= 5 * d.std(ddof=1) / np.sqrt(d.size)
-    # early exits happen before the paths decorrelate: those exit steps agree
-    early = st < 300
+    # Early exits happen before the paths decorrelate: those exit steps agree.
+    # At dt = 1e-3 float and FP64 paths through this flow stay together to
+    # t = 0.2 (200 steps); from there on a few per cent separate each 0.1.
+    for lo, hi in ((0, 100), (100, 200), (200, 300), (300, 600)):
+        m = (st >= lo) & (st < hi)
+        print(f"exit steps [{lo}, {hi}): {int(m.sum())} paths, {int((r['steps'][m] != st[m]).sum())} differ")
+    early = st < 200
     assert early.sum() > 20
-    assert np.mean(r["steps"][early] == st[early]) >= 0.99
+    assert np.mean(r["steps"][early] == st[early]) >= 0.999
 
 
 def test_start_outside_and_step_cap(c):
