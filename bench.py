@@ -16,6 +16,7 @@ scaling, no data-path collective); the time is the maximum over ranks.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -472,6 +473,9 @@ def run_aux(args):
     pm.pm_set_kernel_timing(ctx, 1)
     if args.workload == "dirichlet":
         w = inputs.dirichlet_disk_k10(M=args.M or 100_000)
+        if args.K:  # another wave-number bound: a prior draw of that size, the same points and steps
+            w = dataclasses.replace(w, name=f"dirichlet_disk_k{args.K}_50obs_M{w.M}_dt1e-4", K=args.K,
+                                    u=inputs.prior_field(args.K, 1002))
         fld = pm.Field(w.K, w.u)
         gd = pm.DirichletData(w.g.R, w.g.quad, w.g.f_const, w.g.a, w.g.b)
         x = torch.from_numpy(w.x).to(dev)
@@ -482,7 +486,7 @@ def run_aux(args):
             pm.pm_forward_dirichlet(ctx, fld, w.drift_scale, w.kappa, gd, x, len(w.x), w.M, w.dt, w.max_steps,
                                     w.seed, pm.PM_FP32 | (pm.PM_TENSOR if args.tensor else 0), mean, var)
         name, cfg = w.name, {"n_obs": len(w.x), "M": w.M, "dt": w.dt, "kappa": w.kappa, "drift_scale": w.drift_scale,
-                             "tensor_cores": bool(args.tensor)}
+                             "K": w.K, "tensor_cores": bool(args.tensor)}
     elif args.workload == "dirichlet_general":
         w, dfw = inputs.dirichlet_general_disk(M=args.M or 100_000)
         fld = pm.Field(w.K, w.u)
@@ -494,12 +498,17 @@ def run_aux(args):
 
         def step():
             pm.pm_forward_dirichlet_general(ctx, fld, w.drift_scale, gd, dfp, x, len(w.x), w.M, w.dt, w.max_steps,
-                                            w.seed, pm.PM_FP32, mean, var)
+                                            w.seed, pm.PM_FP32 | (pm.PM_TENSOR if args.tensor else 0), mean, var)
         name, cfg = w.name, {"n_obs": len(w.x), "M": w.M, "dt": w.dt, "drift_scale": w.drift_scale,
                              "sigma": "diag(0.3 + 0.15 x1, 0.3 - 0.1 x2), Milstein", "sources": 3,
-                             "kernel": "dirichlet_general_kernel<float,10> (FP32 pipes)"}
+                             "tensor_cores": bool(args.tensor),
+                             "kernel": ("dirichlet_tc_kernel<10, general> (velocity on the tensor cores)" if args.tensor
+                                        else "dirichlet_general_kernel<float,10> (FP32 pipes)")}
     else:
         ws = inputs.batched_instances(B=args.B, M=args.M or 4096)
+        if args.K:  # another wave-number bound: prior draws of that size
+            for b, w in enumerate(ws):
+                w.K, w.u = args.K, inputs.prior_field(args.K, 1003, counter=b)
         xs, ts, inst = [], [], []
         row = 0
         for w in ws:
@@ -516,14 +525,14 @@ def run_aux(args):
         g = next(w.g for w in ws if isinstance(w, inputs.DirichletWorkload))
         xt = torch.from_numpy(np.ascontiguousarray(np.concatenate(xs))).to(dev)
         tt = torch.from_numpy(np.ascontiguousarray(np.concatenate(ts))).to(dev)
-        batch = pm.Batch(10, inst, xt, tt, pm.Fourier(th.k, th.a, th.b), pm.DirichletData(g.R, g.quad, g.f_const, g.a, g.b))
+        batch = pm.Batch(ws[0].K, inst, xt, tt, pm.Fourier(th.k, th.a, th.b), pm.DirichletData(g.R, g.quad, g.f_const, g.a, g.b))
         mean = torch.empty(row, dtype=torch.float64, device=dev)
         var = torch.empty_like(mean)
 
         def step():
             pm.pm_forward_batched(ctx, batch, pm.PM_FP32 | (pm.PM_TENSOR if args.tensor else 0), mean, var)
-        name, cfg = f"batched_{args.B}x100obs_M{args.M or 4096}", {"B": args.B, "rows": row,
-                                                                    "tensor_cores": bool(args.tensor)}
+        name, cfg = (f"batched_{args.B}x100obs_M{args.M or 4096}" + (f"_k{args.K}" if args.K else ""),
+                     {"B": args.B, "rows": row, "K": ws[0].K, "tensor_cores": bool(args.tensor)})
     tuned = None
     if args.autotune and args.workload in ("dirichlet", "batched"):
         flags = pm.PM_FP32 | (pm.PM_TENSOR if args.tensor else 0)
@@ -534,7 +543,7 @@ def run_aux(args):
         else:
             pm.pm_autotune_batched(ctx, batch, flags)
             kind = pm.PM_TUNE_BATCHED
-        ctas, pairs = pm.pm_tuned_shape(ctx, kind, 10, pm.PM_TENSOR if args.tensor else 0)
+        ctas, pairs = pm.pm_tuned_shape(ctx, kind, args.K or 10, pm.PM_TENSOR if args.tensor else 0)
         tuned = {"ctas_per_sm": ctas, "refill_step_pairs": pairs if args.tensor else None}
     for _ in range(args.warmup):
         step()
@@ -978,6 +987,7 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=8, help="mcmc: steps of the plain sampler (configured sigma)")
     ap.add_argument("--da-steps", type=int, default=50, help="mcmc: delayed-acceptance steps (configured sigma)")
     ap.add_argument("--B", type=int, default=256, help="instances of the batched workload")
+    ap.add_argument("--K", type=int, default=0, help="dirichlet, batched: wave-number bound (default: the workload's 10)")
     ap.add_argument("--tensor", dest="tensor", action="store_true", default=True,
                     help="timedep: velocity sum on the tensor cores (PM_TENSOR; the default)")
     ap.add_argument("--no-tensor", dest="tensor", action="store_false",

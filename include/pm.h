@@ -21,8 +21,9 @@
  *   ordered by m, then n ascending; u = (a_0, b_0, a_1, b_1, ...) has 2|H_K| =
  *   (2K+1)^2 - 1 doubles.  v = (-d psi/dx2, d psi/dx1), i.e. the paper's
  *   k_perp = (-k_y, k_x) direction.  Supported K: 0..6, 8, 10, 12, 16; the
- *   time-dependent map with float paths also takes the wide bounds K = 24,
- *   32, 40, 48, 56, 64 (N_u = 2400 ... 16640; PM_EINVAL elsewhere).
+ *   time-dependent and Dirichlet maps with float paths also take the wide
+ *   bounds K = 24, 32, 40, 48, 56, 64 (N_u = 2400 ... 16640; PM_EINVAL
+ *   elsewhere).
  * Random numbers.  Step n of path i of observation j in instance b draws
  *   Philox4x32-10 (Salmon et al., SC'11) on counter {n/2, i, j, b} under key
  *   {seed & 0xffffffff, seed >> 32}; words (r0, r1) feed even n and (r2, r3)
@@ -81,7 +82,7 @@ extern "C" {
  * three-term hi/lo split of TF32 operands for K <= 8 and of FP16 operands,
  * with W scaled by a power of two, from K = 10: about float accuracy, results
  * differ from the FP32-pipe kernels by rounding); supported for K in
- * {4, 5, 6, 8, 10, 12, 16} (and the wide K for the time-dependent map),
+ * {4, 5, 6, 8, 10, 12, 16} (and the wide K for the time-dependent and Dirichlet maps),
  * other K run on the FP32 pipes. */
 #define PM_TENSOR 8u
 /* pm_forward_timedep: observations at bit-identical points x
@@ -260,8 +261,10 @@ int pm_forward_dirichlet(pm_ctx* ctx, const pm_field* field, double drift_scale,
  * integrated by the left-point rule dt sum_{m < n} f(X_m); the constant-
  * coefficient map is the case s0 = sqrt(2 kappa), s1 = 0, n_src = 0 (results
  * equal up to rounding).  Other arguments, outputs and return values as for
- * pm_forward_dirichlet; the kernels run on the FP32 pipes (float or double
- * paths; PM_TENSOR is ignored). */
+ * pm_forward_dirichlet, with K up to 16: float or double paths on the FP32 /
+ * FP64 pipes, or with PM_TENSOR (float paths, K in {4, 5, 6, 8, 10, 12, 16})
+ * the velocity sum on the tensor cores as in pm_forward_dirichlet, the
+ * diffusion, Milstein and forcing terms unchanged. */
 typedef struct pm_diffusion_forcing {
     double s0[2], s1[2];  /* sigma_i(x) = s0[i] + s1[i] x_i */
     int32_t milstein;     /* 1: Eq. millstein, 0: Eq. euler */

@@ -660,23 +660,53 @@ int pm_forward_timedep(pm_ctx* c, const pm_field* field, double kappa, const pm_
 namespace {
 bool dirichlet_uses_tc(int K, uint32_t flags)
 {
-    return !(flags & PM_FP64) && (flags & PM_TENSOR) && (K == 4 || K == 5 || K == 6 || K == 8 || K == 10 || K == 12 || K == 16);
+    return !(flags & PM_FP64) && (flags & PM_TENSOR) &&
+           (K == 4 || K == 5 || K == 6 || K == 8 || K == 10 || K == 12 || K == 16 || wide_K(K));
 }
 
-int dirichlet_resident(int K, bool fp64, bool use_tc)
+int dirichlet_resident(int K, bool fp64, bool use_tc, bool gen = false)
 {
     if (use_tc) {
         switch (K) {
-        case 4: return tdtc::dirichlet_tc_blocks_per_sm<4>();
-        case 5: return tdtc::dirichlet_tc_blocks_per_sm<5>();
-        case 6: return tdtc::dirichlet_tc_blocks_per_sm<6>();
-        case 8: return tdtc::dirichlet_tc_blocks_per_sm<8>();
-        case 10: return tdtc::dirichlet_tc_blocks_per_sm<10>();
-        case 12: return tdtc::dirichlet_tc_blocks_per_sm<12>();
-        default: return tdtc::dirichlet_tc_blocks_per_sm<16>();
+        case 4: return tdtc::dirichlet_tc_blocks_per_sm<4>(gen);
+        case 5: return tdtc::dirichlet_tc_blocks_per_sm<5>(gen);
+        case 6: return tdtc::dirichlet_tc_blocks_per_sm<6>(gen);
+        case 8: return tdtc::dirichlet_tc_blocks_per_sm<8>(gen);
+        case 10: return tdtc::dirichlet_tc_blocks_per_sm<10>(gen);
+        case 12: return tdtc::dirichlet_tc_blocks_per_sm<12>(gen);
+        case 24: return tdtc::dirichlet_tc_blocks_per_sm<24>(gen);
+        case 32: return tdtc::dirichlet_tc_blocks_per_sm<32>(gen);
+        case 40: return tdtc::dirichlet_tc_blocks_per_sm<40>(gen);
+        case 48: return tdtc::dirichlet_tc_blocks_per_sm<48>(gen);
+        case 56: return tdtc::dirichlet_tc_blocks_per_sm<56>(gen);
+        case 64: return tdtc::dirichlet_tc_blocks_per_sm<64>(gen);
+        default: return tdtc::dirichlet_tc_blocks_per_sm<16>(gen);
         }
     }
+    switch (K) {
+    case 24: return dirichlet_blocks_per_sm<float, 24>();
+    case 32: return dirichlet_blocks_per_sm<float, 32>();
+    case 40: return dirichlet_blocks_per_sm<float, 40>();
+    case 48: return dirichlet_blocks_per_sm<float, 48>();
+    case 56: return dirichlet_blocks_per_sm<float, 56>();
+    case 64: return dirichlet_blocks_per_sm<float, 64>();
+    default: break;
+    }
     return fp64 ? dispatch_dirichlet_occupancy<double>(K) : dispatch_dirichlet_occupancy<float>(K);
+}
+
+// The wide-K FP32-pipe Dirichlet launch (table in shared memory).
+cudaError_t launch_dirichlet_wide(int K, const DirichletLaunch& L, cudaStream_t s)
+{
+    switch (K) {
+    case 24: return launch_dirichlet<float, 24>(L, s);
+    case 32: return launch_dirichlet<float, 32>(L, s);
+    case 40: return launch_dirichlet<float, 40>(L, s);
+    case 48: return launch_dirichlet<float, 48>(L, s);
+    case 56: return launch_dirichlet<float, 56>(L, s);
+    case 64: return launch_dirichlet<float, 64>(L, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 }  // namespace
 
@@ -717,8 +747,10 @@ int dirichlet_call(pm_ctx* c, const pm_field* field, double drift_scale, double 
                    int64_t* n_unexited, const pm_path_opts* opts)
 {
     if (!c) return fail(PM_EINVAL, "ctx is NULL");
-    int rc = check_field(field);
+    int rc = check_field(field, !gen);
     if (rc) return rc;
+    const bool wide = wide_K(field->K);
+    if (wide && (flags & PM_FP64)) return fail(PM_EINVAL, "K=%d runs with float paths only", field->K);
     if (!gd) return fail(PM_EINVAL, "boundary data is NULL");
     if (!(std::isfinite(gd->R) && gd->R > 0)) return fail(PM_EINVAL, "R must be finite and > 0");
     if (!std::isfinite(gd->quad) || !std::isfinite(gd->f_const)) return fail(PM_EINVAL, "quad and f_const must be finite");
@@ -771,8 +803,9 @@ int dirichlet_call(pm_ctx* c, const pm_field* field, double drift_scale, double 
     }
 
     auto layout = [&](Bump& b) {
-        struct P { unsigned long long* ctr; double *g, *x, *mean, *var, *xo; int32_t* es; double2* rpart; int32_t* order; } p{};
+        struct P { unsigned long long* ctr; double *g, *x, *mean, *var, *xo; int32_t* es; double2* rpart; int32_t* order; float* tab; } p{};
         p.ctr = b.take<unsigned long long>(4);  // next path, unexited, steps, tensor-core error flag
+        p.tab = wide ? b.take<float>((size_t)wide_table_floats(field->K)) : nullptr;
         p.order = order_obs ? b.take<int32_t>((size_t)n_obs) : nullptr;
         p.rpart = b.take<double2>((size_t)(n_obs * (int64_t)reduce_path_chunks(M)));
         p.g = (dev && g_out) ? nullptr : b.take<double>((size_t)total);
@@ -841,10 +874,13 @@ int dirichlet_call(pm_ctx* c, const pm_field* field, double drift_scale, double 
     L.key0 = (uint32_t)(seed & 0xffffffffu);
     L.key1 = (uint32_t)(seed >> 32);
     L.gen = gen;
+    L.table_dev = W.tab;
     const int Kd = field->K;
-    const bool use_tc = !gen && dirichlet_uses_tc(Kd, flags);
+    const bool use_tc = dirichlet_uses_tc(Kd, flags);
     int per_sm;
-    if (gen) {
+    if (gen && use_tc) {
+        per_sm = dirichlet_resident(Kd, false, true, true);
+    } else if (gen) {
         per_sm = fp64 ? dispatch_dirichlet_general_occupancy<double>(Kd) : dispatch_dirichlet_general_occupancy<float>(Kd);
     } else {
         per_sm = dirichlet_resident(Kd, fp64, use_tc);
@@ -860,9 +896,9 @@ int dirichlet_call(pm_ctx* c, const pm_field* field, double drift_scale, double 
     if (c->timing) PM_CUDA(cudaEventRecord(c->ev0, c->stream), "event");
     cudaError_t e;
     unsigned* tc_err = (unsigned*)(W.ctr + 3);
-    if (gen) {
+    if (gen && !use_tc) {
         e = fp64 ? dispatch_dirichlet_general<double>(Kd, L, c->stream) : dispatch_dirichlet_general<float>(Kd, L, c->stream);
-    } else if (use_tc) {
+    } else if (use_tc) {  // L.gen selects the general map's variant
         switch (Kd) {
         case 4: e = tdtc::launch_dirichlet_tc<4>(L, tc_err, c->stream); break;
         case 5: e = tdtc::launch_dirichlet_tc<5>(L, tc_err, c->stream); break;
@@ -870,8 +906,16 @@ int dirichlet_call(pm_ctx* c, const pm_field* field, double drift_scale, double 
         case 8: e = tdtc::launch_dirichlet_tc<8>(L, tc_err, c->stream); break;
         case 10: e = tdtc::launch_dirichlet_tc<10>(L, tc_err, c->stream); break;
         case 12: e = tdtc::launch_dirichlet_tc<12>(L, tc_err, c->stream); break;
+        case 24: e = tdtc::launch_dirichlet_tc<24>(L, tc_err, c->stream); break;
+        case 32: e = tdtc::launch_dirichlet_tc<32>(L, tc_err, c->stream); break;
+        case 40: e = tdtc::launch_dirichlet_tc<40>(L, tc_err, c->stream); break;
+        case 48: e = tdtc::launch_dirichlet_tc<48>(L, tc_err, c->stream); break;
+        case 56: e = tdtc::launch_dirichlet_tc<56>(L, tc_err, c->stream); break;
+        case 64: e = tdtc::launch_dirichlet_tc<64>(L, tc_err, c->stream); break;
         default: e = tdtc::launch_dirichlet_tc<16>(L, tc_err, c->stream); break;
         }
+    } else if (wide) {
+        e = launch_dirichlet_wide(Kd, L, c->stream);
     } else {
         e = fp64 ? dispatch_dirichlet<double>(Kd, L, c->stream) : dispatch_dirichlet<float>(Kd, L, c->stream);
     }
@@ -960,7 +1004,7 @@ int pm_forward_dirichlet_general(pm_ctx* c, const pm_field* field, double drift_
         G.c[2 * q + 1] = df->c[2 * q + 1];
         G.F[q] = df->F[q];
     }
-    return dirichlet_call(c, field, drift_scale, 0.0, gd, &G, x, n_obs, M, dt, max_steps, seed, flags & ~PM_TENSOR,
+    return dirichlet_call(c, field, drift_scale, 0.0, gd, &G, x, n_obs, M, dt, max_steps, seed, flags,
                           mean, var, exit_step, n_unexited, opts);
 }
 

@@ -33,6 +33,7 @@ cudaError_t launch_batched_tc_K(int K, const BatchKernelParams& p, int grid, cud
     switch (K) {
 #define PM_CASE(k) case k: return tdtc::launch_batched_tc<k>(p, grid, s);
         PM_CASE(4) PM_CASE(5) PM_CASE(6) PM_CASE(8) PM_CASE(10) PM_CASE(12) PM_CASE(16)
+        PM_CASE(24) PM_CASE(32) PM_CASE(40) PM_CASE(48) PM_CASE(56) PM_CASE(64)
 #undef PM_CASE
     }
     return cudaErrorInvalidValue;
@@ -43,12 +44,13 @@ int blocks_per_sm_tc_K(int K)
     switch (K) {
 #define PM_CASE(k) case k: return tdtc::batched_tc_blocks_per_sm<k>();
         PM_CASE(4) PM_CASE(5) PM_CASE(6) PM_CASE(8) PM_CASE(10) PM_CASE(12) PM_CASE(16)
+        PM_CASE(24) PM_CASE(32) PM_CASE(40) PM_CASE(48) PM_CASE(56) PM_CASE(64)
 #undef PM_CASE
     }
     return 1;
 }
 
-bool tc_supported(int K) { return K == 4 || K == 5 || K == 6 || K == 8 || K == 10 || K == 12 || K == 16; }
+bool tc_supported(int K) { return K == 4 || K == 5 || K == 6 || K == 8 || K == 10 || K == 12 || K == 16 || wide_K(K); }
 
 int blocks_per_sm_K(int K)
 {
@@ -87,7 +89,12 @@ extern "C" int pm_forward_batched(pm_ctx* c, const pm_batch* bt, uint32_t flags,
     if (!bt) return fail(PM_EINVAL, "batch is NULL");
     if (flags & PM_FP64) return fail(PM_EINVAL, "the batched map runs float paths only (PM_FP64 unsupported)");
     const int K = bt->K, B = bt->B;
-    if (!supported_K(K)) return fail(PM_EINVAL, "K=%d is not one of the compiled bounds 0..6, 8, 10, 12, 16", K);
+    // The wide bounds run on the tensor cores only: the FP32-pipe kernel keeps
+    // one velocity table per warp in shared memory, too large above K = 16.
+    if (wide_K(K) && !(flags & PM_TENSOR))
+        return fail(PM_EINVAL, "K=%d: the batched map runs the wide bounds with PM_TENSOR only", K);
+    if (!supported_K(K) && !wide_K(K))
+        return fail(PM_EINVAL, "K=%d is not one of the compiled bounds 0..6, 8, 10, 12, 16 (24, 32, 40, 48, 56, 64 with PM_TENSOR)", K);
     if (B < 1 || B > 65535) return fail(PM_EINVAL, "B must be in [1, 65535]");
     if (!bt->inst) return fail(PM_EINVAL, "instance array is NULL");
     if (bt->n_rows < 1 || bt->n_rows > ((int64_t)1 << 31)) return fail(PM_EINVAL, "n_rows out of range");

@@ -11,27 +11,29 @@
 // rebuilds its tiles.  Results are stored per path, so the estimates do not
 // depend on which CTA ran which path.
 #pragma once
+#include <type_traits>
 #include "pm_batched.cuh"
 #include "pm_timedep_tc.cuh"
 
 namespace pm {
 namespace tdtc {
 
-// Entry W[k][nc] of the coefficient matrix (unfolded shape) from the
-// product-basis table tab[(m (K+1) + n) 8 + q] (e0..e3, f0..f3): A column k
-// holds S2_n (k = 2(n-1)), C2_n (k = 2(n-1)+1) or the constant 1 (k = 2K);
-// accumulator column pcol(m, j) holds P1c, P1s, P2c, P2s (j = 0..3) of m and
-// column p0col(K) P(0) (the layout of build_W).
-template <int K>
+// Entry W[k][nc] of the coefficient matrix from the product-basis table
+// tab[(m (K+1) + n) 8 + q] (e0..e3, f0..f3): A column k holds S2_n
+// (k = 2(n-1)), C2_n (k = 2(n-1)+1) or, unfolded, the constant 1 (k = 2K);
+// accumulator column pcol(m, j) holds P1c, P1s, P2c, P2s (j = 0..3) of m and,
+// unfolded, column p0col(K) P(0) (the layout of build_W).  The folded shape
+// leaves the constant column and P(0) to the FP32 pipes.
+template <int K, bool F = false>
 __device__ __forceinline__ float w_entry(const float* tab, int nc, int k)
 {
     int n = 0, type = 0;  // type 0: S2_n, 1: C2_n, 2: constant
     if (k < 2 * K) { n = k / 2 + 1; type = k & 1; }
-    else if (k == 2 * K) { type = 2; }
+    else if (!F && k == 2 * K) { type = 2; }
     else return 0.f;
     auto T = [&](int m, int nn, int q) { return tab[(m * (K + 1) + nn) * 8 + q]; };
-    if (nc == p0col(K)) return type == 0 ? T(0, n, 0) : type == 1 ? T(0, n, 1) : 0.f;  // P(0)
-    if (nc > p0col(K)) return 0.f;
+    if (!F && nc == p0col(K)) return type == 0 ? T(0, n, 0) : type == 1 ? T(0, n, 1) : 0.f;  // P(0)
+    if (nc >= p0col(K)) return 0.f;
     const int r = nc % 8, j = r / 2, m = 2 * (nc / 8) + 1 + (r & 1);  // inverse of pcol
     if (m > K) return 0.f;
     if (j == 0) return type == 0 ? T(m, n, 0) : type == 1 ? T(m, n, 1) : 0.f;          // P1c
@@ -40,14 +42,20 @@ __device__ __forceinline__ float w_entry(const float* tab, int nc, int k)
     return type == 1 ? T(m, n, 6) : type == 0 ? T(m, n, 7) : T(m, 0, 6);               // P2s
 }
 
+// Wide K: the folded shape where the time-dependent kernel folds (N within
+// one MMA at K = 64), as in the Dirichlet kernel.
 template <int K>
-using BatShape = Shape<K, false, half_of<K>()>;
+using BatShape = Shape<K, (K > kMaxUnrolledK) && fold_of<K>(), half_of<K>()>;
 
 template <int K>
 __global__ void __launch_bounds__(128, BatShape<K>::MIN_CTAS6) batched_tc_kernel(const __grid_constant__ BatchKernelParams p)
 {
     using S = BatShape<K>;
+    constexpr bool F = S::FOLD;
     constexpr bool H = S::HALF;
+    // x1 harmonics: all of them during the product up to the unrolled bound,
+    // streamed after the wait above it (registers).
+    using Harm1 = std::conditional_t<(K > kMaxUnrolledK), HarmStream, HarmArray<K>>;
     constexpr int TS = table_size(K);
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
@@ -92,6 +100,10 @@ __global__ void __launch_bounds__(128, BatShape<K>::MIN_CTAS6) batched_tc_kernel
     // step loop reads every step stay in registers.
     __shared__ BatchInstDev sI;
     __shared__ int s_wmax;  // FP16 operands: bits of max |table entry| of the instance
+    // Folded shape: the instance's m = 0 terms of v1 and (scaled with W) n = 0
+    // terms of v2, in the layout of Params<K>::T0 and N0.
+    __shared__ __align__(8) float sT0[F ? 2 * K : 2];
+    __shared__ __align__(8) float sN0[F ? 2 * K : 2];
     float inv_s = 1.f;      // FP16 operands: 1 / (power-of-two scale of W)
     int kind = 0;
     uint32_t stream = 0, key0 = 0, key1 = 0;
@@ -184,9 +196,14 @@ __global__ void __launch_bounds__(128, BatShape<K>::MIN_CTAS6) batched_tc_kernel
             const float* tab = p.tables + (size_t)b * TS;
             float sc = 1.f;
             if constexpr (H) {
-                // the scale of W: every nonzero table entry is an entry of W
+                // the scale of W: unfolded, every nonzero table entry is an
+                // entry of W; folded, all but the m = 0 row and the n = 0
+                // column (T0 and N0), as in scale_W_host
                 float wm = 0.f;
-                for (int q = tid; q < TS; q += 128) wm = fmaxf(wm, fabsf(tab[q]));
+                for (int q = tid; q < TS; q += 128) {
+                    const int mn = q >> 3, m = mn / (K + 1), n = mn - m * (K + 1);
+                    if (!F || (m > 0 && n > 0)) wm = fmaxf(wm, fabsf(tab[q]));
+                }
                 atomicMax(&s_wmax, __float_as_int(wm));
                 __syncthreads();
                 const int e = w_scale_exp(__int_as_float(s_wmax));
@@ -195,7 +212,7 @@ __global__ void __launch_bounds__(128, BatShape<K>::MIN_CTAS6) batched_tc_kernel
             }
             for (int q = tid; q < S::NP * S::WS; q += 128) {
                 const int nc = q / S::WS, k = q - nc * S::WS;
-                const float w = w_entry<K>(tab, nc, k) * sc;
+                const float w = w_entry<K, F>(tab, nc, k) * sc;
                 if constexpr (H) {
                     const __half hi = __float2half_rn(w);
                     const __half lo = __float2half_rn(w - __half2float(hi));
@@ -207,6 +224,14 @@ __global__ void __launch_bounds__(128, BatShape<K>::MIN_CTAS6) batched_tc_kernel
                     const uint32_t off = tile_off<S::KC>(nc, k >> 2) + 4u * (uint32_t)(k & 3);
                     *reinterpret_cast<float*>(B_hi + off) = hi;
                     *reinterpret_cast<float*>(B_lo + off) = to_tf32(w - hi);
+                }
+            }
+            if constexpr (F) {
+                for (int q = tid; q < K; q += 128) {
+                    sT0[q] = tab[(q + 1) * 8 + 0];                    // m = 0, n = q + 1: multiplies S2_n
+                    sT0[K + q] = tab[(q + 1) * 8 + 1];                // multiplies C2_n
+                    sN0[q] = tab[(q + 1) * (K + 1) * 8 + 4] * sc;     // n = 0 term of P2c(m = q + 1)
+                    sN0[K + q] = tab[(q + 1) * (K + 1) * 8 + 6] * sc; // n = 0 term of P2s(m = q + 1)
                 }
             }
             __syncthreads();
@@ -224,24 +249,24 @@ __global__ void __launch_bounds__(128, BatShape<K>::MIN_CTAS6) batched_tc_kernel
             for (int half = 0; half < 2; ++half) {
                 float2 sx, cx;
                 sincos_turns2(make_float2(X1.val(), X2.val()), sx, cx);
-                write_row_stream<K, false, H>(sb + row, (uint32_t)S::A_BYTES, sx.y, cx.y, nullptr);
+                const float p0 = write_row_stream<K, F, H>(sb + row, (uint32_t)S::A_BYTES, sx.y, cx.y, sT0);
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 // One barrier per step: the rows are in place, and a wait that gave
                 // up in the previous step (any thread) stops the whole CTA.
                 if (__syncthreads_or(failed)) { stop = true; break; }
-                if (tid == 0) issue_step_mma<K, false, H>(tmem, sb, bar_a);
+                if (tid == 0) issue_step_mma<K, F, H>(tmem, sb, bar_a);
                 // While the product runs: the Brownian increment and the x1 harmonics.
                 if (half == 0) box_muller2(r.x, r.y, r.z, r.w, z1, z2);
                 const float xi1 = half ? z1.y : z1.x, xi2 = half ? z2.y : z2.x;
-                HarmArray<K> h1;  // during the product
+                Harm1 h1;  // during the product (HarmArray)
                 h1.init(sx.x, cx.x);
                 issued_any = true;
                 failed = !tc::mbar_wait(bar_a, phase);
                 phase ^= 1u;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 float v1, v2;
-                velocity_stream<K, false, H>(t_row, h1, nullptr, 0.f, inv_s, v1, v2);
+                velocity_stream<K, F, H>(t_row, h1, sN0, p0, inv_s, v1, v2);
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 if (pid < 0) continue;
                 if (kind == 0) {

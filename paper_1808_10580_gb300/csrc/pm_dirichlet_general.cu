@@ -1,59 +1,21 @@
 // pm_dirichlet_general.cu -- Algorithm 2 in the disk |x| < R with a general
-// forcing and a state-dependent diffusion (Theorem 3.2 with f(x) and sigma(x)).
-//
-//   dX = -d v(X) ds + sigma(X) dW,  sigma(x) = diag(s0_1 + s1_1 x_1, s0_2 + s1_2 x_2):
-// each coordinate has its own Brownian motion and a diffusion coefficient of
-// its own coordinate, so the Milstein scheme (Eq. millstein) applies
-// coordinate by coordinate,
-//   X_i <- X_i - d v_i dt + sigma_i sqrt(dt) xi_i + (1/2) sigma_i s1_i (xi_i^2 - 1) dt,
-// sigma_i at the step's start point (without the last term: Euler-Maruyama,
-// Eq. euler).  The forcing f(x) = f_const + sum_q F_q exp(-w |x - c_q|^2) is
-// integrated by the left-point rule, dt sum_{m < n} f(X_m), in a compensated
-// sum (float paths) or in double.  Everything else -- the product-basis
-// velocity, the random numbers, the persistent lanes that take a new path as
-// soon as theirs exits, the exit test, the boundary data, the per-path values
-// reduced in path order -- is that of the constant-coefficient disk kernel
-// (pm_kernels.cuh).  FP32-pipe kernels only (float and double paths).
+// forcing and a state-dependent diffusion (Theorem 3.2 with f(x) and
+// sigma(x)) on the FP32 / FP64 pipes; the step's terms (the Milstein or
+// Euler-Maruyama increment per coordinate, the left-point forcing sum) are in
+// pm_general_step.cuh.  Everything else -- the product-basis velocity, the
+// random numbers, the persistent lanes that take a new path as soon as theirs
+// exits, the exit test, the boundary data, the per-path values reduced in path
+// order -- is that of the constant-coefficient disk kernel (pm_kernels.cuh).
+#include "pm_general_step.cuh"
 #include "pm_kernels.cuh"
 
 namespace pm {
 namespace {
 
-template <typename Real>
-struct ForcingSum;
-template <>
-struct ForcingSum<float> {
-    float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void add(float v)
-    {
-        const float y = v - c;
-        const float t = s + y;
-        c = (t - s) - y;
-        s = t;
-    }
-    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
-};
-template <>
-struct ForcingSum<double> {
-    double s = 0.0;
-    __device__ __forceinline__ void add(double v) { s += v; }
-    __device__ __forceinline__ double value() const { return s; }
-};
-
-__device__ __forceinline__ float exp_g(float a) { return expf(a); }
-__device__ __forceinline__ double exp_g(double a) { return exp(a); }
-
 template <typename Real, int K>
 struct GeneralParams {
     DirichletParams<Real, K> d;  // field, boundary data, paths, outputs (d.f_const: the constant part of f)
-    Real s0[2], s1[2];           // sigma_i(x) = s0[i] + s1[i] x_i
-    Real sqdt;                   // sqrt(dt)
-    Real half_dt_m;              // dt / 2 with the Milstein term, else 0
-    Real w;
-    Real fc;                     // f_const in the path's precision
-    Real c[2 * kMaxSources];
-    Real F[kMaxSources];
-    int32_t n_src;
+    GeneralCoef<Real> gc;
     double drift_scale;          // double paths: the drift factor and the step's
     double s0d[2], s1d[2];       // coefficients, applied in the plain sequential
     double sdt;                  // order of the scheme's statement
@@ -70,29 +32,6 @@ __device__ __forceinline__ double update_d(double X, double v, double d, double 
     if (milstein)
         Xn = __dadd_rn(Xn, __dmul_rn(__dmul_rn(__dmul_rn(__dmul_rn(0.5, sig), s1), __dsub_rn(__dmul_rn(xi, xi), 1.0)), dt));
     return Xn;
-}
-
-// f(X) = f_const + sum_q F_q exp(-w |X - c_q|^2) at the step's start point.
-template <typename Real, int K>
-__device__ __forceinline__ Real forcing(const GeneralParams<Real, K>& p, Real x1, Real x2)
-{
-    Real f = p.fc;
-    for (int q = 0; q < p.n_src; ++q) {
-        const Real a = x1 - p.c[2 * q], b = x2 - p.c[2 * q + 1];
-        f += p.F[q] * exp_g(-p.w * (a * a + b * b));
-    }
-    return f;
-}
-
-// One coordinate's increment: -d v dt + sigma sqrt(dt) xi (+ Milstein).
-template <typename Real>
-__device__ __forceinline__ Real increment(Real x, Real v, Real drift_dt, Real s0, Real s1, Real sqdt, Real half_dt_m,
-                                          Real xi)
-{
-    const Real sig = s0 + s1 * x;
-    Real d = -v * drift_dt + (sig * sqdt) * xi;
-    d += ((sig * s1) * half_dt_m) * (xi * xi - (Real)1);
-    return d;
 }
 
 template <typename Real, int K>
@@ -176,16 +115,16 @@ __global__ void __launch_bounds__(kDirichletBlock)
             Real xi1, xi2;
             box_muller<Real>(half ? r.z : r.x, half ? r.w : r.y, xi1, xi2);
             const Real x1v = X1.val(), x2v = X2.val();
-            fs.add(forcing(gp, x1v, x2v));
+            fs.add(gp.gc.forcing(x1v, x2v));
             Real x1[1] = {x1v}, x2[1] = {x2v}, v1[1], v2[1];
             velocity<Real, K, 1>(tab, x1, x2, v1, v2);
             if constexpr (sizeof(Real) == 8) {
-                const bool mil = gp.half_dt_m != (Real)0;
+                const bool mil = gp.gc.half_dt_m != (Real)0;
                 X1.hi = update_d(X1.hi, v1[0], gp.drift_scale, p.dt, gp.s0d[0], gp.s1d[0], gp.sdt, mil, xi1);
                 X2.hi = update_d(X2.hi, v2[0], gp.drift_scale, p.dt, gp.s0d[1], gp.s1d[1], gp.sdt, mil, xi2);
             } else {
-                X1.add(increment<Real>(x1v, v1[0], p.drift_dt, gp.s0[0], gp.s1[0], gp.sqdt, gp.half_dt_m, xi1));
-                X2.add(increment<Real>(x2v, v2[0], p.drift_dt, gp.s0[1], gp.s1[1], gp.sqdt, gp.half_dt_m, xi2));
+                X1.add(gp.gc.increment(0, x1v, v1[0], p.drift_dt, xi1));
+                X2.add(gp.gc.increment(1, x2v, v2[0], p.drift_dt, xi2));
             }
             ++n;
             const bool exited = radial_excess(X1, X2, p.R2hi, p.R2lo) >= (Real)0;
@@ -240,26 +179,12 @@ cudaError_t launch_dirichlet_general(const DirichletLaunch& L, cudaStream_t stre
     p.inst = L.inst;
     p.key0 = L.key0;
     p.key1 = L.key1;
-    for (int k = 0; k < 2; ++k) {
-        gp.s0[k] = (Real)G.s0[k];
-        gp.s1[k] = (Real)G.s1[k];
-    }
-    gp.sqdt = (Real)std::sqrt(L.dt);
+    gp.gc.set(G, L.dt, L.f_const);
     gp.sdt = std::sqrt(L.dt);
     gp.drift_scale = L.drift_scale;
     for (int k = 0; k < 2; ++k) {
         gp.s0d[k] = G.s0[k];
         gp.s1d[k] = G.s1[k];
-    }
-    gp.half_dt_m = G.milstein ? (Real)(0.5 * L.dt) : (Real)0;
-    gp.w = (Real)G.w;
-    gp.fc = (Real)L.f_const;
-    gp.n_src = G.n_src;
-    for (int q = 0; q < kMaxSources; ++q) {
-        const bool on = q < G.n_src;
-        gp.c[2 * q] = on ? (Real)G.c[2 * q] : (Real)0;
-        gp.c[2 * q + 1] = on ? (Real)G.c[2 * q + 1] : (Real)0;
-        gp.F[q] = on ? (Real)G.F[q] : (Real)0;
     }
     dirichlet_general_kernel<Real, K><<<L.grid, kDirichletBlock, 0, stream>>>(gp);
     return cudaGetLastError();

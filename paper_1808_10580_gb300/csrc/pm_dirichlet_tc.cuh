@@ -9,17 +9,28 @@
 // result is ignored).  The CTA leaves when every lane has found the path
 // counter exhausted.
 #pragma once
+#include <type_traits>
+#include "pm_general_step.cuh"
 #include "pm_timedep_tc.cuh"
 
 namespace pm {
 namespace tdtc {
 
+// Wide K (above the unrolled bound) takes the time-dependent kernel's folded
+// shape where that kernel folds (it keeps N within one MMA at K = 64), and
+// reads W from global memory.
 template <int K>
-using DirShape = Shape<K, false, half_of<K>()>;
+using DirShape = Shape<K, (K > kMaxUnrolledK) && fold_of<K>(), half_of<K>()>;
 
 template <int K>
 struct DirParams {
-    float W[DirShape<K>::NP * DirShape<K>::WS];
+    // W^T (see build_W): in the parameter bank, or at Wg.
+    float W[DirShape<K>::W_PARAM ? DirShape<K>::NP * DirShape<K>::WS : 1];
+    const float* Wg;
+    // Folded shape: the m = 0 terms of v1 and the n = 0 terms of v2 on the
+    // FP32 pipes (the layout of Params<K>::T0 and N0).
+    alignas(8) float T0[2 * K + 2];
+    alignas(8) float N0[2 * K + 2];
     float inv_s;  // FP16 operands: 1 / (power-of-two scale of W)
     double ga[kMaxBoundary];
     double gb[kMaxBoundary];
@@ -39,11 +50,13 @@ struct DirParams {
     unsigned* err;
     uint32_t wait_limit;  // polls of the per-step MMA wait (tc::kWaitLimit unless a test lowers it)
     int32_t refill_pairs; // pairs of Euler steps between lane refills (a launch shape: results do not depend on it)
+    GeneralCoef<float> gc;  // the general map (kernel's GEN): sigma(x), Milstein, forcing
 };
 
+// integral: the path's int f (f_const n dt, or the general map's left-point sum)
 template <int K>
 __device__ __forceinline__ void dir_finish(const DirParams<K>& p, int64_t pid, bool exited, int64_t n,
-                                           const Coord<float>& X1, const Coord<float>& X2)
+                                           const Coord<float>& X1, const Coord<float>& X2, double integral)
 {
     double g = 0.0;
     if (exited) {
@@ -58,7 +71,7 @@ __device__ __forceinline__ void dir_finish(const DirParams<K>& p, int64_t pid, b
             cm = cn;
             g += p.ga[m - 1] * cm + p.gb[m - 1] * sm;
         }
-        g -= p.f_const * ((double)n * p.dt);
+        g -= integral;
     } else {
         atomicAdd(p.n_unexited, 1ull);
     }
@@ -67,11 +80,18 @@ __device__ __forceinline__ void dir_finish(const DirParams<K>& p, int64_t pid, b
     if (p.x_out) { p.x_out[2 * pid] = X1.full(); p.x_out[2 * pid + 1] = X2.full(); }
 }
 
-template <int K>
+// GEN: the general map (state-dependent diffusion with the Milstein term,
+// Gaussian-source forcing; pm_general_step.cuh) instead of the constant
+// diffusion and forcing; the velocity sum is the same.
+template <int K, bool GEN = false>
 __global__ void __launch_bounds__(128, DirShape<K>::MIN_CTAS6) dirichlet_tc_kernel(const __grid_constant__ DirParams<K> p)
 {
     using S = DirShape<K>;
+    constexpr bool F = S::FOLD;
     constexpr bool H = S::HALF;
+    // x1 harmonics: all of them during the product up to the unrolled bound,
+    // streamed after the wait above it (registers).
+    using Harm1 = std::conditional_t<(K > kMaxUnrolledK), HarmStream, HarmArray<K>>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     uint8_t* A_hi = smem;
@@ -84,7 +104,8 @@ __global__ void __launch_bounds__(128, DirShape<K>::MIN_CTAS6) dirichlet_tc_kern
     const unsigned full = 0xffffffffu;
     const uint32_t bar_a = tc::smem_u32(bar);
 
-    stage_B<S>(B_hi, B_lo, tid, [&](int q) { return p.W[q]; });
+    if constexpr (S::W_PARAM) stage_B<S>(B_hi, B_lo, tid, [&](int q) { return p.W[q]; });
+    else stage_B<S>(B_hi, B_lo, tid, [&](int q) { return __ldg(p.Wg + q); });
     for (int c = 0; c < S::KC; ++c) {
         *reinterpret_cast<float4*>(A_hi + tile_off<S::KC>(tid, c)) = make_float4(0.f, 0.f, 0.f, 0.f);
         *reinterpret_cast<float4*>(A_lo + tile_off<S::KC>(tid, c)) = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -119,6 +140,7 @@ __global__ void __launch_bounds__(128, DirShape<K>::MIN_CTAS6) dirichlet_tc_kern
     Coord<float> X1, X2;
     X1.set(0.0);
     X2.set(0.0);
+    ForcingSum<float> fs;  // the general map's forcing sum (GEN)
 
     for (;;) {
         // Refill (per warp).
@@ -140,8 +162,9 @@ __global__ void __launch_bounds__(128, DirShape<K>::MIN_CTAS6) dirichlet_tc_kern
                     X1.set(p.x[2 * (int64_t)j]);
                     X2.set(p.x[2 * (int64_t)j + 1]);
                     n = 0;
+                    fs = ForcingSum<float>{};
                     if (radial_excess(X1, X2, p.R2hi, p.R2lo) >= 0.f) {  // starts outside
-                        dir_finish(p, pid, true, 0, X1, X2);
+                        dir_finish(p, pid, true, 0, X1, X2, 0.0);
                         pid = -1;
                     }
                 } else {
@@ -165,17 +188,17 @@ __global__ void __launch_bounds__(128, DirShape<K>::MIN_CTAS6) dirichlet_tc_kern
             for (int half = 0; half < 2; ++half) {
                 float2 sx, cx;
                 sincos_turns2(make_float2(X1.val(), X2.val()), sx, cx);
-                write_row_stream<K, false, H>(sb + row, (uint32_t)S::A_BYTES, sx.y, cx.y, nullptr);
+                const float p0 = write_row_stream<K, F, H>(sb + row, (uint32_t)S::A_BYTES, sx.y, cx.y, p.T0);
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 // One barrier per step: the rows are in place, and a wait that gave
                 // up in the previous step (any thread) stops the whole CTA.
                 if (__syncthreads_or(failed)) { stop = true; break; }
-                if (tid == 0) issue_step_mma<K, false, H>(tmem, sb, bar_a);
+                if (tid == 0) issue_step_mma<K, F, H>(tmem, sb, bar_a);
                 // While the product runs: the Brownian increment and the x1 harmonics.
                 if (half == 0) box_muller2(r.x, r.y, r.z, r.w, z1, z2);
                 const float xi1 = half ? z1.y : z1.x, xi2 = half ? z2.y : z2.x;
-                HarmArray<K> h1;  // during the product
+                Harm1 h1;  // during the product (HarmArray)
                 h1.init(sx.x, cx.x);
                 issued_any = true;
                 failed = p.wait_limit >= tc::kWaitLimit ? !tc::mbar_wait(bar_a, phase)
@@ -183,14 +206,22 @@ __global__ void __launch_bounds__(128, DirShape<K>::MIN_CTAS6) dirichlet_tc_kern
                 phase ^= 1u;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 float v1, v2;
-                velocity_stream<K, false, H>(t_row, h1, nullptr, 0.f, p.inv_s, v1, v2);
+                velocity_stream<K, F, H>(t_row, h1, p.N0, p0, p.inv_s, v1, v2);
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 if (pid >= 0) {
-                    em_update2(X1, X2, v1, v2, p.drift_dt, p.s_dt, xi1, xi2);
+                    if constexpr (GEN) {
+                        const float x1v = X1.val(), x2v = X2.val();  // the step's start point
+                        fs.add(p.gc.forcing(x1v, x2v));
+                        X1.add(p.gc.increment(0, x1v, v1, p.drift_dt, xi1));
+                        X2.add(p.gc.increment(1, x2v, v2, p.drift_dt, xi2));
+                    } else {
+                        em_update2(X1, X2, v1, v2, p.drift_dt, p.s_dt, xi1, xi2);
+                    }
                     ++n;
                     const bool exited = radial_excess(X1, X2, p.R2hi, p.R2lo) >= 0.f;
                     if (exited || n >= p.max_steps) {
-                        dir_finish(p, pid, exited, n, X1, X2);
+                        dir_finish(p, pid, exited, n, X1, X2,
+                                   GEN ? fs.value() * p.dt : p.f_const * ((double)n * p.dt));
                         lane_steps += (unsigned long long)n;
                         pid = -1;
                     }
@@ -217,8 +248,29 @@ cudaError_t launch_dirichlet_tc(const DirichletLaunch& L, unsigned* err, cudaStr
 {
     using S = DirShape<K>;
     DirParams<K> p;
-    build_W<K, false, S::HALF>(L.coef, p.W);
-    p.inv_s = scale_W_host<S>(p.W, nullptr, 0);
+    p.Wg = nullptr;
+    for (int q = 0; q < 2 * K + 2; ++q) p.T0[q] = p.N0[q] = 0.f;
+    if constexpr (S::FOLD) {
+        auto T = [&](int m, int n, int q) { return L.coef[(size_t)(m * (K + 1) + n) * 8 + q]; };
+        for (int n = 1; n <= K; ++n) {
+            p.T0[n - 1] = (float)T(0, n, 0);
+            p.T0[K + n - 1] = (float)T(0, n, 1);
+            p.N0[n - 1] = (float)T(n, 0, 4);
+            p.N0[K + n - 1] = (float)T(n, 0, 6);
+        }
+    }
+    std::vector<float> Wv((size_t)(S::NP * S::WS));
+    build_W<K, S::FOLD, S::HALF>(L.coef, Wv.data());
+    p.inv_s = scale_W_host<S>(Wv.data(), p.N0, S::FOLD ? 2 * K : 0);
+    if constexpr (S::W_PARAM) {
+        for (size_t q = 0; q < Wv.size(); ++q) p.W[q] = Wv[q];
+    } else {
+        // into the caller's device buffer (the host vector is read before the copy call returns)
+        if (!L.table_dev) return cudaErrorInvalidValue;
+        const cudaError_t e = cudaMemcpyAsync(L.table_dev, Wv.data(), Wv.size() * sizeof(float), cudaMemcpyHostToDevice, stream);
+        if (e != cudaSuccess) return e;
+        p.Wg = L.table_dev;
+    }
     for (int m = 0; m < kMaxBoundary; ++m) {
         p.ga[m] = m < L.n_ang ? L.ga[m] : 0.0;
         p.gb[m] = m < L.n_ang ? L.gb[m] : 0.0;
@@ -252,16 +304,38 @@ cudaError_t launch_dirichlet_tc(const DirichletLaunch& L, unsigned* err, cudaStr
     p.err = err;
     p.wait_limit = L.wait_limit;
     p.refill_pairs = L.refill_pairs > 0 ? L.refill_pairs : 1;
+    p.gc = GeneralCoef<float>{};
+    if (L.gen) {
+        // the general map: up to the unrolled bound
+        if constexpr (K <= kMaxUnrolledK) {
+            p.gc.set(*L.gen, L.dt, L.f_const);
+            cudaError_t e = cudaFuncSetAttribute(dirichlet_tc_kernel<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 S::SMEM);
+            if (e != cudaSuccess) return e;
+            dirichlet_tc_kernel<K, true><<<L.grid, 128, S::SMEM, stream>>>(p);
+            return cudaGetLastError();
+        } else {
+            return cudaErrorInvalidValue;
+        }
+    }
     cudaError_t e = cudaFuncSetAttribute(dirichlet_tc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
     if (e != cudaSuccess) return e;
     dirichlet_tc_kernel<K><<<L.grid, 128, S::SMEM, stream>>>(p);
     return cudaGetLastError();
 }
 
+// Resident CTAs per SM of the kernel (gen: the general map's variant); also
+// sets its dynamic shared-memory limit.
 template <int K>
-int dirichlet_tc_blocks_per_sm()
+int dirichlet_tc_blocks_per_sm(bool gen)
 {
     using S = DirShape<K>;
+    if constexpr (K <= kMaxUnrolledK) {
+        if (gen) {
+            cudaFuncSetAttribute(dirichlet_tc_kernel<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+            return resident_ctas((const void*)dirichlet_tc_kernel<K, true>, 128, S::SMEM, (int)S::TMEM_COLS);
+        }
+    }
     cudaFuncSetAttribute(dirichlet_tc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
     return resident_ctas((const void*)dirichlet_tc_kernel<K>, 128, S::SMEM, (int)S::TMEM_COLS);
 }
@@ -271,4 +345,4 @@ int dirichlet_tc_blocks_per_sm()
 
 #define PM_INSTANTIATE_DIR_TC(K)                                                                                 \
     template cudaError_t pm::tdtc::launch_dirichlet_tc<K>(const pm::DirichletLaunch&, unsigned*, cudaStream_t); \
-    template int pm::tdtc::dirichlet_tc_blocks_per_sm<K>();
+    template int pm::tdtc::dirichlet_tc_blocks_per_sm<K>(bool);

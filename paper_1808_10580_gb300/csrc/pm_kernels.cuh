@@ -305,8 +305,7 @@ cudaError_t launch_timedep(const TimedepLaunch& L, cudaStream_t stream)
 // path order, so the estimate does not depend on which lane ran which path.
 // ---------------------------------------------------------------------------
 template <typename Real, int K>
-struct DirichletParams {
-    FieldTable<Real, K> field;
+struct DirichletParams : FieldSource<Real, K> {
     double ga[kMaxBoundary];
     double gb[kMaxBoundary];
     double R, quad, f_const, dt;
@@ -358,7 +357,7 @@ __global__ void __launch_bounds__(kDirichletBlock) dirichlet_kernel(const __grid
 {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const ParamTable<Real, K> tab{p.field};
+    const auto tab = field_table<Real, K>(p);
     int64_t pid = -1;  // current path (global index j*M + i), -1 = none
     bool done = false;
     int64_t n = 0;
@@ -424,7 +423,20 @@ template <typename Real, int K>
 cudaError_t launch_dirichlet(const DirichletLaunch& L, cudaStream_t stream)
 {
     DirichletParams<Real, K> p;
-    for (int t = 0; t < table_size(K); ++t) p.field.c[t] = (Real)L.coef[t];
+    constexpr int smem = field_smem<Real, K>();
+    if constexpr (K > kMaxUnrolledK) {
+        static_assert(sizeof(Real) == 4, "wide K: float paths only");
+        if (!L.table_dev) return cudaErrorInvalidValue;
+        std::vector<float> h((size_t)table_size(K));
+        for (int t = 0; t < table_size(K); ++t) h[(size_t)t] = (float)L.coef[t];
+        cudaError_t e = cudaMemcpyAsync(L.table_dev, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, stream);
+        if (e != cudaSuccess) return e;
+        p.table = reinterpret_cast<const float4*>(L.table_dev);
+        e = cudaFuncSetAttribute(dirichlet_kernel<Real, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+    } else {
+        for (int t = 0; t < table_size(K); ++t) p.field.c[t] = (Real)L.coef[t];
+    }
     for (int m = 0; m < kMaxBoundary; ++m) {
         p.ga[m] = m < L.n_ang ? L.ga[m] : 0.0;
         p.gb[m] = m < L.n_ang ? L.gb[m] : 0.0;
@@ -455,15 +467,20 @@ cudaError_t launch_dirichlet(const DirichletLaunch& L, cudaStream_t stream)
     p.inst = L.inst;
     p.key0 = L.key0;
     p.key1 = L.key1;
-    dirichlet_kernel<Real, K><<<L.grid, kDirichletBlock, 0, stream>>>(p);
+    dirichlet_kernel<Real, K><<<L.grid, kDirichletBlock, smem, stream>>>(p);
     return cudaGetLastError();
 }
 
 template <typename Real, int K>
 int dirichlet_blocks_per_sm()
 {
+    constexpr int smem = field_smem<Real, K>();
+    if constexpr (smem > 0) {
+        if (cudaFuncSetAttribute(dirichlet_kernel<Real, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+            return 1;
+    }
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dirichlet_kernel<Real, K>, kDirichletBlock, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dirichlet_kernel<Real, K>, kDirichletBlock, smem) != cudaSuccess)
         return 1;
     return nb > 0 ? nb : 1;
 }
@@ -509,9 +526,11 @@ cudaError_t launch_velocity(const double* coef, const double* x, int64_t n, doub
 
 }  // namespace pm
 
-// Wide K: the time-dependent map only (float paths).
-#define PM_INSTANTIATE_WIDE(K) \
-    template cudaError_t pm::launch_timedep<float, K>(const pm::TimedepLaunch&, cudaStream_t);
+// Wide K: the time-dependent and Dirichlet maps (float paths).
+#define PM_INSTANTIATE_WIDE(K)                                                                     \
+    template cudaError_t pm::launch_timedep<float, K>(const pm::TimedepLaunch&, cudaStream_t);     \
+    template cudaError_t pm::launch_dirichlet<float, K>(const pm::DirichletLaunch&, cudaStream_t); \
+    template int pm::dirichlet_blocks_per_sm<float, K>();
 
 // Explicit instantiation of the launchers for one precision and one K.
 #define PM_INSTANTIATE(Real, K)                                                                        \

@@ -112,6 +112,9 @@ struct DirichletLaunch {
     uint32_t wait_limit = kWaitPolls;  // tensor-core kernel: polls of the per-step MMA wait
     const DirichletGeneral* gen = nullptr;  // host: general forcing and diffusion, or nullptr
     int refill_pairs = 4;            // tensor-core kernel: pairs of steps between lane refills
+    // Wide K (K > 16, float paths): device buffer of wide_table_floats(K)
+    // floats that the launcher fills with its coefficient table.
+    float* table_dev = nullptr;
 };
 
 // Kernel block size of the time-dependent kernel (one path per thread).
@@ -221,7 +224,7 @@ cudaError_t launch_reduce_rows(const BatchInstDev* inst, int B, int max_obs, con
 namespace tdtc {
 template <int K> cudaError_t launch_timedep_tc(const TimedepLaunch& L, unsigned* err, cudaStream_t s);
 template <int K> cudaError_t launch_dirichlet_tc(const DirichletLaunch& L, unsigned* err, cudaStream_t s);
-template <int K> int dirichlet_tc_blocks_per_sm();
+template <int K> int dirichlet_tc_blocks_per_sm(bool gen = false);
 template <int K> cudaError_t launch_batched_tc(const BatchKernelParams& p, int grid, cudaStream_t s);
 template <int K> int batched_tc_blocks_per_sm();
 }

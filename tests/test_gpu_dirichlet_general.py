@@ -1,8 +1,9 @@
 """The disk map with a general forcing and a state-dependent diffusion
 (pm_forward_dirichlet_general: Algorithm 2 / Theorem 3.2 with f(x) and
-sigma(x), Milstein steps of Eq. millstein) against the FP64 oracle on the same
-streams: path by path where the paths do not separate under rounding (no
-drift; straight lines without diffusion), in distribution on the 440-mode
+sigma(x), Milstein steps of Eq. millstein), on the FP32 / FP64 pipes and with
+the velocity sum on the tensor cores (PM_TENSOR), against the FP64 oracle on
+the same streams: path by path where the paths do not separate under rounding
+(no drift; straight lines without diffusion), in distribution on the 440-mode
 drift field (tests/_stats.py)."""
 import dataclasses
 
@@ -65,13 +66,17 @@ def test_double_paths_without_drift_equal_the_oracle_path_by_path(c, orc, milste
     np.testing.assert_allclose(r["g"], go, rtol=0, atol=1e-10)
 
 
-def test_float_paths_without_drift_match_the_oracle(c, orc):
+@pytest.mark.parametrize("tensor", [False, True])
+def test_float_paths_without_drift_match_the_oracle(c, orc, tensor):
     # Without drift the float paths stay within rounding of the double ones
     # (nothing amplifies the difference), so the comparison is path by path:
     # a paired test would only measure float rounding against an error bar of
-    # that same size.
+    # that same size.  The tensor-core kernel needs K >= 4: the 440-mode
+    # lattice with all coefficients zero.
     w, df = no_drift()
-    r = run(c, w, df, pm.PM_FP32)
+    if tensor:
+        w = dataclasses.replace(w, K=10, u=np.zeros(440))
+    r = run(c, w, df, pm.PM_FP32 | (pm.PM_TENSOR if tensor else 0))
     go, so = oracle(orc, w, df, w.M)
     same = r["steps"] == so
     assert np.mean(same) >= 0.999
@@ -87,7 +92,7 @@ def test_straight_lines_without_diffusion(c, orc):
                             x=np.array([[0.1, 0.2], [-0.3, 0.4], [0.5, -0.5], [0.0, 0.0]]))
     df = dataclasses.replace(df, s0=np.zeros(2), s1=np.zeros(2))
     go, so = oracle(orc, w, df, w.M)
-    for flags, tol in ((pm.PM_FP64, 1e-10), (pm.PM_FP32, 2e-5)):
+    for flags, tol in ((pm.PM_FP64, 1e-10), (pm.PM_FP32, 2e-5), (pm.PM_FP32 | pm.PM_TENSOR, 2e-5)):
         r = run(c, w, df, flags)
         assert np.array_equal(r["steps"], so)
         np.testing.assert_allclose(r["g"], go, rtol=0, atol=tol)
@@ -104,18 +109,21 @@ def test_constant_sigma_without_sources_reduces_to_the_disk_map(c):
     assert zc["ok"], zc
 
 
-def test_drift_field_in_distribution(c, orc):
+@pytest.mark.parametrize("tensor", [False, True])
+def test_drift_field_in_distribution(c, orc, tensor):
     MO = 400
     w, df = inputs.dirichlet_general_disk(M=10_000)
     go, so = oracle(orc, w, df, MO)
     mo, _, seo = orc.estimate(go)
-    same = run(c, w, df, pm.PM_FP32 | pm.PM_TENSOR, M=MO)         # PM_TENSOR is ignored: FP32 pipes
-    ind = run(c, w, df, pm.PM_FP32, seed=w.seed + 7919)
+    flags = pm.PM_FP32 | (pm.PM_TENSOR if tensor else 0)
+    same = run(c, w, df, flags, M=MO)
+    ind = run(c, w, df, flags, seed=w.seed + 7919)
     assert same["unexited"] == 0 and ind["unexited"] == 0
     paired = S.zcheck(S.paired_z(same["g"], go))
     two = S.zcheck(S.two_sample_z(ind["mean"], np.sqrt(ind["var"] / w.M), mo, seo))
     early = so < 1000
     agree = float(np.mean(same["steps"][early] == so[early]))
-    print("general disk: paired", paired, "two-sample", two, "early exit agreement", agree, "of", int(early.sum()))
+    print("general disk,", "tensor cores:" if tensor else "FP32 pipes:", "paired", paired, "two-sample", two,
+          "early exit agreement", agree, "of", int(early.sum()))
     assert paired["ok"] and two["ok"], (paired, two)
     assert agree >= 0.999

@@ -215,12 +215,14 @@ def test_fp16_scale_of_w_at_extreme_field_sizes(c, orc, K, scale):
     assert np.abs(d).max() <= w.dt * 4e-6 * term_scale + 1e-7, np.abs(d).max()
 
 
-@pytest.mark.parametrize("K", [4, 8, 16])
+@pytest.mark.parametrize("K", [4, 8, 16, 24, 40, 64])
 def test_batched_tensor_at_other_bounds(K):
     # The batched kernel at other wave-number bounds against single-instance calls:
-    # Dirichlet instances share the unfolded shape, so bit for bit; time-dependent
-    # instances equal too where the single-problem kernel is unfolded (K = 4), and
-    # agree within Monte Carlo error where it folds the constant column (K = 8, 16).
+    # Dirichlet instances share the shape (unfolded up to K = 16, folded like the
+    # time-dependent kernel above it), so bit for bit; time-dependent instances
+    # equal too where both kernels take the same shape (K = 4, 24 unfolded; 40,
+    # 64 folded), and agree within Monte Carlo error where only the
+    # single-problem kernel folds the constant column (K = 8, 16).
     from tests.test_gpu_batched import small_instances
     h, s = _gpu.side_stream_ctx()
     try:
@@ -244,7 +246,7 @@ def test_batched_tensor_at_other_bounds(K):
                     pm.pm_forward_timedep(h, pm.Field(w.K, w.u), w.kappa,
                                           pm.Fourier(w.theta0.k, w.theta0.a, w.theta0.b), w.x, w.t, n, w.M, w.dt,
                                           w.seed, pm.PM_FP32 | pm.PM_TENSOR, m, v, instance=k)
-                    if K % 4:  # unfolded shape in both kernels
+                    if K > 16 or K % 4 or K < 8:  # the same shape in both kernels
                         np.testing.assert_allclose(got[row:row + n], m, rtol=0, atol=1e-12)
                     else:
                         se = np.sqrt((gv[row:row + n] + v) / w.M)

@@ -117,7 +117,9 @@ def test_host_pointers_and_repeatability(c):
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
 
 
-def test_wide_bounds_are_float_and_time_dependent_only(c):
+def test_wide_bounds_are_float_only(c):
+    # FP64 paths stop at K = 16; the batched map takes the wide bounds on the
+    # tensor cores only; the general disk map (forcing and diffusion) stops at 16.
     w = wide_workload(24, 128, n_pts=2)
     w.t = np.full(2, 0.01)
     with pytest.raises(pm.PMError):
@@ -126,4 +128,16 @@ def test_wide_bounds_are_float_and_time_dependent_only(c):
     d.K = 24
     d.u = inputs.prior_field(24, 7)
     with pytest.raises(pm.PMError):
-        _gpu.dirichlet(c, d, obs=np.array([0]))
+        _gpu.dirichlet(c, d, pm.PM_FP64, obs=np.array([0]))
+    ws = [w, d]
+    d.x = d.x[:2]
+    with pytest.raises(pm.PMError):
+        _gpu.batched(c, ws, flags=pm.PM_FP32)
+    gw, df = inputs.dirichlet_general_disk(M=16)
+    gw.K, gw.u = 24, inputs.prior_field(24, 7)
+    x = np.ascontiguousarray(gw.x[:1])
+    with pytest.raises(pm.PMError):
+        pm.pm_forward_dirichlet_general(c, pm.Field(gw.K, gw.u), gw.drift_scale,
+                                        pm.DirichletData(gw.g.R, gw.g.quad, gw.g.f_const, gw.g.a, gw.g.b),
+                                        pm.DiffusionForcing(df.s0, df.s1, df.milstein, df.c, df.F, df.w),
+                                        x, 1, 16, gw.dt, 100, gw.seed, pm.PM_FP32, np.empty(1))
