@@ -575,7 +575,10 @@ int pm_philox(pm_ctx* ctx, const uint32_t* ctr, uint32_t key0, uint32_t key1, in
 
 /* The normals (xi1, xi2) of steps n0 .. n0+count-1 of path (b, j, i) as the
  * kernels draw them, in the precision the flags select -> out[count][2]
- * (double).  Pointers follow PM_DEVICE_PTRS. */
+ * (double): PM_FP64, PM_FP32 (the FP32-pipe kernels: sincospif for the
+ * angle), or PM_FP32 | PM_TENSOR (the tensor-core kernels: the two steps of a
+ * Philox block in one packed pass with the library's own sin and cos of 2 pi u,
+ * see pm_sincos_turns).  Pointers follow PM_DEVICE_PTRS. */
 int pm_normals(pm_ctx* ctx, uint64_t seed, uint32_t b, uint32_t j, uint32_t i, int64_t n0,
                int64_t count, double* out, uint32_t flags);
 

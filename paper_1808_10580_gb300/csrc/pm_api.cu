@@ -471,7 +471,7 @@ int pm_forward_timedep(pm_ctx* c, const pm_field* field, double kappa, const pm_
     const bool tc = !fp64 && (flags & PM_TENSOR) && (K == 4 || K == 5 || K == 6 || K == 8 || K == 10 || K == 12 || K == 16 ||
                                                      wide_K(K));
     const bool wide = wide_K(K);
-    const int rows = tc ? td_tc_rows(K) : kTimedepBlock;  // paths per CTA
+    const int rows = tc ? td_tc_rows(K) : td_simt_rows(K);  // paths per CTA
     const int64_t chunks64 = (M + rows - 1) / rows;
     if (n_obs * chunks64 > 0x7fffffffLL) return fail(PM_EINVAL, "n_obs * ceil(M/%d) exceeds the grid limit", rows);
     const int32_t chunks = (int32_t)chunks64;
@@ -1073,7 +1073,8 @@ int pm_normals(pm_ctx* c, uint64_t seed, uint32_t b, uint32_t j, uint32_t i, int
         if ((rc = ensure_workspace(c, (size_t)count * 16 + 256))) return rc;
         dout = (double*)c->ws;
     }
-    PM_CUDA(launch_normals(seed, b, j, i, n0, count, dout, flags & PM_FP64, c->stream), "normals kernel");
+    const bool packed = !(flags & PM_FP64) && (flags & PM_TENSOR);
+    PM_CUDA(launch_normals(seed, b, j, i, n0, count, dout, flags & PM_FP64, packed, c->stream), "normals kernel");
     count_launch(c);
     if (!dev) PM_CUDA(cudaMemcpyAsync(out, dout, (size_t)count * 16, cudaMemcpyDeviceToHost, c->stream), "copy out");
     if (dev && (flags & PM_ASYNC)) return PM_OK;

@@ -39,6 +39,30 @@ __device__ __forceinline__ u32x4 philox4x32_10(u32x4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
+// The same generator with its round keys precomputed (rk[2r] = k0 + r W0,
+// rk[2r+1] = k1 + r W1, modulo 2^32; round_keys below): where the keys are
+// the same for every thread, the table sits in the kernel-parameter bank and
+// each key is an operand of the XOR, with no additions in the rounds.
+__device__ __forceinline__ u32x4 philox4x32_10_rk(u32x4 c, const uint32_t (&rk)[20])
+{
+    constexpr uint32_t kMul0 = 0xD2511F53u, kMul1 = 0xCD9E8D57u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = kMul0 * c.x, hi0 = __umulhi(kMul0, c.x);
+        const uint32_t lo1 = kMul1 * c.z, hi1 = __umulhi(kMul1, c.z);
+        c = u32x4{hi1 ^ c.y ^ rk[2 * r], lo1, hi0 ^ c.w ^ rk[2 * r + 1], lo0};
+    }
+    return c;
+}
+
+inline void round_keys(uint32_t k0, uint32_t k1, uint32_t (&rk)[20])
+{
+    for (int r = 0; r < 10; ++r) {
+        rk[2 * r] = k0 + (uint32_t)r * 0x9E3779B9u;
+        rk[2 * r + 1] = k1 + (uint32_t)r * 0xBB67AE85u;
+    }
+}
+
 // Uniform in (0, 1) from the top 23 bits: (2q + 1) 2^-24, exact in float.
 template <typename Real>
 __device__ __forceinline__ Real uniform23(uint32_t r)
@@ -112,22 +136,13 @@ __device__ __forceinline__ void box_muller(uint32_t ra, uint32_t rb, Real& xi1, 
 // uniform23, without an integer-to-float conversion.
 __device__ __forceinline__ float one_plus_mantissa(uint32_t r) { return __uint_as_float(0x3F800000u | (r >> 9)); }
 
-// In float the same transform takes the angle's sin and cos from
-// sincos_turns2 (error below 1e-7) instead of sincospif.
-template <>
-__device__ __forceinline__ void box_muller<float>(uint32_t ra, uint32_t rb, float& xi1, float& xi2)
-{
-    const float ua = one_plus_mantissa(ra) - 0x1.fffffep-1f, ub = one_plus_mantissa(rb) - 0x1.fffffep-1f;
-    const float rho = sqrtf(-2.0f * logf(ua));
-    float2 s, c;
-    sincos_turns2(pair(ub), s, c);
-    xi1 = rho * c.x;
-    xi2 = rho * s.x;
-}
-
-// The normals of two consecutive steps from one Philox block, packed: .x from
-// words (a0, b0), .y from (a1, b1); each component equals box_muller<float>'s
-// result bit for bit (the packed operations round per component).
+// The normals of two consecutive steps from one Philox block, packed (the
+// tensor-core kernels): .x from words (a0, b0), .y from (a1, b1); the same
+// transform as box_muller<float> with the angle's sin and cos from
+// sincos_turns2 (error below 1e-7) instead of sincospif, so the two forms agree
+// to that error, not bit for bit.  The FP32-pipe kernels keep the scalar form:
+// there the extra code of the series changed the compiler's register
+// allocation of the velocity loop and cost up to 3.7x (K = 64).
 __device__ __forceinline__ void box_muller2(uint32_t a0, uint32_t b0, uint32_t a1, uint32_t b1, float2& xi1,
                                             float2& xi2)
 {

@@ -47,6 +47,7 @@ struct DirParams {
     int32_t* exit_step;
     double* x_out;
     uint32_t inst, key0, key1;
+    uint32_t rk[20];      // Philox round keys of (key0, key1)
     unsigned* err;
     uint32_t wait_limit;  // polls of the per-step MMA wait (tc::kWaitLimit unless a test lowers it)
     int32_t refill_pairs; // pairs of Euler steps between lane refills (a launch shape: results do not depend on it)
@@ -182,7 +183,7 @@ __global__ void __launch_bounds__(128, DirShape<K>::MIN_CTAS6) dirichlet_tc_kern
 #pragma unroll 1
         for (int pair = 0; pair < p.refill_pairs && !stop; ++pair) {
             u32x4 r{0, 0, 0, 0};
-            if (pid >= 0) r = philox4x32_10(u32x4{(uint32_t)(n >> 1), i, j, p.inst}, p.key0, p.key1);
+            if (pid >= 0) r = philox4x32_10_rk(u32x4{(uint32_t)(n >> 1), i, j, p.inst}, p.rk);
             float2 z1, z2;  // the two steps' normals, formed during the first product
 #pragma unroll 1
             for (int half = 0; half < 2; ++half) {
@@ -301,6 +302,7 @@ cudaError_t launch_dirichlet_tc(const DirichletLaunch& L, unsigned* err, cudaStr
     p.inst = L.inst;
     p.key0 = L.key0;
     p.key1 = L.key1;
+    round_keys(L.key0, L.key1, p.rk);
     p.err = err;
     p.wait_limit = L.wait_limit;
     p.refill_pairs = L.refill_pairs > 0 ? L.refill_pairs : 1;

@@ -256,7 +256,7 @@ cudaError_t launch_timedep(const TimedepLaunch& L, cudaStream_t stream)
         cudaError_t e = cudaMemcpyAsync(L.table_dev, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, stream);
         if (e != cudaSuccess) return e;
         p.table = reinterpret_cast<const float4*>(L.table_dev);
-        e = cudaFuncSetAttribute(L.groups ? timedep_shared_kernel<Real, K, kTimedepBlock> : timedep_kernel<Real, K, kTimedepBlock>,
+        e = cudaFuncSetAttribute(L.groups ? timedep_shared_kernel<Real, K, td_simt_rows(K)> : timedep_kernel<Real, K, td_simt_rows(K)>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
     } else {
@@ -288,11 +288,11 @@ cudaError_t launch_timedep(const TimedepLaunch& L, cudaStream_t stream)
     p.members = L.members;
     if (L.groups) {
         const int64_t grid = (int64_t)L.n_groups * L.chunks;
-        timedep_shared_kernel<Real, K, kTimedepBlock><<<(unsigned)grid, kTimedepBlock, smem, stream>>>(p);
+        timedep_shared_kernel<Real, K, td_simt_rows(K)><<<(unsigned)grid, td_simt_rows(K), smem, stream>>>(p);
         return cudaGetLastError();
     }
     const int64_t grid = (int64_t)L.n_obs * L.chunks;
-    timedep_kernel<Real, K, kTimedepBlock><<<(unsigned)grid, kTimedepBlock, smem, stream>>>(p);
+    timedep_kernel<Real, K, td_simt_rows(K)><<<(unsigned)grid, td_simt_rows(K), smem, stream>>>(p);
     return cudaGetLastError();
 }
 

@@ -119,6 +119,14 @@ struct DirichletLaunch {
 
 // Kernel block size of the time-dependent kernel (one path per thread).
 constexpr int kTimedepBlock = 128;
+// Paths (threads) per CTA of the FP32-pipe time-dependent kernel at K: 256
+// where one CTA's shared-memory copy of the velocity table (32 (K+1)^2 bytes)
+// leaves no room for a second CTA on the SM (K = 64), so that each scheduler
+// still has two warps to hide the table loads; kTimedepBlock otherwise.
+constexpr int td_simt_rows(int K)
+{
+    return K > 16 && 2 * 32 * (K + 1) * (K + 1) > 227 * 1024 ? 2 * kTimedepBlock : kTimedepBlock;
+}
 // Block size of the persistent Dirichlet kernel.
 constexpr int kDirichletBlock = 128;
 
@@ -150,7 +158,7 @@ cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, int64_t
                           cudaStream_t s);
 cudaError_t launch_sincos_turns(const float* x, int64_t n, float* s, float* c, cudaStream_t st);
 cudaError_t launch_normals(uint64_t seed, uint32_t b, uint32_t j, uint32_t i, int64_t n0, int64_t count,
-                           double* out, bool fp64, cudaStream_t s);
+                           double* out, bool fp64, bool packed, cudaStream_t s);
 
 }  // namespace pm
 

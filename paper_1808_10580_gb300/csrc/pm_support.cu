@@ -273,12 +273,31 @@ __global__ void normals_kernel(uint32_t k0, uint32_t k1, uint32_t b, uint32_t j,
     out[2 * q + 1] = (double)xi2;
 }
 
+// The tensor-core kernels' form: both steps of a Philox block from one packed
+// Box-Muller pass (box_muller2), the step's half taken.
+__global__ void normals_packed_kernel(uint32_t k0, uint32_t k1, uint32_t b, uint32_t j, uint32_t i, int64_t n0,
+                                      int64_t count, double* __restrict__ out)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= count) return;
+    const int64_t n = n0 + q;
+    const u32x4 r = philox4x32_10(u32x4{(uint32_t)(n >> 1), i, j, b}, k0, k1);
+    float2 z1, z2;
+    box_muller2(r.x, r.y, r.z, r.w, z1, z2);
+    out[2 * q] = (double)((n & 1) ? z1.y : z1.x);
+    out[2 * q + 1] = (double)((n & 1) ? z2.y : z2.x);
+}
+
 cudaError_t launch_normals(uint64_t seed, uint32_t b, uint32_t j, uint32_t i, int64_t n0, int64_t count, double* out,
-                           bool fp64, cudaStream_t s)
+                           bool fp64, bool packed, cudaStream_t s)
 {
     if (count == 0) return cudaSuccess;
     const uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32);
     const unsigned grid = (unsigned)((count + 255) / 256);
+    if (packed) {
+        normals_packed_kernel<<<grid, 256, 0, s>>>(k0, k1, b, j, i, n0, count, out);
+        return cudaGetLastError();
+    }
     if (fp64) normals_kernel<double><<<grid, 256, 0, s>>>(k0, k1, b, j, i, n0, count, out);
     else normals_kernel<float><<<grid, 256, 0, s>>>(k0, k1, b, j, i, n0, count, out);
     return cudaGetLastError();

@@ -201,6 +201,7 @@ struct Params {
     int64_t M, path_offset;
     int32_t n_obs, chunks;
     uint32_t inst, key0, key1;
+    uint32_t rk[20];          // Philox round keys of (key0, key1)
     unsigned* err;
     uint32_t wait_limit;      // polls of the per-step MMA wait (tc::kWaitLimit unless a test lowers it)
     const int4* groups;       // shared paths: {m0, m1, stream, nmax} per grid row, or nullptr
@@ -776,7 +777,7 @@ __global__ void __launch_bounds__(TdLaunch<K>::THREADS, TdLaunch<K>::MIN_CTAS)
         }
         // While the product runs: the Brownian increment and the x1 harmonics.
         if ((n & 1) == 0) {
-            const u32x4 r = philox4x32_10(u32x4{(uint32_t)(n >> 1), pid, (uint32_t)stream, p.inst}, p.key0, p.key1);
+            const u32x4 r = philox4x32_10_rk(u32x4{(uint32_t)(n >> 1), pid, (uint32_t)stream, p.inst}, p.rk);
             box_muller2(r.x, r.y, r.z, r.w, z1, z2);
         }
         const float xi1 = (n & 1) ? z1.y : z1.x, xi2 = (n & 1) ? z2.y : z2.x;
@@ -904,6 +905,7 @@ cudaError_t launch_timedep_tc(const TimedepLaunch& L, unsigned* err, cudaStream_
     p.inst = L.inst;
     p.key0 = L.key0;
     p.key1 = L.key1;
+    round_keys(L.key0, L.key1, p.rk);
     p.err = err;
     p.wait_limit = L.wait_limit;
     p.groups = L.groups;

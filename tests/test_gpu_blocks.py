@@ -28,17 +28,35 @@ def test_philox_bit_exact_on_a_million_counters(c, orc):
     assert np.array_equal(out, ref)
 
 
-@pytest.mark.parametrize("fp64", [False, True])
-def test_normals_match_oracle(c, orc, fp64):
+@pytest.mark.parametrize("form", ["fp64", "fp32", "fp32_tensor"])
+def test_normals_match_oracle(c, orc, form):
+    # fp32: the FP32-pipe kernels' scalar form (sincospif for the angle);
+    # fp32_tensor: the tensor-core kernels' packed form (both steps of a Philox
+    # block at once, the angle's sin and cos from the library's own series).
     seed = (12345 << 32) | 678
     out = np.empty((4096, 2))
-    pm.pm_normals(c, seed, 3, 7, 11, 5, 4096, out, pm.PM_FP64 if fp64 else pm.PM_FP32)
+    flags = {"fp64": pm.PM_FP64, "fp32": pm.PM_FP32, "fp32_tensor": pm.PM_FP32 | pm.PM_TENSOR}[form]
+    pm.pm_normals(c, seed, 3, 7, 11, 5, 4096, out, flags)
     ref = orc.normals(seed, 3, 7, 11, 5, 4096)
-    # float: log and sqrt within a few ulp, the angle's sin and cos from the
-    # quarter-turn series (absolute error below 1e-7)
-    tol = 1e-13 if fp64 else 4e-6
-    print("normals, fp64" if fp64 else "normals, float", "largest |GPU - oracle|", np.abs(out - ref).max())
+    # float: log and sqrt within a few ulp; sincospif within 1 ulp, the series
+    # within 1e-7 absolute
+    tol = 1e-13 if form == "fp64" else 4e-6
+    print("normals,", form, "largest |GPU - oracle|", np.abs(out - ref).max())
     assert np.abs(out - ref).max() < tol
+
+
+def test_packed_normals_differ_from_the_scalar_form_by_the_angle_rounding_only(c):
+    seed = (777 << 32) | 9
+    a, b = np.empty((4096, 2)), np.empty((4096, 2))
+    pm.pm_normals(c, seed, 1, 2, 3, 0, 4096, a, pm.PM_FP32)
+    pm.pm_normals(c, seed, 1, 2, 3, 0, 4096, b, pm.PM_FP32 | pm.PM_TENSOR)
+    rho = np.hypot(a[:, 0], a[:, 1])
+    d = np.abs(a - b).max(axis=1)
+    # the radius is the same computation in both; the angle's sin and cos differ
+    # by at most 1.2e-7 (1 ulp of sincospif plus the series' 8.4e-8)
+    print("packed vs scalar float normals: identical", np.mean(d == 0), "largest difference / radius",
+          (d / rho).max())
+    assert np.all(d <= rho * 1.5e-7 + 1e-12)
 
 
 @pytest.mark.parametrize("K", [0, 1, 2, 3, 4, 5, 6, 8, 10, 12, 16])
