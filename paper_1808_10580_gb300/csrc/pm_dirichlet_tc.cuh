@@ -9,7 +9,6 @@
 // result is ignored).  The CTA leaves when every lane has found the path
 // counter exhausted.
 #pragma once
-#include <type_traits>
 #include "pm_general_step.cuh"
 #include "pm_timedep_tc.cuh"
 
@@ -85,14 +84,15 @@ __device__ __forceinline__ void dir_finish(const DirParams<K>& p, int64_t pid, b
 // Gaussian-source forcing; pm_general_step.cuh) instead of the constant
 // diffusion and forcing; the velocity sum is the same.
 template <int K, bool GEN = false>
-__global__ void __launch_bounds__(128, DirShape<K>::MIN_CTAS6) dirichlet_tc_kernel(const __grid_constant__ DirParams<K> p)
+__global__ void __launch_bounds__(128, DirShape<K>::MIN_CTAS) dirichlet_tc_kernel(const __grid_constant__ DirParams<K> p)
 {
     using S = DirShape<K>;
     constexpr bool F = S::FOLD;
     constexpr bool H = S::HALF;
-    // x1 harmonics: all of them during the product up to the unrolled bound,
-    // streamed after the wait above it (registers).
-    using Harm1 = std::conditional_t<(K > kMaxUnrolledK), HarmStream, HarmArray<K>>;
+    // x1 harmonics streamed after the MMA wait (as in the time-dependent
+    // kernel): 64 registers and 8 CTAs per SM at K = 10, 388.5 against 395.9 ms
+    // on the disk workload with all of them computed during the product at 6.
+    using Harm1 = HarmStream;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     uint8_t* A_hi = smem;
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(128, DirShape<K>::MIN_CTAS6) dirichlet_tc_kern
                 // While the product runs: the Brownian increment and the x1 harmonics.
                 if (half == 0) box_muller2(r.x, r.y, r.z, r.w, z1, z2);
                 const float xi1 = half ? z1.y : z1.x, xi2 = half ? z2.y : z2.x;
-                Harm1 h1;  // during the product (HarmArray)
+                Harm1 h1;  // its base from x1; the harmonics follow in the velocity sum
                 h1.init(sx.x, cx.x);
                 issued_any = true;
                 failed = p.wait_limit >= tc::kWaitLimit ? !tc::mbar_wait(bar_a, phase)
