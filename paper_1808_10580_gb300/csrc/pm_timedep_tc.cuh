@@ -744,10 +744,10 @@ __global__ void __launch_bounds__(TdLaunch<K>::THREADS, TdLaunch<K>::MIN_CTAS)
     const int N = m < m1 ? steps_of(m1 - 1) : 0;
     int stop = steps_of(m) - 1;  // the step at which member m takes its last step
     bool failed = false;
-    int issued = -1;  // the last step whose product was issued
+    int n = 0;  // the step; after the loop, n - 1 is the last step whose product was issued
     float2 z1 = make_float2(0.f, 0.f), z2 = z1;  // the normals of the even step (.x) and the next (.y)
 
-    for (int n = 0; n < N; ++n) {
+    for (; n < N; ++n) {
         // sin and cos of 2 pi x of both coordinates, then the row of A: x2
         // harmonics (hi and lo); folded: the m = 0 part of v1 here.
         float2 sx, cx;
@@ -758,7 +758,6 @@ __global__ void __launch_bounds__(TdLaunch<K>::THREADS, TdLaunch<K>::MIN_CTAS)
         // One barrier per step: the rows are in place, and a wait that gave up
         // in the previous step (any thread) ends the loop for the whole CTA.
         if (__syncthreads_or(failed)) { failed = true; break; }
-        issued = n;
         if (tid == 0) {
             if constexpr (SETS == 1) {
                 issue_step_mma<K, F, H>(tmem, sb, bar_a);
@@ -813,7 +812,7 @@ __global__ void __launch_bounds__(TdLaunch<K>::THREADS, TdLaunch<K>::MIN_CTAS)
     while (m < m1) finish(m++, X1, X2, false);  // only after a failed wait
     // No product may still write tensor memory when it is freed: after a wait
     // that gave up, wait (full bound) for the last one issued.
-    if (failed && issued >= 0) tc::mbar_wait(bar_a, (uint32_t)(issued & 1));
+    if (failed && n > 0) tc::mbar_wait(bar_a, (uint32_t)((n - 1) & 1));
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
