@@ -261,10 +261,10 @@ int pm_forward_dirichlet(pm_ctx* ctx, const pm_field* field, double drift_scale,
  * integrated by the left-point rule dt sum_{m < n} f(X_m); the constant-
  * coefficient map is the case s0 = sqrt(2 kappa), s1 = 0, n_src = 0 (results
  * equal up to rounding).  Other arguments, outputs and return values as for
- * pm_forward_dirichlet, with K up to 16: float or double paths on the FP32 /
- * FP64 pipes, or with PM_TENSOR (float paths, K in {4, 5, 6, 8, 10, 12, 16})
- * the velocity sum on the tensor cores as in pm_forward_dirichlet, the
- * diffusion, Milstein and forcing terms unchanged. */
+ * pm_forward_dirichlet: float or double paths on the FP32 / FP64 pipes (K up to
+ * 16), or with PM_TENSOR (float paths, K in {4, 5, 6, 8, 10, 12, 16} and the
+ * wide bounds 24 ... 64) the velocity sum on the tensor cores as in
+ * pm_forward_dirichlet, the diffusion, Milstein and forcing terms unchanged. */
 typedef struct pm_diffusion_forcing {
     double s0[2], s1[2];  /* sigma_i(x) = s0[i] + s1[i] x_i */
     int32_t milstein;     /* 1: Eq. millstein, 0: Eq. euler */

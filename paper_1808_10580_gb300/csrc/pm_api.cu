@@ -747,10 +747,12 @@ int dirichlet_call(pm_ctx* c, const pm_field* field, double drift_scale, double 
                    int64_t* n_unexited, const pm_path_opts* opts)
 {
     if (!c) return fail(PM_EINVAL, "ctx is NULL");
-    int rc = check_field(field, !gen);
+    int rc = check_field(field, true);
     if (rc) return rc;
     const bool wide = wide_K(field->K);
     if (wide && (flags & PM_FP64)) return fail(PM_EINVAL, "K=%d runs with float paths only", field->K);
+    if (wide && gen && !(flags & PM_TENSOR))
+        return fail(PM_EINVAL, "K=%d: the general disk map runs the wide bounds with PM_TENSOR only", field->K);
     if (!gd) return fail(PM_EINVAL, "boundary data is NULL");
     if (!(std::isfinite(gd->R) && gd->R > 0)) return fail(PM_EINVAL, "R must be finite and > 0");
     if (!std::isfinite(gd->quad) || !std::isfinite(gd->f_const)) return fail(PM_EINVAL, "quad and f_const must be finite");

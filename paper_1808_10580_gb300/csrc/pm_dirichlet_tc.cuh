@@ -307,18 +307,13 @@ cudaError_t launch_dirichlet_tc(const DirichletLaunch& L, unsigned* err, cudaStr
     p.wait_limit = L.wait_limit;
     p.refill_pairs = L.refill_pairs > 0 ? L.refill_pairs : 1;
     p.gc = GeneralCoef<float>{};
-    if (L.gen) {
-        // the general map: up to the unrolled bound
-        if constexpr (K <= kMaxUnrolledK) {
-            p.gc.set(*L.gen, L.dt, L.f_const);
-            cudaError_t e = cudaFuncSetAttribute(dirichlet_tc_kernel<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 S::SMEM);
-            if (e != cudaSuccess) return e;
-            dirichlet_tc_kernel<K, true><<<L.grid, 128, S::SMEM, stream>>>(p);
-            return cudaGetLastError();
-        } else {
-            return cudaErrorInvalidValue;
-        }
+    if (L.gen) {  // the general map
+        p.gc.set(*L.gen, L.dt, L.f_const);
+        cudaError_t e = cudaFuncSetAttribute(dirichlet_tc_kernel<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             S::SMEM);
+        if (e != cudaSuccess) return e;
+        dirichlet_tc_kernel<K, true><<<L.grid, 128, S::SMEM, stream>>>(p);
+        return cudaGetLastError();
     }
     cudaError_t e = cudaFuncSetAttribute(dirichlet_tc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
     if (e != cudaSuccess) return e;
@@ -332,11 +327,9 @@ template <int K>
 int dirichlet_tc_blocks_per_sm(bool gen)
 {
     using S = DirShape<K>;
-    if constexpr (K <= kMaxUnrolledK) {
-        if (gen) {
-            cudaFuncSetAttribute(dirichlet_tc_kernel<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
-            return resident_ctas((const void*)dirichlet_tc_kernel<K, true>, 128, S::SMEM, (int)S::TMEM_COLS);
-        }
+    if (gen) {
+        cudaFuncSetAttribute(dirichlet_tc_kernel<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+        return resident_ctas((const void*)dirichlet_tc_kernel<K, true>, 128, S::SMEM, (int)S::TMEM_COLS);
     }
     cudaFuncSetAttribute(dirichlet_tc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
     return resident_ctas((const void*)dirichlet_tc_kernel<K>, 128, S::SMEM, (int)S::TMEM_COLS);

@@ -151,3 +151,71 @@ def test_prior_field_in_distribution(c, orc):
               "exit steps before step 100 identical", agree, "of", int(early.sum()))
         assert paired["ok"] and two["ok"], (paired, two)
         assert agree >= 0.99
+
+
+def run_general(c, w, df, M=None, max_steps=None, seed=None):
+    M = w.M if M is None else M
+    n = len(w.x)
+    total = n * M
+    dx = torch.from_numpy(np.ascontiguousarray(w.x)).cuda()
+    mean = torch.empty(n, dtype=torch.float64, device="cuda")
+    var = torch.empty_like(mean)
+    es = torch.empty(total, dtype=torch.int32, device="cuda")
+    g = torch.empty(total, dtype=torch.float64, device="cuda")
+    xo = torch.empty(2 * total, dtype=torch.float64, device="cuda")
+    nu = torch.zeros(1, dtype=torch.int64, device="cuda")
+    gd = pm.DirichletData(w.g.R, w.g.quad, w.g.f_const, w.g.a, w.g.b)
+    d = pm.DiffusionForcing(df.s0, df.s1, df.milstein, df.c, df.F, df.w)
+    rc = pm.pm_forward_dirichlet_general(c, pm.Field(w.K, w.u), w.drift_scale, gd, d, dx, n, M, w.dt,
+                                         w.max_steps if max_steps is None else max_steps,
+                                         w.seed if seed is None else seed, TC, mean, var, es, nu, g_out=g, x_out=xo)
+    torch.cuda.synchronize()
+    return dict(rc=rc, mean=mean.cpu().numpy(), var=var.cpu().numpy(), unexited=int(nu.item()),
+                steps=es.cpu().numpy().reshape(n, M), g=g.cpu().numpy().reshape(n, M),
+                x=xo.cpu().numpy().reshape(n, M, 2))
+
+
+@pytest.mark.parametrize("K", [24, 64])
+def test_general_map_short_horizon_paths_match_oracle(c, orc, K):
+    # The general disk map (sigma(x) with the Milstein term, Gaussian sources)
+    # on the tensor cores at a wide bound: 20 steps at dt = 1e-4 from interior
+    # and edge points, path by path against the FP64 oracle, within the velocity
+    # rounding times the FP64 flow's stretching of a small change (as above).
+    gw, df = inputs.dirichlet_general_disk(M=64)
+    ang = 0.3 + np.arange(4) * np.pi / 2
+    edge = 0.99 * np.stack([np.cos(ang), np.sin(ang)], 1)
+    w = dataclasses.replace(gw, K=K, u=inputs.prior_field(K, 600 + K), dt=1e-4,
+                            x=np.concatenate([inputs.disk_points(6, 0.9, 700 + K), edge]))
+    args = (w.K, w.u, w.drift_scale, df, w.g)
+    go, so, xo = orc.dirichlet_general_paths(*args, w.x, w.dt, N_SHORT, w.seed, npaths=w.M, want_x=True)
+    amp = np.ones((len(w.x), w.M))
+    for e in ((1e-9, 0.0), (0.0, 1e-9)):
+        _, s2, x2 = orc.dirichlet_general_paths(*args, w.x + np.array(e), w.dt, N_SHORT, w.seed, npaths=w.M,
+                                                want_x=True)
+        amp = np.maximum(amp, np.where(s2 == so, np.linalg.norm(x2 - xo, axis=-1) / 1e-9, np.inf))
+    r = run_general(c, w, df, max_steps=N_SHORT)
+    assert r["rc"] in (0, pm.PM_WARN_UNEXITED)
+    same = (r["steps"] == so) & np.isfinite(amp)
+    assert (so >= 0).sum() > 10 and np.mean(same) >= 0.995
+    tol = 2 * amp * N_SHORT * w.dt * w.drift_scale * 4e-6 * velocity_scale(orc, K, w.u) + 1e-6
+    ratio = (np.linalg.norm(r["x"] - xo, axis=-1) / tol)[same]
+    print(f"general map, K = {K}: exit steps identical {np.mean(same):.4f}, largest deviation / bound {ratio.max():.3f}")
+    assert ratio.max() <= 1.0
+
+
+def test_general_map_wide_in_distribution(c, orc):
+    # K = 24, the disk of radius 0.5: paired means on the oracle's streams
+    # (1000 paths per observation) and an independent full launch.
+    MO = 1000
+    gw, df = inputs.dirichlet_general_disk(M=20_000)
+    w = dataclasses.replace(gw, K=24, u=inputs.prior_field(24, 624), dt=1e-3,
+                            x=inputs.disk_points(10, 0.4, 724), g=dataclasses.replace(gw.g, R=0.5))
+    go, so = orc.dirichlet_general_paths(w.K, w.u, w.drift_scale, df, w.g, w.x, w.dt, w.max_steps, w.seed, npaths=MO)
+    mo, _, seo = orc.estimate(go)
+    same = run_general(c, w, df, M=MO)
+    ind = run_general(c, w, df, seed=w.seed + 7919)
+    assert same["unexited"] == 0 and ind["unexited"] == 0
+    paired = S.zcheck(S.paired_z(same["g"], go))
+    two = S.zcheck(S.two_sample_z(ind["mean"], np.sqrt(ind["var"] / w.M), mo, seo))
+    print("general map, K = 24 disk: paired", paired, "two-sample", two)
+    assert paired["ok"] and two["ok"], (paired, two)

@@ -118,8 +118,8 @@ def test_host_pointers_and_repeatability(c):
 
 
 def test_wide_bounds_are_float_only(c):
-    # FP64 paths stop at K = 16; the batched map takes the wide bounds on the
-    # tensor cores only; the general disk map (forcing and diffusion) stops at 16.
+    # FP64 paths stop at K = 16; the batched map and the general disk map
+    # (forcing and diffusion) take the wide bounds on the tensor cores only.
     w = wide_workload(24, 128, n_pts=2)
     w.t = np.full(2, 0.01)
     with pytest.raises(pm.PMError):
