@@ -1129,8 +1129,9 @@ int pm_autotune_dirichlet(pm_ctx* c, const pm_field* field, double drift_scale, 
                           int64_t max_steps, uint64_t seed, uint32_t flags, int32_t* best_ctas_per_sm)
 {
     if (!c) return fail(PM_EINVAL, "ctx is NULL");
-    int rc = check_field(field);
+    int rc = check_field(field, true);
     if (rc) return rc;
+    if (wide_K(field->K) && (flags & PM_FP64)) return fail(PM_EINVAL, "K=%d runs with float paths only", field->K);
     if (n_obs < 1 || M < 1) return fail(PM_EINVAL, "autotuning needs n_obs >= 1 and M >= 1");
     if ((rc = set_device(c))) return rc;
     flags &= ~PM_ASYNC;

@@ -349,7 +349,8 @@ extern "C" int pm_autotune_batched(pm_ctx* c, const pm_batch* bt, uint32_t flags
 {
     if (!c || !bt) return fail(PM_EINVAL, "ctx or batch is NULL");
     if (bt->n_rows < 1 || bt->B < 1) return fail(PM_EINVAL, "autotuning needs a non-empty batch");
-    if (!supported_K(bt->K)) return fail(PM_EINVAL, "unsupported K %d", bt->K);
+    if (!supported_K(bt->K) && !(wide_K(bt->K) && (flags & PM_TENSOR)))
+        return fail(PM_EINVAL, "unsupported K %d (24 ... 64 with PM_TENSOR only)", bt->K);
     int rc = set_device(c);
     if (rc) return rc;
     flags &= ~PM_ASYNC;

@@ -66,6 +66,26 @@ def test_dirichlet_autotune_changes_the_grid_not_the_results():
         pm.pm_destroy(c)
 
 
+def test_dirichlet_autotune_at_a_wide_bound():
+    # K = 24 on the tensor cores: the tuner's candidates, then the same results
+    c = _gpu.ctx()
+    try:
+        w = inputs.dirichlet_disk_k10(M=4096)
+        w.K, w.u = 24, inputs.prior_field(24, 624)
+        w.max_steps = 2000
+        r0 = _gpu.dirichlet(c, w, TC)
+        resident = pm.pm_last_grid(c) // sms()
+        best = pm.pm_autotune_dirichlet(c, pm.Field(w.K, w.u), w.drift_scale, w.kappa,
+                                        pm.DirichletData(w.g.R, w.g.quad, w.g.f_const, w.g.a, w.g.b), w.x, len(w.x),
+                                        w.M, w.dt, w.max_steps, w.seed, TC)
+        assert 1 <= best <= resident
+        r1 = _gpu.dirichlet(c, w, TC)
+        assert pm.pm_last_grid(c) == best * sms()
+        assert np.array_equal(r0["mean"], r1["mean"]) and np.array_equal(r0["var"], r1["var"])
+    finally:
+        pm.pm_destroy(c)
+
+
 def test_cache_file_round_trip(tmp_path):
     path = tmp_path / "tune.json"
     os.environ["PM_AUTOTUNE_CACHE"] = str(path)
