@@ -249,6 +249,7 @@ extern "C" int pm_forward_batched(pm_ctx* c, const pm_batch* bt, uint32_t flags,
     const double R2 = p.R * p.R;
     p.R2hi = (float)R2;
     p.R2lo = (float)(R2 - (double)p.R2hi);
+    p.band = std::ldexp(p.R2hi, -16);
     p.inst = W.inst;
     p.rows = W.rows;
     p.tables = W.tables;

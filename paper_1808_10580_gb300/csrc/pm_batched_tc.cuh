@@ -108,8 +108,8 @@ __global__ void __launch_bounds__(128, BatShape<K>::MIN_CTAS6) batched_tc_kernel
     int kind = 0;
     uint32_t stream = 0, key0 = 0, key1 = 0;
     float s_dt = 0.f, drift_dt = 0.f, dt = 0.f;
-    int64_t pid = -1, n = 0;
-    int32_t N = 0;
+    int64_t pid = -1;
+    int32_t n = 0, N = 0;  // steps taken and step count of the lane's path (max_steps < 2^31)
     float h_last = 0.f, s_last = 0.f;
     uint32_t j = 0, i = 0;
     unsigned long long lane_steps = 0;
@@ -242,8 +242,6 @@ __global__ void __launch_bounds__(128, BatShape<K>::MIN_CTAS6) batched_tc_kernel
         // pairs between refills (a lane whose path ends waits for the next refill)
 #pragma unroll 1
         for (int pair = 0; pair < p.refill_pairs && !stop; ++pair) {
-            u32x4 r{0, 0, 0, 0};
-            if (pid >= 0) r = philox4x32_10(u32x4{(uint32_t)(n >> 1), i, j, stream}, key0, key1);
             float2 z1, z2;  // the two steps' normals, formed during the first product
 #pragma unroll 1
             for (int half = 0; half < 2; ++half) {
@@ -257,7 +255,11 @@ __global__ void __launch_bounds__(128, BatShape<K>::MIN_CTAS6) batched_tc_kernel
                 if (__syncthreads_or(failed)) { stop = true; break; }
                 if (tid == 0) issue_step_mma<K, F, H>(tmem, sb, bar_a);
                 // While the product runs: the Brownian increment and the x1 harmonics.
-                if (half == 0) box_muller2(r.x, r.y, r.z, r.w, z1, z2);
+                if (half == 0) {
+                    u32x4 r{0, 0, 0, 0};
+                    if (pid >= 0) r = philox4x32_10(u32x4{(uint32_t)(n >> 1), i, j, stream}, key0, key1);
+                    box_muller2(r.x, r.y, r.z, r.w, z1, z2);
+                }
                 const float xi1 = half ? z1.y : z1.x, xi2 = half ? z2.y : z2.x;
                 Harm1 h1;  // during the product (HarmArray)
                 h1.init(sx.x, cx.x);
@@ -284,7 +286,7 @@ __global__ void __launch_bounds__(128, BatShape<K>::MIN_CTAS6) batched_tc_kernel
                 } else {
                     em_update2(X1, X2, v1, v2, drift_dt, s_dt, xi1, xi2);
                     ++n;
-                    const bool exited = radial_excess(X1, X2, p.R2hi, p.R2lo) >= 0.f;
+                    const bool exited = exits_disk(X1, X2, p.R2hi, p.R2lo, p.band);
                     if (exited || n >= sI.max_steps) {
                         double gv = 0.0;
                         if (exited) gv = boundary_value(p.ga, p.gb, p.n_ang, p.R, p.quad, X1.full(), X2.full()) -

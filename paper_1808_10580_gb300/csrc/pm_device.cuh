@@ -370,6 +370,21 @@ __device__ __forceinline__ float radial_excess(const Coord<float>& a, const Coor
     return d + (ed + es + e1 + e2 + cross - R2lo);
 }
 
+// The exit decision radial_excess(a, b, R2hi, R2lo) >= 0, with a float test
+// first.  For a compensated position (|lo| <= ulp(hi) / 2) the float value
+// q = a.hi^2 + b.hi^2 is within 2^-22 (relative) of the exact |X|^2, and R^2 =
+// R2hi + R2lo within 2^-24, so wherever q - R2hi exceeds `band` = 2^-16 R2hi in
+// magnitude its sign is that of |X|^2 - R^2 (a margin of 2^5 over the bound);
+// only inside the band, a few millionths of R^2 wide, the exact form runs.
+// The decision is the same as the exact form's in every case.
+__device__ __forceinline__ bool exits_disk(const Coord<float>& a, const Coord<float>& b, float R2hi, float R2lo,
+                                           float band)
+{
+    const float d = fmaf(a.hi, a.hi, b.hi * b.hi) - R2hi;
+    if (fabsf(d) > band) return d > 0.f;
+    return radial_excess(a, b, R2hi, R2lo) >= 0.f;
+}
+
 // Double paths: |X|^2 with each product and the sum rounded once (no fused
 // multiply-add), compared with R^2.
 __device__ __forceinline__ double radial_excess(const Coord<double>& a, const Coord<double>& b, double R2hi, double)

@@ -36,6 +36,7 @@ struct DirParams {
     double R, quad, f_const, dt;
     int32_t n_ang;
     float drift_dt, s_dt, R2hi, R2lo;
+    float band;              // exits_disk: 2^-16 R2hi
     const double* x;
     const int32_t* order;    // [n_obs] observation claimed in slot s, or nullptr
     int64_t n_obs, M, total, max_steps, path_offset;
@@ -132,7 +133,8 @@ __global__ void __launch_bounds__(128, DirShape<K>::MIN_CTAS) dirichlet_tc_kerne
     const uint32_t sb = tc::smem_u32(A_hi);  // A_hi, A_lo, B_hi, B_lo back to back
     int64_t pid = -1;
     bool done = false;
-    int64_t n = 0;
+    int32_t n = 0;  // steps of the lane's path (max_steps < 2^31)
+    const int32_t max_steps = (int32_t)p.max_steps;
     uint32_t j = 0, i = 0;
     unsigned long long lane_steps = 0;
     uint32_t phase = 0;
@@ -182,8 +184,6 @@ __global__ void __launch_bounds__(128, DirShape<K>::MIN_CTAS) dirichlet_tc_kerne
         // waits for the next refill; the RNG stays keyed by the step index).
 #pragma unroll 1
         for (int pair = 0; pair < p.refill_pairs && !stop; ++pair) {
-            u32x4 r{0, 0, 0, 0};
-            if (pid >= 0) r = philox4x32_10_rk(u32x4{(uint32_t)(n >> 1), i, j, p.inst}, p.rk);
             float2 z1, z2;  // the two steps' normals, formed during the first product
 #pragma unroll 1
             for (int half = 0; half < 2; ++half) {
@@ -197,7 +197,11 @@ __global__ void __launch_bounds__(128, DirShape<K>::MIN_CTAS) dirichlet_tc_kerne
                 if (__syncthreads_or(failed)) { stop = true; break; }
                 if (tid == 0) issue_step_mma<K, F, H>(tmem, sb, bar_a);
                 // While the product runs: the Brownian increment and the x1 harmonics.
-                if (half == 0) box_muller2(r.x, r.y, r.z, r.w, z1, z2);
+                if (half == 0) {
+                    u32x4 r{0, 0, 0, 0};
+                    if (pid >= 0) r = philox4x32_10_rk(u32x4{(uint32_t)(n >> 1), i, j, p.inst}, p.rk);
+                    box_muller2(r.x, r.y, r.z, r.w, z1, z2);
+                }
                 const float xi1 = half ? z1.y : z1.x, xi2 = half ? z2.y : z2.x;
                 Harm1 h1;  // its base from x1; the harmonics follow in the velocity sum
                 h1.init(sx.x, cx.x);
@@ -219,8 +223,8 @@ __global__ void __launch_bounds__(128, DirShape<K>::MIN_CTAS) dirichlet_tc_kerne
                         em_update2(X1, X2, v1, v2, p.drift_dt, p.s_dt, xi1, xi2);
                     }
                     ++n;
-                    const bool exited = radial_excess(X1, X2, p.R2hi, p.R2lo) >= 0.f;
-                    if (exited || n >= p.max_steps) {
+                    const bool exited = exits_disk(X1, X2, p.R2hi, p.R2lo, p.band);
+                    if (exited || n >= max_steps) {
                         dir_finish(p, pid, exited, n, X1, X2,
                                    GEN ? fs.value() * p.dt : p.f_const * ((double)n * p.dt));
                         lane_steps += (unsigned long long)n;
@@ -286,6 +290,7 @@ cudaError_t launch_dirichlet_tc(const DirichletLaunch& L, unsigned* err, cudaStr
     const double R2 = L.R * L.R;
     p.R2hi = (float)R2;
     p.R2lo = (float)(R2 - (double)p.R2hi);
+    p.band = std::ldexp(p.R2hi, -16);
     p.x = L.x;
     p.order = L.order;
     p.n_obs = L.n_obs;

@@ -203,6 +203,7 @@ struct BatchKernelParams {
     double R, quad, f_const;
     int32_t n_ang;
     float R2hi, R2lo;
+    float band;                        // exits_disk: 2^-16 R2hi
     const BatchInstDev* inst;
     const RowRec* rows;
     const float* tables;               // [B][table_size(K)]
