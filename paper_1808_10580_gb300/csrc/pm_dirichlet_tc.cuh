@@ -9,6 +9,7 @@
 // result is ignored).  The CTA leaves when every lane has found the path
 // counter exhausted.
 #pragma once
+#include <type_traits>
 #include "pm_general_step.cuh"
 #include "pm_timedep_tc.cuh"
 
@@ -145,6 +146,125 @@ __global__ void __launch_bounds__(128, DirShape<K>::MIN_CTAS) dirichlet_tc_kerne
     X2.set(0.0);
     ForcingSum<float> fs;  // the general map's forcing sum (GEN)
 
+    // 2 refill_pairs Euler steps (a lane whose path exits waits for the next
+    // refill; the RNG stays keyed by the step index).  Warps without a path
+    // at the start take no part in the step's work but the barrier and the
+    // phase (their rows of A keep old values, whose products nobody reads).
+    auto run_interval = [&]() {
+        const bool on = __any_sync(full, pid >= 0);
+#pragma unroll 1
+        for (int pair = 0; pair < p.refill_pairs && !stop; ++pair) {
+            float2 z1, z2;  // the two steps' normals, formed during the first product
+#pragma unroll 1
+            for (int half = 0; half < 2; ++half) {
+                float2 sx = make_float2(0.f, 0.f), cx = sx;
+                float p0 = 0.f;
+                if (on) {
+                    sincos_turns2(make_float2(X1.val(), X2.val()), sx, cx);
+                    p0 = write_row_stream<K, F, H>(sb + row, (uint32_t)S::A_BYTES, sx.y, cx.y, p.T0);
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                // One barrier per step: the rows are in place, and a wait that gave
+                // up in the previous step (any thread) stops the whole CTA.
+                if (__syncthreads_or(failed)) { stop = true; break; }
+                if (tid == 0) issue_step_mma<K, F, H>(tmem, sb, bar_a);
+                issued_any = true;
+                if (!on) {
+                    phase ^= 1u;
+                    continue;
+                }
+                // While the product runs: the Brownian increment and the x1 harmonics.
+                if (half == 0) {
+                    u32x4 r{0, 0, 0, 0};
+                    if (pid >= 0) r = philox4x32_10_rk(u32x4{(uint32_t)(n >> 1), i, j, p.inst}, p.rk);
+                    box_muller2(r.x, r.y, r.z, r.w, z1, z2);
+                }
+                const float xi1 = half ? z1.y : z1.x, xi2 = half ? z2.y : z2.x;
+                Harm1 h1;  // its base from x1; the harmonics follow in the velocity sum
+                h1.init(sx.x, cx.x);
+                failed = p.wait_limit >= tc::kWaitLimit ? !tc::mbar_wait(bar_a, phase)
+                                                        : !tc::mbar_wait(bar_a, phase, p.wait_limit);
+                phase ^= 1u;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                float v1, v2;
+                velocity_stream<K, F, H>(t_row, h1, p.N0, p0, p.inv_s, v1, v2);
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                if (pid >= 0) {
+                    if constexpr (GEN) {
+                        const float x1v = X1.val(), x2v = X2.val();  // the step's start point
+                        fs.add(p.gc.forcing(x1v, x2v));
+                        X1.add(p.gc.increment(0, x1v, v1, p.drift_dt, xi1));
+                        X2.add(p.gc.increment(1, x2v, v2, p.drift_dt, xi2));
+                    } else {
+                        em_update2(X1, X2, v1, v2, p.drift_dt, p.s_dt, xi1, xi2);
+                    }
+                    ++n;
+                    const bool exited = exits_disk(X1, X2, p.R2hi, p.R2lo, p.band);
+                    if (exited || n >= max_steps) {
+                        dir_finish(p, pid, exited, n, X1, X2,
+                                   GEN ? fs.value() * p.dt : p.f_const * ((double)n * p.dt));
+                        lane_steps += (unsigned long long)n;
+                        pid = -1;
+                    }
+                }
+            }
+        }
+    };
+
+    // Moves the CTA's `active` paths to lanes 0 .. active - 1 (in lane order)
+    // through the A tiles, when that leaves fewer warps with a path; no
+    // product is in flight here (every thread has waited for the last one).
+    // The tiles' rows are cleared again afterwards (zero padding columns).
+    auto compact_paths = [&](int active) {
+        const unsigned bal = __ballot_sync(full, pid >= 0);
+        const int warps_on = __syncthreads_count(lane == 0 && bal != 0u);
+        if ((active + 31) / 32 >= warps_on) return;
+        int* wc = reinterpret_cast<int*>(B_lo + S::B_BYTES) + 8;  // 4 ints after the barrier words
+        if (lane == 0) wc[warp] = __popc(bal);
+        __syncthreads();
+        uint32_t* slot = reinterpret_cast<uint32_t*>(A_hi);  // 12 words per path
+        if (pid >= 0) {
+            int rank = __popc(bal & ((1u << lane) - 1u));
+            for (int w = 0; w < warp; ++w) rank += wc[w];
+            uint32_t* q = slot + 12 * rank;
+            q[0] = j;
+            q[1] = i;
+            q[2] = (uint32_t)n;
+            q[3] = (uint32_t)(uint64_t)pid;
+            q[4] = (uint32_t)((uint64_t)pid >> 32);
+            q[5] = __float_as_uint(X1.hi);
+            q[6] = __float_as_uint(X1.lo);
+            q[7] = __float_as_uint(X2.hi);
+            q[8] = __float_as_uint(X2.lo);
+            q[9] = __float_as_uint(fs.s);
+            q[10] = __float_as_uint(fs.c);
+        }
+        __syncthreads();
+        pid = -1;
+        if (tid < active) {
+            const uint32_t* q = slot + 12 * tid;
+            j = q[0];
+            i = q[1];
+            n = (int32_t)q[2];
+            pid = (int64_t)(((uint64_t)q[4] << 32) | q[3]);
+            X1.hi = __uint_as_float(q[5]);
+            X1.lo = __uint_as_float(q[6]);
+            X2.hi = __uint_as_float(q[7]);
+            X2.lo = __uint_as_float(q[8]);
+            fs.s = __uint_as_float(q[9]);
+            fs.c = __uint_as_float(q[10]);
+        }
+        __syncthreads();
+        for (int c = 0; c < S::KC; ++c) {
+            *reinterpret_cast<float4*>(A_hi + tile_off<S::KC>(tid, c)) = make_float4(0.f, 0.f, 0.f, 0.f);
+            *reinterpret_cast<float4*>(A_lo + tile_off<S::KC>(tid, c)) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+    };
+    static_assert(12 * 4 * 128 <= 2 * S::A_BYTES, "the exchange fits the A tiles");
+
     for (;;) {
         // Refill (per warp).
         const bool need = !done && pid < 0;
@@ -176,63 +296,18 @@ __global__ void __launch_bounds__(128, DirShape<K>::MIN_CTAS) dirichlet_tc_kerne
             }
         }
         // Leave when every lane of the CTA is out of work; step while any lane has a path.
-        if (!__syncthreads_or(pid >= 0)) {
+        const int active = __syncthreads_count(pid >= 0);
+        if (active == 0) {
             if (__syncthreads_and(done)) break;
             continue;
         }
-        // refill_pairs pairs of steps between refills (a lane whose path exits
-        // waits for the next refill; the RNG stays keyed by the step index).
-#pragma unroll 1
-        for (int pair = 0; pair < p.refill_pairs && !stop; ++pair) {
-            float2 z1, z2;  // the two steps' normals, formed during the first product
-#pragma unroll 1
-            for (int half = 0; half < 2; ++half) {
-                float2 sx, cx;
-                sincos_turns2(make_float2(X1.val(), X2.val()), sx, cx);
-                const float p0 = write_row_stream<K, F, H>(sb + row, (uint32_t)S::A_BYTES, sx.y, cx.y, p.T0);
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                // One barrier per step: the rows are in place, and a wait that gave
-                // up in the previous step (any thread) stops the whole CTA.
-                if (__syncthreads_or(failed)) { stop = true; break; }
-                if (tid == 0) issue_step_mma<K, F, H>(tmem, sb, bar_a);
-                // While the product runs: the Brownian increment and the x1 harmonics.
-                if (half == 0) {
-                    u32x4 r{0, 0, 0, 0};
-                    if (pid >= 0) r = philox4x32_10_rk(u32x4{(uint32_t)(n >> 1), i, j, p.inst}, p.rk);
-                    box_muller2(r.x, r.y, r.z, r.w, z1, z2);
-                }
-                const float xi1 = half ? z1.y : z1.x, xi2 = half ? z2.y : z2.x;
-                Harm1 h1;  // its base from x1; the harmonics follow in the velocity sum
-                h1.init(sx.x, cx.x);
-                issued_any = true;
-                failed = p.wait_limit >= tc::kWaitLimit ? !tc::mbar_wait(bar_a, phase)
-                                                        : !tc::mbar_wait(bar_a, phase, p.wait_limit);
-                phase ^= 1u;
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                float v1, v2;
-                velocity_stream<K, F, H>(t_row, h1, p.N0, p0, p.inv_s, v1, v2);
-                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                if (pid >= 0) {
-                    if constexpr (GEN) {
-                        const float x1v = X1.val(), x2v = X2.val();  // the step's start point
-                        fs.add(p.gc.forcing(x1v, x2v));
-                        X1.add(p.gc.increment(0, x1v, v1, p.drift_dt, xi1));
-                        X2.add(p.gc.increment(1, x2v, v2, p.drift_dt, xi2));
-                    } else {
-                        em_update2(X1, X2, v1, v2, p.drift_dt, p.s_dt, xi1, xi2);
-                    }
-                    ++n;
-                    const bool exited = exits_disk(X1, X2, p.R2hi, p.R2lo, p.band);
-                    if (exited || n >= max_steps) {
-                        dir_finish(p, pid, exited, n, X1, X2,
-                                   GEN ? fs.value() * p.dt : p.f_const * ((double)n * p.dt));
-                        lane_steps += (unsigned long long)n;
-                        pid = -1;
-                    }
-                }
-            }
-        }
+        // The tail: with at most three warps' worth of paths left and the path
+        // counter exhausted (no lane is refilled again), move the paths to the
+        // lowest lanes when that empties a warp, and let warps without a path
+        // skip the step's work.  A path's state moves whole and its random
+        // numbers are keyed by its own step index: every result is unchanged.
+        if (active <= 96 && __syncthreads_or(done)) compact_paths(active);
+        run_interval();
         if (stop) break;
     }
     if (failed) atomicExch(p.err, 1u);
