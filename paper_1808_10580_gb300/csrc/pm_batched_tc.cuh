@@ -275,8 +275,10 @@ __global__ void __launch_bounds__(128, BatShape<K>::MIN_CTAS6) batched_tc_kernel
                     const bool last = (n == N - 1);
                     const float h = last ? h_last : dt, s = last ? s_last : s_dt;
                     em_update2(X1, X2, v1, v2, h, s, xi1, xi2);
-                    X1.wrap();
-                    X2.wrap();
+                    if (last || wrap_due(n)) {  // the schedule of timedep_tc_kernel
+                        X1.wrap();
+                        X2.wrap();
+                    }
                     ++n;
                     if (n >= N) {
                         p.g[sI.path_base + pid] = theta0_eval(p.th, X1, X2);

@@ -344,6 +344,12 @@ template <bool F>
 __host__ __device__ constexpr int pcol(int m, int j) { return 8 * ((m - 1) / 2) + 2 * j + ((m - 1) & 1); }
 __host__ __device__ constexpr int p0col(int K) { return 8 * ((K + 1) / 2); }
 
+// Whether the position is wrapped into [0, 1) after step n (other than a
+// path's last step, after which it always is): every eighth step.  The
+// kernels that must give the same bits (the single-problem and batched
+// time-dependent steps) share this schedule, keyed by the path's own step.
+__device__ __forceinline__ bool wrap_due(int n) { return (n & 7) == 7; }
+
 // Packed FP32 pairs (sm_100 and later: one instruction for two independent
 // float operations, each rounded exactly as its scalar form).
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
@@ -803,8 +809,14 @@ __global__ void __launch_bounds__(TdLaunch<K>::THREADS, TdLaunch<K>::MIN_CTAS)
         }
         if (n + 1 < N) {
             em_update2(X1, X2, v1, v2, p.dt, p.s_dt, xi1, xi2);
-            X1.wrap();
-            X2.wrap();
+            // Periodic wrap after every eighth step (wrap_due): the harmonics
+            // of x and x - 1 are the same bits (sincos_turns2 reduces x
+            // exactly), so between wraps a position may stand a few steps
+            // outside [0, 1); a path's last step always wraps.
+            if (wrap_due(n)) {
+                X1.wrap();
+                X2.wrap();
+            }
         }
     }
     failed = __syncthreads_or(failed);
