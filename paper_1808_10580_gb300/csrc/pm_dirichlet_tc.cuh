@@ -85,7 +85,10 @@ __device__ __forceinline__ void dir_finish(const DirParams<K>& p, int64_t pid, b
 // GEN: the general map (state-dependent diffusion with the Milstein term,
 // Gaussian-source forcing; pm_general_step.cuh) instead of the constant
 // diffusion and forcing; the velocity sum is the same.
-template <int K, bool GEN = false>
+// LIMIT: the per-step MMA wait takes the launch's poll limit (a test lowered
+// it, pm_set_wait_limit); otherwise the compile-time full bound, with no
+// per-step test of the setting.
+template <int K, bool GEN = false, bool LIMIT = false>
 __global__ void __launch_bounds__(128, DirShape<K>::MIN_CTAS) dirichlet_tc_kernel(const __grid_constant__ DirParams<K> p)
 {
     using S = DirShape<K>;
@@ -183,8 +186,8 @@ __global__ void __launch_bounds__(128, DirShape<K>::MIN_CTAS) dirichlet_tc_kerne
                 const float xi1 = half ? z1.y : z1.x, xi2 = half ? z2.y : z2.x;
                 Harm1 h1;  // its base from x1; the harmonics follow in the velocity sum
                 h1.init(sx.x, cx.x);
-                failed = p.wait_limit >= tc::kWaitLimit ? !tc::mbar_wait(bar_a, phase)
-                                                        : !tc::mbar_wait(bar_a, phase, p.wait_limit);
+                if constexpr (LIMIT) failed = !tc::mbar_wait(bar_a, phase, p.wait_limit);
+                else failed = !tc::mbar_wait(bar_a, phase);
                 phase ^= 1u;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 float v1, v2;
@@ -385,19 +388,23 @@ cudaError_t launch_dirichlet_tc(const DirichletLaunch& L, unsigned* err, cudaStr
     round_keys(L.key0, L.key1, p.rk);
     p.err = err;
     p.wait_limit = L.wait_limit;
+    const bool limited = L.wait_limit < tc::kWaitLimit;
     p.refill_pairs = L.refill_pairs > 0 ? L.refill_pairs : 1;
     p.gc = GeneralCoef<float>{};
     if (L.gen) {  // the general map
         p.gc.set(*L.gen, L.dt, L.f_const);
-        cudaError_t e = cudaFuncSetAttribute(dirichlet_tc_kernel<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             S::SMEM);
+        cudaError_t e = cudaFuncSetAttribute(limited ? dirichlet_tc_kernel<K, true, true> : dirichlet_tc_kernel<K, true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
         if (e != cudaSuccess) return e;
-        dirichlet_tc_kernel<K, true><<<L.grid, 128, S::SMEM, stream>>>(p);
+        if (limited) dirichlet_tc_kernel<K, true, true><<<L.grid, 128, S::SMEM, stream>>>(p);
+        else dirichlet_tc_kernel<K, true><<<L.grid, 128, S::SMEM, stream>>>(p);
         return cudaGetLastError();
     }
-    cudaError_t e = cudaFuncSetAttribute(dirichlet_tc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(limited ? dirichlet_tc_kernel<K, false, true> : dirichlet_tc_kernel<K>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
     if (e != cudaSuccess) return e;
-    dirichlet_tc_kernel<K><<<L.grid, 128, S::SMEM, stream>>>(p);
+    if (limited) dirichlet_tc_kernel<K, false, true><<<L.grid, 128, S::SMEM, stream>>>(p);
+    else dirichlet_tc_kernel<K><<<L.grid, 128, S::SMEM, stream>>>(p);
     return cudaGetLastError();
 }
 

@@ -345,10 +345,12 @@ __host__ __device__ constexpr int pcol(int m, int j) { return 8 * ((m - 1) / 2) 
 __host__ __device__ constexpr int p0col(int K) { return 8 * ((K + 1) / 2); }
 
 // Whether the position is wrapped into [0, 1) after step n (other than a
-// path's last step, after which it always is): every eighth step.  The
-// kernels that must give the same bits (the single-problem and batched
-// time-dependent steps) share this schedule, keyed by the path's own step.
-__device__ __forceinline__ bool wrap_due(int n) { return (n & 7) == 7; }
+// path's last step, after which it always is): every 32nd step (between
+// wraps a position drifts at most 32 steps outside the cell; sincos_turns2
+// reduces any |x| < 2^20 exactly).  The kernels that must give the same
+// bits (the single-problem and batched time-dependent steps) share this
+// schedule, keyed by the path's own step.
+__device__ __forceinline__ bool wrap_due(int n) { return (n & 31) == 31; }
 
 // Packed FP32 pairs (sm_100 and later: one instruction for two independent
 // float operations, each rounded exactly as its scalar form).
@@ -656,7 +658,10 @@ struct TdLaunch {
     static_assert(SETS == 1 || (S::NP <= 256 && SMEM + 1024 <= 233472), "two tiles fit");
 };
 
-template <int K>
+// LIMIT: the per-step MMA wait takes the launch's poll limit (a test lowered
+// it, pm_set_wait_limit); otherwise the compile-time full bound, with no
+// per-step test of the setting.
+template <int K, bool LIMIT = false>
 __global__ void __launch_bounds__(TdLaunch<K>::THREADS, TdLaunch<K>::MIN_CTAS)
     timedep_tc_kernel(const __grid_constant__ Params<K> p)
 {
@@ -790,8 +795,8 @@ __global__ void __launch_bounds__(TdLaunch<K>::THREADS, TdLaunch<K>::MIN_CTAS)
         h1.init(sx.x, cx.x);
         // (the full bound unless a test lowered it: the common path keeps the
         // compile-time bound)
-        failed = p.wait_limit >= tc::kWaitLimit ? !tc::mbar_wait(bar_a, (uint32_t)(n & 1))
-                                                : !tc::mbar_wait(bar_a, (uint32_t)(n & 1), p.wait_limit);
+        if constexpr (LIMIT) failed = !tc::mbar_wait(bar_a, (uint32_t)(n & 1), p.wait_limit);
+        else failed = !tc::mbar_wait(bar_a, (uint32_t)(n & 1));
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         float v1, v2;
         velocity_stream<K, F, H>(t_row, h1, p.N0, p0, p.inv_s, v1, v2);
@@ -809,7 +814,7 @@ __global__ void __launch_bounds__(TdLaunch<K>::THREADS, TdLaunch<K>::MIN_CTAS)
         }
         if (n + 1 < N) {
             em_update2(X1, X2, v1, v2, p.dt, p.s_dt, xi1, xi2);
-            // Periodic wrap after every eighth step (wrap_due): the harmonics
+            // Periodic wrap after every 32nd step (wrap_due): the harmonics
             // of x and x - 1 are the same bits (sincos_turns2 reduces x
             // exactly), so between wraps a position may stand a few steps
             // outside [0, 1); a path's last step always wraps.
@@ -922,10 +927,13 @@ cudaError_t launch_timedep_tc(const TimedepLaunch& L, unsigned* err, cudaStream_
     p.groups = L.groups;
     p.members = L.members;
     using LC = TdLaunch<K>;
-    cudaError_t e = cudaFuncSetAttribute(timedep_tc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, LC::SMEM);
+    const bool limited = L.wait_limit < tc::kWaitLimit;
+    cudaError_t e = cudaFuncSetAttribute(limited ? timedep_tc_kernel<K, true> : timedep_tc_kernel<K, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, LC::SMEM);
     if (e != cudaSuccess) return e;
     const int64_t grid = (int64_t)(L.groups ? L.n_groups : L.n_obs) * L.chunks;
-    timedep_tc_kernel<K><<<(unsigned)grid, LC::THREADS, LC::SMEM, stream>>>(p);
+    if (limited) timedep_tc_kernel<K, true><<<(unsigned)grid, LC::THREADS, LC::SMEM, stream>>>(p);
+    else timedep_tc_kernel<K, false><<<(unsigned)grid, LC::THREADS, LC::SMEM, stream>>>(p);
     return cudaGetLastError();
 }
 
