@@ -607,8 +607,8 @@ def run_sweep(args):
     observations x M paths with a prior field of each K, on the FP32 pipes and
     on the tensor cores where the tensor path has the K (auxiliary line).
     K = 24 ... 64 (N_u up to 16640, beyond the 3209 coefficients of the
-    paper's second example and near the 20081 of its third) run the wide-K
-    kernels."""
+    paper's second example) run the wide-K kernels, K = 80 (N_u = 25920,
+    which holds the 20081 of its third, |k|_2 <= 80) the FP32 pipes only."""
     import torch
 
     import paper_1808_10580_gb300 as pm
@@ -625,7 +625,7 @@ def run_sweep(args):
     mean = torch.empty(len(w.t), dtype=torch.float64, device=dev)
     steps = particle_steps(w)
     rows = []
-    ks = [int(k) for k in args.sweep_k.split(",")] if args.sweep_k else [2, 3, 4, 5, 6, 8, 10, 12, 16, 24, 32, 40, 48, 56, 64]
+    ks = [int(k) for k in args.sweep_k.split(",")] if args.sweep_k else [2, 3, 4, 5, 6, 8, 10, 12, 16, 24, 32, 40, 48, 56, 64, 80]
     for K in ks:
         fld = pm.Field(K, inputs.prior_field(K, 1001))
         row = {"K": K, "n_u": (2 * K + 1) ** 2 - 1}
@@ -962,7 +962,7 @@ def main():
                     help="timedep: skip the one FP64-path evaluation reported beside the line")
     ap.add_argument("--M", type=int, default=0, help="particles per observation (default: the workload's own; "
                     "smaller values are for profiling captures only)")
-    ap.add_argument("--sweep-k", default="", help="sweep: comma-separated K values (default 2..64)")
+    ap.add_argument("--sweep-k", default="", help="sweep: comma-separated K values (default 2..80)")
     ap.add_argument("--workload", default="timedep", choices=["timedep", "dirichlet", "dirichlet_general", "batched", "mcmc", "sweep", "surrogate",
                              "bvp", "layout"],
                     help="timedep: the headline line; dirichlet / batched / mcmc: auxiliary measurements")

@@ -22,8 +22,10 @@
  *   (2K+1)^2 - 1 doubles.  v = (-d psi/dx2, d psi/dx1), i.e. the paper's
  *   k_perp = (-k_y, k_x) direction.  Supported K: 0..6, 8, 10, 12, 16; the
  *   time-dependent and Dirichlet maps with float paths also take the wide
- *   bounds K = 24, 32, 40, 48, 56, 64 (N_u = 2400 ... 16640; PM_EINVAL
- *   elsewhere).
+ *   bounds K = 24, 32, 40, 48, 56, 64 (N_u = 2400 ... 16640), and the
+ *   time-dependent map with float paths K = 80 (N_u = 25920, which holds the
+ *   |k|_2 <= 80 basis; FP32 pipes only, PM_TENSOR then runs the FP32 pipes);
+ *   PM_EINVAL elsewhere.
  * Random numbers.  Step n of path i of observation j in instance b draws
  *   Philox4x32-10 (Salmon et al., SC'11) on counter {n/2, i, j, b} under key
  *   {seed & 0xffffffff, seed >> 32}; words (r0, r1) feed even n and (r2, r3)
@@ -32,7 +34,9 @@
  *   and the seed, never on launch shapes or the GPU count.
  * Steps.  Time-dependent: N_j = ceil(t_j/dt - 1e-9) steps, all of length dt
  *   except the last, t_j - (N_j - 1) dt; positions wrap into [0,1)^2 after each
- *   step.  Dirichlet: domain |x| < R; a path exits at the first step n with
+ *   step (the tensor-core kernels: after every 32nd step and after a path's
+ *   last; their harmonics of x and x - 1 are the same, so only rounding
+ *   differs).  Dirichlet: domain |x| < R; a path exits at the first step n with
  *   |X_n|^2 >= R^2; g is evaluated at R X_n/|X_n|; int f = f_const n dt; a path
  *   that has not exited after max_steps contributes 0 and is counted as
  *   unexited.

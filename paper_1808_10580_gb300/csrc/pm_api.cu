@@ -220,14 +220,15 @@ int set_device(pm_ctx* c)
 }
 
 // Common checks of a field description.
-int check_field(const pm_field* f, bool allow_wide)
+int check_field(const pm_field* f, bool allow_wide, bool allow_simt_wide)
 {
     if (!f) return fail(PM_EINVAL, "field is NULL");
-    if (allow_wide && wide_K(f->K)) {
-        // accepted: the time-dependent map with float paths (checked by the caller)
+    if ((allow_wide && wide_K(f->K)) || (allow_simt_wide && simt_wide_K(f->K))) {
+        // accepted: float paths (checked by the caller)
     } else if (!supported_K(f->K)) {
-        return fail(PM_EINVAL, "K=%d is not one of the compiled bounds 0..6, 8, 10, 12, 16%s", f->K,
-                    allow_wide ? " (24, 32, 40, 48, 56, 64: float paths)" : "");
+        return fail(PM_EINVAL, "K=%d is not one of the compiled bounds 0..6, 8, 10, 12, 16%s%s", f->K,
+                    allow_wide ? " (24, 32, 40, 48, 56, 64: float paths)" : "",
+                    allow_simt_wide ? " (80: float paths on the FP32 pipes)" : "");
     }
     const int64_t nu = (int64_t)(2 * f->K + 1) * (2 * f->K + 1) - 1;
     if (nu > 0 && !f->u) return fail(PM_EINVAL, "field coefficients are NULL");
@@ -449,9 +450,10 @@ int pm_forward_timedep(pm_ctx* c, const pm_field* field, double kappa, const pm_
                        double* mean, double* var, const pm_path_opts* opts)
 {
     if (!c) return fail(PM_EINVAL, "ctx is NULL");
-    int rc = check_field(field, true);
+    int rc = check_field(field, true, true);
     if (rc) return rc;
-    if (wide_K(field->K) && (flags & PM_FP64)) return fail(PM_EINVAL, "K=%d runs with float paths only", field->K);
+    if ((wide_K(field->K) || simt_wide_K(field->K)) && (flags & PM_FP64))
+        return fail(PM_EINVAL, "K=%d runs with float paths only", field->K);
     if ((rc = check_theta0(th))) return rc;
     if (!(std::isfinite(kappa) && kappa >= 0)) return fail(PM_EINVAL, "kappa must be finite and >= 0");
     if (!(std::isfinite(dt) && dt > 0)) return fail(PM_EINVAL, "dt must be finite and > 0");
@@ -470,7 +472,7 @@ int pm_forward_timedep(pm_ctx* c, const pm_field* field, double kappa, const pm_
     const int K = field->K;
     const bool tc = !fp64 && (flags & PM_TENSOR) && (K == 4 || K == 5 || K == 6 || K == 8 || K == 10 || K == 12 || K == 16 ||
                                                      wide_K(K));
-    const bool wide = wide_K(K);
+    const bool wide = wide_K(K) || simt_wide_K(K);  // (K = 80: never on the tensor cores, tc is false)
     const int rows = tc ? td_tc_rows(K) : td_simt_rows(K);  // paths per CTA
     const int64_t chunks64 = (M + rows - 1) / rows;
     if (n_obs * chunks64 > 0x7fffffffLL) return fail(PM_EINVAL, "n_obs * ceil(M/%d) exceeds the grid limit", rows);
@@ -609,7 +611,9 @@ int pm_forward_timedep(pm_ctx* c, const pm_field* field, double kappa, const pm_
         case 40: e = launch_timedep<float, 40>(L, c->stream); break;
         case 48: e = launch_timedep<float, 48>(L, c->stream); break;
         case 56: e = launch_timedep<float, 56>(L, c->stream); break;
-        default: e = launch_timedep<float, 64>(L, c->stream); break;
+        case 64: e = launch_timedep<float, 64>(L, c->stream); break;
+        case 80: e = launch_timedep<float, 80>(L, c->stream); break;
+        default: return fail(PM_EINVAL, "K=%d has no float-path kernel", K);
         }
     } else {
         e = fp64 ? dispatch_timedep<double>(K, L, c->stream) : dispatch_timedep<float>(K, L, c->stream);

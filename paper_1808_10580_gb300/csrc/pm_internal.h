@@ -66,7 +66,7 @@ bool is_device_pointer(const void* p, int device);
 int ensure_workspace(pm_ctx* c, size_t bytes);
 int ensure_host(pm_ctx* c, size_t bytes);
 int set_device(pm_ctx* c);
-int check_field(const pm_field* f, bool allow_wide = false);
+int check_field(const pm_field* f, bool allow_wide = false, bool allow_simt_wide = false);
 int check_ptrs(const pm_ctx* c, uint32_t flags, std::initializer_list<const void*> ptrs);
 // theta0 description: modes within PM_MAX_THETA0_MODES, arrays present and
 // finite, wave numbers |k| <= 4096 (the float phase reduction's range).

@@ -59,6 +59,11 @@ inline int td_tc_rows(int K) { return K == 56 ? 256 : 128; }
 
 // Wave-number bounds of the time-dependent map beyond the unrolled kernels.
 inline bool wide_K(int K) { return K == 24 || K == 32 || K == 40 || K == 48 || K == 56 || K == 64; }
+// The widest bound, K = 80 (N_u = 25,920, which holds the paper's 20,081
+// coefficients of |k|_2 <= 80): the time-dependent map with float paths on the
+// FP32 pipes only (its 8 (K+1)^2-float table, 210 KB, still fits one CTA's
+// shared memory; the tensor-core tiles of this bound would not).
+inline bool simt_wide_K(int K) { return K == 80; }
 
 // Floats of the device table a wide-K launch needs: the product-basis table
 // (8 (K+1)^2) of the FP32-pipe kernel or the padded W^T of the tensor-core

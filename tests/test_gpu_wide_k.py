@@ -141,3 +141,55 @@ def test_wide_bounds_are_float_only(c):
                                         pm.DirichletData(gw.g.R, gw.g.quad, gw.g.f_const, gw.g.a, gw.g.b),
                                         pm.DiffusionForcing(df.s0, df.s1, df.milstein, df.c, df.F, df.w),
                                         x, 1, 16, gw.dt, 100, gw.seed, pm.PM_FP32, np.empty(1))
+
+
+# The widest bound, K = 80 (N_u = 25,920: the |k|_2 <= 80 basis of the paper's
+# third example fits in it): the time-dependent map with float paths on the
+# FP32 pipes only.
+def test_k80_one_step_positions_match_oracle(c, orc):
+    K = 80
+    w = wide_workload(K, 128, n_pts=16)
+    w.dt = 0.01
+    w.t = np.full(len(w.x), w.dt)
+    _, _, xe = _gpu.timedep(c, w, pm.PM_FP32, x_out=True)
+    _, xo = orc.timedep_paths(K, w.u, w.kappa, w.theta0, w.x, w.t, w.dt, w.seed, npaths=128, want_x=True)
+    modes = orc.half_modes(K).astype(float)
+    scale = float((2 * np.pi * np.sqrt((modes ** 2).sum(1)) * np.abs(w.u.reshape(-1, 2)).sum(1)).sum())
+    d = xe - xo
+    d -= np.round(d)
+    assert np.abs(d).max() <= w.dt * 4e-6 * scale + 1e-7, np.abs(d).max()
+
+
+def test_k80_shear_at_the_highest_modes_matches_oracle(c, orc):
+    K = 80
+    w = wide_workload(K, 256, n_pts=3)
+    modes = [tuple(m) for m in orc.half_modes(K)]
+    h = modes.index((K - 1, -(K - 3)))
+    w.u = np.zeros_like(w.u)
+    w.u[2 * h], w.u[2 * h + 1] = 2e-4, -1e-4
+    w.t = np.full(3, 0.05)
+    g = orc.timedep_paths(K, w.u, w.kappa, w.theta0, w.x, w.t, w.dt, w.seed, npaths=w.M, obs_id=np.arange(3))
+    rm, _, _ = orc.estimate(g)
+    mean, _ = _gpu.timedep(c, w, pm.PM_FP32)
+    assert np.abs(mean - rm).max() <= 1e-5, np.abs(mean - rm).max()
+
+
+def test_k80_tensor_flag_runs_the_fp32_pipes_and_other_maps_refuse_it(c):
+    K = 80
+    w = wide_workload(K, 300, n_pts=4)
+    w.t = np.full(4, 0.02)
+    a = _gpu.timedep(c, w, pm.PM_FP32, g_out=True)
+    b = _gpu.timedep(c, w, TC, g_out=True)
+    assert all(np.array_equal(p, q) for p, q in zip(a, b))
+    assert pm.pm_last_grid(c) == 4 * 2  # 256 paths per CTA: two CTAs per observation
+    with pytest.raises(pm.PMError):
+        _gpu.timedep(c, w, pm.PM_FP64)
+    d = inputs.dirichlet_disk_k10(M=16)
+    d.K = K
+    d.u = inputs.prior_field(K, 7)
+    for flags in (pm.PM_FP32, TC):
+        with pytest.raises(pm.PMError):
+            _gpu.dirichlet(c, d, flags, obs=np.array([0]))
+    d.x = d.x[:2]
+    with pytest.raises(pm.PMError):
+        _gpu.batched(c, [w, d], flags=TC)
