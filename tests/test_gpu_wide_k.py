@@ -2,7 +2,8 @@
 (N_u = 2400 ... 16640 real coefficients; Section 4's larger Fourier bases):
 the FP32-pipe kernel with its velocity table in shared memory and the
 tensor-core kernel with 256 accumulator columns, each against the FP64 oracle,
-against each other, and with shared paths against single-observation calls."""
+against each other, and with shared paths against single-observation calls;
+and at K = 80 (N_u = 25920) on the FP32 pipes alone."""
 import copy
 
 import numpy as np
