@@ -381,8 +381,11 @@ int pm_set_ctas_per_sm(pm_ctx* ctx, int32_t kind, int32_t K, uint32_t flags, int
 
 /* The second free shape of the tensor-core forms of the persistent kernels
  * (flags containing PM_TENSOR): the pairs of Euler steps between two refills
- * of the lanes whose paths have ended (default 4; every path's random numbers
- * are keyed by its own step index, so results do not depend on it).  The
+ * of the lanes whose paths have ended (default for the disk map: 16 when the
+ * observations' mean driftless exit time (R^2 - |x|^2) / (4 kappa dt) is at
+ * least 16384 steps, 8 from 4096, else 4; for the batched map 4; every path's
+ * random numbers are keyed by its own step index, so results do not depend
+ * on it).  The
  * autotuners choose it after the CTAs per SM (coordinate descent over 1, 2,
  * 4, 8, 16); this sets it by hand (<= 0 removes the setting, at most 64). */
 int pm_set_refill_pairs(pm_ctx* ctx, int32_t kind, int32_t K, uint32_t flags, int32_t pairs);

@@ -793,6 +793,7 @@ int dirichlet_call(pm_ctx* c, const pm_field* field, double drift_scale, double 
     // Paths keep their (j, i) streams and slots, so results do not change.
     const bool order_obs = n_obs >= 2 && n_obs <= ((int64_t)1 << 24);
     std::vector<int32_t> obs_order;
+    double walk_steps = 0.0;  // mean driftless exit time in steps, (R^2 - |x|^2) / (4 kappa dt)
     if (order_obs) {
         std::vector<double> hx;
         const double* px = x;
@@ -806,6 +807,11 @@ int dirichlet_call(pm_ctx* c, const pm_field* field, double drift_scale, double 
         for (int64_t j = 0; j < n_obs; ++j) obs_order[(size_t)j] = (int32_t)j;
         auto r2 = [&](int32_t j) { return px[2 * (int64_t)j] * px[2 * (int64_t)j] + px[2 * (int64_t)j + 1] * px[2 * (int64_t)j + 1]; };
         std::stable_sort(obs_order.begin(), obs_order.end(), [&](int32_t a, int32_t b) { return r2(a) < r2(b); });
+        if (kappa > 0) {
+            double sum = 0.0;
+            for (int64_t j = 0; j < n_obs; ++j) sum += std::max(gd->R * gd->R - r2((int32_t)j), 0.0);
+            walk_steps = sum / (double)n_obs / (4.0 * kappa * dt);
+        }
     }
 
     auto layout = [&](Bump& b) {
@@ -891,7 +897,11 @@ int dirichlet_call(pm_ctx* c, const pm_field* field, double drift_scale, double 
     } else {
         per_sm = dirichlet_resident(Kd, fp64, use_tc);
         per_sm = tuned_ctas_per_sm(c, PM_TUNE_DIRICHLET, Kd, flags & (PM_FP64 | (use_tc ? PM_TENSOR : 0u)), per_sm);
-        if (use_tc) L.refill_pairs = tuned_refill_pairs(c, PM_TUNE_DIRICHLET, Kd, PM_TENSOR, kDefaultRefillPairs);
+        // Untuned: longer walks take longer intervals between refills (fewer
+        // refill barriers against a longer wait of the lanes whose paths ended;
+        // the autotuner picked 16 pairs on walks of ~3e4 driftless steps).
+        const int def_pairs = walk_steps >= 16384.0 ? 16 : walk_steps >= 4096.0 ? 8 : kDefaultRefillPairs;
+        if (use_tc) L.refill_pairs = tuned_refill_pairs(c, PM_TUNE_DIRICHLET, Kd, PM_TENSOR, def_pairs);
     }
     int64_t grid = (int64_t)per_sm * c->sm_count;
     const int64_t need = (total + kDirichletBlock - 1) / kDirichletBlock;
