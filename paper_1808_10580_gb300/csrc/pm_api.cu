@@ -807,10 +807,13 @@ int dirichlet_call(pm_ctx* c, const pm_field* field, double drift_scale, double 
         for (int64_t j = 0; j < n_obs; ++j) obs_order[(size_t)j] = (int32_t)j;
         auto r2 = [&](int32_t j) { return px[2 * (int64_t)j] * px[2 * (int64_t)j] + px[2 * (int64_t)j + 1] * px[2 * (int64_t)j + 1]; };
         std::stable_sort(obs_order.begin(), obs_order.end(), [&](int32_t a, int32_t b) { return r2(a) < r2(b); });
-        if (kappa > 0) {
+        // (the general map: kappa of its diffusion at the origin, the mean of
+        // sigma_i(0)^2 / 2 over the two coordinates)
+        const double kap = gen ? 0.25 * (gen->s0[0] * gen->s0[0] + gen->s0[1] * gen->s0[1]) : kappa;
+        if (kap > 0) {
             double sum = 0.0;
             for (int64_t j = 0; j < n_obs; ++j) sum += std::max(gd->R * gd->R - r2((int32_t)j), 0.0);
-            walk_steps = sum / (double)n_obs / (4.0 * kappa * dt);
+            walk_steps = sum / (double)n_obs / (4.0 * kap * dt);
         }
     }
 
@@ -890,17 +893,18 @@ int dirichlet_call(pm_ctx* c, const pm_field* field, double drift_scale, double 
     const int Kd = field->K;
     const bool use_tc = dirichlet_uses_tc(Kd, flags);
     int per_sm;
+    // Untuned: longer walks take longer intervals between refills (fewer
+    // refill barriers against a longer wait of the lanes whose paths ended;
+    // the autotuner picked 16 pairs on walks of ~3e4 driftless steps).
+    const int def_pairs = walk_steps >= 16384.0 ? 16 : walk_steps >= 4096.0 ? 8 : kDefaultRefillPairs;
     if (gen && use_tc) {
         per_sm = dirichlet_resident(Kd, false, true, true);
+        L.refill_pairs = def_pairs;
     } else if (gen) {
         per_sm = fp64 ? dispatch_dirichlet_general_occupancy<double>(Kd) : dispatch_dirichlet_general_occupancy<float>(Kd);
     } else {
         per_sm = dirichlet_resident(Kd, fp64, use_tc);
         per_sm = tuned_ctas_per_sm(c, PM_TUNE_DIRICHLET, Kd, flags & (PM_FP64 | (use_tc ? PM_TENSOR : 0u)), per_sm);
-        // Untuned: longer walks take longer intervals between refills (fewer
-        // refill barriers against a longer wait of the lanes whose paths ended;
-        // the autotuner picked 16 pairs on walks of ~3e4 driftless steps).
-        const int def_pairs = walk_steps >= 16384.0 ? 16 : walk_steps >= 4096.0 ? 8 : kDefaultRefillPairs;
         if (use_tc) L.refill_pairs = tuned_refill_pairs(c, PM_TUNE_DIRICHLET, Kd, PM_TENSOR, def_pairs);
     }
     int64_t grid = (int64_t)per_sm * c->sm_count;
