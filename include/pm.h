@@ -384,7 +384,7 @@ int pm_set_ctas_per_sm(pm_ctx* ctx, int32_t kind, int32_t K, uint32_t flags, int
  * of the lanes whose paths have ended (default for the disk maps: 16 when the
  * observations' mean driftless exit time (R^2 - |x|^2) / (4 kappa dt) is at
  * least 16384 steps, 8 from 4096, else 4, with kappa = (sigma_1(0)^2 +
- * sigma_2(0)^2) / 4 for the general map; for the batched map 4; every path's
+ * sigma_2(0)^2) / 4 for the general map; for the batched map 8; every path's
  * random numbers are keyed by its own step index, so results do not depend
  * on it).  The
  * autotuners choose it after the CTAs per SM (coordinate descent over 1, 2,

@@ -262,7 +262,7 @@ extern "C" int pm_forward_batched(pm_ctx* c, const pm_batch* bt, uint32_t flags,
     p.B = B;
     const int resident = use_tc ? blocks_per_sm_tc_K(K) : blocks_per_sm_K(K);  // also sets the shared-memory attribute
     const int per_sm = tuned_ctas_per_sm(c, PM_TUNE_BATCHED, K, use_tc ? PM_TENSOR : 0u, resident);
-    p.refill_pairs = use_tc ? tuned_refill_pairs(c, PM_TUNE_BATCHED, K, PM_TENSOR, kDefaultRefillPairs) : 1;
+    p.refill_pairs = use_tc ? tuned_refill_pairs(c, PM_TUNE_BATCHED, K, PM_TENSOR, kBatchedRefillPairs) : 1;
     int64_t grid = (int64_t)per_sm * c->sm_count;
     const int64_t need = (total + kBatchWarpsHost * 32 - 1) / (kBatchWarpsHost * 32);
     grid = std::max<int64_t>(1, std::min(grid, need));

@@ -87,6 +87,9 @@ int tuned_ctas_per_sm(pm_ctx* c, int kind, int K, uint32_t flags, int resident);
 // kernel: the tuned value unless PM_AUTOTUNE=0 or none is known, else `def`.
 int tuned_refill_pairs(pm_ctx* c, int kind, int K, uint32_t flags, int def);
 constexpr int kDefaultRefillPairs = 4;
+// Untuned refill interval of the batched tensor-core kernel (what its
+// autotuner picked on 256 mixed instances of 100 observations x 4096 paths).
+constexpr int kBatchedRefillPairs = 8;
 // Reads this device's entries of the PM_AUTOTUNE_CACHE file into the context.
 void load_tune_cache(pm_ctx* c);
 // Runs the timing sweep over CTAs per SM in [1, resident] and, with
