@@ -126,11 +126,13 @@ struct DirichletLaunch {
 constexpr int kTimedepBlock = 128;
 // Paths (threads) per CTA of the FP32-pipe time-dependent kernel at K: 256
 // where one CTA's shared-memory copy of the velocity table (32 (K+1)^2 bytes)
-// leaves no room for a second CTA on the SM (K = 64), so that each scheduler
-// still has two warps to hide the table loads; kTimedepBlock otherwise.
+// leaves no room for a second CTA on the SM (K = 64, 80), so that each
+// scheduler still has two warps to hide the table loads, and at K = 56, where
+// two 128-thread CTAs with a 104 KB table each measured 1.6x slower (3.88
+// against 2.47 s on the 300 x 1e4-path workload); kTimedepBlock otherwise.
 constexpr int td_simt_rows(int K)
 {
-    return K > 16 && 2 * 32 * (K + 1) * (K + 1) > 227 * 1024 ? 2 * kTimedepBlock : kTimedepBlock;
+    return K > 16 && (K >= 56 || 2 * 32 * (K + 1) * (K + 1) > 227 * 1024) ? 2 * kTimedepBlock : kTimedepBlock;
 }
 // Block size of the persistent Dirichlet kernel.
 constexpr int kDirichletBlock = 128;
